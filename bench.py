@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the hologram-rendering hot path through the C ABI.
+
+Default workload ("paper-scale stream"): 256x256 12-bit frames at fs = 71.4 kHz,
+Fresnel transform at z = 0.25 m, STFT window T = 512 with stride S = 64, moments
+M0/M1/M2 over 1-35 kHz (bins 8..250). One step streams 102,400 raw frames (25
+batches of 4,096 frames: hv_push_frames from a device-resident pool, then
+hv_render of every complete window). Metric: raw frames rendered per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hv|reference]
+                    [--workload NAME]
+
+Prints one JSON line (rank 0). Multi-GPU: one independent stream per rank
+(replicas; the path needs no exchange), barrier and max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2508_03911_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "stream_fresnel_256_t512_s64": dict(
+        desc="256x256 uint16 (12-bit) frames, fs=71.4 kHz, Fresnel z=0.25 m, STFT T=512 "
+             "stride 64, M0/M1/M2 over 1-35 kHz (bins 8..250), 102,400-frame stream per step",
+        N=256, bits=12, spatial="fresnel", z=0.25, T=512, S=64, fs=71400.0,
+        band_hz=(1000.0, 35000.0), moments=("M0", "M1", "M2"), batch=4096, batches=25,
+        pool=1024, scene="scene_stream_fresnel"),
+    "asp_stft_256_t512_s512": dict(
+        desc="256x256 uint16 (12-bit) frames, fs=71.4 kHz, ASP z=0.30 m, STFT T=512 stride 512, "
+             "M0/M1/M2 over 1-35 kHz, 102,400-frame stream per step (the paper's Table IV ASP+STFT "
+             "512/512 row shape)",
+        N=256, bits=12, spatial="asp", z=0.30, T=512, S=512, fs=71400.0,
+        band_hz=(1000.0, 35000.0), moments=("M0", "M1", "M2"), batch=4096, batches=25,
+        pool=1024, scene="scene_stream_fresnel"),
+    "tiny_asp_stft_256_t64": dict(
+        desc="256x256 uint8 frames, fs=20 kHz, ASP z=0.30 m, STFT T=64 stride 64, M0 over bins "
+             "4..28, 102,400-frame stream per step",
+        N=256, bits=8, spatial="asp", z=0.30, T=64, S=64, fs=20000.0, band=(4, 28),
+        moments=("M0",), batch=4096, batches=25, pool=1024, scene="scene_tiny_asp_stft"),
+}
+DEFAULT = "stream_fresnel_256_t512_s64"
+METRIC = "raw frames/s rendered"
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def band_bins(w):
+    if "band_hz" in w:
+        lo, hi = w["band_hz"]
+        return (math.ceil(lo * w["T"] / w["fs"] - 1e-12), math.floor(hi * w["T"] / w["fs"] + 1e-12))
+    return w["band"]
+
+
+def oracle_params(w):
+    klo, khi = band_bins(w)
+    return dict(spatial=w["spatial"], z_m=w["z"], lambda_m=852e-9, pitch_x_m=20e-6,
+                pitch_y_m=20e-6, fftshift=1, temporal="stft", T=w["T"], stride=w["S"],
+                fs_hz=w["fs"], band_lo_bin=klo, band_hi_bin=khi, moments=w["moments"])
+
+
+def make_pool(w, n):
+    sc = getattr(synth, w["scene"])(N=w["N"], bits=w["bits"])
+    synth.build(sc)
+    return synth.frames(sc, 0, n)
+
+
+def algorithmic(w):
+    """Algorithmic bytes and flops per raw frame (method dataflow, see the design notes)."""
+    hw = w["N"] * w["N"]
+    bpp = 1 if w["bits"] <= 8 else 2
+    nmom = len(w["moments"])
+    T, S = w["T"], w["S"]
+    frame_bytes = hw * (bpp + 16 + 4.0 * nmom / S)
+    fft2 = 5.0 * hw * math.log2(hw)
+    spatial_flops = 2 * fft2 + 6 * hw if w["spatial"] == "asp" else fft2 + 6 * hw
+    stft_flops = hw * 5.0 * T * math.log2(T) / S
+    stft_bytes = hw * (8 + 4.0 * nmom / S)
+    return dict(frame_bytes=frame_bytes, spatial_flops=spatial_flops, stft_flops=stft_flops,
+                stft_bytes=stft_bytes)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                     text=True)
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inside = [r for ts, r in rows if self.t0 and self.t1 and self.t0 - 0.15 <= ts <= self.t1 + 0.15]
+        use = inside or [r for _, r in rows]
+        if not use:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in use if num(r[1]) is not None]
+        mx = [num(r[2]) for r in use if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in use:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(use),
+                "samples_in_timed_region": len(inside)}
+
+
+# --------------------------------------------------------------- hv arm
+
+def run_hv(args, w, rank, world, dist):
+    import torch
+
+    from paper_2508_03911_gb300 import hv
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    pool_np = make_pool(w, w["pool"])
+    B = w["batch"]
+    reps = B // w["pool"]
+    pool_t = torch.from_numpy(pool_np.view(np.int16) if pool_np.dtype == np.uint16 else pool_np)
+    pool_dev = pool_t.to(dev).repeat(reps, 1, 1).contiguous()
+    klo, khi = band_bins(w)
+    N = w["N"]
+
+    def open_renderer():
+        r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream)
+        r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"], fs=w["fs"],
+                     band=(klo, khi), moments=w["moments"])
+        return r
+
+    r = open_renderer()
+    wf = r.window_floats()
+    max_win = B // w["S"] + 2
+    out = torch.empty(max_win * wf, dtype=torch.float32, device=dev)
+
+    def step(events=None):
+        for _ in range(w["batches"]):
+            if events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            st = r.push(pool_dev)
+            assert st == hv.HV_OK, st
+            r.render(out)
+            if events is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                events.append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_idx = None
+    try:
+        gpu_idx = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_idx.startswith("GPU-"):
+            gpu_idx = "GPU-" + gpu_idx
+    except Exception:
+        gpu_idx = None
+    clocks = ClockSampler(gpu_idx) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.6)
+    stats0 = r.stats()
+    hv.hv_profile_enable(r.h, True)
+    lat = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark("t0")
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(lat)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark("t1")
+    if dist:
+        dist.barrier()
+    prof = hv.hv_profile_read(r.h)
+    hv.hv_profile_enable(r.h, False)
+    stats1 = r.stats()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    frames_per_step = B * w["batches"]
+    value = world * args.steps * frames_per_step / (elapsed_ms / 1e3)
+    launches = stats1["kernel_launches"] - stats0["kernel_launches"]
+    r.close()
+
+    # ----- end-to-end through host buffers (pinned frames in, images out)
+    host_pool = pool_t.repeat(reps, 1, 1).contiguous().pin_memory()
+    r2 = open_renderer()
+    out_host = torch.empty(max_win * wf, dtype=torch.float32).pin_memory()
+    h2d = d2h = 0
+
+    def step_host(count):
+        nonlocal h2d, d2h
+        for _ in range(w["batches"]):
+            assert r2.push(host_pool) == hv.HV_OK
+            n = r2.render(out_host)
+            if count:
+                h2d += host_pool.numel() * host_pool.element_size()
+                d2h += n * wf * 4
+    for _ in range(max(1, args.warmup // 2)):
+        step_host(False)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, args.steps // 2)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host(True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps * frames_per_step / e2e_s
+    r2.close()
+
+    return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
+                clocks=clk, e2e=dict(value=e2e_value, unit="frames/s",
+                                     h2d_bytes_per_step=h2d // e2e_steps,
+                                     d2h_bytes_per_step=d2h // e2e_steps),
+                frames_per_step=frames_per_step)
+
+
+def roofline(w, res, peaks):
+    """Roofline entry of the dominant stage, from the live per-stage event timing."""
+    prof = res["prof"]
+    alg = algorithmic(w)
+    renders = max(1, prof["renders"])
+    frames = res["frames_per_step"] * 0 + prof["frames"]
+    t_sp = prof["spatial_ms"] / renders
+    t_tm = prof["temporal_ms"] / renders
+    frames_per_render = frames / renders
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    if t_tm >= t_sp:
+        flops = alg["stft_flops"] * frames_per_render
+        byts = alg["stft_bytes"] * frames_per_render
+        kern, t = "k_stft (time FFT + band moments)", t_tm
+    else:
+        flops = alg["spatial_flops"] * frames_per_render
+        byts = (w["N"] ** 2) * ((1 if w["bits"] <= 8 else 2) + 8) * frames_per_render
+        kern, t = "spatial passes (FFT2)", t_sp
+    tflops = flops / (t / 1e3) / 1e12
+    gbs = byts / (t / 1e3) / 1e9
+    alu_frac = tflops / FP32_PEAK_TFLOPS
+    hbm_frac = gbs / hbm
+    if alu_frac >= hbm_frac:
+        return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": None, "kernel": kern,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "hbm_achieved_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4),
+                "stage_ms_per_render": {"spatial": round(t_sp, 4), "temporal": round(t_tm, 4)}}
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(hbm_frac, 4), "traffic": None, "kernel": kern,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "alu_achieved_tflops": round(tflops, 3),
+            "stage_ms_per_render": {"spatial": round(t_sp, 4), "temporal": round(t_tm, 4)}}
+
+
+# -------------------------------------------------------- oracle timing
+
+_FRAME_CACHE = {}
+
+
+def oracle_sample(w, n_frames):
+    """Time the FP64 oracle on the first n_frames of the workload (all complete windows)."""
+    from oracle import hv_oracle as O
+    key = (w["desc"], n_frames)
+    if key not in _FRAME_CACHE:
+        _FRAME_CACHE[key] = make_pool(w, n_frames)
+    fr = _FRAME_CACHE[key]
+    p = oracle_params(w)
+    t0 = time.perf_counter()
+    img = O.render(fr, p)
+    dt = time.perf_counter() - t0
+    return n_frames / dt, img.shape[0], dt
+
+
+def cpu_baseline(w):
+    n = w["T"] + 2 * w["S"] if w["S"] < w["T"] else 2 * w["T"]
+    fps, nwin, dt = oracle_sample(w, n)
+    return {"value": round(fps, 2), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the workload ({nwin} windows), FP64 numpy oracle, "
+                      f"{dt:.1f} s on 1 host core"}
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return None
+    fps_list = []
+    n = w["T"] + w["S"] if w["S"] < w["T"] else w["T"]
+    for i in range(args.warmup + args.steps):
+        fps, nwin, dt = oracle_sample(w, n)
+        if i >= args.warmup:
+            fps_list.append(n / dt / 1.0)
+    value = float(np.median(fps_list))
+    return value, n
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["hv", "reference"], default="hv")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    klo, khi = band_bins(w)
+    config = {"workload": args.workload, "description": w["desc"], "frame": [w["N"], w["N"]],
+              "pixel_bits": w["bits"], "spatial": w["spatial"], "z_m": w["z"], "T": w["T"],
+              "stride": w["S"], "fs_hz": w["fs"], "band_bins": [klo, khi],
+              "moments": list(w["moments"]), "frames_per_step": w["batch"] * w["batches"],
+              "batch_frames": w["batch"],
+              "l2": "inputs larger than L2: each step streams >10 GB through the time queue",
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        res = run_reference(args, w, rank)
+        if rank == 0:
+            value, n = res
+            line = {"impl": "reference", "metric": METRIC, "value": round(value, 3),
+                    "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+                    "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                    "cpu_baseline": {"value": round(value, 3), "unit": "frames/s", "cores": 1,
+                                     "kind": "oracle",
+                                     "sample": f"each step: first {n} frames of the workload "
+                                               "through the FP64 numpy oracle on 1 host core"},
+                    "e2e": {"value": round(value, 3), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                            "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    res = run_hv(args, w, rank, world, dist)
+    if rank == 0:
+        peaks = load_peaks()
+        lat = res["lat_ms"]
+        p50 = float(np.percentile(lat, 50)) if lat else None
+        p99 = float(np.percentile(lat, 99)) if lat else None
+        alg = algorithmic(w)
+        hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+        line = {
+            "metric": METRIC, "value": round(res["value"], 1), "unit": "frames/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["elapsed_ms"] / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config,
+            "latency_ms": {"p50": p50, "p99": p99, "what": f"per {w['batch']}-frame batch: push + "
+                                                          "render, CUDA events"},
+            "hbm_pct_of_measured": round(100 * res["value"] / world * alg["frame_bytes"] / 1e9 / hbm, 2),
+            "algorithmic_bytes_per_frame": alg["frame_bytes"],
+            "roofline": roofline(w, res, peaks),
+            "e2e": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in res["e2e"].items()},
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * hv.h -- C ABI of the GB300 hologram-rendering hot path.
+ *
+ * The library turns a stream of raw camera interferograms into rendered images
+ * (the paper's computation pipeline, Sec. III-B and Fig. 1):
+ *
+ *   raw frames --convert--> complex --spatial--> time-transformation queue
+ *              --temporal (STFT moments | PCA energy)--> images
+ *
+ * All types in the signatures are plain C. Pointers are either host pointers
+ * or CUDA device pointers, as each argument says. Every call returns an
+ * hv_status; nothing throws across the ABI. Calls on one handle must be
+ * serialised by the caller; separate handles are independent.
+ *
+ * Device work runs on the handle's stream (the cudaStream_t given at open, or
+ * one the library creates). Results written to device memory are ready when
+ * that stream reaches them; results written to host memory are ready when the
+ * call returns.
+ */
+#ifndef HV_H
+#define HV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hv_handle hv_handle; /* opaque; created by hv_open, owned by the library */
+
+typedef enum {
+  HV_OK = 0,
+  HV_ERR_ARG = -1,         /* invalid argument (NULL, size, unsupported value)   */
+  HV_ERR_STATE = -2,       /* call not valid in the handle's state (no params)    */
+  HV_ERR_QUEUE_FULL = -3,  /* input queue cannot take the frames; nothing copied  */
+  HV_ERR_NOMEM = -4,       /* device or host allocation failed                    */
+  HV_ERR_CUDA = -5,        /* a CUDA runtime call failed; see hv_last_error       */
+  HV_ERR_TIMEOUT = -6,     /* a bounded device wait gave up                       */
+  HV_ERR_UNSUPPORTED = -7  /* valid request this build does not implement         */
+} hv_status;
+
+enum { HV_MEM_HOST = 0, HV_MEM_DEVICE = 1 };
+
+/* Spatial demodulation (Sec. III-B.1; benchmarks Sec. VI-B). */
+enum { HV_SPATIAL_NONE = 0, HV_SPATIAL_ASP = 1, HV_SPATIAL_FRESNEL = 2 };
+
+/* Temporal analysis (Sec. III-B.1). HV_TEMPORAL_NONE renders every propagated
+ * frame as a complex image (2 floats per pixel, re then im). */
+enum { HV_TEMPORAL_STFT = 0, HV_TEMPORAL_PCA = 1, HV_TEMPORAL_NONE = 2 };
+
+/* STFT outputs, rendered in this order for the bits set. */
+enum {
+  HV_MOM_M0 = 1,   /* sum over band of |S_k|^2                         */
+  HV_MOM_M1 = 2,   /* sum over band of f_k |S_k|^2, f_k in kHz         */
+  HV_MOM_M2 = 4,   /* sum over band of f_k^2 |S_k|^2                   */
+  HV_MOM_M1N = 8,  /* M1 / M0 (kHz), computed in FP64, 0 where M0 = 0  */
+  HV_MOM_M2N = 16  /* sqrt(M2 / M0) (kHz), FP64, 0 where M0 = 0        */
+};
+
+/* Arithmetic of the PCA covariance. */
+enum { HV_PREC_FP32 = 0, HV_PREC_BF16 = 1, HV_PREC_SPLIT_BF16 = 2 };
+
+typedef struct {
+  uint32_t struct_size;       /* sizeof(hv_open_desc)                                 */
+  int32_t device;             /* CUDA device ordinal                                   */
+  uint32_t max_width;         /* largest frame width this handle will accept           */
+  uint32_t max_height;        /* largest frame height                                  */
+  uint32_t pixel_bits;        /* 8 (uint8 frames) or 16 (uint16 frames, e.g. 12-bit)   */
+  uint32_t queue_capacity_frames; /* raw input ring capacity in frames (>= 1)          */
+  uint32_t time_queue_frames; /* propagated-frame ring capacity (0 = automatic)        */
+  uint32_t reserved;
+  void* stream;               /* cudaStream_t for all device work; NULL = own stream   */
+} hv_open_desc;
+
+typedef struct {
+  uint32_t struct_size;       /* sizeof(hv_params)                                     */
+  uint32_t width, height;     /* frame size; powers of two in [16, 1024]               */
+  int32_t spatial;            /* HV_SPATIAL_*                                          */
+  int32_t fftshift;           /* Fresnel only: 1 = centre the zero frequency           */
+  double z_m;                 /* propagation distance [m] (ASP, Fresnel)               */
+  double lambda_m;            /* wavelength [m]                                        */
+  double pitch_x_m, pitch_y_m;/* sensor pixel pitch [m]                                */
+  int32_t temporal;           /* HV_TEMPORAL_*                                         */
+  uint32_t T;                 /* window length in frames (power of two, 8..1024)       */
+  uint32_t stride;            /* time stride S in frames (>= 1)                        */
+  uint32_t moments_mask;      /* STFT: OR of HV_MOM_*                                  */
+  double fs_hz;               /* camera frame rate [Hz]                                */
+  uint32_t band_lo_bin;       /* STFT band, inclusive bin indices, used when           */
+  uint32_t band_hi_bin;       /*   band_lo_hz and band_hi_hz are both <= 0             */
+  double band_lo_hz;          /* STFT band in Hz (> 0 to use): bins ceil(lo T/fs) ..   */
+  double band_hi_hz;          /*   floor(hi T/fs)                                      */
+  uint32_t pca_lo, pca_hi;    /* PCA: eigenvectors ranked pca_lo..pca_hi (1-based,
+                                 inclusive, descending eigenvalue)                     */
+  int32_t precision;          /* PCA covariance arithmetic, HV_PREC_*                  */
+  int32_t tuned;              /* 1 = tuned form (graph replay, fused kernels)          */
+  uint32_t spatial_chunk;     /* frames per spatial launch (0 = automatic)             */
+  uint32_t reserved;
+} hv_params;
+
+typedef struct {
+  uint64_t frames_pushed;     /* frames accepted by hv_push_frames                     */
+  uint64_t frames_rejected;   /* frames refused with HV_ERR_QUEUE_FULL                 */
+  uint64_t frames_dropped;    /* frames lost after acceptance (always 0)               */
+  uint64_t frames_propagated; /* frames through the spatial transform                 */
+  uint64_t windows_rendered;  /* windows through the temporal transform               */
+  uint64_t kernel_launches;   /* kernels launched by this handle                       */
+} hv_stats;
+
+/* Open a handle on a device: allocates the raw input ring (capacity x max frame
+ * size) and creates or adopts the stream. Nothing is rendered until
+ * hv_set_params. *out receives the handle (NULL on failure).
+ * Errors: HV_ERR_ARG (bad descriptor), HV_ERR_NOMEM, HV_ERR_CUDA. */
+hv_status hv_open(const hv_open_desc* desc, hv_handle** out);
+
+/* Set the compute settings. Validated now; applied at the next window boundary,
+ * i.e. at the start of the next hv_render (the paper's "delayed" settings,
+ * Sec. IV-B). On application the time-transformation queue is flushed and the
+ * next window starts at the first frame that the previous window sequence had
+ * not yet consumed; the device workspace (time queue, tables) is (re)allocated
+ * when sizes change. Errors: HV_ERR_ARG (invalid or unsupported combination).
+ * The previous settings stay in force when an error is returned. */
+hv_status hv_set_params(hv_handle* h, const hv_params* p);
+
+/* Read back the settings last accepted by hv_set_params. */
+hv_status hv_get_params(const hv_handle* h, hv_params* p);
+
+/* Enqueue n raw frames (width x height of the current settings, or of max size
+ * when none are set) into the input ring (Sec. III-A): `frames` is a host
+ * pointer (mem_kind HV_MEM_HOST; copied before return, the caller may reuse it)
+ * or a device pointer (HV_MEM_DEVICE; copied on the handle's stream, so it must
+ * stay valid until that stream passes this point). Frames are uint8 or uint16
+ * by pixel_bits, row-major, frames contiguous. All-or-nothing: if the ring
+ * cannot take all n frames, nothing is copied and HV_ERR_QUEUE_FULL is returned
+ * (backpressure; frames are never dropped). */
+hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_kind);
+
+/* Render every complete window in the queue (at most as many as fit in `out`).
+ * Images are written window-major: STFT -> one float image per selected moment
+ * (order M0, M1, M2, M1N, M2N); PCA -> one float image E; TEMPORAL_NONE -> one
+ * complex image per frame (2 floats per pixel). out_capacity_floats bounds the
+ * write; *n_windows receives the number of windows rendered (0 is not an
+ * error). out_mem_kind says whether `out` is host or device memory.
+ * Errors: HV_ERR_STATE (no params), HV_ERR_ARG, HV_ERR_CUDA. */
+hv_status hv_render(hv_handle* h, float* out, size_t out_capacity_floats, int out_mem_kind,
+                    uint32_t* n_windows);
+
+/* Number of floats one rendered window occupies with the current settings. */
+hv_status hv_window_floats(const hv_handle* h, size_t* floats_per_window);
+
+/* Eigenvalues (descending, FP64) of the last PCA window rendered; n <= T. */
+hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n);
+
+/* Counters of the handle. */
+hv_status hv_get_stats(const hv_handle* h, hv_stats* s);
+
+/* Per-stage device timing (CUDA events on the handle's stream around the
+ * spatial and the temporal launches of every hv_render). */
+typedef struct {
+  double spatial_ms;          /* summed device time of the spatial stage           */
+  double temporal_ms;         /* summed device time of the temporal stage          */
+  uint64_t renders;           /* hv_render calls recorded                          */
+  uint64_t frames;            /* frames propagated while recording                 */
+  uint64_t windows;           /* windows rendered while recording                  */
+} hv_profile;
+
+/* Start (on = 1, counters reset) or stop (on = 0) recording stage times. */
+hv_status hv_profile_enable(hv_handle* h, int on);
+
+/* Stage times recorded so far; waits for the handle's stream. */
+hv_status hv_profile_read(hv_handle* h, hv_profile* out);
+
+/* Wait for all device work of the handle. */
+hv_status hv_synchronize(hv_handle* h);
+
+/* Free every resource of the handle. NULL is accepted (no-op). */
+hv_status hv_close(hv_handle* h);
+
+/* Text of the handle's last error (or of the last failed hv_open when h is
+ * NULL). Valid until the next call on the handle. */
+const char* hv_last_error(const hv_handle* h);
+
+/* Version string of the library. */
+const char* hv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HV_H */

@@ -1,0 +1,155 @@
+// fft_dev.cuh -- device building blocks for batched complex FFTs in shared memory.
+//
+// The spatial transforms (FFT2 of every frame, Sec. III-B.1) and the temporal
+// transform (FFT along the frame axis of every pixel) are both many independent
+// 1-D FFTs of one power-of-two length L. A CTA holds BT of them side by side in
+// shared memory with the batch index fastest: element t of line b lives at
+// buf[t * LD + b]. Batch-fastest means every global load and store of a line
+// segment is coalesced and every shared-memory stage access by a warp is a
+// contiguous run along b (conflict-free).
+//
+// Algorithm: Stockham autosort decimation in time, radix 8 while the remaining
+// length allows it, then radix 4 or 2. Stage with span NS (product of the
+// radices already applied) and radix R: butterfly j in [0, L/R) reads the R
+// inputs j + m L/R, multiplies input m by w_L^{(j mod NS) m L/(NS R)}, applies an
+// R-point DFT, and writes output m to (j / NS) NS R + (j mod NS) + m NS. The
+// last stage leaves bin k = j + m L/R of butterfly j in registers and hands it
+// to an epilogue. Twiddles come from a per-length table w_L^e = exp(-2 pi i e/L)
+// computed in float64 on the host and rounded to float.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hv {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// v * (DIR * i): DIR = -1 is the forward transform's -i, DIR = +1 the inverse's +i.
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 v) {
+  if constexpr (DIR < 0) return make_float2(v.y, -v.x);
+  else return make_float2(-v.y, v.x);
+}
+
+// In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8}.
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R == 2) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = mul_i<DIR>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  } else {
+    static_assert(R == 8, "radix");
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    dft<4, DIR>(e);
+    dft<4, DIR>(o);
+    const float c = 0.70710678118654752440f;
+    // o_k *= exp(DIR 2 pi i k / 8)
+    float2 o1 = make_float2(c * (o[1].x - DIR * o[1].y), c * (o[1].y + DIR * o[1].x));
+    float2 o2 = mul_i<DIR>(o[2]);
+    float2 o3 = make_float2(c * (-o[3].x - DIR * o[3].y), c * (-o[3].y + DIR * o[3].x));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+}
+
+template <int REM>
+struct RadixOf {
+  static constexpr int value = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+};
+
+// Threads per CTA for BT lines of length L: one radix-8 butterfly pair per
+// thread (<= 16 complex values in registers per stage), clamped to [32, 1024].
+template <int L, int BT>
+struct FftThreads {
+  static constexpr int raw = BT * L / 16;
+  static constexpr int value = raw < 32 ? 32 : (raw > 1024 ? 1024 : raw);
+};
+
+// One Stockham stage and (recursively) the rest. `src` holds the stage input
+// with leading dimension src_ld (it may alias buf); intermediate stages write
+// buf (leading dimension LD). The last stage calls epi(b, k, value) for every
+// output bin, after a barrier (so the epilogue may overwrite buf).
+template <int L, int NS, int DIR, int BT, int NT, int LD, class Epi>
+__device__ __forceinline__ void fft_stages(const float2* src, int src_ld, float2* buf,
+                                           const float2* __restrict__ tw, Epi& epi) {
+  constexpr int REM = L / NS;
+  constexpr int R = RadixOf<REM>::value;
+  constexpr int NB = L / R;
+  static_assert((BT * NB) % NT == 0, "thread count must divide the butterflies");
+  constexpr int ITEMS = BT * NB / NT;
+  static_assert(ITEMS >= 1, "too many threads");
+  float2 v[ITEMS][R];
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    const int idx = threadIdx.x + it * NT;
+    const int b = idx % BT, j = idx / BT;
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[it][m] = src[(j + m * NB) * src_ld + b];
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int m = 1; m < R; ++m) {
+        float2 w = __ldg(&tw[jm * m * (L / (NS * R))]);
+        if constexpr (DIR > 0) w.y = -w.y;
+        v[it][m] = cmul(v[it][m], w);
+      }
+    }
+    dft<R, DIR>(v[it]);
+  }
+  __syncthreads();
+  if constexpr (NS * R == L) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int idx = threadIdx.x + it * NT;
+      const int b = idx % BT, j = idx / BT;
+#pragma unroll
+      for (int m = 0; m < R; ++m) epi(b, j + m * NB, v[it][m]);
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int idx = threadIdx.x + it * NT;
+      const int b = idx % BT, j = idx / BT;
+      const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[(base + m * NS) * LD + b] = v[it][m];
+    }
+    __syncthreads();
+    fft_stages<L, NS * R, DIR, BT, NT, LD, Epi>(buf, LD, buf, tw, epi);
+  }
+}
+
+// Full FFT of the BT lines in buf (in place through registers).
+template <int L, int DIR, int BT, int NT, int LD, class Epi>
+__device__ __forceinline__ void fft_lines(float2* buf, const float2* __restrict__ tw, Epi& epi) {
+  fft_stages<L, 1, DIR, BT, NT, LD, Epi>(buf, LD, buf, tw, epi);
+}
+
+// Epilogue that stores bin k of line b back to buf in natural order.
+template <int LD>
+struct StoreSmem {
+  float2* buf;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { buf[k * LD + b] = v; }
+};
+
+}  // namespace hv

@@ -1,0 +1,605 @@
+// hv_api.cu -- the C ABI (include/hv.h): handle, input ring, time-transformation
+// queue, delayed settings and the render scheduler.
+//
+// Buffers follow Sec. II-B.1: fixed-size device buffers allocated once per
+// setting (Sec. VII-C: allocate up front, never in the per-batch loop) and a
+// ring FIFO for input frames with backpressure instead of frame drops. Compute
+// settings are "delayed" (Sec. IV-B): hv_set_params validates and stores them;
+// they take effect at the next window boundary (start of the next hv_render).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hv.h"
+#include "hv_internal.h"
+
+using namespace hv;
+
+struct hv_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_pushed = nullptr, ev_consumed = nullptr;
+  uint32_t max_w = 0, max_h = 0, bits = 8, cap = 0, tq_req = 0;
+  void* raw = nullptr;
+  // settings
+  bool has_params = false, pending = false;
+  hv_params cur{}, pend{};
+  uint32_t W = 0, H = 0, T = 1, S = 1, klo = 0, khi = 0, nout = 0;
+  size_t win_floats = 0;
+  // device workspace
+  float2* tq = nullptr;
+  uint32_t Q = 0;
+  size_t tq_bytes = 0;
+  float2* s1 = nullptr;
+  float2* s2 = nullptr;
+  size_t s1_bytes = 0, s2_bytes = 0;
+  uint32_t chunk = 0;
+  float2* tw = nullptr;  // all twiddle tables, length 8..1024 packed
+  float2* asp_ht = nullptr;
+  float2* chirp = nullptr;  // [W] x factors then [H] y factors
+  size_t table_bytes = 0;
+  float* staging = nullptr;
+  size_t staging_bytes = 0;
+  // stream state (frame indices since open)
+  uint64_t pushed = 0, next_win = 0, propagated = 0;
+  hv_stats st{};
+  std::string err;
+  std::vector<double> pca_lam;
+  // stage timing
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // triples: before spatial, after spatial, after temporal
+  size_t prof_used = 0;
+  hv_profile prof_acc{};
+};
+
+namespace {
+
+thread_local std::string g_open_err;
+
+constexpr int kMinLog = 3, kMaxLog = 10;  // twiddle tables for L = 8 .. 1024
+
+size_t tw_offset(uint32_t L) {  // tables packed by increasing length
+  size_t off = 0;
+  for (uint32_t l = 1u << kMinLog; l < L; l <<= 1) off += l;
+  return off;
+}
+
+bool is_pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+hv_status fail(hv_handle* h, hv_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_open_err = msg;
+  return s;
+}
+
+hv_status cuda_fail(hv_handle* h, cudaError_t e, const char* what) {
+  return fail(h, HV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define HV_CU(h, call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <class Tp>
+void dfree(Tp*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+uint32_t popcount5(uint32_t m) {
+  uint32_t n = 0;
+  for (int i = 0; i < 5; ++i) n += (m >> i) & 1u;
+  return n;
+}
+
+// Derived quantities of a settings block; also the validation.
+struct Derived {
+  uint32_t T, S, klo, khi, nout;
+  size_t win_floats;
+};
+
+hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::string& why) {
+  if (p.struct_size != sizeof(hv_params)) { why = "hv_params.struct_size mismatch"; return HV_ERR_ARG; }
+  if (!is_pow2(p.width) || !is_pow2(p.height) || p.width < 16 || p.height < 16 || p.width > 1024 ||
+      p.height > 1024) {
+    why = "width and height must be powers of two in [16, 1024]";
+    return HV_ERR_ARG;
+  }
+  if (p.width > h->max_w || p.height > h->max_h) { why = "frame larger than the handle's maximum"; return HV_ERR_ARG; }
+  if (p.spatial != HV_SPATIAL_NONE && p.spatial != HV_SPATIAL_ASP && p.spatial != HV_SPATIAL_FRESNEL) {
+    why = "unknown spatial transform";
+    return HV_ERR_ARG;
+  }
+  if (p.spatial != HV_SPATIAL_NONE) {
+    if (!(p.lambda_m > 0) || !(p.pitch_x_m > 0) || !(p.pitch_y_m > 0) || !std::isfinite(p.z_m)) {
+      why = "lambda, pitches must be > 0 and z finite";
+      return HV_ERR_ARG;
+    }
+    if (p.spatial == HV_SPATIAL_FRESNEL && p.z_m == 0.0) { why = "Fresnel needs z != 0"; return HV_ERR_ARG; }
+  }
+  const size_t hw = size_t(p.width) * p.height;
+  if (p.temporal == HV_TEMPORAL_NONE) {
+    d = Derived{1, 1, 0, 0, 0, 2 * hw};
+    return HV_OK;
+  }
+  if (p.temporal == HV_TEMPORAL_PCA) { why = "PCA temporal analysis is not built yet"; return HV_ERR_UNSUPPORTED; }
+  if (p.temporal != HV_TEMPORAL_STFT) { why = "unknown temporal transform"; return HV_ERR_ARG; }
+  if (!is_pow2(p.T) || p.T < 8 || p.T > 1024) { why = "T must be a power of two in [8, 1024]"; return HV_ERR_ARG; }
+  if (p.stride < 1) { why = "stride must be >= 1"; return HV_ERR_ARG; }
+  if (!(p.fs_hz > 0)) { why = "fs_hz must be > 0"; return HV_ERR_ARG; }
+  uint32_t klo = p.band_lo_bin, khi = p.band_hi_bin;
+  if (p.band_lo_hz > 0 && p.band_hi_hz > 0) {
+    const double a = std::ceil(p.band_lo_hz * p.T / p.fs_hz - 1e-12);
+    const double b = std::floor(p.band_hi_hz * p.T / p.fs_hz + 1e-12);
+    if (a < 0 || b < a || b >= p.T) { why = "band in Hz selects no bin inside [0, T)"; return HV_ERR_ARG; }
+    klo = uint32_t(a);
+    khi = uint32_t(b);
+  }
+  if (klo > khi || khi >= p.T) { why = "band bins must satisfy lo <= hi < T"; return HV_ERR_ARG; }
+  if (p.moments_mask == 0 || p.moments_mask > 31) { why = "moments_mask must select M0..M2N bits"; return HV_ERR_ARG; }
+  const uint32_t nout = popcount5(p.moments_mask);
+  d = Derived{p.T, p.stride, klo, khi, nout, size_t(nout) * hw};
+  return HV_OK;
+}
+
+// exp(i a) in float64, rounded to float
+float2 cis(double a) { return make_float2(float(std::cos(a)), float(std::sin(a))); }
+
+// Build ASP / Fresnel tables for p in float64 and upload them.
+hv_status build_tables(hv_handle* h, const hv_params& p) {
+  const uint32_t W = p.width, H = p.height;
+  const size_t need = (size_t(W) * H + W + H) * sizeof(float2);
+  if (need > h->table_bytes) {
+    dfree(h->asp_ht);
+    HV_CU(h, cudaMalloc(&h->asp_ht, need));
+    h->table_bytes = need;
+  }
+  h->chirp = h->asp_ht + size_t(W) * H;
+  std::vector<float2> host(size_t(W) * H + W + H, make_float2(0.f, 0.f));
+  if (p.spatial == HV_SPATIAL_ASP) {
+    // H(kx, ky) = exp(i z sqrt(k^2 - kx^2 - ky^2)), zero where evanescent; stored
+    // transposed [kx][ky] with the inverse transform's 1/(W H) folded in.
+    const double k = 2.0 * M_PI / p.lambda_m;
+    const double scale = 1.0 / (double(W) * double(H));
+    for (uint32_t kx = 0; kx < W; ++kx) {
+      const double mx = kx < W / 2 ? double(kx) : double(kx) - W;
+      const double fx = 2.0 * M_PI * mx / (W * p.pitch_x_m);
+      for (uint32_t ky = 0; ky < H; ++ky) {
+        const double my = ky < H / 2 ? double(ky) : double(ky) - H;
+        const double fy = 2.0 * M_PI * my / (H * p.pitch_y_m);
+        const double kz2 = k * k - fx * fx - fy * fy;
+        float2 v = make_float2(0.f, 0.f);
+        if (kz2 >= 0) {
+          const double ph = p.z_m * std::sqrt(kz2);
+          v = make_float2(float(std::cos(ph) * scale), float(std::sin(ph) * scale));
+        }
+        host[size_t(kx) * H + ky] = v;
+      }
+    }
+  } else if (p.spatial == HV_SPATIAL_FRESNEL) {
+    // chirp exp(i pi (x^2 + y^2) / (lam z)) = cx(x) cy(y), x = (j - W/2) dx; the
+    // fftshift of the output is the input modulation (-1)^(j + l).
+    const double c = M_PI / (p.lambda_m * p.z_m);
+    for (uint32_t j = 0; j < W; ++j) {
+      const double x = (double(j) - W / 2.0) * p.pitch_x_m;
+      double ph = c * x * x + ((p.fftshift && (j & 1)) ? M_PI : 0.0);
+      host[size_t(W) * H + j] = cis(ph);
+    }
+    for (uint32_t l = 0; l < H; ++l) {
+      const double y = (double(l) - H / 2.0) * p.pitch_y_m;
+      double ph = c * y * y + ((p.fftshift && (l & 1)) ? M_PI : 0.0);
+      host[size_t(W) * H + W + l] = cis(ph);
+    }
+  }
+  HV_CU(h, cudaMemcpyAsync(h->asp_ht, host.data(), need, cudaMemcpyHostToDevice, h->stream));
+  HV_CU(h, cudaStreamSynchronize(h->stream));
+  return HV_OK;
+}
+
+hv_status ensure(hv_handle* h, void** p, size_t* have, size_t need) {
+  if (need <= *have) return HV_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(p, need);
+  if (e != cudaSuccess) return fail(h, HV_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  *have = need;
+  return HV_OK;
+}
+
+// Apply the pending settings (window boundary).
+hv_status apply_pending(hv_handle* h) {
+  if (!h->pending) return HV_OK;
+  const hv_params& p = h->pend;
+  Derived d{};
+  std::string why;
+  hv_status s = validate(h, p, d, why);
+  if (s != HV_OK) return fail(h, s, why);
+  // make sure earlier work that used the old workspace is finished
+  HV_CU(h, cudaStreamSynchronize(h->stream));
+  const uint32_t W = p.width, H = p.height;
+  const size_t fbytes = size_t(W) * H * sizeof(float2);
+  // time-transformation queue: T frames plus room for many windows per launch
+  uint32_t Q = h->tq_req;
+  if (Q == 0) {
+    const uint64_t target = uint64_t(d.T) + uint64_t(d.S) * 63;  // 64 windows per launch
+    const uint64_t cap_frames = std::max<uint64_t>(d.T, (size_t(4) << 30) / fbytes);
+    Q = uint32_t(std::min<uint64_t>(target, cap_frames));
+  }
+  Q = std::max(Q, d.T);
+  s = ensure(h, reinterpret_cast<void**>(&h->tq), &h->tq_bytes, size_t(Q) * fbytes);
+  if (s != HV_OK) return s;
+  uint32_t chunk = p.spatial_chunk ? p.spatial_chunk : std::max<uint32_t>(1, uint32_t((size_t(32) << 20) / fbytes));
+  chunk = std::min<uint32_t>(chunk, 1024);
+  const size_t sbytes = size_t(chunk) * fbytes;
+  if (p.spatial != HV_SPATIAL_NONE) {
+    s = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, sbytes);
+    if (s != HV_OK) return s;
+    if (p.spatial == HV_SPATIAL_ASP) {
+      s = ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, sbytes);
+      if (s != HV_OK) return s;
+    }
+  }
+  s = build_tables(h, p);
+  if (s != HV_OK) return s;
+  h->cur = p;
+  h->has_params = true;
+  h->pending = false;
+  h->W = W;
+  h->H = H;
+  h->T = d.T;
+  h->S = d.S;
+  h->klo = d.klo;
+  h->khi = d.khi;
+  h->nout = d.nout;
+  h->win_floats = d.win_floats;
+  h->Q = Q;
+  h->chunk = chunk;
+  // queue flush: the next window starts at the first unconsumed frame and is
+  // propagated entirely with the new settings
+  h->propagated = h->next_win;
+  return HV_OK;
+}
+
+// Fold the completed event triples into the accumulator.
+hv_status prof_flush(hv_handle* h) {
+  if (h->prof_used == 0) return HV_OK;
+  HV_CU(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < h->prof_used; i += 3) {
+    float a = 0.f, b = 0.f;
+    HV_CU(h, cudaEventElapsedTime(&a, h->prof_ev[i], h->prof_ev[i + 1]));
+    HV_CU(h, cudaEventElapsedTime(&b, h->prof_ev[i + 1], h->prof_ev[i + 2]));
+    h->prof_acc.spatial_ms += a;
+    h->prof_acc.temporal_ms += b;
+  }
+  h->prof_used = 0;
+  return HV_OK;
+}
+
+hv_status prof_mark(hv_handle* h, int which) {
+  if (!h->prof) return HV_OK;
+  if (which == 0 && h->prof_used + 3 > h->prof_ev.size()) {
+    hv_status s = prof_flush(h);
+    if (s != HV_OK) return s;
+  }
+  HV_CU(h, cudaEventRecord(h->prof_ev[h->prof_used++], h->stream));
+  return HV_OK;
+}
+
+hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
+  for (uint64_t a = f0; a < f1; a += h->chunk) {
+    const uint32_t n = uint32_t(std::min<uint64_t>(h->chunk, f1 - a));
+    SpatialArgs sa{};
+    sa.spatial = h->cur.spatial;
+    sa.in_kind = h->bits == 8 ? IN_U8 : IN_U16;
+    sa.W = h->W;
+    sa.H = h->H;
+    sa.n = n;
+    sa.raw = RingRef{h->raw, h->cap, uint32_t(a % h->cap)};
+    sa.tq = RingRef{h->tq, h->Q, uint32_t(a % h->Q)};
+    sa.scratch1 = h->s1;
+    sa.scratch2 = h->s2;
+    sa.tw_w = h->tw + tw_offset(h->W);
+    sa.tw_h = h->tw + tw_offset(h->H);
+    sa.asp_ht = h->asp_ht;
+    sa.chirp_x = h->chirp;
+    sa.chirp_y = h->chirp + h->W;
+    int launches = 0;
+    cudaError_t e = launch_spatial(sa, h->stream, &launches);
+    h->st.kernel_launches += launches;
+    if (e != cudaSuccess) return cuda_fail(h, e, "spatial transform launch");
+    h->st.frames_propagated += n;
+  }
+  return HV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hv_status hv_open(const hv_open_desc* desc, hv_handle** out) {
+  if (!out) return fail(nullptr, HV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc || desc->struct_size != sizeof(hv_open_desc)) return fail(nullptr, HV_ERR_ARG, "bad hv_open_desc");
+  if (desc->pixel_bits != 8 && desc->pixel_bits != 16) return fail(nullptr, HV_ERR_ARG, "pixel_bits must be 8 or 16");
+  if (desc->max_width < 16 || desc->max_height < 16 || desc->max_width > 1024 || desc->max_height > 1024)
+    return fail(nullptr, HV_ERR_ARG, "max frame size must be within [16, 1024]");
+  if (desc->queue_capacity_frames < 1) return fail(nullptr, HV_ERR_ARG, "queue capacity must be >= 1");
+  hv_handle* h = new hv_handle();
+  h->device = desc->device;
+  h->max_w = desc->max_width;
+  h->max_h = desc->max_height;
+  h->bits = desc->pixel_bits;
+  h->cap = desc->queue_capacity_frames;
+  h->tq_req = desc->time_queue_frames;
+  auto bail = [&](hv_status s, const std::string& m) {
+    g_open_err = m;
+    hv_close(h);
+    return s;
+  };
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return bail(HV_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  if (desc->stream) {
+    h->stream = static_cast<cudaStream_t>(desc->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(HV_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    h->own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pushed, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_consumed, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(HV_ERR_CUDA, std::string("stream/event: ") + cudaGetErrorString(e));
+  const size_t raw_bytes = size_t(h->cap) * h->max_w * h->max_h * (h->bits / 8);
+  e = cudaMalloc(&h->raw, raw_bytes);
+  if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("input ring: ") + cudaGetErrorString(e));
+  // twiddle tables exp(-2 pi i e / L), L = 8..1024, computed in float64
+  std::vector<float2> tw(tw_offset(1u << (kMaxLog + 1)));
+  for (uint32_t L = 1u << kMinLog; L <= (1u << kMaxLog); L <<= 1)
+    for (uint32_t i = 0; i < L; ++i) tw[tw_offset(L) + i] = cis(-2.0 * M_PI * double(i) / double(L));
+  e = cudaMalloc(&h->tw, tw.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpy(h->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("twiddles: ") + cudaGetErrorString(e));
+  *out = h;
+  return HV_OK;
+}
+
+hv_status hv_set_params(hv_handle* h, const hv_params* p) {
+  if (!h || !p) return fail(h, HV_ERR_ARG, "NULL argument");
+  Derived d{};
+  std::string why;
+  hv_status s = validate(h, *p, d, why);
+  if (s != HV_OK) return fail(h, s, why);
+  const hv_params& ref = h->pending ? h->pend : h->cur;
+  const bool have = h->pending || h->has_params;
+  if (have && (ref.width != p->width || ref.height != p->height)) {
+    // a new frame size cannot reuse queued frames of the old size
+    const uint64_t queued = h->pushed - h->next_win;
+    h->st.frames_dropped += queued;
+    h->next_win = h->pushed;
+    h->propagated = h->pushed;
+  }
+  h->pend = *p;
+  h->pending = true;
+  return HV_OK;
+}
+
+hv_status hv_get_params(const hv_handle* h, hv_params* p) {
+  if (!h || !p) return HV_ERR_ARG;
+  if (!h->has_params && !h->pending) return HV_ERR_STATE;
+  *p = h->pending ? h->pend : h->cur;
+  return HV_OK;
+}
+
+hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_kind) {
+  if (!h) return HV_ERR_ARG;
+  if (n == 0) return HV_OK;
+  if (!frames) return fail(h, HV_ERR_ARG, "frames is NULL");
+  if (mem_kind != HV_MEM_HOST && mem_kind != HV_MEM_DEVICE) return fail(h, HV_ERR_ARG, "bad mem_kind");
+  if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "hv_set_params must come first");
+  const hv_params& p = h->pending ? h->pend : h->cur;
+  if (h->pushed + n - h->next_win > h->cap) {
+    h->st.frames_rejected += n;
+    return fail(h, HV_ERR_QUEUE_FULL, "input queue full");
+  }
+  HV_CU(h, cudaSetDevice(h->device));
+  const size_t fb = size_t(p.width) * p.height * (h->bits / 8);
+  const uint32_t slot = uint32_t(h->pushed % h->cap);
+  const uint32_t n1 = std::min(n, h->cap - slot);
+  const char* src = static_cast<const char*>(frames);
+  char* ring = static_cast<char*>(h->raw);
+  if (mem_kind == HV_MEM_DEVICE) {
+    HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyDeviceToDevice, h->stream));
+    if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    // copy stream: wait until the slots being overwritten have been consumed
+    HV_CU(h, cudaStreamWaitEvent(h->copy_stream, h->ev_consumed, 0));
+    HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyHostToDevice, h->copy_stream));
+    if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyHostToDevice, h->copy_stream));
+    HV_CU(h, cudaEventRecord(h->ev_pushed, h->copy_stream));
+    HV_CU(h, cudaEventSynchronize(h->ev_pushed));  // host buffer consumed on return
+    HV_CU(h, cudaStreamWaitEvent(h->stream, h->ev_pushed, 0));
+  }
+  h->pushed += n;
+  h->st.frames_pushed += n;
+  return HV_OK;
+}
+
+hv_status hv_window_floats(const hv_handle* h, size_t* f) {
+  if (!h || !f) return HV_ERR_ARG;
+  if (h->pending) {
+    Derived d{};
+    std::string why;
+    hv_status s = validate(h, h->pend, d, why);
+    if (s != HV_OK) return s;
+    *f = d.win_floats;
+    return HV_OK;
+  }
+  if (!h->has_params) return HV_ERR_STATE;
+  *f = h->win_floats;
+  return HV_OK;
+}
+
+hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, uint32_t* n_windows) {
+  if (!h || !n_windows) return fail(h, HV_ERR_ARG, "NULL argument");
+  *n_windows = 0;
+  if (out_kind != HV_MEM_HOST && out_kind != HV_MEM_DEVICE) return fail(h, HV_ERR_ARG, "bad mem_kind");
+  if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "no settings");
+  HV_CU(h, cudaSetDevice(h->device));
+  hv_status s = apply_pending(h);
+  if (s != HV_OK) return s;
+  const bool none = h->cur.temporal == HV_TEMPORAL_NONE;
+  const uint32_t T = h->T, S = h->S;
+  uint64_t avail = 0;
+  if (h->pushed >= h->next_win + T) avail = (h->pushed - h->next_win - T) / S + 1;
+  const uint64_t by_q = (h->Q - T) / S + 1;
+  const uint64_t by_out = out ? cap_floats / h->win_floats : 0;
+  const uint32_t nw = uint32_t(std::min({avail, by_q, by_out}));
+  if (nw == 0) return HV_OK;
+  float* dst = out;
+  if (out_kind == HV_MEM_HOST) {
+    s = ensure(h, reinterpret_cast<void**>(&h->staging), &h->staging_bytes, size_t(nw) * h->win_floats * sizeof(float));
+    if (s != HV_OK) return s;
+    dst = h->staging;
+  }
+  const uint64_t prop_before = h->st.frames_propagated;
+  s = prof_mark(h, 0);
+  if (s != HV_OK) return s;
+  // spatial transform of every frame of these windows not yet in the queue
+  for (uint32_t w = 0; w < nw; ++w) {
+    const uint64_t a = h->next_win + uint64_t(w) * S;
+    const uint64_t lo = std::max(a, h->propagated);
+    if (lo < a + T) {
+      s = propagate(h, lo, a + T);
+      if (s != HV_OK) return s;
+      h->propagated = a + T;
+    }
+  }
+  s = prof_mark(h, 1);
+  if (s != HV_OK) return s;
+  int launches = 0;
+  cudaError_t e;
+  const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
+  if (none) {
+    e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
+  } else {
+    StftArgs sa{};
+    sa.W = h->W;
+    sa.H = h->H;
+    sa.T = T;
+    sa.S = S;
+    sa.nwin = nw;
+    sa.tq = tq;
+    sa.tw_t = h->tw + tw_offset(T);
+    sa.klo = h->klo;
+    sa.khi = h->khi;
+    sa.fscale = float(h->cur.fs_hz / double(T) / 1000.0);
+    sa.mask = h->cur.moments_mask;
+    sa.nout = h->nout;
+    sa.out = dst;
+    e = launch_stft(sa, h->stream, &launches);
+  }
+  h->st.kernel_launches += launches;
+  if (e != cudaSuccess) return cuda_fail(h, e, "temporal transform launch");
+  s = prof_mark(h, 2);
+  if (s != HV_OK) return s;
+  if (h->prof) {
+    h->prof_acc.renders += 1;
+    h->prof_acc.frames += h->st.frames_propagated - prop_before;
+    h->prof_acc.windows += nw;
+  }
+  HV_CU(h, cudaEventRecord(h->ev_consumed, h->stream));
+  h->next_win += uint64_t(nw) * S;
+  h->st.windows_rendered += nw;
+  if (out_kind == HV_MEM_HOST) {
+    HV_CU(h, cudaMemcpyAsync(out, dst, size_t(nw) * h->win_floats * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    HV_CU(h, cudaStreamSynchronize(h->stream));
+  }
+  *n_windows = nw;
+  return HV_OK;
+}
+
+hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n) {
+  if (!h || !out) return HV_ERR_ARG;
+  if (h->pca_lam.empty()) return HV_ERR_STATE;
+  if (n > h->pca_lam.size()) return HV_ERR_ARG;
+  std::memcpy(out, h->pca_lam.data(), n * sizeof(double));
+  return HV_OK;
+}
+
+hv_status hv_get_stats(const hv_handle* h, hv_stats* s) {
+  if (!h || !s) return HV_ERR_ARG;
+  *s = h->st;
+  return HV_OK;
+}
+
+hv_status hv_profile_enable(hv_handle* h, int on) {
+  if (!h) return HV_ERR_ARG;
+  HV_CU(h, cudaSetDevice(h->device));
+  if (on && h->prof_ev.empty()) {
+    h->prof_ev.resize(3 * 256, nullptr);
+    for (auto& e : h->prof_ev) HV_CU(h, cudaEventCreate(&e));
+  }
+  if (on) {
+    HV_CU(h, cudaStreamSynchronize(h->stream));
+    h->prof_used = 0;
+    h->prof_acc = hv_profile{};
+  }
+  h->prof = on != 0;
+  return HV_OK;
+}
+
+hv_status hv_profile_read(hv_handle* h, hv_profile* out) {
+  if (!h || !out) return HV_ERR_ARG;
+  HV_CU(h, cudaSetDevice(h->device));
+  hv_status s = prof_flush(h);
+  if (s != HV_OK) return s;
+  *out = h->prof_acc;
+  return HV_OK;
+}
+
+hv_status hv_synchronize(hv_handle* h) {
+  if (!h) return HV_ERR_ARG;
+  HV_CU(h, cudaSetDevice(h->device));
+  HV_CU(h, cudaStreamSynchronize(h->stream));
+  return HV_OK;
+}
+
+hv_status hv_close(hv_handle* h) {
+  if (!h) return HV_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->copy_stream) {
+    cudaStreamSynchronize(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream);
+  }
+  if (h->ev_pushed) cudaEventDestroy(h->ev_pushed);
+  if (h->ev_consumed) cudaEventDestroy(h->ev_consumed);
+  for (auto& e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
+  dfree(h->tq);
+  dfree(h->s1);
+  dfree(h->s2);
+  dfree(h->tw);
+  dfree(h->asp_ht);
+  dfree(h->staging);
+  if (h->raw) cudaFree(h->raw);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return HV_OK;
+}
+
+const char* hv_last_error(const hv_handle* h) { return h ? h->err.c_str() : g_open_err.c_str(); }
+
+const char* hv_version(void) { return "hv-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// hv_internal.h -- launchers shared between the C-ABI runtime and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hv {
+
+// Frames live in rings: frame f of the stream sits in slot (f mod capacity).
+// A launch covers n consecutive frames starting at ring slot `slot0`.
+struct RingRef {
+  void* base;        // ring storage
+  uint32_t cap;      // capacity in frames
+  uint32_t slot0;    // slot of the first frame of the launch
+};
+
+// Input element kinds of the first spatial pass.
+enum InKind { IN_U8 = 0, IN_U16 = 1 };
+
+// Spatial transform of n frames (Sec. III-B.1), raw ring -> time-queue ring.
+struct SpatialArgs {
+  int spatial;          // HV_SPATIAL_*
+  int in_kind;          // IN_U8 / IN_U16
+  uint32_t W, H;
+  uint32_t n;           // frames in this launch
+  RingRef raw;          // uint8/uint16 frames
+  RingRef tq;           // complex64 frames
+  float2* scratch1;     // n * W * H complex64 (transposed intermediate)
+  float2* scratch2;     // n * W * H complex64 (ASP only)
+  const float2* tw_w;   // twiddle table of length W
+  const float2* tw_h;   // twiddle table of length H
+  const float2* asp_ht; // ASP transfer function, transposed [kx][ky], includes 1/(W H)
+  const float2* chirp_x;// Fresnel chirp factors along x (length W), fftshift folded in
+  const float2* chirp_y;// along y (length H)
+};
+cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
+
+// STFT band moments of nwin windows (Sec. III-B.1), time-queue ring -> images.
+struct StftArgs {
+  uint32_t W, H, T, S;
+  uint32_t nwin;
+  RingRef tq;           // complex64 frames; slot0 = slot of window 0's first frame
+  const float2* tw_t;   // twiddle table of length T
+  uint32_t klo, khi;    // inclusive band
+  float fscale;         // kHz per bin: fs / T / 1000
+  uint32_t mask;        // HV_MOM_* bits
+  uint32_t nout;        // popcount(mask)
+  float* out;           // [nwin][nout][H*W]
+};
+cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
+
+// Copy propagated frames out as interleaved complex images.
+cudaError_t launch_copy_frames(const RingRef& tq, uint32_t n, uint32_t hw, float* out,
+                               cudaStream_t s, int* launches);
+
+}  // namespace hv

@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle.
+
+Tolerances: conversion bit-exact; FP32 complex fields relative L2 <= 1e-5;
+rendered moment images relative L2 <= 1e-4 (per rendered image).
+"""
+import numpy as np
+import pytest
+
+from oracle import hv_oracle as O
+from paper_2508_03911_gb300 import hv, synth
+from tests._util import images_from, oracle_params, rel_l2, to_device, to_hv
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+IMAGE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hv.lib()  # fails loudly when the extension is missing
+
+
+def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=None):
+    """Push `frames` (in packets) and render all complete windows through the C ABI."""
+    import torch
+    n, H, W = frames.shape
+    bits = 8 if frames.dtype == np.uint8 else 16
+    r = hv.Renderer(W, H, bits, queue or max(n, 1))
+    try:
+        hv.hv_set_params(r.h, to_hv(p, **(extra or {})))
+        wf = r.window_floats()
+        nwin_max = max(n, 1)
+        if out_kind == "device":
+            out = torch.zeros(nwin_max * wf + 7, dtype=torch.float32, device="cuda")
+        else:
+            out = np.zeros(nwin_max * wf + 7, dtype=np.float32)
+        dev = to_device(frames) if out_kind == "device" else frames
+        packets = packets or [n]
+        done, got = 0, 0
+        for k in packets:
+            assert r.push(dev[done:done + k]) == hv.HV_OK
+            done += k
+            view = out[got * wf:]
+            got += r.render(view)
+        torch.cuda.synchronize()
+        host = out.cpu().numpy() if out_kind == "device" else out
+        return images_from(host, got, p), r.stats()
+    finally:
+        r.close()
+
+
+def oracle_fields(frames, p):
+    return np.stack([O.spatial(O.convert(f), p) for f in frames])[:, None]
+
+
+# ----------------------------------------------------------- conversion
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_conversion_bit_exact_exhaustive(bits):
+    if bits == 8:
+        fr = np.arange(256, dtype=np.uint8).reshape(1, 16, 16)
+    else:
+        fr = np.arange(65536, dtype=np.uint16).reshape(1, 256, 256)
+    p = oracle_params(spatial="none", temporal="none", T=1, stride=1, H=fr.shape[1], W=fr.shape[2])
+    img, _ = gpu_render(fr, p)
+    assert np.array_equal(img.real, fr.astype(np.float64))
+    assert np.all(img.imag == 0)
+
+
+# ------------------------------------------------------- complex fields
+
+SIZES = [(16, 16), (32, 64), (64, 32), (128, 128), (256, 256), (512, 512), (1024, 1024)]
+
+
+@pytest.mark.parametrize("H,W", SIZES)
+@pytest.mark.parametrize("spatial", ["asp", "fresnel"])
+def test_spatial_field_parity(H, W, spatial):
+    n = 3 if H * W <= 256 * 256 else 1
+    fr = synth.random_frames(n, H, W, 12, seed=100 + H + W)
+    p = oracle_params(spatial=spatial, z_m=0.25, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
+                      H=H, W=W)
+    img, st = gpu_render(fr, p)
+    ref = oracle_fields(fr, p)
+    assert img.shape == ref.shape
+    for i in range(n):
+        assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
+    assert st["frames_propagated"] == n
+
+
+def test_fresnel_without_fftshift_and_negative_z():
+    fr = synth.random_frames(2, 64, 128, 8, seed=5)
+    for shift, z in ((0, 0.2), (1, -0.3)):
+        p = oracle_params(spatial="fresnel", fftshift=shift, z_m=z, temporal="none", T=1, stride=1,
+                          H=64, W=128)
+        img, _ = gpu_render(fr, p)
+        assert rel_l2(img, oracle_fields(fr, p)) <= FIELD_TOL
+    p = oracle_params(spatial="asp", z_m=-0.4, temporal="none", T=1, stride=1, H=64, W=128)
+    img, _ = gpu_render(fr, p)
+    assert rel_l2(img, oracle_fields(fr, p)) <= FIELD_TOL
+
+
+# -------------------------------------------------------- STFT moments
+
+def check_images(img, ref, tol=IMAGE_TOL):
+    assert img.shape == ref.shape, (img.shape, ref.shape)
+    for w in range(ref.shape[0]):
+        for q in range(ref.shape[1]):
+            e = rel_l2(img[w, q], ref[w, q])
+            assert e <= tol, (w, q, e)
+
+
+def test_tiny_asp_stft_scene():
+    """64 frames of 256x256 uint8, ASP z=0.30 m, STFT T=64, M0 over bins 4..28."""
+    sc = synth.build(synth.scene_tiny_asp_stft())
+    fr = synth.frames(sc, 0, 64)
+    p = oracle_params(H=256, W=256)
+    img, st = gpu_render(fr, p)
+    check_images(img, O.render(fr, p))
+    assert st["windows_rendered"] == 1 and st["frames_dropped"] == 0
+
+
+ALL_MOMENTS = ("M0", "M1", "M2", "M1N", "M2N")
+
+
+@pytest.mark.parametrize("T,S,spatial", [(8, 8, "asp"), (16, 4, "asp"), (32, 5, "fresnel"),
+                                         (64, 96, "fresnel"), (128, 32, "none"), (256, 64, "asp")])
+def test_stft_windows_strides_and_moments(T, S, spatial):
+    H, W = 32, 64
+    n = T + 3 * S + 5  # ragged tail: frames after the last complete window stay queued
+    fr = synth.random_frames(n, H, W, 12, seed=T * 7 + S)
+    p = oracle_params(spatial=spatial, T=T, stride=S, fs_hz=71400.0, band_lo_bin=1,
+                      band_hi_bin=T // 2 + 1, moments=ALL_MOMENTS, H=H, W=W)
+    img, st = gpu_render(fr, p)
+    ref = O.render(fr, p)
+    check_images(img, ref)
+    assert st["windows_rendered"] == len(O.window_starts(n, T, S))
+
+
+def test_streaming_packets_match_one_shot():
+    """Ragged packets and renders interleaved give the windows of the whole stream."""
+    H = W = 64
+    T, S = 32, 8
+    fr = synth.random_frames(150, H, W, 8, seed=77)
+    p = oracle_params(spatial="asp", T=T, stride=S, band_lo_bin=2, band_hi_bin=12,
+                      moments=("M0", "M2"), H=H, W=W)
+    img, st = gpu_render(fr, p, packets=[1, 30, 7, 50, 3, 59])
+    check_images(img, O.render(fr, p))
+    assert st["frames_pushed"] == 150
+
+
+def test_host_buffers_path():
+    H = W = 64
+    fr = synth.random_frames(40, H, W, 12, seed=3)
+    p = oracle_params(spatial="fresnel", T=16, stride=8, band_lo_bin=1, band_hi_bin=7,
+                      moments=ALL_MOMENTS, H=H, W=W)
+    img, _ = gpu_render(fr, p, out_kind="host", packets=[13, 27])
+    check_images(img, O.render(fr, p))
+
+
+def test_max_window_length():
+    H, W, T = 16, 32, 1024
+    fr = synth.random_frames(T + 256, H, W, 12, seed=11)
+    p = oracle_params(spatial="asp", T=T, stride=256, band_lo_bin=3, band_hi_bin=900,
+                      moments=ALL_MOMENTS, H=H, W=W)
+    img, _ = gpu_render(fr, p)
+    check_images(img, O.render(fr, p))
+
+
+@pytest.mark.slow
+def test_paper_scale_stream_prefix():
+    """256x256 12-bit, Fresnel z=0.25 m, T=512 S=64, M0/M1/M2 over 1..35 kHz at
+    fs = 71.4 kHz (bins 8..250): the first 768 frames (5 windows), every pixel."""
+    sc = synth.build(synth.scene_stream_fresnel())
+    fr = synth.frames(sc, 0, 768)
+    klo, khi = O.band_bins_from_hz(1000.0, 35000.0, 71400.0, 512)
+    p = oracle_params(spatial="fresnel", z_m=0.25, T=512, stride=64, fs_hz=71400.0,
+                      band_lo_bin=klo, band_hi_bin=khi, moments=("M0", "M1", "M2"), H=256, W=256)
+    img, _ = gpu_render(fr, p)
+    check_images(img, O.render(fr, p))
+
+
+# --------------------------------------------------------- C-ABI edges
+
+def test_queue_full_backpressure_and_empty_render():
+    import torch
+    r = hv.Renderer(32, 32, 16, 10)
+    try:
+        p = oracle_params(H=32, W=32, T=8, stride=8, band_lo_bin=1, band_hi_bin=3)
+        hv.hv_set_params(r.h, to_hv(p))
+        out = torch.zeros(10 * 32 * 32, device="cuda")
+        assert r.render(out) == 0                              # nothing queued
+        fr = to_device(synth.random_frames(12, 32, 32, 12, 1))
+        assert r.push(fr[:11]) == hv.HV_ERR_QUEUE_FULL        # all-or-nothing
+        assert r.stats()["frames_pushed"] == 0
+        assert r.push(fr[:10]) == hv.HV_OK
+        assert r.push(fr[10:12]) == hv.HV_ERR_QUEUE_FULL
+        assert r.render(out[:100]) == 0                        # capacity below one window
+        assert r.render(out) == 1
+        assert r.push(fr[10:12]) == hv.HV_OK                   # space freed by the window
+        s = r.stats()
+        assert s["frames_rejected"] == 13 and s["frames_dropped"] == 0
+    finally:
+        r.close()
+
+
+def test_set_params_is_delayed_to_the_next_window():
+    """A new z applies from the next window on; that window is computed wholly
+    with the new settings."""
+    import torch
+    H = W = 32
+    fr = synth.random_frames(48, H, W, 12, seed=21)
+    p1 = oracle_params(H=H, W=W, T=16, stride=8, z_m=0.2, band_lo_bin=1, band_hi_bin=7)
+    p2 = dict(p1, z_m=0.35)
+    r = hv.Renderer(W, H, 16, 64)
+    try:
+        hv.hv_set_params(r.h, to_hv(p1))
+        out = torch.zeros(8 * H * W, device="cuda")
+        dev = to_device(fr)
+        r.push(dev[:24])
+        n1 = r.render(out)                      # windows at 0, 8
+        hv.hv_set_params(r.h, to_hv(p2))
+        r.push(dev[24:])
+        n2 = r.render(out[n1 * H * W:])          # windows at 16, 24, 32 with z = 0.35
+        torch.cuda.synchronize()
+        img = out.cpu().numpy()[: (n1 + n2) * H * W].reshape(n1 + n2, 1, H, W)
+        assert (n1, n2) == (2, 3)
+        ref1 = O.render(fr[:24], p1)
+        ref2 = O.render(fr[16:], p2)
+        check_images(img[:2], ref1)
+        check_images(img[2:], ref2)
+    finally:
+        r.close()
+
+
+def test_invalid_settings_are_rejected_and_previous_kept():
+    r = hv.Renderer(64, 64, 8, 8)
+    try:
+        bad = [dict(W=48), dict(W=128), dict(T=12), dict(T=2048), dict(band_hi_bin=64),
+               dict(moments=()), dict(spatial="fresnel", z_m=0.0)]
+        for b in bad:
+            p = oracle_params(H=64, W=64, T=16, stride=16, band_lo_bin=1, band_hi_bin=5)
+            p.update(b)
+            with pytest.raises(hv.HvError) as ei:
+                hv.hv_set_params(r.h, to_hv(p))
+            assert ei.value.status == hv.HV_ERR_ARG
+    finally:
+        r.close()
