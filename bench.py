@@ -266,6 +266,9 @@ def run_hv(args, w, rank, world, dist):
     launches = stats1["kernel_launches"] - stats0["kernel_launches"]
     r.close()
 
+    if args.no_e2e:
+        return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
+                    clocks=clk, e2e=None, frames_per_step=frames_per_step)
     # ----- end-to-end through host buffers (pinned frames in, images out)
     host_pool = pool_t.repeat(reps, 1, 1).contiguous().pin_memory()
     r2 = open_renderer()
@@ -390,6 +393,7 @@ def main():
     ap.add_argument("--impl", choices=["hv", "reference"], default="hv")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -446,7 +450,8 @@ def main():
             "hbm_pct_of_measured": round(100 * res["value"] / world * alg["frame_bytes"] / 1e9 / hbm, 2),
             "algorithmic_bytes_per_frame": alg["frame_bytes"],
             "roofline": roofline(w, res, peaks),
-            "e2e": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in res["e2e"].items()},
+            "e2e": ({k: (round(v, 1) if isinstance(v, float) else v) for k, v in res["e2e"].items()}
+                    if res["e2e"] else None),
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
         }

@@ -66,7 +66,8 @@ def test_conversion_bit_exact_exhaustive(bits):
         fr = np.arange(65536, dtype=np.uint16).reshape(1, 256, 256)
     p = oracle_params(spatial="none", temporal="none", T=1, stride=1, H=fr.shape[1], W=fr.shape[2])
     img, _ = gpu_render(fr, p)
-    assert np.array_equal(img.real, fr.astype(np.float64))
+    assert img.shape == (1, 1) + fr.shape[1:]
+    assert np.array_equal(img[:, 0].real, fr.astype(np.float64))
     assert np.all(img.imag == 0)
 
 
