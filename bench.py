@@ -184,7 +184,10 @@ def run_hv(args, w, rank, world, dist):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
+    # one explicit stream for the library and for every timing event
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
     pool_np = make_pool(w, w["pool"])
     B = w["batch"]
     reps = B // w["pool"]
