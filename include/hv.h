@@ -176,6 +176,37 @@ hv_status hv_synchronize(hv_handle* h);
 /* Free every resource of the handle. NULL is accepted (no-op). */
 hv_status hv_close(hv_handle* h);
 
+/* Maximum n * width * height of one hv_spatial_static call (12 frames of
+ * 256 x 256, or 3 of 512 x 512). */
+#define HV_STATIC_MAX_PIXELS 786432u
+
+/* Spatial transform of n frames that allocates nothing -- for callers that may
+ * not call cudaMalloc/cudaFree where they run (allocator or memory-pool
+ * callbacks, plugins inside a host framework that owns all device memory,
+ * real-time loops that must never enter the allocator). The paper has no
+ * counterpart; it is the same transform as HV_TEMPORAL_NONE rendering.
+ *
+ * `frames`: device pointer to n raw frames (uint8 or uint16 by pixel_bits),
+ * p->width x p->height, row-major, contiguous. `out`: device pointer to
+ * n * width * height complex values (2 floats each, re then im). Only the
+ * spatial fields of `p` are read (width, height, spatial, z_m, lambda_m,
+ * pitch_x_m, pitch_y_m, fftshift). Work is queued on `stream` (NULL = the
+ * default stream); the caller keeps ownership of both buffers.
+ *
+ * Scratch (tables and the intermediates of the 2-D FFT passes, about 14 MiB)
+ * is a file-scope __device__ array that every GPU loading the library holds
+ * until exit. The first call on a device resolves that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture. Every call shares the array and leaves its
+ * contents behind; nothing in it needs to start at zero. Calls whose GPU work
+ * may overlap race on it, so order them on one stream or with events.
+ *
+ * Errors: HV_ERR_ARG for NULL pointers, n = 0, width or height not a power of
+ * two in [16, 512], n * width * height > HV_STATIC_MAX_PIXELS, or invalid
+ * optics; HV_ERR_CUDA if a CUDA call fails. No error text is recorded. */
+hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, uint32_t n, const hv_params* p,
+                            float* out, void* stream);
+
 /* Text of the handle's last error (or of the last failed hv_open when h is
  * NULL). Valid until the next call on the handle. */
 const char* hv_last_error(const hv_handle* h);
