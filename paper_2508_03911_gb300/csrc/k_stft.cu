@@ -94,6 +94,213 @@ __global__ void __launch_bounds__(StftCfg<T>::NT) k_stft(StftArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------
+// Long windows (T >= 256): one warp per pixel.
+//
+// A CTA owns BT = 8 adjacent pixels, one warp each. Their samples sit in a
+// shared ring of RS = T + min(S, T) slots per pixel, so the S frames that the
+// next window adds are fetched with cp.async while the current window is
+// transformed (S < T: frame o of the launch in slot o mod RS; S >= T: windows
+// alternate between the two halves). The per-pixel FFT is a Stockham pass
+// sequence private to the warp (only __syncwarp between stages) through a
+// padded work buffer, index i at i + i/16, which keeps every stage's shared
+// accesses at two wavefronts. When the band lies below T/2 the last stage only
+// forms the lower half of its outputs.
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
+
+struct MomAcc {
+  uint32_t klo, khi;
+  float fscale;
+  float m0, m1, m2;
+  template <int T>
+  __device__ __forceinline__ void add(int k, float2 v) {
+    if (uint32_t(k) - klo <= khi - klo) {
+      const float P = fmaf(v.x, v.x, v.y * v.y);
+      const float f = float(k < T / 2 ? k : k - T) * fscale;
+      m0 += P;
+      m1 = fmaf(f, P, m1);
+      m2 = fmaf(f, f * P, m2);
+    }
+  }
+};
+
+// Lower half X_0 .. X_{R/2-1} of an R-point forward DFT.
+template <int R>
+__device__ __forceinline__ void dft_lower(float2* v) {
+  if constexpr (R == 2) {
+    v[0] = cadd(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = mul_i<-1>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
+  } else {
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    dft<4, -1>(e);
+    dft<4, -1>(o);
+    const float c = 0.70710678118654752440f;
+    v[0] = cadd(e[0], o[0]);
+    v[1] = cadd(e[1], make_float2(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x)));
+    v[2] = cadd(e[2], mul_i<-1>(o[2]));
+    v[3] = cadd(e[3], make_float2(c * (-o[3].x + o[3].y), c * (-o[3].y - o[3].x)));
+  }
+}
+
+template <int T, int NS>
+__device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, float2* work,
+                                         const float2* tw, int lane, MomAcc& acc, bool lower) {
+  constexpr int R = RadixOf<T / NS>::value;
+  constexpr int NB = T / R;
+  static_assert(NB >= 32, "one warp per pixel needs >= 32 butterflies per stage");
+  constexpr int IT = NB / 32;
+  float2 v[IT][R];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = lane + 32 * it;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int t = j + m * NB;
+      if constexpr (NS == 1) {
+        int sl = rbase + t;
+        if (sl >= RS) sl -= RS;
+        v[it][m] = ring[sl];
+      } else {
+        v[it][m] = work[wpad(t)];
+      }
+    }
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int m = 1; m < R; ++m) v[it][m] = cmul(v[it][m], tw[jm * m * (T / (NS * R))]);
+    }
+  }
+  if constexpr (NS * R == T) {
+    if (lower) {
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        dft_lower<R>(v[it]);
+#pragma unroll
+        for (int m = 0; m < R / 2; ++m) acc.add<T>(lane + 32 * it + m * NB, v[it][m]);
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        dft<R, -1>(v[it]);
+#pragma unroll
+        for (int m = 0; m < R; ++m) acc.add<T>(lane + 32 * it + m * NB, v[it][m]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) dft<R, -1>(v[it]);
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int j = lane + 32 * it;
+      const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int m = 0; m < R; ++m) work[wpad(base + m * NS)] = v[it][m];
+    }
+    __syncwarp();
+    warp_fft<T, NS * R>(ring, rbase, RS, work, tw, lane, acc, lower);
+  }
+}
+
+constexpr int WARP_BT = 8;
+
+template <int T>
+__host__ __device__ constexpr size_t warp_smem(uint32_t S) {
+  return (size_t(WARP_BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T +
+          size_t(WARP_BT) * (T + T / 16)) * sizeof(float2);
+}
+
+template <int T>
+__global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
+  constexpr int BT = WARP_BT, NT = 32 * BT;
+  extern __shared__ float2 smem[];
+  const int S = int(a.S);
+  const int RS = T + (S < T ? S : T);
+  const int RLD = RS + 1;
+  float2* ring = smem;
+  float2* tw = ring + BT * RLD;
+  float2* work = tw + T;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t HW = size_t(a.W) * a.H;
+  const uint32_t p0 = blockIdx.x * BT;
+  const float2* tq = static_cast<const float2*>(a.tq.base);
+  const bool lower = a.khi < uint32_t(T / 2);
+
+  auto fetch = [&](int w) {  // issue the loads of window w's new frames
+    int o0, n, s0;
+    if (w == 0) {
+      o0 = 0; n = T; s0 = 0;
+    } else if (S < T) {
+      o0 = w * S + T - S; n = S; s0 = o0 % RS;
+    } else {
+      o0 = w * S; n = T; s0 = (w & 1) * T;
+    }
+    for (int idx = tid; idx < n * BT; idx += NT) {
+      const int b = idx % BT, f = idx / BT;
+      int sl = s0 + f;
+      if (sl >= RS) sl -= RS;
+      const size_t g = (size_t(a.tq.slot0) + uint32_t(o0 + f)) % a.tq.cap;
+      cp_async8(&ring[b * RLD + sl], &tq[g * HW + p0 + b]);
+    }
+    cp_async_commit();
+  };
+
+  for (int i = tid; i < T; i += NT) tw[i] = a.tw_t[i];
+  fetch(0);
+  for (uint32_t w = 0; w < a.nwin; ++w) {
+    cp_async_wait_all();
+    __syncthreads();
+    if (w + 1 < a.nwin) fetch(int(w) + 1);
+    const int rbase = S < T ? int((size_t(w) * S) % RS) : int(w & 1) * T;
+    MomAcc acc{a.klo, a.khi, a.fscale, 0.f, 0.f, 0.f};
+    warp_fft<T, 1>(ring + warp * RLD, rbase, RS, work + warp * (T + T / 16), tw, lane, acc, lower);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
+      acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
+      acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
+    }
+    if (lane == 0) {
+      float* o = a.out + size_t(w) * a.nout * HW + p0 + warp;
+      int q = 0;
+      if (a.mask & HV_MOM_M0) o[HW * q++] = acc.m0;
+      if (a.mask & HV_MOM_M1) o[HW * q++] = acc.m1;
+      if (a.mask & HV_MOM_M2) o[HW * q++] = acc.m2;
+      const double d0 = acc.m0;
+      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(acc.m1) / d0) : 0.f;
+      if (a.mask & HV_MOM_M2N) {
+        const double r = d0 > 0.0 ? double(acc.m2) / d0 : 0.0;
+        o[HW * q++] = float(sqrt(r > 0.0 ? r : 0.0));
+      }
+    }
+  }
+}
+
+template <int T>
+static cudaError_t launch_warp(const StftArgs& a, cudaStream_t s) {
+  const size_t hw = size_t(a.W) * a.H;
+  if (hw % WARP_BT) return cudaErrorInvalidValue;
+  const size_t smem = warp_smem<T>(a.S);
+  cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem));
+  if (e != cudaSuccess) return e;
+  k_stft_warp<T><<<unsigned(hw / WARP_BT), 32 * WARP_BT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int T>
 static cudaError_t launch_t(const StftArgs& a, cudaStream_t s) {
   using C = StftCfg<T>;
@@ -115,9 +322,9 @@ cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches) {
     case 32: return launch_t<32>(a, s);
     case 64: return launch_t<64>(a, s);
     case 128: return launch_t<128>(a, s);
-    case 256: return launch_t<256>(a, s);
-    case 512: return launch_t<512>(a, s);
-    case 1024: return launch_t<1024>(a, s);
+    case 256: return launch_warp<256>(a, s);
+    case 512: return launch_warp<512>(a, s);
+    case 1024: return launch_warp<1024>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -140,6 +140,20 @@ def test_stft_windows_strides_and_moments(T, S, spatial):
     assert st["windows_rendered"] == len(O.window_starts(n, T, S))
 
 
+@pytest.mark.parametrize("T,S,band", [(256, 3, (2, 100)), (512, 700, (8, 250)), (512, 64, (1, 255)),
+                                      (1024, 1024, (10, 300)), (256, 256, (0, 127))])
+def test_long_window_kernel_paths(T, S, band):
+    """Long windows: S < T ring prefetch, S > T alternating halves, bands below
+    T/2 (pruned last stage) and up to the half-spectrum edge."""
+    H, W = 16, 32
+    n = T + 4 * S + 3
+    fr = synth.random_frames(n, H, W, 12, seed=T + S)
+    p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=band[0],
+                      band_hi_bin=band[1], moments=ALL_MOMENTS, H=H, W=W)
+    img, _ = gpu_render(fr, p)
+    check_images(img, O.render(fr, p))
+
+
 def test_streaming_packets_match_one_shot():
     """Ragged packets and renders interleaved give the windows of the whole stream."""
     H = W = 64
