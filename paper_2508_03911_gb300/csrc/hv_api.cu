@@ -52,6 +52,11 @@ struct hv_handle {
   hv_stats st{};
   std::string err;
   std::vector<double> pca_lam;
+  // PCA workspace
+  void* pca_ws = nullptr;
+  size_t pca_ws_bytes = 0;
+  PcaArgs pca{};
+  bool pca_has_lam = false;
   // stage timing
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // triples: before spatial, after spatial, after temporal
@@ -131,7 +136,17 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     d = Derived{1, 1, 0, 0, 0, 2 * hw};
     return HV_OK;
   }
-  if (p.temporal == HV_TEMPORAL_PCA) { why = "PCA temporal analysis is not built yet"; return HV_ERR_UNSUPPORTED; }
+  if (p.temporal == HV_TEMPORAL_PCA) {
+    if (!is_pow2(p.T) || p.T < 32 || p.T > 512) { why = "PCA needs T a power of two in [32, 512]"; return HV_ERR_ARG; }
+    if (p.stride < 1) { why = "stride must be >= 1"; return HV_ERR_ARG; }
+    if (p.pca_lo < 1 || p.pca_hi < p.pca_lo || p.pca_hi > p.T) {
+      why = "PCA sub-basis must satisfy 1 <= pca_lo <= pca_hi <= T";
+      return HV_ERR_ARG;
+    }
+    if (p.precision != HV_PREC_FP32) { why = "this PCA covariance precision is not built"; return HV_ERR_UNSUPPORTED; }
+    d = Derived{p.T, p.stride, 0, 0, 1, hw};
+    return HV_OK;
+  }
   if (p.temporal != HV_TEMPORAL_STFT) { why = "unknown temporal transform"; return HV_ERR_ARG; }
   if (!is_pow2(p.T) || p.T < 8 || p.T > 1024) { why = "T must be a power of two in [8, 1024]"; return HV_ERR_ARG; }
   if (p.stride < 1) { why = "stride must be >= 1"; return HV_ERR_ARG; }
@@ -251,6 +266,53 @@ hv_status apply_pending(hv_handle* h) {
   }
   s = build_tables(h, p);
   if (s != HV_OK) return s;
+  if (p.temporal == HV_TEMPORAL_PCA) {
+    const size_t hw = size_t(W) * H;
+    uint32_t nchunks = uint32_t(std::min<size_t>(64, std::max<size_t>(1, hw / 1024)));
+    uint32_t chunk = uint32_t((hw + nchunks - 1) / nchunks);
+    chunk = (chunk + 31) / 32 * 32;
+    nchunks = uint32_t((hw + chunk - 1) / chunk);
+    const uint32_t T = d.T, M = p.pca_hi - p.pca_lo + 1, Mpad = (M + 63) / 64 * 64;
+    const size_t b_part = pca_partials_floats2(T, nchunks) * sizeof(float2);
+    const size_t b_mat = size_t(T) * T * sizeof(double2);
+    const size_t b_rot = size_t(T / 2) * 4 * sizeof(double);
+    const size_t b_cnt = 64;
+    const size_t b_lam = size_t(T) * sizeof(double);
+    const size_t b_vs = size_t(T) * Mpad * sizeof(float2);
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t total = al(b_part) + 2 * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs);
+    s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
+    if (s != HV_OK) return s;
+    char* b = static_cast<char*>(h->pca_ws);
+    PcaArgs& a = h->pca;
+    a = PcaArgs{};
+    a.W = W;
+    a.H = H;
+    a.T = T;
+    a.chunk = chunk;
+    a.nchunks = nchunks;
+    a.lo = p.pca_lo;
+    a.M = M;
+    a.Mpad = Mpad;
+    a.max_sweeps = 30;
+    a.tol = 1e-14;
+    a.tol_abs = 1e-16;
+    a.partials = reinterpret_cast<float2*>(b);
+    b += al(b_part);
+    a.C = reinterpret_cast<double2*>(b);
+    b += al(b_mat);
+    a.V = reinterpret_cast<double2*>(b);
+    b += al(b_mat);
+    a.rot = reinterpret_cast<double*>(b);
+    b += al(b_rot);
+    a.counters = reinterpret_cast<unsigned*>(b);
+    a.cmax = reinterpret_cast<double*>(a.counters + 4);
+    b += al(b_cnt);
+    a.lam = reinterpret_cast<double*>(b);
+    b += al(b_lam);
+    a.Vs = reinterpret_cast<float2*>(b);
+    h->pca_has_lam = false;
+  }
   h->cur = p;
   h->has_params = true;
   h->pending = false;
@@ -491,6 +553,13 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
   const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
   if (none) {
     e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
+  } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
+    e = cudaSuccess;
+    for (uint32_t w = 0; w < nw && e == cudaSuccess; ++w) {
+      h->pca.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
+      e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches);
+    }
+    h->pca_has_lam = true;
   } else {
     StftArgs sa{};
     sa.W = h->W;
@@ -530,9 +599,12 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
 
 hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n) {
   if (!h || !out) return HV_ERR_ARG;
-  if (h->pca_lam.empty()) return HV_ERR_STATE;
-  if (n > h->pca_lam.size()) return HV_ERR_ARG;
-  std::memcpy(out, h->pca_lam.data(), n * sizeof(double));
+  if (!h->pca_has_lam || h->cur.temporal != HV_TEMPORAL_PCA) return HV_ERR_STATE;
+  if (n > h->T) return HV_ERR_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HV_ERR_CUDA;
+  if (cudaMemcpyAsync(out, h->pca.lam, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return HV_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HV_ERR_CUDA;
   return HV_OK;
 }
 
@@ -592,6 +664,7 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->tw);
   dfree(h->asp_ht);
   dfree(h->staging);
+  if (h->pca_ws) cudaFree(h->pca_ws);
   if (h->raw) cudaFree(h->raw);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

@@ -48,6 +48,27 @@ struct StftArgs {
 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
+// PCA of one window (Sec. III-B.1), time-queue ring -> energy image.
+struct PcaArgs {
+  uint32_t W, H, T;
+  RingRef tq;           // slot0 = slot of the window's first frame
+  uint32_t chunk;       // pixels per covariance CTA
+  uint32_t nchunks;
+  uint32_t lo, M, Mpad; // sub-basis: ranks lo .. lo+M-1 (1-based), padded to 64
+  int max_sweeps;
+  double tol, tol_abs;  // Jacobi skip thresholds (relative, and x largest diagonal)
+  float2* partials;     // nchunks x upper tiles x TS x TS
+  double2* C;           // T x T
+  double2* V;           // T x T
+  double* rot;          // T/2 rotations (4 doubles each)
+  unsigned* counters;   // 4 counters followed by one double (largest diagonal)
+  double* cmax;         // = (double*)(counters + 4)
+  double* lam;          // T eigenvalues, descending
+  float2* Vs;           // T x Mpad sub-basis
+};
+size_t pca_partials_floats2(uint32_t T, uint32_t nchunks);
+cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches);
+
 // Copy propagated frames out as interleaved complex images.
 cudaError_t launch_copy_frames(const RingRef& tq, uint32_t n, uint32_t hw, float* out,
                                cudaStream_t s, int* launches);

@@ -1,0 +1,350 @@
+// k_pca.cu -- PCA temporal analysis of one window (Sec. III-B.1: a covariance
+// matrix of the window, its eigendecomposition, projection onto a sub-basis).
+//
+// With X the P x T matrix whose column t is propagated frame t (P = W H):
+//   C = X^H X                      (T x T Hermitian, unnormalised)
+//   C = V diag(lam) V^H            (cyclic complex Jacobi, float64)
+//   E(p) = sum_{j = lo..hi} |(X v_j)_p|^2, eigenvectors ranked by descending lam.
+//
+// Kernels (one window at a time, all on the handle's stream):
+//   k_cov_fp32     split-K covariance: each CTA multiplies a 64 x 64 tile of the
+//                  upper triangle over one pixel chunk (float32 FMA), partials
+//                  written per chunk (deterministic, no atomics)
+//   k_cov_reduce   sums the chunk partials in float64 -> C (full Hermitian), V = I
+//   k_jacobi       cooperative launch over all SMs: parallel cyclic (round-robin)
+//                  two-sided Jacobi in float64 until a sweep makes no rotation
+//   k_pca_select   ranks eigenvalues (descending) and gathers the sub-basis
+//   k_project      Y = X V_s for 64-pixel tiles and E(p) = sum_j |Y_pj|^2
+#include <cooperative_groups.h>
+
+#include "fft_dev.cuh"
+#include "hv_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace hv {
+
+// ----------------------------------------------------------------- covariance
+
+constexpr int COV_TS = 64;   // output tile (frames x frames)
+constexpr int COV_KS = 32;   // pixels per smem stage
+
+__device__ __forceinline__ const float2* frame_ptr(const RingRef& r, uint32_t t, size_t hw) {
+  return static_cast<const float2*>(r.base) + ((size_t(r.slot0) + t) % r.cap) * hw;
+}
+
+// grid (n_upper_tiles, n_chunks), 256 threads; thread (ty, tx) owns rows
+// a0 + ty + 16 i and columns b0 + tx + 16 j of the TS x TS tile (TS = min(T, 64)).
+__global__ void __launch_bounds__(256) k_cov_fp32(PcaArgs a) {
+  __shared__ float2 As[COV_KS][COV_TS + 1];
+  __shared__ float2 Bs[COV_KS][COV_TS + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int TS = a.T < COV_TS ? int(a.T) : COV_TS;
+  const int nI = TS / 16;
+  const int nT = a.T / TS;
+  int u = blockIdx.x, ta = 0;
+  while (u >= nT - ta) {
+    u -= nT - ta;
+    ++ta;
+  }
+  const int tb = ta + u;
+  const size_t hw = size_t(a.W) * a.H;
+  const size_t p_begin = size_t(blockIdx.y) * a.chunk;
+  const size_t p_end = p_begin + a.chunk < hw ? p_begin + a.chunk : hw;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (size_t p0 = p_begin; p0 < p_end; p0 += COV_KS) {
+    for (int e = tid; e < TS * COV_KS; e += 256) {
+      const int k = e % COV_KS, f = e / COV_KS;
+      const size_t p = p0 + k;
+      float2 va = make_float2(0.f, 0.f), vb = va;
+      if (p < p_end) {
+        va = frame_ptr(a.tq, ta * TS + f, hw)[p];
+        vb = frame_ptr(a.tq, tb * TS + f, hw)[p];
+      }
+      As[k][f] = va;
+      Bs[k][f] = vb;
+    }
+    __syncthreads();
+    if (ty < TS && tx < TS) {
+#pragma unroll 4
+      for (int k = 0; k < COV_KS; ++k) {
+        float2 x[4], y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = i < nI ? As[k][ty + 16 * i] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = j < nI ? Bs[k][tx + 16 * j] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // conj(x) * y
+            acc[i][j].x = fmaf(x[i].x, y[j].x, fmaf(x[i].y, y[j].y, acc[i][j].x));
+            acc[i][j].y = fmaf(x[i].x, y[j].y, fmaf(-x[i].y, y[j].x, acc[i][j].y));
+          }
+      }
+    }
+    __syncthreads();
+  }
+  const int ntile_up = nT * (nT + 1) / 2;
+  float2* out = a.partials + (size_t(blockIdx.y) * ntile_up + blockIdx.x) * TS * TS;
+  for (int i = 0; i < nI; ++i)
+    for (int j = 0; j < nI; ++j) out[(ty + 16 * i) * TS + tx + 16 * j] = acc[i][j];
+}
+
+// C[a][b] = sum over chunks (float64), mirrored to the lower triangle; V = I.
+__global__ void k_cov_reduce(PcaArgs a) {
+  const int T = a.T, TS = T < COV_TS ? T : COV_TS, nT = T / TS, ntile_up = nT * (nT + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T * T; e += gridDim.x * blockDim.x) {
+    const int r = e / T, c = e % T;
+    a.V[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    if (r > c) continue;
+    const int ta = r / TS, tb = c / TS;
+    const int up = ta * nT - ta * (ta - 1) / 2 + (tb - ta);
+    const int off = (r % TS) * TS + (c % TS);
+    double sx = 0.0, sy = 0.0;
+    for (uint32_t k = 0; k < a.nchunks; ++k) {
+      const float2 v = a.partials[(size_t(k) * ntile_up + up) * TS * TS + off];
+      sx += v.x;
+      sy += v.y;
+    }
+    if (r == c) {
+      sy = 0.0;
+      // non-negative doubles order like their bit patterns
+      atomicMax(reinterpret_cast<unsigned long long*>(a.cmax),
+                static_cast<unsigned long long>(__double_as_longlong(sx > 0.0 ? sx : 0.0)));
+    }
+    a.C[r * T + c] = make_double2(sx, sy);
+    a.C[c * T + r] = make_double2(sx, -sy);
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi
+
+// Round robin (circle method): position 0 holds index 0, position k >= 1 holds
+// ((k - 1 + r) mod (T - 1)) + 1; pair p of round r is (pos p, pos T-1-p).
+__device__ __forceinline__ int rr_elem(int k, int r, int T) {
+  return k == 0 ? 0 : ((k - 1 + r) % (T - 1)) + 1;
+}
+
+struct Rot {  // J = [[c, -s], [conj(ph) s, conj(ph) c]]
+  double c, s, px, py;
+};
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int T = a.T, NP = T / 2;
+  const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t gsz = size_t(gridDim.x) * blockDim.x;
+  Rot* rot = reinterpret_cast<Rot*>(a.rot);
+  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    if (gtid == 0) a.counters[sweep & 1] = 0;  // reset the other parity's counter
+    for (int r = 0; r < T - 1; ++r) {
+      // phase 1: rotation of each pair from the current C
+      for (size_t p = gtid; p < size_t(NP); p += gsz) {
+        const int i = rr_elem(int(p), r, T), j = rr_elem(T - 1 - int(p), r, T);
+        const double al = a.C[i * T + i].x, be = a.C[j * T + j].x;
+        const double2 g = a.C[i * T + j];
+        const double ag = sqrt(g.x * g.x + g.y * g.y);
+        Rot q{1.0, 0.0, 1.0, 0.0};
+        const double floor_abs = a.tol_abs * (*a.cmax);
+        if (ag > a.tol * sqrt(fabs(al * be)) && ag > floor_abs && ag > 0.0) {
+          const double zeta = (be - al) / (2.0 * ag);
+          const double t = -(zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          q = Rot{c, t * c, g.x / ag, g.y / ag};
+          atomicAdd(&a.counters[(sweep & 1) ^ 1], 1u);
+        }
+        rot[p] = q;
+      }
+      grid.sync();
+      // phase 2: C <- J^H C J on 2 x 2 blocks (pairs p, q), V <- V J
+      const size_t nblk = size_t(NP) * NP;
+      for (size_t e = gtid; e < nblk + size_t(T) * NP; e += gsz) {
+        if (e < nblk) {
+          const int p = int(e / NP), q = int(e % NP);
+          const Rot& Jp = rot[p];
+          const Rot& Jq = rot[q];
+          if (Jp.s == 0.0 && Jq.s == 0.0) continue;
+          const int i0 = rr_elem(p, r, T), i1 = rr_elem(T - 1 - p, r, T);
+          const int j0 = rr_elem(q, r, T), j1 = rr_elem(T - 1 - q, r, T);
+          const double2 b00 = a.C[i0 * T + j0], b01 = a.C[i0 * T + j1];
+          const double2 b10 = a.C[i1 * T + j0], b11 = a.C[i1 * T + j1];
+          // M = B Jq
+          const double2 qph = make_double2(Jq.px, -Jq.py);  // conj(ph_q)
+          const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
+          const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
+          const double2 m00 = zadd(make_double2(b00.x * Jq.c, b00.y * Jq.c), zmul(b01, q10));
+          const double2 m01 = zadd(make_double2(-b00.x * Jq.s, -b00.y * Jq.s), zmul(b01, q11));
+          const double2 m10 = zadd(make_double2(b10.x * Jq.c, b10.y * Jq.c), zmul(b11, q10));
+          const double2 m11 = zadd(make_double2(-b10.x * Jq.s, -b10.y * Jq.s), zmul(b11, q11));
+          // Jp^H = [[c, ph s], [-s, ph c]]
+          const double2 ph = make_double2(Jp.px, Jp.py);
+          const double2 p01 = make_double2(ph.x * Jp.s, ph.y * Jp.s);
+          const double2 p11 = make_double2(ph.x * Jp.c, ph.y * Jp.c);
+          double2 c00 = zadd(make_double2(Jp.c * m00.x, Jp.c * m00.y), zmul(p01, m10));
+          double2 c01 = zadd(make_double2(Jp.c * m01.x, Jp.c * m01.y), zmul(p01, m11));
+          double2 c10 = zadd(make_double2(-Jp.s * m00.x, -Jp.s * m00.y), zmul(p11, m10));
+          double2 c11 = zadd(make_double2(-Jp.s * m01.x, -Jp.s * m01.y), zmul(p11, m11));
+          if (p == q) {  // the pair's own block: exactly diagonal, real diagonal
+            c01 = make_double2(0.0, 0.0);
+            c10 = make_double2(0.0, 0.0);
+            c00.y = 0.0;
+            c11.y = 0.0;
+          }
+          a.C[i0 * T + j0] = c00;
+          a.C[i0 * T + j1] = c01;
+          a.C[i1 * T + j0] = c10;
+          a.C[i1 * T + j1] = c11;
+        } else {
+          const size_t f = e - nblk;
+          const int row = int(f / NP), q = int(f % NP);
+          const Rot& Jq = rot[q];
+          if (Jq.s == 0.0) continue;
+          const int j0 = rr_elem(q, r, T), j1 = rr_elem(T - 1 - q, r, T);
+          const double2 v0 = a.V[row * T + j0], v1 = a.V[row * T + j1];
+          const double2 qph = make_double2(Jq.px, -Jq.py);
+          const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
+          const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
+          a.V[row * T + j0] = zadd(make_double2(v0.x * Jq.c, v0.y * Jq.c), zmul(v1, q10));
+          a.V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
+        }
+      }
+      grid.sync();
+    }
+    // a sweep without any rotation: converged (every block reads the same count)
+    const unsigned n = *reinterpret_cast<volatile unsigned*>(&a.counters[(sweep & 1) ^ 1]);
+    grid.sync();
+    if (n == 0) break;
+  }
+  if (gtid == 0) a.counters[2] = 1;
+}
+
+// Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
+// sub-basis columns lo..hi of V as float32.
+__global__ void k_pca_select(PcaArgs a) {
+  const int T = a.T;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    const double li = a.C[i * T + i].x;
+    int rank = 0;
+    for (int j = 0; j < T; ++j) {
+      const double lj = a.C[j * T + j].x;
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    a.lam[rank] = li;
+    const int m = rank - int(a.lo - 1);
+    if (m >= 0 && m < int(a.M))
+      for (int t = 0; t < T; ++t) {
+        const double2 v = a.V[t * T + i];
+        a.Vs[size_t(t) * a.Mpad + m] = make_float2(float(v.x), float(v.y));
+      }
+  }
+  for (int e = threadIdx.x; e < T * int(a.Mpad); e += blockDim.x)
+    if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
+}
+
+// ---------------------------------------------------------------- projection
+
+constexpr int PRJ_PB = 64;  // pixels per CTA
+constexpr int PRJ_MB = 64;  // sub-basis columns per pass
+constexpr int PRJ_KS = 32;  // frames per smem stage
+
+__global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
+  __shared__ float2 Xs[PRJ_KS][PRJ_PB + 1];
+  __shared__ float2 Vss[PRJ_KS][PRJ_MB + 1];
+  __shared__ float Er[16][PRJ_PB];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // tx: pixel group, ty: column group
+  const size_t hw = size_t(a.W) * a.H;
+  const size_t pb = size_t(blockIdx.x) * PRJ_PB;
+  float e_acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (uint32_t m0 = 0; m0 < a.Mpad; m0 += PRJ_MB) {
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int t0 = 0; t0 < a.T; t0 += PRJ_KS) {
+      for (int e = tid; e < PRJ_KS * PRJ_PB; e += 256) {
+        const int k = e / PRJ_PB, px = e % PRJ_PB;
+        Xs[k][px] = frame_ptr(a.tq, t0 + k, hw)[pb + px];
+      }
+      for (int e = tid; e < PRJ_KS * PRJ_MB; e += 256) {
+        const int k = e / PRJ_MB, m = e % PRJ_MB;
+        Vss[k][m] = a.Vs[size_t(t0 + k) * a.Mpad + m0 + m];
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < PRJ_KS; ++k) {
+        float2 x[4], v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = Xs[k][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = Vss[k][ty * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j].x = fmaf(x[i].x, v[j].x, fmaf(-x[i].y, v[j].y, acc[i][j].x));
+            acc[i][j].y = fmaf(x[i].x, v[j].y, fmaf(x[i].y, v[j].x, acc[i][j].y));
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) e_acc[i] = fmaf(acc[i][j].x, acc[i][j].x, fmaf(acc[i][j].y, acc[i][j].y, e_acc[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Er[ty][tx + 16 * i] = e_acc[i];
+  __syncthreads();
+  if (tid < PRJ_PB) {
+    float s = 0.f;
+    for (int g = 0; g < 16; ++g) s += Er[g][tid];
+    out[pb + tid] = s;
+  }
+}
+
+size_t pca_partials_floats2(uint32_t T, uint32_t nchunks) {
+  const uint32_t TS = T < uint32_t(COV_TS) ? T : COV_TS, nT = T / TS;
+  return size_t(nchunks) * (nT * (nT + 1) / 2) * TS * TS;
+}
+
+cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches) {
+  const size_t hw = size_t(a.W) * a.H;
+  const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
+  if (a.T % TS || TS % 16 || hw % PRJ_PB || a.T % PRJ_KS) return cudaErrorInvalidValue;
+  const int nT = a.T / TS;
+  const dim3 g1(nT * (nT + 1) / 2, a.nchunks);
+  cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
+  if (e0 != cudaSuccess) return e0;
+  k_cov_fp32<<<g1, 256, 0, s>>>(a);
+  k_cov_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+  *launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), args, 0, s);
+  if (e != cudaSuccess) return e;
+  k_pca_select<<<1, 256, 0, s>>>(a);
+  k_project<<<unsigned(hw / PRJ_PB), 256, 0, s>>>(a, out);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace hv
