@@ -51,6 +51,13 @@ WORKLOADS = {
              "4..28, 102,400-frame stream per step",
         N=256, bits=8, spatial="asp", z=0.30, T=64, S=64, fs=20000.0, band=(4, 28),
         moments=("M0",), batch=4096, batches=25, pool=1024, scene="scene_tiny_asp_stft"),
+    "pca_512_t256": dict(
+        desc="512x512 uint16 (12-bit) frames, ASP z=0.40 m, PCA over windows of T=256 (stride 256): "
+             "FP32 covariance, FP64 Jacobi, energy of the projection on eigenvectors 2..64; "
+             "1,024 frames (4 windows) per step",
+        N=512, bits=12, spatial="asp", z=0.40, T=256, S=256, fs=20000.0, band=(0, 0),
+        moments=(), temporal="pca", pca=(2, 64), batch=1024, batches=1, pool=256,
+        scene="scene_pca"),
 }
 DEFAULT = "stream_fresnel_256_t512_s64"
 METRIC = "raw frames/s rendered"
@@ -76,9 +83,11 @@ def band_bins(w):
 
 def oracle_params(w):
     klo, khi = band_bins(w)
+    lo, hi = w.get("pca", (2, 64))
     return dict(spatial=w["spatial"], z_m=w["z"], lambda_m=852e-9, pitch_x_m=20e-6,
-                pitch_y_m=20e-6, fftshift=1, temporal="stft", T=w["T"], stride=w["S"],
-                fs_hz=w["fs"], band_lo_bin=klo, band_hi_bin=khi, moments=w["moments"])
+                pitch_y_m=20e-6, fftshift=1, temporal=w.get("temporal", "stft"), T=w["T"],
+                stride=w["S"], fs_hz=w["fs"], band_lo_bin=klo, band_hi_bin=khi,
+                moments=w["moments"], pca_lo=lo, pca_hi=hi)
 
 
 def make_pool(w, n):
@@ -91,7 +100,7 @@ def algorithmic(w):
     """Algorithmic bytes and flops per raw frame (method dataflow, see the design notes)."""
     hw = w["N"] * w["N"]
     bpp = 1 if w["bits"] <= 8 else 2
-    nmom = len(w["moments"])
+    nmom = max(1, len(w["moments"]))
     T, S = w["T"], w["S"]
     frame_bytes = hw * (bpp + 16 + 4.0 * nmom / S)
     fft2 = 5.0 * hw * math.log2(hw)
@@ -198,8 +207,12 @@ def run_hv(args, w, rank, world, dist):
 
     def open_renderer():
         r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream)
-        r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"], fs=w["fs"],
-                     band=(klo, khi), moments=w["moments"])
+        if w.get("temporal") == "pca":
+            r.set_params(N, N, spatial=w["spatial"], z=w["z"], temporal="pca", T=w["T"],
+                         stride=w["S"], pca=w["pca"])
+        else:
+            r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"],
+                         fs=w["fs"], band=(klo, khi), moments=w["moments"])
         return r
 
     r = open_renderer()
