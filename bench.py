@@ -324,8 +324,45 @@ def run_hv(args, w, rank, world, dist):
                 frames_per_step=frames_per_step)
 
 
+def roofline_pca(w, res, peaks):
+    """PCA: dominant sub-stage from the live event timing (covariance, Jacobi, projection)."""
+    prof = res["prof"]
+    nwin = max(1, prof["windows"])
+    P, T = w["N"] ** 2, w["T"]
+    M = w["pca"][1] - w["pca"][0] + 1
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    st = {"spatial": prof["spatial_ms"] / nwin, "covariance": prof["pca_cov_ms"] / nwin,
+          "jacobi_fp64": prof["pca_eig_ms"] / nwin, "projection": prof["pca_proj_ms"] / nwin}
+    kern = max(st, key=st.get)
+    t = st[kern] / 1e3
+    if kern == "covariance":
+        flops, byts = 8.0 * P * T * T, 8.0 * P * T
+    elif kern == "projection":
+        flops, byts = 8.0 * P * T * M, 8.0 * P * T
+    elif kern == "jacobi_fp64":
+        sweeps = prof["pca_sweeps"] / nwin
+        flops, byts = sweeps * (T - 1) * (T // 2) ** 2 * 96.0 + sweeps * (T - 1) * T * (T // 2) * 32.0, 0.0
+        fp64_peak = 1.25
+        return {"bound": "alu", "achieved": round(flops / t / 1e12, 4), "peak": fp64_peak,
+                "unit": "TFLOP/s (FP64)", "frac": round(flops / t / 1e12 / fp64_peak, 4),
+                "traffic": None, "kernel": "k_jacobi (FP64 cyclic Jacobi)",
+                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)",
+                "sweeps_per_window": round(sweeps, 2),
+                "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
+    else:
+        flops, byts = 0.0, P * (2 + 8.0)
+    return {"bound": "alu", "achieved": round(flops / t / 1e12, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(flops / t / 1e12 / FP32_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": kern, "hbm_achieved_gbs": round(byts / t / 1e9, 1),
+            "hbm_frac_of_measured": round(byts / t / 1e9 / hbm, 4),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+            "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
+
+
 def roofline(w, res, peaks):
     """Roofline entry of the dominant stage, from the live per-stage event timing."""
+    if w.get("temporal") == "pca":
+        return roofline_pca(w, res, peaks)
     prof = res["prof"]
     alg = algorithmic(w)
     renders = max(1, prof["renders"])

@@ -162,6 +162,10 @@ typedef struct {
   uint64_t renders;           /* hv_render calls recorded                          */
   uint64_t frames;            /* frames propagated while recording                 */
   uint64_t windows;           /* windows rendered while recording                  */
+  double pca_cov_ms;          /* PCA: covariance (partials and reduction)           */
+  double pca_eig_ms;          /* PCA: Jacobi eigendecomposition and selection       */
+  double pca_proj_ms;         /* PCA: projection and energy                         */
+  uint64_t pca_sweeps;        /* PCA: Jacobi sweeps summed over recorded windows    */
 } hv_profile;
 
 /* Start (on = 1, counters reset) or stop (on = 0) recording stage times. */

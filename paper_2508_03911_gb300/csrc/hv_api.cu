@@ -62,6 +62,8 @@ struct hv_handle {
   std::vector<cudaEvent_t> prof_ev;  // triples: before spatial, after spatial, after temporal
   size_t prof_used = 0;
   hv_profile prof_acc{};
+  std::vector<cudaEvent_t> pca_ev;   // groups of 4 per recorded PCA window
+  size_t pca_ev_used = 0;
 };
 
 namespace {
@@ -295,8 +297,11 @@ hv_status apply_pending(hv_handle* h) {
     a.M = M;
     a.Mpad = Mpad;
     a.max_sweeps = 30;
+    // skip a rotation when |C_ab| <= 1e-14 sqrt(C_aa C_bb) or <= 1e-13 max_i C_ii: the
+    // second bound sits above the rounding noise that rotations leave in small
+    // entries (~1e-16 max C_ii), so sweeps stop once only noise is left
     a.tol = 1e-14;
-    a.tol_abs = 1e-16;
+    a.tol_abs = 1e-13;
     a.partials = reinterpret_cast<float2*>(b);
     b += al(b_part);
     a.C = reinterpret_cast<double2*>(b);
@@ -334,16 +339,29 @@ hv_status apply_pending(hv_handle* h) {
 
 // Fold the completed event triples into the accumulator.
 hv_status prof_flush(hv_handle* h) {
-  if (h->prof_used == 0) return HV_OK;
+  if (h->prof_used == 0 && h->pca_ev_used == 0) return HV_OK;
   HV_CU(h, cudaStreamSynchronize(h->stream));
-  for (size_t i = 0; i < h->prof_used; i += 3) {
+  for (size_t i = 0; i < h->pca_ev_used; i += 4) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    HV_CU(h, cudaEventElapsedTime(&a, h->pca_ev[i], h->pca_ev[i + 1]));
+    HV_CU(h, cudaEventElapsedTime(&b, h->pca_ev[i + 1], h->pca_ev[i + 2]));
+    HV_CU(h, cudaEventElapsedTime(&c, h->pca_ev[i + 2], h->pca_ev[i + 3]));
+    h->prof_acc.pca_cov_ms += a;
+    h->prof_acc.pca_eig_ms += b;
+    h->prof_acc.pca_proj_ms += c;
+  }
+  h->pca_ev_used = 0;
+  for (size_t i = 0; i + 2 < h->prof_used; i += 3) {
     float a = 0.f, b = 0.f;
     HV_CU(h, cudaEventElapsedTime(&a, h->prof_ev[i], h->prof_ev[i + 1]));
     HV_CU(h, cudaEventElapsedTime(&b, h->prof_ev[i + 1], h->prof_ev[i + 2]));
     h->prof_acc.spatial_ms += a;
     h->prof_acc.temporal_ms += b;
   }
-  h->prof_used = 0;
+  // an incomplete triple (flush called inside a render) stays for the next flush
+  const size_t keep = h->prof_used % 3;
+  for (size_t k = 0; k < keep; ++k) std::swap(h->prof_ev[k], h->prof_ev[h->prof_used - keep + k]);
+  h->prof_used = keep;
   return HV_OK;
 }
 
@@ -557,7 +575,22 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
     e = cudaSuccess;
     for (uint32_t w = 0; w < nw && e == cudaSuccess; ++w) {
       h->pca.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
-      e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches);
+      cudaEvent_t* ev = nullptr;
+      if (h->prof) {
+        if (h->pca_ev_used + 4 > h->pca_ev.size()) {
+          s = prof_flush(h);
+          if (s != HV_OK) return s;
+        }
+        ev = &h->pca_ev[h->pca_ev_used];
+        h->pca_ev_used += 4;
+      }
+      e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
+      if (h->prof && e == cudaSuccess) {
+        unsigned sw = 0;  // sweeps of this window (synchronous read; profiling only)
+        HV_CU(h, cudaMemcpyAsync(&sw, h->pca.counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        HV_CU(h, cudaStreamSynchronize(h->stream));
+        h->prof_acc.pca_sweeps += sw;
+      }
     }
     h->pca_has_lam = true;
   } else {
@@ -620,10 +653,13 @@ hv_status hv_profile_enable(hv_handle* h, int on) {
   if (on && h->prof_ev.empty()) {
     h->prof_ev.resize(3 * 256, nullptr);
     for (auto& e : h->prof_ev) HV_CU(h, cudaEventCreate(&e));
+    h->pca_ev.resize(4 * 64, nullptr);
+    for (auto& e : h->pca_ev) HV_CU(h, cudaEventCreate(&e));
   }
   if (on) {
     HV_CU(h, cudaStreamSynchronize(h->stream));
     h->prof_used = 0;
+    h->pca_ev_used = 0;
     h->prof_acc = hv_profile{};
   }
   h->prof = on != 0;
@@ -657,6 +693,8 @@ hv_status hv_close(hv_handle* h) {
   if (h->ev_pushed) cudaEventDestroy(h->ev_pushed);
   if (h->ev_consumed) cudaEventDestroy(h->ev_consumed);
   for (auto& e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->pca_ev)
     if (e) cudaEventDestroy(e);
   dfree(h->tq);
   dfree(h->s1);

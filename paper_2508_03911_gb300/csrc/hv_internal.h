@@ -67,7 +67,8 @@ struct PcaArgs {
   float2* Vs;           // T x Mpad sub-basis
 };
 size_t pca_partials_floats2(uint32_t T, uint32_t nchunks);
-cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches);
+// ev (optional, 4 events): before covariance, after covariance, after eigensolver, after projection
+cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev);
 
 // Copy propagated frames out as interleaved complex images.
 cudaError_t launch_copy_frames(const RingRef& tq, uint32_t n, uint32_t hw, float* out,

@@ -224,9 +224,9 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
     // a sweep without any rotation: converged (every block reads the same count)
     const unsigned n = *reinterpret_cast<volatile unsigned*>(&a.counters[(sweep & 1) ^ 1]);
     grid.sync();
+    if (gtid == 0) a.counters[2] = unsigned(sweep + 1);  // sweeps performed
     if (n == 0) break;
   }
-  if (gtid == 0) a.counters[2] = 1;
 }
 
 // Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
@@ -319,7 +319,7 @@ size_t pca_partials_floats2(uint32_t T, uint32_t nchunks) {
   return size_t(nchunks) * (nT * (nT + 1) / 2) * TS * TS;
 }
 
-cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches) {
+cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev) {
   const size_t hw = size_t(a.W) * a.H;
   const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
   if (a.T % TS || TS % 16 || hw % PRJ_PB || a.T % PRJ_KS) return cudaErrorInvalidValue;
@@ -327,8 +327,10 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches) {
   const dim3 g1(nT * (nT + 1) / 2, a.nchunks);
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
   if (e0 != cudaSuccess) return e0;
+  if (ev) cudaEventRecord(ev[0], s);
   k_cov_fp32<<<g1, 256, 0, s>>>(a);
   k_cov_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+  if (ev) cudaEventRecord(ev[1], s);
   *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -342,7 +344,9 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches) {
   e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), args, 0, s);
   if (e != cudaSuccess) return e;
   k_pca_select<<<1, 256, 0, s>>>(a);
+  if (ev) cudaEventRecord(ev[2], s);
   k_project<<<unsigned(hw / PRJ_PB), 256, 0, s>>>(a, out);
+  if (ev) cudaEventRecord(ev[3], s);
   *launches += 3;
   return cudaGetLastError();
 }
