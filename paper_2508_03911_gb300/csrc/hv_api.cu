@@ -393,6 +393,7 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.asp_ht = h->asp_ht;
     sa.chirp_x = h->chirp;
     sa.chirp_y = h->chirp + h->W;
+    sa.use_cluster = h->cur.tuned;
     int launches = 0;
     cudaError_t e = launch_spatial(sa, h->stream, &launches);
     h->st.kernel_launches += launches;

@@ -23,12 +23,13 @@ def _cuda():
     hv.lib()  # fails loudly when the extension is missing
 
 
-def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=None):
-    """Push `frames` (in packets) and render all complete windows through the C ABI."""
+def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=None, tq=0):
+    """Push `frames` (in packets) and render all complete windows through the C ABI
+    (rendering repeatedly after each packet until no window is left)."""
     import torch
     n, H, W = frames.shape
     bits = 8 if frames.dtype == np.uint8 else 16
-    r = hv.Renderer(W, H, bits, queue or max(n, 1))
+    r = hv.Renderer(W, H, bits, queue or max(n, 1), time_queue_frames=tq)
     try:
         hv.hv_set_params(r.h, to_hv(p, **(extra or {})))
         wf = r.window_floats()
@@ -43,8 +44,11 @@ def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=Non
         for k in packets:
             assert r.push(dev[done:done + k]) == hv.HV_OK
             done += k
-            view = out[got * wf:]
-            got += r.render(view)
+            while True:
+                k_win = r.render(out[got * wf:])
+                got += k_win
+                if k_win == 0:
+                    break
         torch.cuda.synchronize()
         host = out.cpu().numpy() if out_kind == "device" else out
         return images_from(host, got, p), r.stats()
@@ -89,6 +93,32 @@ def test_spatial_field_parity(H, W, spatial):
     for i in range(n):
         assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
     assert st["frames_propagated"] == n
+
+
+@pytest.mark.parametrize("N", [128, 256, 512])
+@pytest.mark.parametrize("spatial", ["asp", "fresnel"])
+@pytest.mark.parametrize("bits", [8, 12])
+def test_cluster_spatial_field_parity(N, spatial, bits):
+    """Tuned form: the whole-frame cluster kernel (frame in distributed shared memory)."""
+    n = 5 if N < 512 else 2
+    fr = synth.random_frames(n, N, N, bits, seed=7 * N + bits)
+    p = oracle_params(spatial=spatial, z_m=0.3, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
+                      H=N, W=N)
+    img, st = gpu_render(fr, p, extra=dict(tuned=1), queue=3, packets=[1, 2, 2][:n] if n == 5 else None)
+    ref = oracle_fields(fr, p)
+    for i in range(n):
+        assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
+
+
+def test_cluster_many_frames_ring_wrap():
+    """More frames than resident clusters, input and time-queue rings wrapping."""
+    N, n = 256, 300
+    fr = synth.random_frames(n, N, N, 12, seed=99)
+    p = oracle_params(spatial="fresnel", T=64, stride=16, fs_hz=71400.0, band_lo_bin=2,
+                      band_hi_bin=30, moments=ALL_MOMENTS, H=N, W=N)
+    img, st = gpu_render(fr, p, extra=dict(tuned=1), packets=[100, 100, 100], queue=200, tq=100)
+    assert st["windows_rendered"] == len(O.window_starts(n, 64, 16))
+    check_images(img, O.render(fr, p))
 
 
 def test_fresnel_without_fftshift_and_negative_z():
