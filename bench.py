@@ -186,7 +186,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------- hv arm
 
-def run_hv(args, w, rank, world, dist):
+def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     import torch
 
     from paper_2508_03911_gb300 import hv
@@ -209,10 +209,10 @@ def run_hv(args, w, rank, world, dist):
         r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream)
         if w.get("temporal") == "pca":
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], temporal="pca", T=w["T"],
-                         stride=w["S"], pca=w["pca"])
+                         stride=w["S"], pca=w["pca"], tuned=tuned)
         else:
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"],
-                         fs=w["fs"], band=(klo, khi), moments=w["moments"])
+                         fs=w["fs"], band=(klo, khi), moments=w["moments"], tuned=tuned)
         return r
 
     r = open_renderer()
@@ -244,7 +244,7 @@ def run_hv(args, w, rank, world, dist):
             gpu_idx = "GPU-" + gpu_idx
     except Exception:
         gpu_idx = None
-    clocks = ClockSampler(gpu_idx) if rank == 0 else None
+    clocks = ClockSampler(gpu_idx) if (rank == 0 and not quick) else None
     if clocks:
         clocks.start()
         time.sleep(0.6)
@@ -282,7 +282,7 @@ def run_hv(args, w, rank, world, dist):
     launches = stats1["kernel_launches"] - stats0["kernel_launches"]
     r.close()
 
-    if args.no_e2e:
+    if args.no_e2e or quick:
         return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
                     clocks=clk, e2e=None, frames_per_step=frames_per_step)
     # ----- end-to-end through host buffers (pinned frames in, images out)
@@ -447,6 +447,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--form", choices=["tuned", "plain", "both"], default="both",
+                    help="tuned: whole-frame cluster kernels; plain: multi-pass kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -484,7 +486,10 @@ def main():
         import torch.distributed as td
         td.init_process_group("nccl")
         dist = td
-    res = run_hv(args, w, rank, world, dist)
+    plain = None
+    if args.form == "both":
+        plain = run_hv(args, w, rank, world, dist, tuned=0, quick=True)
+    res = run_hv(args, w, rank, world, dist, tuned=0 if args.form == "plain" else 1)
     if rank == 0:
         peaks = load_peaks()
         lat = res["lat_ms"]
@@ -507,7 +512,13 @@ def main():
                     if res["e2e"] else None),
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
+            "form": "plain" if args.form == "plain" else "tuned",
         }
+        if plain is not None:
+            line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),
+                             "plain_stage_ms_per_render": {
+                                 "spatial": round(plain["prof"]["spatial_ms"] / max(1, plain["prof"]["renders"]), 4),
+                                 "temporal": round(plain["prof"]["temporal_ms"] / max(1, plain["prof"]["renders"]), 4)}}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
