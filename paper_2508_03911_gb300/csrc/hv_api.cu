@@ -376,8 +376,13 @@ hv_status prof_mark(hv_handle* h, int which) {
 }
 
 hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
-  for (uint64_t a = f0; a < f1; a += h->chunk) {
-    const uint32_t n = uint32_t(std::min<uint64_t>(h->chunk, f1 - a));
+  // the cluster kernel needs no scratch: one persistent launch for all frames
+  const bool whole = h->cur.tuned && h->W == h->H &&
+                     (h->W == 128 || h->W == 256 || h->W == 512) &&
+                     (h->cur.spatial == HV_SPATIAL_ASP || h->cur.spatial == HV_SPATIAL_FRESNEL);
+  const uint64_t step = whole ? f1 - f0 : h->chunk;
+  for (uint64_t a = f0; a < f1; a += step) {
+    const uint32_t n = uint32_t(std::min<uint64_t>(step, f1 - a));
     SpatialArgs sa{};
     sa.spatial = h->cur.spatial;
     sa.in_kind = h->bits == 8 ? IN_U8 : IN_U16;

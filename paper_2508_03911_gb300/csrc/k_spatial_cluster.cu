@@ -165,9 +165,8 @@ __global__ void __launch_bounds__(ClCfg<N>::NT, 1) k_spatial_cluster(SpatialArgs
       StoreTqCols out{tq, uint32_t(N), uint32_t(x0)};
       fft_lines<N, +1, C::SB, C::NT, C::LD>(buf, a.tw_h, out);
     }
-    // the exchange of the next frame reads remote buffers: keep them intact until
-    // every CTA of the cluster is done with this frame
-    cluster.sync();
+    // No barrier needed here: remote buffers are read only inside the next
+    // frame's exchange, which every CTA reaches after a cluster barrier.
   }
   cpa_wait();
 }

@@ -178,9 +178,11 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
       }
     }
     if constexpr (NS > 1) {
+      // stage table: entry (m, jm) at (NS - R1) + (m - 1) NS + jm, contiguous in jm
+      constexpr int R1 = RadixOf<T>::value;
       const int jm = j % NS;
 #pragma unroll
-      for (int m = 1; m < R; ++m) v[it][m] = cmul(v[it][m], tw[jm * m * (T / (NS * R))]);
+      for (int m = 1; m < R; ++m) v[it][m] = cmul(v[it][m], tw[(NS - R1) + (m - 1) * NS + jm]);
     }
   }
   if constexpr (NS * R == T) {
@@ -258,7 +260,21 @@ __global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(
     cp_async_commit();
   };
 
-  for (int i = tid; i < T; i += NT) tw[i] = a.tw_t[i];
+  // per-stage twiddle tables, laid out so that a warp's reads are contiguous:
+  // stage of span NS and radix R keeps w_T^{jm m T/(NS R)} at (NS - R1) + (m-1) NS + jm
+  {
+    constexpr int R1 = RadixOf<T>::value;
+    int NS = R1;
+    while (NS < T) {
+      const int rem = T / NS;
+      const int R = rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2);
+      for (int idx = tid; idx < (R - 1) * NS; idx += NT) {
+        const int m = idx / NS + 1, jm = idx % NS;
+        tw[(NS - R1) + idx] = a.tw_t[jm * m * (T / (NS * R))];
+      }
+      NS *= R;
+    }
+  }
   fetch(0);
   for (uint32_t w = 0; w < a.nwin; ++w) {
     cp_async_wait_all();
