@@ -8,8 +8,8 @@
 // segment is coalesced and every shared-memory stage access by a warp is a
 // contiguous run along b (conflict-free).
 //
-// Algorithm: Stockham autosort decimation in time, radix 8 while the remaining
-// length allows it, then radix 4 or 2. Stage with span NS (product of the
+// Algorithm: Stockham autosort decimation in time, radix 16 where the thread
+// layout allows it, else radix 8 while the remaining length allows, then 4 or 2. Stage with span NS (product of the
 // radices already applied) and radix R: butterfly j in [0, L/R) reads the R
 // inputs j + m L/R, multiplies input m by w_L^{(j mod NS) m L/(NS R)}, applies an
 // R-point DFT, and writes output m to (j / NS) NS R + (j mod NS) + m NS. The
@@ -36,7 +36,19 @@ __device__ __forceinline__ float2 mul_i(float2 v) {
   else return make_float2(-v.y, v.x);
 }
 
-// In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8}.
+// v * exp(DIR 2 pi i e / 16) for the exponents a 16-point DFT uses.
+template <int E, int DIR>
+__device__ __forceinline__ float2 tw16(float2 v) {
+  constexpr float C1 = 0.92387953251128675613f;  // cos(pi/8)
+  constexpr float S1 = 0.38268343236508977173f;  // sin(pi/8)
+  constexpr float R2 = 0.70710678118654752440f;  // cos(pi/4)
+  constexpr float c = E == 1 ? C1 : E == 2 ? R2 : E == 3 ? S1 : E == 6 ? -R2 : -C1;
+  constexpr float s = E == 1 ? S1 : E == 2 ? R2 : E == 3 ? C1 : E == 6 ? R2 : -S1;
+  if constexpr (E == 4) return mul_i<DIR>(v);
+  else return make_float2(fmaf(v.x, c, -v.y * (DIR * s)), fmaf(v.y, c, v.x * (DIR * s)));
+}
+
+// In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8, 16}.
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) {
@@ -50,6 +62,35 @@ __device__ __forceinline__ void dft(float2* v) {
     v[2] = csub(t0, t2);
     v[1] = cadd(t1, t3);
     v[3] = csub(t1, t3);
+  } else if constexpr (R == 16) {
+    // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle w16^(n2 k1), DFT4 over n2
+    float2 a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      a[n2][0] = v[n2];
+      a[n2][1] = v[4 + n2];
+      a[n2][2] = v[8 + n2];
+      a[n2][3] = v[12 + n2];
+      dft<4, DIR>(a[n2]);
+    }
+    a[1][1] = tw16<1, DIR>(a[1][1]);
+    a[1][2] = tw16<2, DIR>(a[1][2]);
+    a[1][3] = tw16<3, DIR>(a[1][3]);
+    a[2][1] = tw16<2, DIR>(a[2][1]);
+    a[2][2] = tw16<4, DIR>(a[2][2]);
+    a[2][3] = tw16<6, DIR>(a[2][3]);
+    a[3][1] = tw16<3, DIR>(a[3][1]);
+    a[3][2] = tw16<6, DIR>(a[3][2]);
+    a[3][3] = tw16<9, DIR>(a[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      dft<4, DIR>(b);
+      v[k1] = b[0];
+      v[k1 + 4] = b[1];
+      v[k1 + 8] = b[2];
+      v[k1 + 12] = b[3];
+    }
   } else {
     static_assert(R == 8, "radix");
     float2 e[4] = {v[0], v[2], v[4], v[6]};
@@ -72,9 +113,18 @@ __device__ __forceinline__ void dft(float2* v) {
   }
 }
 
+// Radix 8 while the remaining length allows it, then 4 or 2.
 template <int REM>
 struct RadixOf {
   static constexpr int value = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+};
+
+// Radix of a block-wide stage: 16 where every thread gets whole butterflies
+// (fewer passes through shared memory), else as RadixOf.
+template <int REM, int L, int BT, int NT>
+struct BlockRadix {
+  static constexpr bool r16 = REM % 16 == 0 && (BT * (L / 16)) % NT == 0 && BT * (L / 16) >= NT;
+  static constexpr int value = r16 ? 16 : RadixOf<REM>::value;
 };
 
 // Threads per CTA for BT lines of length L: one radix-8 butterfly pair per
@@ -93,7 +143,7 @@ template <int L, int NS, int DIR, int BT, int NT, int LD, class Epi>
 __device__ __forceinline__ void fft_stages(const float2* src, int src_ld, float2* buf,
                                            const float2* __restrict__ tw, Epi& epi) {
   constexpr int REM = L / NS;
-  constexpr int R = RadixOf<REM>::value;
+  constexpr int R = BlockRadix<REM, L, BT, NT>::value;
   constexpr int NB = L / R;
   static_assert((BT * NB) % NT == 0, "thread count must divide the butterflies");
   constexpr int ITEMS = BT * NB / NT;

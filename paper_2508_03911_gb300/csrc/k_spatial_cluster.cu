@@ -28,15 +28,24 @@ namespace hv {
 
 template <int N>
 struct ClCfg {
-  static constexpr int CL = N <= 64 ? 1 : (N <= 256 ? N / 64 : 16);
+  // N <= 256: two strip buffers per CTA (exchange reads remote rows straight
+  // into the other buffer); N = 512: one buffer, exchange staged in registers.
+  static constexpr bool DB = N <= 256;
+  static constexpr int CL = N == 128 ? 2 : (N == 256 ? 8 : 16);
   static constexpr int SB = N / CL;          // lines per CTA
   static constexpr int LD = SB + 1;          // padded: transposed accesses conflict-free
-  static constexpr int NT = 1024;
+  static constexpr int NT = 512;
   static constexpr size_t DATA = size_t(N) * LD * sizeof(float2);
   static constexpr size_t RAW = size_t(N) * SB * 2;  // uint16 worst case
-  static constexpr size_t SMEM = DATA + RAW;
-  static constexpr int EXCH = SB * N / NT;    // complex values per thread per exchange
+  static constexpr size_t SMEM = (DB ? 2 : 1) * DATA + RAW;
 };
+
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -79,33 +88,58 @@ struct StoreTqCols {  // column strip to the queue: element (y, x0 + b)
   }
 };
 
-// Move the frame between strip layouts. Source CTA r holds lines [r SB, r SB + SB)
-// of the "from" orientation as buf[t * LD + b]; this CTA gathers, for its own
-// SB lines of the other orientation, element t' = r SB + b_src of every source
-// line t' ... see the kernel comment: we read src[t_own * LD + b] for t_own in
-// this CTA's range and write dst[(r SB + b) * LD + t_own - own0].
+// Move the frame between strip layouts (a transpose across the cluster). Every
+// CTA holds its SB lines as buf[t * LD + b]; afterwards CTA c holds, as its SB
+// lines of the other orientation, element t = c SB + tl of line r SB + b of
+// CTA r, at buf[(r SB + b) * LD + tl]. All remote reads go to registers first,
+// then a cluster barrier, then the local writes (the buffer is reused in place).
+// 32-bit address of `p` (this CTA's shared memory) in CTA `rank`'s shared window.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
 template <int N>
-__device__ __forceinline__ void exchange(cg::cluster_group& cluster, float2* buf, int c) {
+__device__ __forceinline__ void exchange(cg::cluster_group& cluster, const float2* src_buf,
+                                         float2* dst_buf, int c) {
   using C = ClCfg<N>;
-  float2 stage[C::EXCH];
+  constexpr int QN = C::NT / C::SB;   // thread groups per source column
+  constexpr int PER = C::SB / QN;     // lines gathered per thread per source CTA
+  static_assert(C::NT % C::SB == 0 && C::SB % QN == 0, "exchange layout");
+  const int b = threadIdx.x % C::SB, q = threadIdx.x / C::SB;
   const int own0 = c * C::SB;
+  const float2* mine = src_buf + (own0 + q) * C::LD + b;
+  float2* dst = dst_buf + b * C::LD + q;
+  cluster.sync();  // every CTA's source strip is complete
+  if constexpr (C::DB) {
+    // separate destination: copy through registers one value at a time
 #pragma unroll
-  for (int i = 0; i < C::EXCH; ++i) {
-    const int e = threadIdx.x + i * C::NT;     // over CL * SB * SB elements
-    const int b = e % C::SB;                    // source column within its strip
-    const int tl = (e / C::SB) % C::SB;         // my line index (0..SB)
-    const int r = e / (C::SB * C::SB);          // source CTA
-    const float2* src = cluster.map_shared_rank(buf, r);
-    stage[i] = src[(own0 + tl) * C::LD + b];
-  }
-  cluster.sync();
+    for (int r = 0; r < C::CL; ++r) {
+      const uint32_t src = cluster_addr(mine, r);
 #pragma unroll
-  for (int i = 0; i < C::EXCH; ++i) {
-    const int e = threadIdx.x + i * C::NT;
-    const int b = e % C::SB;
-    const int tl = (e / C::SB) % C::SB;
-    const int r = e / (C::SB * C::SB);
-    buf[(r * C::SB + b) * C::LD + tl] = stage[i];
+      for (int s = 0; s < PER; ++s)
+        dst[r * C::SB * C::LD + s * QN] = ld_cluster(src + uint32_t(s * QN * C::LD * sizeof(float2)));
+    }
+  } else {
+    float2 stage[C::CL][PER];
+#pragma unroll
+    for (int r = 0; r < C::CL; ++r) {
+      const uint32_t src = cluster_addr(mine, r);
+#pragma unroll
+      for (int s = 0; s < PER; ++s) stage[r][s] = ld_cluster(src + uint32_t(s * QN * C::LD * sizeof(float2)));
+    }
+    cluster.sync();  // all reads of the (shared) buffer done before it is overwritten
+#pragma unroll
+    for (int r = 0; r < C::CL; ++r)
+#pragma unroll
+      for (int s = 0; s < PER; ++s) dst[r * C::SB * C::LD + s * QN] = stage[r][s];
   }
   __syncthreads();
 }
@@ -115,8 +149,9 @@ __global__ void __launch_bounds__(ClCfg<N>::NT, 1) k_spatial_cluster(SpatialArgs
   using C = ClCfg<N>;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);
-  unsigned char* raw = smem_raw + C::DATA;
+  float2* buf = reinterpret_cast<float2*>(smem_raw);                     // column strips
+  float2* buf2 = C::DB ? reinterpret_cast<float2*>(smem_raw + C::DATA) : buf;  // row strips
+  unsigned char* raw = smem_raw + (C::DB ? 2 : 1) * C::DATA;
   const int c = int(cluster.block_rank());
   const int ncl = gridDim.x / C::CL;
   const int cid = blockIdx.x / C::CL;
@@ -125,8 +160,13 @@ __global__ void __launch_bounds__(ClCfg<N>::NT, 1) k_spatial_cluster(SpatialArgs
   const int x0 = c * C::SB;
 
   if (cid < int(a.n)) fetch_raw<N>(a, raw, (a.raw.slot0 + cid) % a.raw.cap, c, bpp);
+  // Double-buffered strips: a CTA may refill `buf` for the next frame only after
+  // every CTA has finished reading it remotely (split barrier: arrive after the
+  // last exchange of a frame, wait before the next frame's conversion).
+  if constexpr (C::DB) cluster_arrive();
   for (int f = cid; f < int(a.n); f += ncl) {
     cpa_wait();
+    if constexpr (C::DB) cluster_wait();
     __syncthreads();
     // 1. convert (+ chirp) into buf[y][b], b = column within the strip
     for (int e = threadIdx.x; e < N * C::SB; e += C::NT) {
@@ -143,31 +183,32 @@ __global__ void __launch_bounds__(ClCfg<N>::NT, 1) k_spatial_cluster(SpatialArgs
     StoreSmem<C::LD> st{buf};
     fft_lines<N, -1, C::SB, C::NT, C::LD>(buf, a.tw_h, st);
     __syncthreads();
-    cluster.sync();
-    exchange<N>(cluster, buf, c);  // now buf[x][b] = F[ky = x0 + b][x]
+    exchange<N>(cluster, buf, buf2, c);  // buf2[x][b] = F[ky = x0 + b][x]
     float2* tq = static_cast<float2*>(a.tq.base) + ((a.tq.slot0 + f) % a.tq.cap) * size_t(N) * N;
+    StoreSmem<C::LD> st2{buf2};
     if (fresnel) {
-      fft_lines<N, -1, C::SB, C::NT, C::LD>(buf, a.tw_w, st);
+      if constexpr (C::DB) cluster_arrive();  // done reading remote column strips
+      fft_lines<N, -1, C::SB, C::NT, C::LD>(buf2, a.tw_w, st2);
       __syncthreads();
       // rows ky = x0 + b to the queue, coalesced along kx
       for (int e = threadIdx.x; e < N * C::SB; e += C::NT) {
         const int k = e % N, b = e / N;
-        tq[size_t(x0 + b) * N + k] = buf[k * C::LD + b];
+        tq[size_t(x0 + b) * N + k] = buf2[k * C::LD + b];
       }
     } else {
-      AspMulStore<C::LD> mul{buf, a.asp_ht, uint32_t(N), uint32_t(x0)};
-      fft_lines<N, -1, C::SB, C::NT, C::LD>(buf, a.tw_w, mul);
+      AspMulStore<C::LD> mul{buf2, a.asp_ht, uint32_t(N), uint32_t(x0)};
+      fft_lines<N, -1, C::SB, C::NT, C::LD>(buf2, a.tw_w, mul);
       __syncthreads();
-      fft_lines<N, +1, C::SB, C::NT, C::LD>(buf, a.tw_w, st);
+      fft_lines<N, +1, C::SB, C::NT, C::LD>(buf2, a.tw_w, st2);
       __syncthreads();
-      cluster.sync();
-      exchange<N>(cluster, buf, c);  // buf[ky][b] = G[ky][x = x0 + b]
+      exchange<N>(cluster, buf2, buf, c);  // buf[ky][b] = G[ky][x = x0 + b]
+      if constexpr (C::DB) cluster_arrive();  // done reading remote row strips
       StoreTqCols out{tq, uint32_t(N), uint32_t(x0)};
       fft_lines<N, +1, C::SB, C::NT, C::LD>(buf, a.tw_h, out);
     }
-    // No barrier needed here: remote buffers are read only inside the next
-    // frame's exchange, which every CTA reaches after a cluster barrier.
   }
+  // no CTA may exit while another can still read its shared memory
+  if constexpr (C::DB) cluster_wait();
   cpa_wait();
 }
 
