@@ -95,8 +95,12 @@ typedef struct {
   int32_t precision;          /* PCA covariance arithmetic, HV_PREC_*                  */
   int32_t tuned;              /* 1 = tuned form (graph replay, fused kernels)          */
   uint32_t spatial_chunk;     /* frames per spatial launch (0 = automatic)             */
-  uint32_t reserved;
+  uint32_t spatial_kernel;    /* HV_SK_*: which spatial kernel (default automatic)     */
 } hv_params;
+
+/* Spatial kernel selection: automatic = the autotuner's choice when tuned = 1,
+ * the multi-pass kernels otherwise. */
+enum { HV_SK_AUTO = 0, HV_SK_MULTIPASS = 1, HV_SK_CLUSTER = 2 };
 
 typedef struct {
   uint64_t frames_pushed;     /* frames accepted by hv_push_frames                     */
@@ -150,6 +154,21 @@ hv_status hv_window_floats(const hv_handle* h, size_t* floats_per_window);
 
 /* Eigenvalues (descending, FP64) of the last PCA window rendered; n <= T. */
 hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n);
+
+/* Choices of the tuned form (hv_params.tuned = 1), made when the settings are
+ * applied by timing each candidate on the handle's own buffers. */
+typedef struct {
+  int32_t tuned;                    /* 1 once the autotuner has run                   */
+  int32_t spatial_kernel;           /* 0 multi-pass FFT kernels, 1 whole-frame cluster */
+  uint32_t spatial_chunk;           /* frames per multi-pass launch                   */
+  uint32_t reserved;
+  float candidate_us_per_frame[8];  /* measured: multi-pass with 16, 32, 64, 128, 256
+                                       frames per launch, then the cluster kernel
+                                       (0 where not applicable)                       */
+} hv_tuning;
+
+/* The autotuner's choices for the applied settings. Errors: HV_ERR_STATE. */
+hv_status hv_get_tuning(const hv_handle* h, hv_tuning* t);
 
 /* Counters of the handle. */
 hv_status hv_get_stats(const hv_handle* h, hv_stats* s);

@@ -41,6 +41,8 @@ struct hv_handle {
   float2* s2 = nullptr;
   size_t s1_bytes = 0, s2_bytes = 0;
   uint32_t chunk = 0;
+  int sp_cluster = 0;         // spatial kernel: 0 multi-pass, 1 whole-frame cluster
+  hv_tuning tuning{};
   float2* tw = nullptr;  // all twiddle tables, length 8..1024 packed
   float2* asp_ht = nullptr;
   float2* chirp = nullptr;  // [W] x factors then [H] y factors
@@ -125,6 +127,13 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
   if (p.spatial != HV_SPATIAL_NONE && p.spatial != HV_SPATIAL_ASP && p.spatial != HV_SPATIAL_FRESNEL) {
     why = "unknown spatial transform";
     return HV_ERR_ARG;
+  }
+  if (p.spatial_kernel > HV_SK_CLUSTER) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.spatial_kernel == HV_SK_CLUSTER &&
+      !(p.width == p.height && (p.width == 128 || p.width == 256 || p.width == 512) &&
+        (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
+    why = "the cluster kernel needs square 128, 256 or 512 frames and ASP or Fresnel";
+    return HV_ERR_UNSUPPORTED;
   }
   if (p.spatial != HV_SPATIAL_NONE) {
     if (!(p.lambda_m > 0) || !(p.pitch_x_m > 0) || !(p.pitch_y_m > 0) || !std::isfinite(p.z_m)) {
@@ -233,6 +242,8 @@ hv_status ensure(hv_handle* h, void** p, size_t* have, size_t need) {
   return HV_OK;
 }
 
+hv_status tune_spatial(hv_handle* h);
+
 // Apply the pending settings (window boundary).
 hv_status apply_pending(hv_handle* h) {
   if (!h->pending) return HV_OK;
@@ -331,6 +342,14 @@ hv_status apply_pending(hv_handle* h) {
   h->win_floats = d.win_floats;
   h->Q = Q;
   h->chunk = chunk;
+  h->sp_cluster = p.spatial_kernel == HV_SK_CLUSTER ? 1 : 0;
+  h->tuning = hv_tuning{};
+  h->tuning.spatial_chunk = chunk;
+  h->tuning.spatial_kernel = h->sp_cluster;
+  if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
+    s = tune_spatial(h);
+    if (s != HV_OK) return s;
+  }
   // queue flush: the next window starts at the first unconsumed frame and is
   // propagated entirely with the new settings
   h->propagated = h->next_win;
@@ -375,11 +394,14 @@ hv_status prof_mark(hv_handle* h, int which) {
   return HV_OK;
 }
 
+bool cluster_ok(const hv_handle* h) {
+  return h->W == h->H && (h->W == 128 || h->W == 256 || h->W == 512) &&
+         (h->cur.spatial == HV_SPATIAL_ASP || h->cur.spatial == HV_SPATIAL_FRESNEL);
+}
+
 hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
   // the cluster kernel needs no scratch: one persistent launch for all frames
-  const bool whole = h->cur.tuned && h->W == h->H &&
-                     (h->W == 128 || h->W == 256 || h->W == 512) &&
-                     (h->cur.spatial == HV_SPATIAL_ASP || h->cur.spatial == HV_SPATIAL_FRESNEL);
+  const bool whole = h->sp_cluster && cluster_ok(h);
   const uint64_t step = whole ? f1 - f0 : h->chunk;
   for (uint64_t a = f0; a < f1; a += step) {
     const uint32_t n = uint32_t(std::min<uint64_t>(step, f1 - a));
@@ -398,13 +420,80 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.asp_ht = h->asp_ht;
     sa.chirp_x = h->chirp;
     sa.chirp_y = h->chirp + h->W;
-    sa.use_cluster = h->cur.tuned;
+    sa.use_cluster = h->sp_cluster;
     int launches = 0;
     cudaError_t e = launch_spatial(sa, h->stream, &launches);
     h->st.kernel_launches += launches;
     if (e != cudaSuccess) return cuda_fail(h, e, "spatial transform launch");
     h->st.frames_propagated += n;
   }
+  return HV_OK;
+}
+
+// Autotuner of the tuned form: times the spatial-kernel candidates (multi-pass
+// with several frames per launch, and the whole-frame cluster kernel) on the
+// handle's own buffers and keeps the fastest. Runs when tuned settings are
+// applied; the time queue is being flushed then, so its contents may be used.
+hv_status tune_spatial(hv_handle* h) {
+  hv_tuning t{};
+  if (h->cur.spatial == HV_SPATIAL_NONE) {
+    h->tuning = t;
+    return HV_OK;
+  }
+  const size_t fbytes = size_t(h->W) * h->H * sizeof(float2);
+  const uint32_t n = std::min<uint32_t>(256, std::min(h->Q, h->cap));
+  cudaEvent_t e0, e1;
+  HV_CU(h, cudaEventCreate(&e0));
+  HV_CU(h, cudaEventCreate(&e1));
+  static const uint32_t chunks[] = {16, 32, 64, 128, 256};
+  float best = 1e30f;
+  int best_cl = 0;
+  uint32_t best_chunk = h->chunk;
+  const uint32_t saved_chunk = h->chunk;
+  const int ncand = 5 + (cluster_ok(h) ? 1 : 0);
+  for (int ci = 0; ci < ncand; ++ci) {
+    const bool cl = ci == 5;
+    uint32_t ch = cl ? n : std::min(chunks[ci], n);
+    if (!cl) {
+      const size_t need = size_t(ch) * fbytes;
+      hv_status st = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need);
+      if (st != HV_OK) continue;
+      if (h->cur.spatial == HV_SPATIAL_ASP) {
+        st = ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need);
+        if (st != HV_OK) continue;
+      }
+    }
+    h->sp_cluster = cl ? 1 : 0;
+    h->chunk = ch;
+    const uint64_t before = h->st.frames_propagated;
+    hv_status st = propagate(h, 0, n);  // warm-up
+    if (st != HV_OK) return st;
+    HV_CU(h, cudaEventRecord(e0, h->stream));
+    for (int rep = 0; rep < 2; ++rep) {
+      st = propagate(h, 0, n);
+      if (st != HV_OK) return st;
+    }
+    HV_CU(h, cudaEventRecord(e1, h->stream));
+    HV_CU(h, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HV_CU(h, cudaEventElapsedTime(&ms, e0, e1));
+    h->st.frames_propagated = before;  // tuning work is not rendering work
+    const float us_per_frame = 1000.f * ms / (2.f * n);
+    if (ci < 6) t.candidate_us_per_frame[ci] = us_per_frame;
+    if (us_per_frame < best) {
+      best = us_per_frame;
+      best_cl = cl ? 1 : 0;
+      best_chunk = cl ? saved_chunk : ch;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->sp_cluster = best_cl;
+  h->chunk = best_chunk;
+  t.spatial_kernel = best_cl;
+  t.spatial_chunk = best_chunk;
+  t.tuned = 1;
+  h->tuning = t;
   return HV_OK;
 }
 
@@ -644,6 +733,13 @@ hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n) {
   if (cudaMemcpyAsync(out, h->pca.lam, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return HV_ERR_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HV_ERR_CUDA;
+  return HV_OK;
+}
+
+hv_status hv_get_tuning(const hv_handle* h, hv_tuning* t) {
+  if (!h || !t) return HV_ERR_ARG;
+  if (!h->has_params) return HV_ERR_STATE;
+  *t = h->tuning;
   return HV_OK;
 }
 

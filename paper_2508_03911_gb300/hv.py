@@ -51,7 +51,7 @@ class hv_params(C.Structure):
                 ("band_lo_bin", C.c_uint32), ("band_hi_bin", C.c_uint32),
                 ("band_lo_hz", C.c_double), ("band_hi_hz", C.c_double),
                 ("pca_lo", C.c_uint32), ("pca_hi", C.c_uint32), ("precision", C.c_int32),
-                ("tuned", C.c_int32), ("spatial_chunk", C.c_uint32), ("reserved", C.c_uint32)]
+                ("tuned", C.c_int32), ("spatial_chunk", C.c_uint32), ("spatial_kernel", C.c_uint32)]
 
 
 class hv_stats(C.Structure):
@@ -65,6 +65,11 @@ class hv_profile(C.Structure):
                 ("frames", C.c_uint64), ("windows", C.c_uint64), ("pca_cov_ms", C.c_double),
                 ("pca_eig_ms", C.c_double), ("pca_proj_ms", C.c_double),
                 ("pca_sweeps", C.c_uint64)]
+
+
+class hv_tuning(C.Structure):
+    _fields_ = [("tuned", C.c_int32), ("spatial_kernel", C.c_int32), ("spatial_chunk", C.c_uint32),
+                ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 8)]
 
 
 class HvError(RuntimeError):
@@ -95,6 +100,7 @@ def lib() -> C.CDLL:
         "hv_window_floats": ([C.c_void_p, P(C.c_size_t)], C.c_int),
         "hv_pca_eigenvalues": ([C.c_void_p, P(C.c_double), C.c_uint32], C.c_int),
         "hv_get_stats": ([C.c_void_p, P(hv_stats)], C.c_int),
+        "hv_get_tuning": ([C.c_void_p, P(hv_tuning)], C.c_int),
         "hv_synchronize": ([C.c_void_p], C.c_int),
         "hv_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
         "hv_profile_read": ([C.c_void_p, P(hv_profile)], C.c_int),
@@ -135,7 +141,7 @@ def hv_open(max_width, max_height, pixel_bits, queue_capacity_frames, device=0,
 def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pitch_y=None,
                 fftshift=1, temporal="stft", T=64, stride=None, fs=20000.0, band=(4, 28),
                 band_hz=None, moments=("M0",), pca=(2, 64), precision="fp32", tuned=0,
-                spatial_chunk=0) -> hv_params:
+                spatial_chunk=0, spatial_kernel="auto") -> hv_params:
     p = hv_params()
     p.struct_size = C.sizeof(hv_params)
     p.width, p.height = width, height
@@ -156,6 +162,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.precision = PRECISION[precision]
     p.tuned = int(tuned)
     p.spatial_chunk = spatial_chunk
+    p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2}[spatial_kernel]
     return p
 
 
@@ -227,6 +234,13 @@ def hv_profile_read(h) -> dict:
     p = hv_profile()
     _check(h, lib().hv_profile_read(h, C.byref(p)))
     return {n: getattr(p, n) for n, _ in hv_profile._fields_}
+
+
+def hv_get_tuning(h) -> dict:
+    t = hv_tuning()
+    _check(h, lib().hv_get_tuning(h, C.byref(t)))
+    return {"tuned": t.tuned, "spatial_kernel": t.spatial_kernel, "spatial_chunk": t.spatial_chunk,
+            "candidate_us_per_frame": list(t.candidate_us_per_frame)}
 
 
 def hv_synchronize(h):

@@ -104,7 +104,7 @@ def test_cluster_spatial_field_parity(N, spatial, bits):
     fr = synth.random_frames(n, N, N, bits, seed=7 * N + bits)
     p = oracle_params(spatial=spatial, z_m=0.3, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
                       H=N, W=N)
-    img, st = gpu_render(fr, p, extra=dict(tuned=1), queue=3, packets=[1, 2, 2][:n] if n == 5 else None)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="cluster"), queue=3, packets=[1, 2, 2][:n] if n == 5 else None)
     ref = oracle_fields(fr, p)
     for i in range(n):
         assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
@@ -116,9 +116,34 @@ def test_cluster_many_frames_ring_wrap():
     fr = synth.random_frames(n, N, N, 12, seed=99)
     p = oracle_params(spatial="fresnel", T=64, stride=16, fs_hz=71400.0, band_lo_bin=2,
                       band_hi_bin=30, moments=ALL_MOMENTS, H=N, W=N)
-    img, st = gpu_render(fr, p, extra=dict(tuned=1), packets=[100, 100, 100], queue=200, tq=100)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="cluster"), packets=[100, 100, 100],
+                       queue=200, tq=100)
     assert st["windows_rendered"] == len(O.window_starts(n, 64, 16))
     check_images(img, O.render(fr, p))
+
+
+def test_autotuned_form_matches_oracle():
+    """tuned = 1: the autotuner times the candidates on the handle's buffers and
+    keeps one; the rendered windows are the oracle's."""
+    N = 256
+    fr = synth.random_frames(200, N, N, 12, seed=5)
+    p = oracle_params(spatial="asp", T=64, stride=32, band_lo_bin=3, band_hi_bin=20,
+                      moments=("M0", "M1"), H=N, W=N)
+    import torch
+    r = hv.Renderer(N, N, 16, 256)
+    try:
+        hv.hv_set_params(r.h, to_hv(p, tuned=1))
+        out = torch.zeros(8 * 2 * N * N, device="cuda")
+        assert r.push(to_device(fr)) == hv.HV_OK
+        n = r.render(out)
+        t = hv.hv_get_tuning(r.h)
+        torch.cuda.synchronize()
+        assert t["tuned"] == 1 and t["spatial_kernel"] in (0, 1)
+        assert all(v > 0 for v in t["candidate_us_per_frame"][:6])
+        img = out.cpu().numpy()[: n * 2 * N * N].reshape(n, 2, N, N)
+        check_images(img, O.render(fr, p))
+    finally:
+        r.close()
 
 
 def test_fresnel_without_fftshift_and_negative_z():
