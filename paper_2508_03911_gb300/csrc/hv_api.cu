@@ -154,7 +154,14 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
       why = "PCA sub-basis must satisfy 1 <= pca_lo <= pca_hi <= T";
       return HV_ERR_ARG;
     }
-    if (p.precision != HV_PREC_FP32) { why = "this PCA covariance precision is not built"; return HV_ERR_UNSUPPORTED; }
+    if (p.precision != HV_PREC_FP32 && p.precision != HV_PREC_BF16 && p.precision != HV_PREC_SPLIT_BF16) {
+      why = "unknown precision";
+      return HV_ERR_ARG;
+    }
+    if (p.precision != HV_PREC_FP32 && p.T < 64) {
+      why = "tensor-core covariance needs T >= 64";
+      return HV_ERR_UNSUPPORTED;
+    }
     d = Derived{p.T, p.stride, 0, 0, 1, hw};
     return HV_OK;
   }
@@ -292,8 +299,23 @@ hv_status apply_pending(hv_handle* h) {
     const size_t b_cnt = 64;
     const size_t b_lam = size_t(T) * sizeof(double);
     const size_t b_vs = size_t(T) * Mpad * sizeof(float2);
+    // tensor-core covariance tiles and chunks (about one CTA per SM)
+    uint8_t ti[32] = {}, tj[32] = {};
+    uint32_t ntiles = 0, tc_nchunks = 0, tc_chunk = 0;
+    size_t b_tc = 0;
+    if (p.precision != HV_PREC_FP32) {
+      ntiles = cov_tc_tiles(T, ti, tj);
+      int dev = 0, nsm = 152;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      tc_nchunks = std::max<uint32_t>(1, uint32_t(nsm) / ntiles);
+      tc_chunk = uint32_t((hw + tc_nchunks - 1) / tc_nchunks);
+      tc_chunk = (tc_chunk + 63) / 64 * 64;
+      tc_nchunks = uint32_t((hw + tc_chunk - 1) / tc_chunk);
+      b_tc = cov_tc_partials_floats(ntiles, tc_nchunks) * sizeof(float);
+    }
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t total = al(b_part) + 2 * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs);
+    const size_t total = al(b_part) + 2 * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs) + al(b_tc);
     s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
     if (s != HV_OK) return s;
     char* b = static_cast<char*>(h->pca_ws);
@@ -327,6 +349,15 @@ hv_status apply_pending(hv_handle* h) {
     a.lam = reinterpret_cast<double*>(b);
     b += al(b_lam);
     a.Vs = reinterpret_cast<float2*>(b);
+    b += al(b_vs);
+    a.precision = p.precision;
+    a.tc_partials = b_tc ? reinterpret_cast<float*>(b) : nullptr;
+    a.tc_chunk = tc_chunk;
+    a.tc_nchunks = tc_nchunks;
+    a.tc_ntiles = ntiles;
+    std::memcpy(a.tc_tile_i, ti, sizeof(ti));
+    std::memcpy(a.tc_tile_j, tj, sizeof(tj));
+    a.err = a.counters + 3;
     h->pca_has_lam = false;
   }
   h->cur = p;

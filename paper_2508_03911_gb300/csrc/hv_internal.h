@@ -68,8 +68,17 @@ struct PcaArgs {
   double* cmax;         // = (double*)(counters + 4)
   double* lam;          // T eigenvalues, descending
   float2* Vs;           // T x Mpad sub-basis
+  // tensor-core covariance (precision BF16 / split-BF16)
+  int precision;        // HV_PREC_*
+  float* tc_partials;   // nchunks x ntiles x 128 x 256 float
+  uint32_t tc_chunk, tc_nchunks, tc_ntiles;
+  uint8_t tc_tile_i[32], tc_tile_j[32];
+  unsigned* err;        // device error flag (bounded waits that gave up)
 };
 size_t pca_partials_floats2(uint32_t T, uint32_t nchunks);
+size_t cov_tc_partials_floats(uint32_t ntiles, uint32_t nchunks);
+uint32_t cov_tc_tiles(uint32_t T, uint8_t* ti, uint8_t* tj);
+cudaError_t launch_cov_tc(PcaArgs& a, cudaStream_t s, int* launches);
 // ev (optional, 4 events): before covariance, after covariance, after eigensolver, after projection
 cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev);
 

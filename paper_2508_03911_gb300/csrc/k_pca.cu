@@ -19,6 +19,7 @@
 
 #include "fft_dev.cuh"
 #include "hv_internal.h"
+#include "../../include/hv.h"
 
 namespace cg = cooperative_groups;
 
@@ -328,10 +329,15 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
   if (e0 != cudaSuccess) return e0;
   if (ev) cudaEventRecord(ev[0], s);
-  k_cov_fp32<<<g1, 256, 0, s>>>(a);
-  k_cov_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+  if (a.precision == HV_PREC_FP32) {
+    k_cov_fp32<<<g1, 256, 0, s>>>(a);
+    k_cov_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+    *launches += 2;
+  } else {
+    cudaError_t et = launch_cov_tc(a, s, launches);
+    if (et != cudaSuccess) return et;
+  }
   if (ev) cudaEventRecord(ev[1], s);
-  *launches += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;

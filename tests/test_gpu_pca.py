@@ -68,19 +68,68 @@ def test_pca_parity(H, W, T, S, lohi, spatial):
     assert np.all(np.diff(lam) <= 0)
 
 
-def test_pca_scene_window_full_size():
-    """One window of the PCA workload: 512x512 12-bit frames, ASP z = 0.40 m,
-    T = 256, energy over eigenvectors 2..64 (every pixel)."""
+@pytest.mark.parametrize("precision,tol", [("split_bf16", 1e-4), ("bf16", 5e-2)])
+@pytest.mark.parametrize("H,W,T", [(64, 64, 64), (128, 64, 256), (64, 128, 128)])
+def test_pca_tensor_core_covariance(precision, tol, H, W, T):
+    """Covariance on the tensor cores (tcgen05, BF16 or split-BF16 inputs, FP32
+    accumulation): E against the FP64 oracle; the error is printed per case."""
+    n = T + 5
+    fr = synth.random_frames(n, H, W, 12, seed=H * 3 + T + len(precision))
+    p = oracle_params(spatial="fresnel", z_m=0.3, temporal="pca", T=T, stride=T, pca_lo=2,
+                      pca_hi=min(T, 40), H=H, W=W)
+    import torch
+    r = hv.Renderer(W, H, 16, n)
+    try:
+        hv.hv_set_params(r.h, to_hv(p, precision=precision))
+        out = torch.zeros(n * H * W, dtype=torch.float32, device="cuda")
+        assert r.push(to_device(fr)) == hv.HV_OK
+        nw = r.render(out)
+        torch.cuda.synchronize()
+        lam = hv.hv_pca_eigenvalues(r.h, T)
+        img = out.cpu().numpy()[: nw * H * W].reshape(nw, H, W)
+    finally:
+        r.close()
+    ref = oracle_windows(fr, p)
+    e = rel_l2(img[0], ref[0]["E"])
+    el = float(np.max(np.abs(lam - ref[0]["lam"])) / ref[0]["lam"][0])
+    print(f"{precision} {H}x{W} T={T}: E rel L2 {e:.3e}, lam max err / lam1 {el:.3e}")
+    assert e <= tol
+    assert el <= tol
+
+
+@pytest.fixture(scope="module")
+def pca_scene_window():
     sc = synth.build(synth.scene_pca())
     fr = synth.frames(sc, 0, 256)
     p = oracle_params(spatial="asp", z_m=0.40, temporal="pca", T=256, stride=256, pca_lo=2,
                       pca_hi=64, H=512, W=512)
-    img, lam = gpu_pca(fr, p)
-    ref = oracle_windows(fr, p)[0]
-    e = rel_l2(img[0], ref["E"])
-    print("E rel L2", e, "lam max abs / lam1", np.max(np.abs(lam - ref["lam"])) / ref["lam"][0])
-    assert e <= IMAGE_TOL
-    assert np.max(np.abs(lam - ref["lam"])) <= LAM_TOL * ref["lam"][0]
+    return fr, p, oracle_windows(fr, p)[0]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", IMAGE_TOL), ("split_bf16", IMAGE_TOL),
+                                           ("bf16", 5e-2)])
+def test_pca_scene_window_full_size(pca_scene_window, precision, tol):
+    """One window of the PCA workload: 512x512 12-bit frames, ASP z = 0.40 m,
+    T = 256, energy over eigenvectors 2..64 (every pixel), per covariance precision."""
+    fr, p, ref = pca_scene_window
+    p = dict(p, precision=precision)
+    import torch
+    r = hv.Renderer(512, 512, 16, 256)
+    try:
+        hv.hv_set_params(r.h, to_hv(p, precision=precision))
+        out = torch.zeros(512 * 512, dtype=torch.float32, device="cuda")
+        assert r.push(to_device(fr)) == hv.HV_OK
+        assert r.render(out) == 1
+        torch.cuda.synchronize()
+        lam = hv.hv_pca_eigenvalues(r.h, 256)
+        img = out.cpu().numpy().reshape(512, 512)
+    finally:
+        r.close()
+    e = rel_l2(img, ref["E"])
+    el = float(np.max(np.abs(lam - ref["lam"])) / ref["lam"][0])
+    print(f"scene {precision}: E rel L2 {e:.3e}, lam max err / lam1 {el:.3e}")
+    assert e <= tol
+    assert el <= max(LAM_TOL, tol)
 
 
 def test_pca_rejects_unbuilt_precisions_and_bad_basis():
