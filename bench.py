@@ -209,7 +209,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream)
         if w.get("temporal") == "pca":
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], temporal="pca", T=w["T"],
-                         stride=w["S"], pca=w["pca"], tuned=tuned)
+                         stride=w["S"], pca=w["pca"], tuned=tuned,
+                         precision=w.get("precision", "fp32"))
         else:
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"],
                          fs=w["fs"], band=(klo, khi), moments=w["moments"], tuned=tuned)
@@ -335,6 +336,18 @@ def roofline_pca(w, res, peaks):
           "jacobi_fp64": prof["pca_eig_ms"] / nwin, "projection": prof["pca_proj_ms"] / nwin}
     kern = max(st, key=st.get)
     t = st[kern] / 1e3
+    if kern == "covariance" and w.get("precision", "fp32") != "fp32":
+        # tensor cores: algorithmic flops of the real Gram matrix G = Y Y^T (2T x 2T, K = P),
+        # times the products per step (3 for split-BF16), against the measured bf16 peak
+        nprod = 3 if w["precision"] == "split_bf16" else 1
+        flops = 2.0 * (2 * T) * (2 * T) * P * nprod
+        peak = (peaks or {}).get("bf16_tflops", 1906.8)
+        tf = flops / t / 1e12
+        return {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(tf / peak, 4), "traffic": None,
+                "kernel": f"k_cov_tc (tcgen05 {w['precision']})",
+                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
     if kern == "covariance":
         flops, byts = 8.0 * P * T * T, 8.0 * P * T
     elif kern == "projection":
@@ -447,12 +460,16 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default=None,
+                    help="PCA covariance arithmetic (PCA workloads)")
     ap.add_argument("--form", choices=["tuned", "plain", "both"], default="both",
                     help="tuned: whole-frame cluster kernels; plain: multi-pass kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.precision:
+        w["precision"] = args.precision
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     klo, khi = band_bins(w)
@@ -460,7 +477,7 @@ def main():
               "pixel_bits": w["bits"], "spatial": w["spatial"], "z_m": w["z"], "T": w["T"],
               "stride": w["S"], "fs_hz": w["fs"], "band_bins": [klo, khi],
               "moments": list(w["moments"]), "frames_per_step": w["batch"] * w["batches"],
-              "batch_frames": w["batch"],
+              "batch_frames": w["batch"], "precision": w.get("precision", "fp32"),
               "l2": "inputs larger than L2: each step streams >10 GB through the time queue",
               "parallelism": f"replicas x{args.gpus}"}
 
