@@ -270,6 +270,7 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         dist.barrier()
     prof = hv.hv_profile_read(r.h)
     hv.hv_profile_enable(r.h, False)
+    tuning = hv.hv_get_tuning(r.h)
     stats1 = r.stats()
     elapsed_ms = t_start.elapsed_time(t_end)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
@@ -285,7 +286,7 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
 
     if args.no_e2e or quick:
         return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
-                    clocks=clk, e2e=None, frames_per_step=frames_per_step)
+                    clocks=clk, e2e=None, frames_per_step=frames_per_step, tuning=tuning)
     # ----- end-to-end through host buffers (pinned frames in, images out)
     host_pool = pool_t.repeat(reps, 1, 1).contiguous().pin_memory()
     r2 = open_renderer()
@@ -322,7 +323,7 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
                 clocks=clk, e2e=dict(value=e2e_value, unit="frames/s",
                                      h2d_bytes_per_step=h2d // e2e_steps,
                                      d2h_bytes_per_step=d2h // e2e_steps),
-                frames_per_step=frames_per_step)
+                frames_per_step=frames_per_step, tuning=tuning)
 
 
 def roofline_pca(w, res, peaks, force=None):
@@ -536,6 +537,9 @@ def main():
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "form": "plain" if args.form == "plain" else "tuned",
+            "tuning": {"spatial_kernel": ["multipass", "cluster"][res["tuning"]["spatial_kernel"]],
+                       "frames_per_launch": res["tuning"]["spatial_chunk"],
+                       "candidate_us_per_frame": [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:6]]},
         }
         if plain is not None:
             line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),

@@ -680,14 +680,25 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
   const uint64_t prop_before = h->st.frames_propagated;
   s = prof_mark(h, 0);
   if (s != HV_OK) return s;
-  // spatial transform of every frame of these windows not yet in the queue
-  for (uint32_t w = 0; w < nw; ++w) {
-    const uint64_t a = h->next_win + uint64_t(w) * S;
-    const uint64_t lo = std::max(a, h->propagated);
-    if (lo < a + T) {
-      s = propagate(h, lo, a + T);
+  // spatial transform of every frame of these windows not yet in the queue: one
+  // contiguous range when windows overlap or touch (S <= T), else per window
+  if (S <= T) {
+    const uint64_t lo = std::max(h->next_win, h->propagated);
+    const uint64_t hi = h->next_win + uint64_t(nw - 1) * S + T;
+    if (lo < hi) {
+      s = propagate(h, lo, hi);
       if (s != HV_OK) return s;
-      h->propagated = a + T;
+      h->propagated = hi;
+    }
+  } else {
+    for (uint32_t w = 0; w < nw; ++w) {
+      const uint64_t a = h->next_win + uint64_t(w) * S;
+      const uint64_t lo = std::max(a, h->propagated);
+      if (lo < a + T) {
+        s = propagate(h, lo, a + T);
+        if (s != HV_OK) return s;
+        h->propagated = a + T;
+      }
     }
   }
   s = prof_mark(h, 1);
