@@ -96,6 +96,11 @@ typedef struct {
   int32_t tuned;              /* 1 = tuned form (graph replay, fused kernels)          */
   uint32_t spatial_chunk;     /* frames per spatial launch (0 = automatic)             */
   uint32_t spatial_kernel;    /* HV_SK_*: which spatial kernel (default automatic)     */
+  double highpass_cpp;        /* ASP only: high-pass spatial filter applied after the
+                                 propagation (Sec. VI-B.1): spatial frequencies whose
+                                 radius sqrt((m/W)^2 + (n/H)^2) in cycles per pixel is
+                                 below this cutoff are zeroed; 0 = off. Folded into
+                                 the transfer function. hv_spatial_static ignores it. */
 } hv_params;
 
 /* Spatial kernel selection: automatic = the autotuner's choice when tuned = 1,

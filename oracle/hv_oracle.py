@@ -122,13 +122,32 @@ def fresnel(u: np.ndarray, lam: float, dx: float, dy: float, z: float,
     return out
 
 
+def highpass(u: np.ndarray, cutoff: float) -> np.ndarray:
+    """Ideal radial high-pass spatial filter (Sec. VI-B.1 applies one after the
+    angular-spectrum propagation; shape and cutoff are unspecified).
+
+    READING: zero every DFT bin whose radius sqrt((m'/W)^2 + (n'/H)^2) in cycles
+    per pixel (signed FFT-order indices) is below `cutoff`.
+    """
+    H, W = u.shape[-2:]
+    m = np.arange(W)
+    m = np.where(m < W // 2, m, m - W) / W
+    n = np.arange(H)
+    n = np.where(n < H // 2, n, n - H) / H
+    keep = (m[None, :] * m[None, :] + n[:, None] * n[:, None]) >= cutoff * cutoff
+    return ifft2(fft2(u) * keep)
+
+
 def spatial(frames_c: np.ndarray, p: dict) -> np.ndarray:
     """Apply the configured spatial transform to complex frames [..., H, W]."""
     kind = p["spatial"]
     if kind == "none":
         return frames_c.copy()
     if kind == "asp":
-        return asp(frames_c, p["lambda_m"], p["pitch_x_m"], p["pitch_y_m"], p["z_m"])
+        out = asp(frames_c, p["lambda_m"], p["pitch_x_m"], p["pitch_y_m"], p["z_m"])
+        if p.get("highpass", 0.0) > 0.0:
+            out = highpass(out, p["highpass"])
+        return out
     if kind == "fresnel":
         return fresnel(frames_c, p["lambda_m"], p["pitch_x_m"], p["pitch_y_m"], p["z_m"],
                        bool(p.get("fftshift", 1)))

@@ -142,6 +142,11 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     }
     if (p.spatial == HV_SPATIAL_FRESNEL && p.z_m == 0.0) { why = "Fresnel needs z != 0"; return HV_ERR_ARG; }
   }
+  if (!(p.highpass_cpp >= 0.0) || p.highpass_cpp > 1.0) { why = "highpass_cpp must be in [0, 1]"; return HV_ERR_ARG; }
+  if (p.highpass_cpp > 0.0 && p.spatial != HV_SPATIAL_ASP) {
+    why = "the high-pass filter is applied with angular-spectrum propagation only";
+    return HV_ERR_ARG;
+  }
   const size_t hw = size_t(p.width) * p.height;
   if (p.temporal == HV_TEMPORAL_NONE) {
     d = Derived{1, 1, 0, 0, 0, 2 * hw};
@@ -211,7 +216,10 @@ hv_status build_tables(hv_handle* h, const hv_params& p) {
         const double fy = 2.0 * M_PI * my / (H * p.pitch_y_m);
         const double kz2 = k * k - fx * fx - fy * fy;
         float2 v = make_float2(0.f, 0.f);
-        if (kz2 >= 0) {
+        // high-pass filter after propagation = mask on the propagated spectrum
+        const double rx = mx / W, ry = my / H;
+        const bool passed = !(p.highpass_cpp > 0.0) || rx * rx + ry * ry >= p.highpass_cpp * p.highpass_cpp;
+        if (kz2 >= 0 && passed) {
           const double ph = p.z_m * std::sqrt(kz2);
           v = make_float2(float(std::cos(ph) * scale), float(std::sin(ph) * scale));
         }

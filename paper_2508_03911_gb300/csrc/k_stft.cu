@@ -5,107 +5,28 @@
 //   M0 = sum_{k=klo..khi} P_k,  M1 = sum f_k P_k,  M2 = sum f_k^2 P_k  (f_k in kHz),
 //   M1N = M1 / M0 and M2N = sqrt(M2 / M0) in float64 (0 where M0 = 0).
 //
-// One CTA owns BT adjacent pixels and walks all windows of the launch. Their
-// samples sit in a shared-memory ring of T slots (frame o of the launch in slot
-// o mod T), so overlapping windows (S < T) load each propagated frame from HBM
-// once per launch: a window only brings in its S newest frames. The ring holds
-// the window circularly rotated; a rotation multiplies S_k by a unit phase and
-// leaves P_k, hence every moment, unchanged, so the FFT reads the ring as is.
-// The frame-to-time-axis transpose is this load: pixel-contiguous rows of the
-// time queue land batch-fastest in shared memory.
+// One CTA owns BT adjacent pixels and walks all windows of the launch, so
+// overlapping windows (S < T) load each propagated frame from HBM once per
+// launch: a window only brings in its S newest frames. The frame-to-time-axis
+// transpose is that load: pixel-contiguous rows of the time queue land in a
+// per-pixel ring in shared memory.
 #include "fft_dev.cuh"
 #include "hv_internal.h"
 #include "../../include/hv.h"
 
 namespace hv {
 
-template <int T>
-struct StftCfg {
-  static constexpr int BT = T <= 8 ? 32 : (T <= 256 ? 16 : 8);
-  static constexpr int NT = FftThreads<T, BT>::value;
-  static constexpr size_t SMEM = 2 * size_t(T) * BT * sizeof(float2) + 3 * NT * sizeof(float);
-};
-
-template <int T>
-struct MomentEpi {
-  uint32_t klo, khi;
-  float fscale;
-  float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-  __device__ __forceinline__ void operator()(int, int k, float2 v) {
-    if (uint32_t(k) >= klo && uint32_t(k) <= khi) {
-      const float P = fmaf(v.x, v.x, v.y * v.y);
-      const float f = float(k < T / 2 ? k : k - T) * fscale;
-      m0 += P;
-      m1 = fmaf(f, P, m1);
-      m2 = fmaf(f, f * P, m2);
-    }
-  }
-};
-
-template <int T>
-__global__ void __launch_bounds__(StftCfg<T>::NT) k_stft(StftArgs a) {
-  using C = StftCfg<T>;
-  constexpr int BT = C::BT, NT = C::NT;
-  extern __shared__ float2 smem[];
-  float2* ring = smem;
-  float2* work = smem + T * BT;
-  float* red = reinterpret_cast<float*>(work + T * BT);
-  const int tid = threadIdx.x;
-  const size_t HW = size_t(a.W) * a.H;
-  const uint32_t p0 = blockIdx.x * BT;
-  const float2* tq = static_cast<const float2*>(a.tq.base);
-
-  for (uint32_t w = 0; w < a.nwin; ++w) {
-    const uint32_t lo = w * a.S;
-    const uint32_t new_lo = (w == 0 || a.S >= uint32_t(T)) ? lo : lo + T - a.S;
-    const uint32_t nnew = lo + T - new_lo;
-    for (uint32_t idx = tid; idx < nnew * BT; idx += NT) {
-      const uint32_t b = idx % BT, o = new_lo + idx / BT;
-      const size_t slot = (size_t(a.tq.slot0) + o) % a.tq.cap;
-      ring[(o & (T - 1)) * BT + b] = tq[slot * HW + p0 + b];
-    }
-    __syncthreads();
-    MomentEpi<T> epi{a.klo, a.khi, a.fscale};
-    fft_stages<T, 1, -1, BT, NT, BT>(ring, BT, work, a.tw_t, epi);
-    red[tid] = epi.m0;
-    red[NT + tid] = epi.m1;
-    red[2 * NT + tid] = epi.m2;
-    __syncthreads();
-    if (tid < BT) {
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-      for (int t = tid; t < NT; t += BT) {
-        s0 += red[t];
-        s1 += red[NT + t];
-        s2 += red[2 * NT + t];
-      }
-      float* o = a.out + size_t(w) * a.nout * HW + p0 + tid;
-      int q = 0;
-      if (a.mask & HV_MOM_M0) o[HW * q++] = s0;
-      if (a.mask & HV_MOM_M1) o[HW * q++] = s1;
-      if (a.mask & HV_MOM_M2) o[HW * q++] = s2;
-      const double d0 = s0;
-      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(s1) / d0) : 0.f;
-      if (a.mask & HV_MOM_M2N) {
-        const double r = d0 > 0.0 ? double(s2) / d0 : 0.0;
-        o[HW * q++] = float(sqrt(r > 0.0 ? r : 0.0));
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------------------
-// Long windows (T >= 256): one warp per pixel.
-//
-// A CTA owns BT = 8 adjacent pixels, one warp each. Their samples sit in a
-// shared ring of RS = T + min(S, T) slots per pixel, so the S frames that the
-// next window adds are fetched with cp.async while the current window is
-// transformed (S < T: frame o of the launch in slot o mod RS; S >= T: windows
-// alternate between the two halves). The per-pixel FFT is a Stockham pass
-// sequence private to the warp (only __syncwarp between stages) through a
-// padded work buffer, index i at i + i/16, which keeps every stage's shared
-// accesses at two wavefronts. When the band lies below T/2 the last stage only
-// forms the lower half of its outputs.
+// Kernel layout: 8 warps per CTA; each pixel's FFT is carried by LP lanes of one
+// warp (LP = 32 for T >= 256, fewer for short windows, a warp then holding
+// 32 / LP pixels). A pixel's samples sit in a shared ring of RS = T + min(S, T)
+// slots, so the S frames that the next window adds are fetched with cp.async
+// while the current window is transformed (S < T: frame o of the launch in slot
+// o mod RS; S >= T: windows alternate between the two halves). The FFT is a
+// Stockham pass sequence private to the warp (only __syncwarp between stages)
+// through a padded work row, index i at i + i/16, which keeps the stage
+// accesses of a pixel at two wavefronts. When the band lies below T/2 the last
+// stage only forms the lower half of its outputs.
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -155,17 +76,31 @@ __device__ __forceinline__ void dft_lower(float2* v) {
   }
 }
 
-template <int T, int NS>
+// Lanes per pixel: one radix-8 (or smaller) butterfly per lane in the first
+// stage, at most 32; a warp then holds 32 / LP pixels.
+template <int T>
+struct WarpLayout {
+  static constexpr int NB1 = T / RadixOf<T>::value;
+  static constexpr int LP = NB1 < 32 ? NB1 : 32;
+  static constexpr int PW = 32 / LP;                                  // pixels per warp
+  static constexpr int BT = 8 * PW;                                   // pixels per CTA (8 warps)
+  static constexpr int WLD = ((T + T / 16 + 15) / 16) * 16 + 8;       // work row stride
+};
+
+// Stockham stages of one pixel's length-T forward FFT, carried by the LP lanes
+// of its group (jl = lane within the group): stage 1 reads the ring, later
+// stages the pixel's work row; the last stage feeds the moment accumulator.
+template <int T, int NS, int LP>
 __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, float2* work,
-                                         const float2* tw, int lane, MomAcc& acc, bool lower) {
+                                         const float2* tw, int jl, MomAcc& acc, bool lower) {
   constexpr int R = RadixOf<T / NS>::value;
   constexpr int NB = T / R;
-  static_assert(NB >= 32, "one warp per pixel needs >= 32 butterflies per stage");
-  constexpr int IT = NB / 32;
+  static_assert(NB % LP == 0, "lanes per pixel must divide the butterflies");
+  constexpr int IT = NB / LP;
   float2 v[IT][R];
 #pragma unroll
   for (int it = 0; it < IT; ++it) {
-    const int j = lane + 32 * it;
+    const int j = jl + LP * it;
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int t = j + m * NB;
@@ -191,14 +126,14 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
       for (int it = 0; it < IT; ++it) {
         dft_lower<R>(v[it]);
 #pragma unroll
-        for (int m = 0; m < R / 2; ++m) acc.add<T>(lane + 32 * it + m * NB, v[it][m]);
+        for (int m = 0; m < R / 2; ++m) acc.add<T>(jl + LP * it + m * NB, v[it][m]);
       }
     } else {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
         dft<R, -1>(v[it]);
 #pragma unroll
-        for (int m = 0; m < R; ++m) acc.add<T>(lane + 32 * it + m * NB, v[it][m]);
+        for (int m = 0; m < R; ++m) acc.add<T>(jl + LP * it + m * NB, v[it][m]);
       }
     }
   } else {
@@ -207,27 +142,27 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
     __syncwarp();
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-      const int j = lane + 32 * it;
+      const int j = jl + LP * it;
       const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
       for (int m = 0; m < R; ++m) work[wpad(base + m * NS)] = v[it][m];
     }
     __syncwarp();
-    warp_fft<T, NS * R>(ring, rbase, RS, work, tw, lane, acc, lower);
+    warp_fft<T, NS * R, LP>(ring, rbase, RS, work, tw, jl, acc, lower);
   }
 }
 
-constexpr int WARP_BT = 8;
-
 template <int T>
 __host__ __device__ constexpr size_t warp_smem(uint32_t S) {
-  return (size_t(WARP_BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T +
-          size_t(WARP_BT) * (T + T / 16)) * sizeof(float2);
+  using Lw = WarpLayout<T>;
+  return (size_t(Lw::BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T + size_t(8 * Lw::PW) * Lw::WLD) *
+         sizeof(float2);
 }
 
 template <int T>
-__global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
-  constexpr int BT = WARP_BT, NT = 32 * BT;
+__global__ void __launch_bounds__(256, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
+  using Lw = WarpLayout<T>;
+  constexpr int BT = Lw::BT, NT = 256, LP = Lw::LP, PW = Lw::PW;
   extern __shared__ float2 smem[];
   const int S = int(a.S);
   const int RS = T + (S < T ? S : T);
@@ -236,6 +171,8 @@ __global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(
   float2* tw = ring + BT * RLD;
   float2* work = tw + T;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pl = lane / LP, jl = lane % LP;  // pixel within the warp, lane within the pixel
+  const int px = warp * PW + pl;             // pixel within the CTA
   const size_t HW = size_t(a.W) * a.H;
   const uint32_t p0 = blockIdx.x * BT;
   const float2* tq = static_cast<const float2*>(a.tq.base);
@@ -282,15 +219,15 @@ __global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(
     if (w + 1 < a.nwin) fetch(int(w) + 1);
     const int rbase = S < T ? int((size_t(w) * S) % RS) : int(w & 1) * T;
     MomAcc acc{a.klo, a.khi, a.fscale, 0.f, 0.f, 0.f};
-    warp_fft<T, 1>(ring + warp * RLD, rbase, RS, work + warp * (T + T / 16), tw, lane, acc, lower);
+    warp_fft<T, 1, LP>(ring + px * RLD, rbase, RS, work + px * Lw::WLD, tw, jl, acc, lower);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = LP / 2; o > 0; o >>= 1) {  // reduce within the pixel's lane group
       acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
       acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
       acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
     }
-    if (lane == 0) {
-      float* o = a.out + size_t(w) * a.nout * HW + p0 + warp;
+    if (jl == 0) {
+      float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
       int q = 0;
       if (a.mask & HV_MOM_M0) o[HW * q++] = acc.m0;
       if (a.mask & HV_MOM_M1) o[HW * q++] = acc.m1;
@@ -307,25 +244,14 @@ __global__ void __launch_bounds__(32 * WARP_BT, (T <= 512 ? 3 : 1)) k_stft_warp(
 
 template <int T>
 static cudaError_t launch_warp(const StftArgs& a, cudaStream_t s) {
+  using Lw = WarpLayout<T>;
   const size_t hw = size_t(a.W) * a.H;
-  if (hw % WARP_BT) return cudaErrorInvalidValue;
+  if (hw % Lw::BT) return cudaErrorInvalidValue;
   const size_t smem = warp_smem<T>(a.S);
   cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
   if (e != cudaSuccess) return e;
-  k_stft_warp<T><<<unsigned(hw / WARP_BT), 32 * WARP_BT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int T>
-static cudaError_t launch_t(const StftArgs& a, cudaStream_t s) {
-  using C = StftCfg<T>;
-  const size_t hw = size_t(a.W) * a.H;
-  if (hw % C::BT) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_stft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(C::SMEM));
-  if (e != cudaSuccess) return e;
-  k_stft<T><<<unsigned(hw / C::BT), C::NT, C::SMEM, s>>>(a);
+  k_stft_warp<T><<<unsigned(hw / Lw::BT), 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -333,11 +259,11 @@ cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches) {
   if (a.nwin == 0) return cudaSuccess;
   ++*launches;
   switch (a.T) {
-    case 8: return launch_t<8>(a, s);
-    case 16: return launch_t<16>(a, s);
-    case 32: return launch_t<32>(a, s);
-    case 64: return launch_t<64>(a, s);
-    case 128: return launch_t<128>(a, s);
+    case 8: return launch_warp<8>(a, s);
+    case 16: return launch_warp<16>(a, s);
+    case 32: return launch_warp<32>(a, s);
+    case 64: return launch_warp<64>(a, s);
+    case 128: return launch_warp<128>(a, s);
     case 256: return launch_warp<256>(a, s);
     case 512: return launch_warp<512>(a, s);
     case 1024: return launch_warp<1024>(a, s);

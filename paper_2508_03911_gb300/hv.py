@@ -51,7 +51,8 @@ class hv_params(C.Structure):
                 ("band_lo_bin", C.c_uint32), ("band_hi_bin", C.c_uint32),
                 ("band_lo_hz", C.c_double), ("band_hi_hz", C.c_double),
                 ("pca_lo", C.c_uint32), ("pca_hi", C.c_uint32), ("precision", C.c_int32),
-                ("tuned", C.c_int32), ("spatial_chunk", C.c_uint32), ("spatial_kernel", C.c_uint32)]
+                ("tuned", C.c_int32), ("spatial_chunk", C.c_uint32), ("spatial_kernel", C.c_uint32),
+                ("highpass_cpp", C.c_double)]
 
 
 class hv_stats(C.Structure):
@@ -141,7 +142,7 @@ def hv_open(max_width, max_height, pixel_bits, queue_capacity_frames, device=0,
 def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pitch_y=None,
                 fftshift=1, temporal="stft", T=64, stride=None, fs=20000.0, band=(4, 28),
                 band_hz=None, moments=("M0",), pca=(2, 64), precision="fp32", tuned=0,
-                spatial_chunk=0, spatial_kernel="auto") -> hv_params:
+                spatial_chunk=0, spatial_kernel="auto", highpass=0.0) -> hv_params:
     p = hv_params()
     p.struct_size = C.sizeof(hv_params)
     p.width, p.height = width, height
@@ -163,6 +164,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.tuned = int(tuned)
     p.spatial_chunk = spatial_chunk
     p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2}[spatial_kernel]
+    p.highpass_cpp = highpass
     return p
 
 

@@ -26,7 +26,8 @@ def to_hv(p: dict, **extra) -> "hv.hv_params":
                           pitch=p["pitch_x_m"], pitch_y=p["pitch_y_m"], fftshift=p["fftshift"],
                           temporal=p["temporal"], T=p["T"], stride=p["stride"], fs=p["fs_hz"],
                           band=(p["band_lo_bin"], p["band_hi_bin"]), moments=p["moments"],
-                          pca=(p["pca_lo"], p["pca_hi"]), **extra)
+                          pca=(p["pca_lo"], p["pca_hi"]), highpass=p.get("highpass", 0.0),
+                          **extra)
 
 
 def images_from(out: np.ndarray, n_win: int, p: dict) -> np.ndarray:

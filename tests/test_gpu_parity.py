@@ -146,6 +146,22 @@ def test_autotuned_form_matches_oracle():
         r.close()
 
 
+@pytest.mark.parametrize("cut", [0.02, 0.1])
+def test_asp_highpass_filter(cut):
+    """High-pass spatial filter after ASP (folded into H on the GPU, applied as an
+    explicit FFT-mask-IFFT after propagation by the oracle)."""
+    fr = synth.random_frames(3, 64, 128, 12, seed=31)
+    p = oracle_params(spatial="asp", z_m=0.3, highpass=cut, temporal="none", T=1, stride=1,
+                      H=64, W=128)
+    img, _ = gpu_render(fr, p)
+    assert rel_l2(img, oracle_fields(fr, p)) <= FIELD_TOL
+    q = oracle_params(spatial="asp", z_m=0.3, highpass=cut, T=16, stride=8, band_lo_bin=1,
+                      band_hi_bin=7, moments=ALL_MOMENTS, H=64, W=128)
+    fr2 = synth.random_frames(40, 64, 128, 12, seed=32)
+    img2, _ = gpu_render(fr2, q)
+    check_images(img2, O.render(fr2, q))
+
+
 def test_fresnel_without_fftshift_and_negative_z():
     fr = synth.random_frames(2, 64, 128, 8, seed=5)
     for shift, z in ((0, 0.2), (1, -0.3)):

@@ -260,3 +260,20 @@ def test_tamura_constant_and_two_level():
     img[:4] = 1.0
     img[4:] = 3.0
     assert O.tamura(img) == pytest.approx(math.sqrt(1.0 / 2.0), rel=1e-12)
+
+
+# ---------------------------------------------------------------- high-pass
+
+def test_highpass_plane_waves_below_and_above_cutoff():
+    """A grid plane wave of radius r cycles/pixel survives the filter iff r >= cutoff."""
+    H, W = 16, 32
+    j = np.arange(W)[None, :]
+    l = np.arange(H)[:, None]
+    for m0, n0 in [(1, 0), (3, -2), (-6, 4), (0, 0)]:
+        u = np.exp(2j * math.pi * (m0 * j / W + n0 * l / H))
+        r = math.hypot(m0 / W, n0 / H)
+        for cut in (0.05, 0.15, 0.3):
+            got = O.highpass(u, cut)
+            expect = u if r >= cut else np.zeros_like(u)
+            assert np.max(np.abs(got - expect)) <= 1e-12
+    assert np.allclose(O.highpass(u, 0.0), u)
