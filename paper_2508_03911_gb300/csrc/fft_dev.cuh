@@ -48,7 +48,48 @@ __device__ __forceinline__ float2 tw16(float2 v) {
   else return make_float2(fmaf(v.x, c, -v.y * (DIR * s)), fmaf(v.y, c, v.x * (DIR * s)));
 }
 
-// In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8, 16}.
+// v * exp(DIR 2 pi i k / 32), k = 0..15 (k a compile-time constant after unrolling).
+template <int DIR>
+__device__ __forceinline__ float2 tw32(float2 v, int k) {
+  constexpr float C[16] = {
+      1.00000000000000000000f,
+      0.98078528040323043058f,
+      0.92387953251128673848f,
+      0.83146961230254523567f,
+      0.70710678118654757274f,
+      0.55557023301960228867f,
+      0.38268343236508983729f,
+      0.19509032201612833135f,
+      0.00000000000000006123f,
+      -0.19509032201612819257f,
+      -0.38268343236508972627f,
+      -0.55557023301960195560f,
+      -0.70710678118654746172f,
+      -0.83146961230254534669f,
+      -0.92387953251128673848f,
+      -0.98078528040323043058f};
+  constexpr float S[16] = {
+      0.00000000000000000000f,
+      0.19509032201612824808f,
+      0.38268343236508978178f,
+      0.55557023301960217765f,
+      0.70710678118654746172f,
+      0.83146961230254523567f,
+      0.92387953251128673848f,
+      0.98078528040323043058f,
+      1.00000000000000000000f,
+      0.98078528040323043058f,
+      0.92387953251128673848f,
+      0.83146961230254545772f,
+      0.70710678118654757274f,
+      0.55557023301960217765f,
+      0.38268343236508989280f,
+      0.19509032201612860891f};
+  const float c = C[k], s = DIR * S[k];
+  return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
+}
+
+// In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8, 16, 32}.
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) {
@@ -90,6 +131,22 @@ __device__ __forceinline__ void dft(float2* v) {
       v[k1 + 4] = b[1];
       v[k1 + 8] = b[2];
       v[k1 + 12] = b[3];
+    }
+  } else if constexpr (R == 32) {
+    // 32 = 2 x 16: DFT16 of even and odd samples, X_k = E_k + w32^k O_k, X_{k+16} = E_k - w32^k O_k
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<16, DIR>(e);
+    dft<16, DIR>(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 t = tw32<DIR>(o[k], k);
+      v[k] = cadd(e[k], t);
+      v[k + 16] = csub(e[k], t);
     }
   } else {
     static_assert(R == 8, "radix");

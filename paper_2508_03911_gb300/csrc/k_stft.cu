@@ -56,7 +56,20 @@ struct MomAcc {
 // Lower half X_0 .. X_{R/2-1} of an R-point forward DFT.
 template <int R>
 __device__ __forceinline__ void dft_lower(float2* v) {
-  if constexpr (R == 2) {
+  if constexpr (R == 32) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<16, -1>(e);
+    dft<16, -1>(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = cadd(e[k], tw32<-1>(o[k], k));
+  } else if constexpr (R == 16) {
+    dft<16, -1>(v);
+  } else if constexpr (R == 2) {
     v[0] = cadd(v[0], v[1]);
   } else if constexpr (R == 4) {
     float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
@@ -76,15 +89,31 @@ __device__ __forceinline__ void dft_lower(float2* v) {
   }
 }
 
-// Lanes per pixel: one radix-8 (or smaller) butterfly per lane in the first
-// stage, at most 32; a warp then holds 32 / LP pixels.
+// Radix plan of the time FFT: two register-heavy stages where the length allows
+// it (one exchange through shared memory), else radix 8, 4, 2.
+template <int T>
+struct WarpPlan {
+  static constexpr int R1 = T == 1024 ? 32 : (T >= 128 ? 16 : RadixOf<T>::value);
+  static constexpr int R2 = T == 128 ? 8 : (T == 256 ? 16 : (T >= 512 ? 32 : 0));
+  static constexpr int RMAX = R1 > R2 ? R1 : R2;
+  template <int NS>
+  __host__ __device__ static constexpr int radix() {
+    if constexpr (R2 != 0) return NS == 1 ? R1 : R2;
+    else return RadixOf<T / NS>::value;
+  }
+};
+
+// Lanes per pixel: every stage's butterflies spread evenly over LP lanes (at
+// most 32); a warp then holds 32 / LP pixels.
 template <int T>
 struct WarpLayout {
-  static constexpr int NB1 = T / RadixOf<T>::value;
-  static constexpr int LP = NB1 < 32 ? NB1 : 32;
+  static constexpr int NBMIN = T / WarpPlan<T>::RMAX;
+  static constexpr int LP = NBMIN < 32 ? NBMIN : 32;
   static constexpr int PW = 32 / LP;                                  // pixels per warp
-  static constexpr int BT = 8 * PW;                                   // pixels per CTA (8 warps)
-  static constexpr int WLD = ((T + T / 16 + 15) / 16) * 16 + 8;       // work row stride
+  static constexpr int NW = PW >= 8 ? 1 : 8 / PW;                     // warps per CTA
+  static constexpr int NT = 32 * NW;
+  static constexpr int BT = NW * PW;                                  // pixels per CTA (>= 8)
+  static constexpr int WLD = T + T / 16;                              // work row stride
 };
 
 // Stockham stages of one pixel's length-T forward FFT, carried by the LP lanes
@@ -93,7 +122,7 @@ struct WarpLayout {
 template <int T, int NS, int LP>
 __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, float2* work,
                                          const float2* tw, int jl, MomAcc& acc, bool lower) {
-  constexpr int R = RadixOf<T / NS>::value;
+  constexpr int R = WarpPlan<T>::template radix<NS>();
   constexpr int NB = T / R;
   static_assert(NB % LP == 0, "lanes per pixel must divide the butterflies");
   constexpr int IT = NB / LP;
@@ -114,7 +143,7 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
     }
     if constexpr (NS > 1) {
       // stage table: entry (m, jm) at (NS - R1) + (m - 1) NS + jm, contiguous in jm
-      constexpr int R1 = RadixOf<T>::value;
+      constexpr int R1 = WarpPlan<T>::R1;
       const int jm = j % NS;
 #pragma unroll
       for (int m = 1; m < R; ++m) v[it][m] = cmul(v[it][m], tw[(NS - R1) + (m - 1) * NS + jm]);
@@ -155,14 +184,14 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
 template <int T>
 __host__ __device__ constexpr size_t warp_smem(uint32_t S) {
   using Lw = WarpLayout<T>;
-  return (size_t(Lw::BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T + size_t(8 * Lw::PW) * Lw::WLD) *
+  return (size_t(Lw::BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T + size_t(Lw::BT) * Lw::WLD) *
          sizeof(float2);
 }
 
 template <int T>
-__global__ void __launch_bounds__(256, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
+__global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
   using Lw = WarpLayout<T>;
-  constexpr int BT = Lw::BT, NT = 256, LP = Lw::LP, PW = Lw::PW;
+  constexpr int BT = Lw::BT, NT = Lw::NT, LP = Lw::LP, PW = Lw::PW;
   extern __shared__ float2 smem[];
   const int S = int(a.S);
   const int RS = T + (S < T ? S : T);
@@ -200,11 +229,11 @@ __global__ void __launch_bounds__(256, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs 
   // per-stage twiddle tables, laid out so that a warp's reads are contiguous:
   // stage of span NS and radix R keeps w_T^{jm m T/(NS R)} at (NS - R1) + (m-1) NS + jm
   {
-    constexpr int R1 = RadixOf<T>::value;
+    constexpr int R1 = WarpPlan<T>::R1;
     int NS = R1;
     while (NS < T) {
       const int rem = T / NS;
-      const int R = rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2);
+      const int R = WarpPlan<T>::R2 != 0 ? WarpPlan<T>::R2 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
       for (int idx = tid; idx < (R - 1) * NS; idx += NT) {
         const int m = idx / NS + 1, jm = idx % NS;
         tw[(NS - R1) + idx] = a.tw_t[jm * m * (T / (NS * R))];
@@ -251,7 +280,7 @@ static cudaError_t launch_warp(const StftArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
   if (e != cudaSuccess) return e;
-  k_stft_warp<T><<<unsigned(hw / Lw::BT), 256, smem, s>>>(a);
+  k_stft_warp<T><<<unsigned(hw / Lw::BT), Lw::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
