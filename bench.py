@@ -537,9 +537,13 @@ def main():
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "form": "plain" if args.form == "plain" else "tuned",
-            "tuning": {"spatial_kernel": ["multipass", "cluster"][res["tuning"]["spatial_kernel"]],
+            "tuning": {"spatial_kernel": {1: "multipass", 2: "cluster", 3: "persistent"}.get(
+                           res["tuning"]["spatial_kernel"], "multipass"),
                        "frames_per_launch": res["tuning"]["spatial_chunk"],
-                       "candidate_us_per_frame": [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:6]]},
+                       "candidates_us_per_frame": dict(zip(
+                           ["mp16", "mp32", "mp64", "mp128", "mp256", "pp64", "pp128", "pp256",
+                            "pp512", "cluster"],
+                           [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:10]]))},
         }
         if plain is not None:
             line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),

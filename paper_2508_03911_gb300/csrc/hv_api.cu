@@ -41,7 +41,8 @@ struct hv_handle {
   float2* s2 = nullptr;
   size_t s1_bytes = 0, s2_bytes = 0;
   uint32_t chunk = 0;
-  int sp_cluster = 0;         // spatial kernel: 0 multi-pass, 1 whole-frame cluster
+  int sp_cluster = 0;         // 1: whole-frame cluster kernel
+  int sp_pp = 0;              // 1: persistent multi-pass kernels
   hv_tuning tuning{};
   float2* tw = nullptr;  // all twiddle tables, length 8..1024 packed
   float2* asp_ht = nullptr;
@@ -128,7 +129,13 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     why = "unknown spatial transform";
     return HV_ERR_ARG;
   }
-  if (p.spatial_kernel > HV_SK_CLUSTER) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.spatial_kernel > HV_SK_PERSISTENT) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.spatial_kernel == HV_SK_PERSISTENT &&
+      !(p.width >= 64 && p.width <= 512 && p.height >= 64 && p.height <= 512 &&
+        (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
+    why = "the persistent multi-pass kernels need sides in [64, 512] and ASP or Fresnel";
+    return HV_ERR_UNSUPPORTED;
+  }
   if (p.spatial_kernel == HV_SK_CLUSTER &&
       !(p.width == p.height && (p.width == 128 || p.width == 256 || p.width == 512) &&
         (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
@@ -382,9 +389,10 @@ hv_status apply_pending(hv_handle* h) {
   h->Q = Q;
   h->chunk = chunk;
   h->sp_cluster = p.spatial_kernel == HV_SK_CLUSTER ? 1 : 0;
+  h->sp_pp = p.spatial_kernel == HV_SK_PERSISTENT ? 1 : 0;
   h->tuning = hv_tuning{};
   h->tuning.spatial_chunk = chunk;
-  h->tuning.spatial_kernel = h->sp_cluster;
+  h->tuning.spatial_kernel = p.spatial_kernel == HV_SK_AUTO ? HV_SK_MULTIPASS : int32_t(p.spatial_kernel);
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
     s = tune_spatial(h);
     if (s != HV_OK) return s;
@@ -460,6 +468,7 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.chirp_x = h->chirp;
     sa.chirp_y = h->chirp + h->W;
     sa.use_cluster = h->sp_cluster;
+    sa.use_pp = h->sp_pp;
     int launches = 0;
     cudaError_t e = launch_spatial(sa, h->stream, &launches);
     h->st.kernel_launches += launches;
@@ -480,30 +489,36 @@ hv_status tune_spatial(hv_handle* h) {
     return HV_OK;
   }
   const size_t fbytes = size_t(h->W) * h->H * sizeof(float2);
-  const uint32_t n = std::min<uint32_t>(256, std::min(h->Q, h->cap));
+  const uint32_t n = std::min<uint32_t>(512, std::min(h->Q, h->cap));
   cudaEvent_t e0, e1;
   HV_CU(h, cudaEventCreate(&e0));
   HV_CU(h, cudaEventCreate(&e1));
-  static const uint32_t chunks[] = {16, 32, 64, 128, 256};
+  struct Cand { int kind; uint32_t chunk; };  // kind: 1 multi-pass, 3 persistent, 2 cluster
+  static const Cand cands[] = {{1, 16}, {1, 32}, {1, 64}, {1, 128}, {1, 256},
+                               {3, 64}, {3, 128}, {3, 256}, {3, 512}, {2, 0}};
+  SpatialArgs probe{};
+  probe.spatial = h->cur.spatial;
+  probe.W = h->W;
+  probe.H = h->H;
+  const bool pp_ok = spatial_pp_supported(probe);
   float best = 1e30f;
-  int best_cl = 0;
+  int best_kind = 1;
   uint32_t best_chunk = h->chunk;
-  const uint32_t saved_chunk = h->chunk;
-  const int ncand = 5 + (cluster_ok(h) ? 1 : 0);
-  for (int ci = 0; ci < ncand; ++ci) {
-    const bool cl = ci == 5;
-    uint32_t ch = cl ? n : std::min(chunks[ci], n);
-    if (!cl) {
+  for (int ci = 0; ci < 10; ++ci) {
+    const Cand c = cands[ci];
+    if (c.kind == 2 && !cluster_ok(h)) continue;
+    if (c.kind == 3 && !pp_ok) continue;
+    const uint32_t ch = c.kind == 2 ? n : std::min(c.chunk, n);
+    if (c.kind != 2) {
       const size_t need = size_t(ch) * fbytes;
-      hv_status st = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need);
-      if (st != HV_OK) continue;
-      if (h->cur.spatial == HV_SPATIAL_ASP) {
-        st = ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need);
-        if (st != HV_OK) continue;
-      }
+      if (ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need) != HV_OK) continue;
+      if (h->cur.spatial == HV_SPATIAL_ASP &&
+          ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need) != HV_OK)
+        continue;
     }
-    h->sp_cluster = cl ? 1 : 0;
-    h->chunk = ch;
+    h->sp_cluster = c.kind == 2;
+    h->sp_pp = c.kind == 3;
+    h->chunk = c.kind == 2 ? h->chunk : ch;
     const uint64_t before = h->st.frames_propagated;
     hv_status st = propagate(h, 0, n);  // warm-up
     if (st != HV_OK) return st;
@@ -518,18 +533,19 @@ hv_status tune_spatial(hv_handle* h) {
     HV_CU(h, cudaEventElapsedTime(&ms, e0, e1));
     h->st.frames_propagated = before;  // tuning work is not rendering work
     const float us_per_frame = 1000.f * ms / (2.f * n);
-    if (ci < 6) t.candidate_us_per_frame[ci] = us_per_frame;
+    t.candidate_us_per_frame[ci] = us_per_frame;
     if (us_per_frame < best) {
       best = us_per_frame;
-      best_cl = cl ? 1 : 0;
-      best_chunk = cl ? saved_chunk : ch;
+      best_kind = c.kind;
+      best_chunk = c.kind == 2 ? best_chunk : ch;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->sp_cluster = best_cl;
+  h->sp_cluster = best_kind == 2;
+  h->sp_pp = best_kind == 3;
   h->chunk = best_chunk;
-  t.spatial_kernel = best_cl;
+  t.spatial_kernel = best_kind == 2 ? HV_SK_CLUSTER : (best_kind == 3 ? HV_SK_PERSISTENT : HV_SK_MULTIPASS);
   t.spatial_chunk = best_chunk;
   t.tuned = 1;
   h->tuning = t;

@@ -32,9 +32,12 @@ struct SpatialArgs {
   const float2* chirp_x;// Fresnel chirp factors along x (length W), fftshift folded in
   const float2* chirp_y;// along y (length H)
   int use_cluster;      // 1: whole-frame cluster kernel when the size allows it
+  int use_pp;           // 1: persistent prefetching multi-pass kernels when the size allows
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);
+bool spatial_pp_supported(const SpatialArgs& a);
+cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launches);
 cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* launches);
 
 // STFT band moments of nwin windows (Sec. III-B.1), time-queue ring -> images.

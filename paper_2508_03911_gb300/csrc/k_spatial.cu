@@ -223,6 +223,7 @@ cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches) 
     return cudaGetLastError();
   }
   if (a.use_cluster && spatial_cluster_supported(a)) return launch_spatial_cluster(a, s, launches);
+  if (a.use_pp && spatial_pp_supported(a)) return launch_spatial_pp(a, s, launches);
   switch (a.H) {
     case 16: return spatial_w<16>(a, s, launches);
     case 32: return spatial_w<32>(a, s, launches);

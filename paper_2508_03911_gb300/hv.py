@@ -70,7 +70,7 @@ class hv_profile(C.Structure):
 
 class hv_tuning(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("spatial_kernel", C.c_int32), ("spatial_chunk", C.c_uint32),
-                ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 8)]
+                ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 12)]
 
 
 class HvError(RuntimeError):
@@ -163,7 +163,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.precision = PRECISION[precision]
     p.tuned = int(tuned)
     p.spatial_chunk = spatial_chunk
-    p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2}[spatial_kernel]
+    p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3}[spatial_kernel]
     p.highpass_cpp = highpass
     return p
 
