@@ -16,6 +16,7 @@ Prints one JSON line (rank 0). Multi-GPU: one independent stream per rank
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -28,9 +29,28 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import re  # noqa: E402
+
 import numpy as np  # noqa: E402
 
 from paper_2508_03911_gb300 import synth  # noqa: E402
+
+CSRC = os.path.join(ROOT, "paper_2508_03911_gb300", "csrc")
+
+
+def profiled_traffic(profile, sources, which=0):
+    """DRAM bytes per launch recorded in profiles/<profile> from an ncu capture, or
+    None when the profiled kernel's sources changed since (hash mismatch)."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        digest = hashlib.sha256(b"".join(open(os.path.join(CSRC, f), "rb").read()
+                                         for f in sources)).hexdigest()[:16]
+        h = re.search(r"source_sha256_16: ([0-9a-f]{16})", text).group(1)
+        vals = re.search(r"traffic_bytes_per_launch: ([^\n]+)", text).group(1)
+        nums = [int(v) for v in re.findall(r"(\d+)", vals)]
+        return nums[which] if h == digest else None
+    except Exception:
+        return None
 
 WORKLOADS = {
     "stream_fresnel_256_t512_s64": dict(
@@ -351,7 +371,9 @@ def roofline_pca(w, res, peaks, force=None):
         peak = (peaks or {}).get("bf16_tflops", 1906.8)
         tf = flops / t / 1e12
         return {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(tf / peak, 4), "traffic": None,
+                "frac": round(tf / peak, 4),
+                "traffic": (profiled_traffic("cov_tc_pca_512_t256_split_bf16.md", ["k_cov_tc.cu"])
+                            if w["precision"] == "split_bf16" and w["N"] == 512 and T == 256 else None),
                 "kernel": f"k_cov_tc (tcgen05 {w['precision']})",
                 "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
                 "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
@@ -403,9 +425,12 @@ def roofline(w, res, peaks):
     gbs = byts / (t / 1e3) / 1e9
     alu_frac = tflops / FP32_PEAK_TFLOPS
     hbm_frac = gbs / hbm
+    traffic = None
+    if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64:
+        traffic = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
     if alu_frac >= hbm_frac:
         return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
-                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": None, "kernel": kern,
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic, "kernel": kern,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "hbm_achieved_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4),
                 "stage_ms_per_render": {"spatial": round(t_sp, 4), "temporal": round(t_tm, 4)}}
