@@ -71,6 +71,13 @@ WORKLOADS = {
              "4..28, 102,400-frame stream per step",
         N=256, bits=8, spatial="asp", z=0.30, T=64, S=64, fs=20000.0, band=(4, 28),
         moments=("M0",), batch=4096, batches=25, pool=1024, scene="scene_tiny_asp_stft"),
+    "pca_fresnel_256_t32": dict(
+        desc="256x256 uint16 (12-bit) frames, Fresnel z=0.25 m, PCA over windows of T=32 "
+             "(stride 32, the paper's Table IV PCA 32/32 shape), energy over eigenvectors 2..16; "
+             "102,400-frame stream per step (25 batches of 4,096)",
+        N=256, bits=12, spatial="fresnel", z=0.25, T=32, S=32, fs=71400.0, band=(0, 0),
+        moments=(), temporal="pca", pca=(2, 16), batch=4096, batches=25, pool=1024,
+        scene="scene_stream_fresnel"),
     "pca_512_t256": dict(
         desc="512x512 uint16 (12-bit) frames, ASP z=0.40 m, PCA over windows of T=256 (stride 256): "
              "FP32 covariance, FP64 Jacobi, energy of the projection on eigenvectors 2..64; "
@@ -248,7 +255,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
                 e0.record(stream)
             st = r.push(pool_dev)
             assert st == hv.HV_OK, st
-            r.render(out)
+            while r.render(out) > 0:  # every complete window, as a caller would
+                pass
             if events is not None:
                 e1 = torch.cuda.Event(enable_timing=True)
                 e1.record(stream)
@@ -317,7 +325,12 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         nonlocal h2d, d2h
         for _ in range(w["batches"]):
             assert r2.push(host_pool) == hv.HV_OK
-            n = r2.render(out_host)
+            n = 0
+            while True:
+                k = r2.render(out_host)
+                n += k
+                if k == 0:
+                    break
             if count:
                 h2d += host_pool.numel() * host_pool.element_size()
                 d2h += n * wf * 4

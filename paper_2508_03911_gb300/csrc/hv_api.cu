@@ -60,6 +60,8 @@ struct hv_handle {
   size_t pca_ws_bytes = 0;
   PcaArgs pca{};
   bool pca_has_lam = false;
+  bool pca_batched = false;   // T <= 64 with FP32 covariance: many windows per launch
+  uint32_t pca_last_nwin = 1;
   // stage timing
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // triples: before spatial, after spatial, after temporal
@@ -281,7 +283,8 @@ hv_status apply_pending(hv_handle* h) {
   // time-transformation queue: T frames plus room for many windows per launch
   uint32_t Q = h->tq_req;
   if (Q == 0) {
-    const uint64_t target = uint64_t(d.T) + uint64_t(d.S) * 63;  // 64 windows per launch
+    // room for about 4096 new frames (and at least 64 windows) per temporal launch
+    const uint64_t target = uint64_t(d.T) + uint64_t(d.S) * std::max<uint64_t>(63, 4095 / d.S);
     const uint64_t cap_frames = std::max<uint64_t>(d.T, (size_t(4) << 30) / fbytes);
     Q = uint32_t(std::min<uint64_t>(target, cap_frames));
   }
@@ -303,17 +306,19 @@ hv_status apply_pending(hv_handle* h) {
   if (s != HV_OK) return s;
   if (p.temporal == HV_TEMPORAL_PCA) {
     const size_t hw = size_t(W) * H;
-    uint32_t nchunks = uint32_t(std::min<size_t>(64, std::max<size_t>(1, hw / 1024)));
+    const bool batched = d.T <= 64 && p.precision == HV_PREC_FP32;
+    const uint32_t NW = batched ? 128 : 1;  // windows per launch
+    uint32_t nchunks = uint32_t(std::min<size_t>(batched ? 8 : 64, std::max<size_t>(1, hw / 1024)));
     uint32_t chunk = uint32_t((hw + nchunks - 1) / nchunks);
     chunk = (chunk + 31) / 32 * 32;
     nchunks = uint32_t((hw + chunk - 1) / chunk);
     const uint32_t T = d.T, M = p.pca_hi - p.pca_lo + 1, Mpad = (M + 63) / 64 * 64;
-    const size_t b_part = pca_partials_floats2(T, nchunks) * sizeof(float2);
+    const size_t b_part = pca_partials_floats2(T, nchunks) * sizeof(float2) * NW;
     const size_t b_mat = size_t(T) * T * sizeof(double2);
     const size_t b_rot = size_t(T / 2) * 4 * sizeof(double);
     const size_t b_cnt = 64;
-    const size_t b_lam = size_t(T) * sizeof(double);
-    const size_t b_vs = size_t(T) * Mpad * sizeof(float2);
+    const size_t b_lam = size_t(T) * sizeof(double) * NW;
+    const size_t b_vs = size_t(T) * Mpad * sizeof(float2) * NW;
     // tensor-core covariance tiles and chunks (about one CTA per SM)
     uint8_t ti[32] = {}, tj[32] = {};
     uint32_t ntiles = 0, tc_nchunks = 0, tc_chunk = 0;
@@ -330,7 +335,7 @@ hv_status apply_pending(hv_handle* h) {
       b_tc = cov_tc_partials_floats(ntiles, tc_nchunks) * sizeof(float);
     }
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t total = al(b_part) + 2 * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs) + al(b_tc);
+    const size_t total = al(b_part) + (NW + 1) * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs) + al(b_tc);
     s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
     if (s != HV_OK) return s;
     char* b = static_cast<char*>(h->pca_ws);
@@ -353,7 +358,7 @@ hv_status apply_pending(hv_handle* h) {
     a.partials = reinterpret_cast<float2*>(b);
     b += al(b_part);
     a.C = reinterpret_cast<double2*>(b);
-    b += al(b_mat);
+    b += NW * al(b_mat);
     a.V = reinterpret_cast<double2*>(b);
     b += al(b_mat);
     a.rot = reinterpret_cast<double*>(b);
@@ -373,6 +378,9 @@ hv_status apply_pending(hv_handle* h) {
     std::memcpy(a.tc_tile_i, ti, sizeof(ti));
     std::memcpy(a.tc_tile_j, tj, sizeof(tj));
     a.err = a.counters + 3;
+    a.nwin = 1;
+    a.wstride = d.S;
+    h->pca_batched = batched;
     h->pca_has_lam = false;
   }
   h->cur = p;
@@ -734,8 +742,12 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
     e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
   } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
     e = cudaSuccess;
-    for (uint32_t w = 0; w < nw && e == cudaSuccess; ++w) {
+    for (uint32_t w = 0; w < nw && e == cudaSuccess;) {
+      const uint32_t k = h->pca_batched ? std::min<uint32_t>(nw - w, 128) : 1;
+      h->pca.nwin = k;
+      h->pca.wstride = S;
       h->pca.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
+      h->pca_last_nwin = k;
       cudaEvent_t* ev = nullptr;
       if (h->prof) {
         if (h->pca_ev_used + 4 > h->pca_ev.size()) {
@@ -746,6 +758,7 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
         h->pca_ev_used += 4;
       }
       e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
+      w += k;
       if (h->prof && e == cudaSuccess) {
         unsigned sw = 0;  // sweeps of this window (synchronous read; profiling only)
         HV_CU(h, cudaMemcpyAsync(&sw, h->pca.counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
@@ -796,7 +809,8 @@ hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n) {
   if (!h->pca_has_lam || h->cur.temporal != HV_TEMPORAL_PCA) return HV_ERR_STATE;
   if (n > h->T) return HV_ERR_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return HV_ERR_CUDA;
-  if (cudaMemcpyAsync(out, h->pca.lam, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  const double* lam = h->pca.lam + size_t(h->pca_last_nwin - 1) * h->T;
+  if (cudaMemcpyAsync(out, lam, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return HV_ERR_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HV_ERR_CUDA;
   return HV_OK;

@@ -57,20 +57,22 @@ cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 // PCA of one window (Sec. III-B.1), time-queue ring -> energy image.
 struct PcaArgs {
   uint32_t W, H, T;
-  RingRef tq;           // slot0 = slot of the window's first frame
+  RingRef tq;           // slot0 = slot of the first window's first frame
+  uint32_t nwin;        // windows in this launch (batched only for T <= 64, else 1)
+  uint32_t wstride;     // frames between window starts (S)
   uint32_t chunk;       // pixels per covariance CTA
   uint32_t nchunks;
   uint32_t lo, M, Mpad; // sub-basis: ranks lo .. lo+M-1 (1-based), padded to 64
   int max_sweeps;
   double tol, tol_abs;  // Jacobi skip thresholds (relative, and x largest diagonal)
-  float2* partials;     // nchunks x upper tiles x TS x TS
-  double2* C;           // T x T
-  double2* V;           // T x T
+  float2* partials;     // nwin x nchunks x upper tiles x TS x TS
+  double2* C;           // nwin x T x T
+  double2* V;           // T x T (large-T path)
   double* rot;          // T/2 rotations (4 doubles each)
   unsigned* counters;   // 4 counters followed by one double (largest diagonal)
   double* cmax;         // = (double*)(counters + 4)
-  double* lam;          // T eigenvalues, descending
-  float2* Vs;           // T x Mpad sub-basis
+  double* lam;          // nwin x T eigenvalues, descending
+  float2* Vs;           // nwin x T x Mpad sub-basis
   // tensor-core covariance (precision BF16 / split-BF16)
   int precision;        // HV_PREC_*
   float* tc_partials;   // nchunks x ntiles x 128 x 256 float

@@ -34,6 +34,11 @@ __device__ __forceinline__ const float2* frame_ptr(const RingRef& r, uint32_t t,
   return static_cast<const float2*>(r.base) + ((size_t(r.slot0) + t) % r.cap) * hw;
 }
 
+// Frame t of window w (windows start S frames apart).
+__device__ __forceinline__ const float2* win_frame(const PcaArgs& a, uint32_t w, uint32_t t, size_t hw) {
+  return frame_ptr(a.tq, w * a.wstride + t, hw);
+}
+
 // grid (n_upper_tiles, n_chunks), 256 threads; thread (ty, tx) owns rows
 // a0 + ty + 16 i and columns b0 + tx + 16 j of the TS x TS tile (TS = min(T, 64)).
 __global__ void __launch_bounds__(256) k_cov_fp32(PcaArgs a) {
@@ -63,8 +68,8 @@ __global__ void __launch_bounds__(256) k_cov_fp32(PcaArgs a) {
       const size_t p = p0 + k;
       float2 va = make_float2(0.f, 0.f), vb = va;
       if (p < p_end) {
-        va = frame_ptr(a.tq, ta * TS + f, hw)[p];
-        vb = frame_ptr(a.tq, tb * TS + f, hw)[p];
+        va = win_frame(a, blockIdx.z, ta * TS + f, hw)[p];
+        vb = win_frame(a, blockIdx.z, tb * TS + f, hw)[p];
       }
       As[k][f] = va;
       Bs[k][f] = vb;
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(256) k_cov_fp32(PcaArgs a) {
     __syncthreads();
   }
   const int ntile_up = nT * (nT + 1) / 2;
-  float2* out = a.partials + (size_t(blockIdx.y) * ntile_up + blockIdx.x) * TS * TS;
+  float2* out = a.partials + ((size_t(blockIdx.z) * a.nchunks + blockIdx.y) * ntile_up + blockIdx.x) * TS * TS;
   for (int i = 0; i < nI; ++i)
     for (int j = 0; j < nI; ++j) out[(ty + 16 * i) * TS + tx + 16 * j] = acc[i][j];
 }
@@ -99,16 +104,19 @@ __global__ void __launch_bounds__(256) k_cov_fp32(PcaArgs a) {
 // C[a][b] = sum over chunks (float64), mirrored to the lower triangle; V = I.
 __global__ void k_cov_reduce(PcaArgs a) {
   const int T = a.T, TS = T < COV_TS ? T : COV_TS, nT = T / TS, ntile_up = nT * (nT + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T * T; e += gridDim.x * blockDim.x) {
+  for (int ew = blockIdx.x * blockDim.x + threadIdx.x; ew < int(a.nwin) * T * T; ew += gridDim.x * blockDim.x) {
+    const int w = ew / (T * T), e = ew % (T * T);
     const int r = e / T, c = e % T;
-    a.V[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    double2* Cw = a.C + size_t(w) * T * T;
+    const float2* Pw = a.partials + size_t(w) * a.nchunks * ntile_up * TS * TS;
+    if (w == 0) a.V[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
     if (r > c) continue;
     const int ta = r / TS, tb = c / TS;
     const int up = ta * nT - ta * (ta - 1) / 2 + (tb - ta);
     const int off = (r % TS) * TS + (c % TS);
     double sx = 0.0, sy = 0.0;
     for (uint32_t k = 0; k < a.nchunks; ++k) {
-      const float2 v = a.partials[(size_t(k) * ntile_up + up) * TS * TS + off];
+      const float2 v = Pw[(size_t(k) * ntile_up + up) * TS * TS + off];
       sx += v.x;
       sy += v.y;
     }
@@ -118,8 +126,8 @@ __global__ void k_cov_reduce(PcaArgs a) {
       atomicMax(reinterpret_cast<unsigned long long*>(a.cmax),
                 static_cast<unsigned long long>(__double_as_longlong(sx > 0.0 ? sx : 0.0)));
     }
-    a.C[r * T + c] = make_double2(sx, sy);
-    a.C[c * T + r] = make_double2(sx, -sy);
+    Cw[r * T + c] = make_double2(sx, sy);
+    Cw[c * T + r] = make_double2(sx, -sy);
   }
 }
 
@@ -141,6 +149,63 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// Rotation J that zeroes the off-diagonal of the Hermitian 2 x 2 block
+// [[al, g], [conj(g), be]] (J = P R, P = diag(1, conj(g)/|g|), R a real rotation
+// with tan(2 theta) = 2|g| / (al - be)); identity when |g| is below either bound.
+__device__ __forceinline__ bool jacobi_rot(double al, double be, double2 g, double tol, double floor_abs,
+                                           Rot& q) {
+  const double ag = sqrt(g.x * g.x + g.y * g.y);
+  q = Rot{1.0, 0.0, 1.0, 0.0};
+  if (!(ag > tol * sqrt(fabs(al * be)) && ag > floor_abs && ag > 0.0)) return false;
+  const double zeta = (be - al) / (2.0 * ag);
+  const double t = -(zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  q = Rot{c, t * c, g.x / ag, g.y / ag};
+  return true;
+}
+
+// B <- Jp^H B Jq for the 2 x 2 block of rows (i0, i1) and columns (j0, j1) of the
+// row-major T x T matrix C; `own` marks the pair's own diagonal block.
+__device__ __forceinline__ void jacobi_block(double2* C, int T, int i0, int i1, int j0, int j1, const Rot& Jp,
+                                             const Rot& Jq, bool own) {
+  const double2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1];
+  const double2 b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
+  const double2 qph = make_double2(Jq.px, -Jq.py);  // conj(ph_q)
+  const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
+  const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
+  const double2 m00 = zadd(make_double2(b00.x * Jq.c, b00.y * Jq.c), zmul(b01, q10));
+  const double2 m01 = zadd(make_double2(-b00.x * Jq.s, -b00.y * Jq.s), zmul(b01, q11));
+  const double2 m10 = zadd(make_double2(b10.x * Jq.c, b10.y * Jq.c), zmul(b11, q10));
+  const double2 m11 = zadd(make_double2(-b10.x * Jq.s, -b10.y * Jq.s), zmul(b11, q11));
+  const double2 ph = make_double2(Jp.px, Jp.py);  // Jp^H = [[c, ph s], [-s, ph c]]
+  const double2 p01 = make_double2(ph.x * Jp.s, ph.y * Jp.s);
+  const double2 p11 = make_double2(ph.x * Jp.c, ph.y * Jp.c);
+  double2 c00 = zadd(make_double2(Jp.c * m00.x, Jp.c * m00.y), zmul(p01, m10));
+  double2 c01 = zadd(make_double2(Jp.c * m01.x, Jp.c * m01.y), zmul(p01, m11));
+  double2 c10 = zadd(make_double2(-Jp.s * m00.x, -Jp.s * m00.y), zmul(p11, m10));
+  double2 c11 = zadd(make_double2(-Jp.s * m01.x, -Jp.s * m01.y), zmul(p11, m11));
+  if (own) {  // exactly diagonal, real diagonal
+    c01 = make_double2(0.0, 0.0);
+    c10 = make_double2(0.0, 0.0);
+    c00.y = 0.0;
+    c11.y = 0.0;
+  }
+  C[i0 * T + j0] = c00;
+  C[i0 * T + j1] = c01;
+  C[i1 * T + j0] = c10;
+  C[i1 * T + j1] = c11;
+}
+
+// Columns (j0, j1) of row `row` of V times Jq.
+__device__ __forceinline__ void jacobi_vrow(double2* V, int T, int row, int j0, int j1, const Rot& Jq) {
+  const double2 v0 = V[row * T + j0], v1 = V[row * T + j1];
+  const double2 qph = make_double2(Jq.px, -Jq.py);
+  const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
+  const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
+  V[row * T + j0] = zadd(make_double2(v0.x * Jq.c, v0.y * Jq.c), zmul(v1, q10));
+  V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
+}
+
 __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int T = a.T, NP = T / 2;
@@ -153,18 +218,9 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
       // phase 1: rotation of each pair from the current C
       for (size_t p = gtid; p < size_t(NP); p += gsz) {
         const int i = rr_elem(int(p), r, T), j = rr_elem(T - 1 - int(p), r, T);
-        const double al = a.C[i * T + i].x, be = a.C[j * T + j].x;
-        const double2 g = a.C[i * T + j];
-        const double ag = sqrt(g.x * g.x + g.y * g.y);
-        Rot q{1.0, 0.0, 1.0, 0.0};
-        const double floor_abs = a.tol_abs * (*a.cmax);
-        if (ag > a.tol * sqrt(fabs(al * be)) && ag > floor_abs && ag > 0.0) {
-          const double zeta = (be - al) / (2.0 * ag);
-          const double t = -(zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          q = Rot{c, t * c, g.x / ag, g.y / ag};
+        Rot q;
+        if (jacobi_rot(a.C[i * T + i].x, a.C[j * T + j].x, a.C[i * T + j], a.tol, a.tol_abs * a.cmax[0], q))
           atomicAdd(&a.counters[(sweep & 1) ^ 1], 1u);
-        }
         rot[p] = q;
       }
       grid.sync();
@@ -176,48 +232,14 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
           const Rot& Jp = rot[p];
           const Rot& Jq = rot[q];
           if (Jp.s == 0.0 && Jq.s == 0.0) continue;
-          const int i0 = rr_elem(p, r, T), i1 = rr_elem(T - 1 - p, r, T);
-          const int j0 = rr_elem(q, r, T), j1 = rr_elem(T - 1 - q, r, T);
-          const double2 b00 = a.C[i0 * T + j0], b01 = a.C[i0 * T + j1];
-          const double2 b10 = a.C[i1 * T + j0], b11 = a.C[i1 * T + j1];
-          // M = B Jq
-          const double2 qph = make_double2(Jq.px, -Jq.py);  // conj(ph_q)
-          const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
-          const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
-          const double2 m00 = zadd(make_double2(b00.x * Jq.c, b00.y * Jq.c), zmul(b01, q10));
-          const double2 m01 = zadd(make_double2(-b00.x * Jq.s, -b00.y * Jq.s), zmul(b01, q11));
-          const double2 m10 = zadd(make_double2(b10.x * Jq.c, b10.y * Jq.c), zmul(b11, q10));
-          const double2 m11 = zadd(make_double2(-b10.x * Jq.s, -b10.y * Jq.s), zmul(b11, q11));
-          // Jp^H = [[c, ph s], [-s, ph c]]
-          const double2 ph = make_double2(Jp.px, Jp.py);
-          const double2 p01 = make_double2(ph.x * Jp.s, ph.y * Jp.s);
-          const double2 p11 = make_double2(ph.x * Jp.c, ph.y * Jp.c);
-          double2 c00 = zadd(make_double2(Jp.c * m00.x, Jp.c * m00.y), zmul(p01, m10));
-          double2 c01 = zadd(make_double2(Jp.c * m01.x, Jp.c * m01.y), zmul(p01, m11));
-          double2 c10 = zadd(make_double2(-Jp.s * m00.x, -Jp.s * m00.y), zmul(p11, m10));
-          double2 c11 = zadd(make_double2(-Jp.s * m01.x, -Jp.s * m01.y), zmul(p11, m11));
-          if (p == q) {  // the pair's own block: exactly diagonal, real diagonal
-            c01 = make_double2(0.0, 0.0);
-            c10 = make_double2(0.0, 0.0);
-            c00.y = 0.0;
-            c11.y = 0.0;
-          }
-          a.C[i0 * T + j0] = c00;
-          a.C[i0 * T + j1] = c01;
-          a.C[i1 * T + j0] = c10;
-          a.C[i1 * T + j1] = c11;
+          jacobi_block(a.C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
+                       rr_elem(T - 1 - q, r, T), Jp, Jq, p == q);
         } else {
           const size_t f = e - nblk;
           const int row = int(f / NP), q = int(f % NP);
           const Rot& Jq = rot[q];
           if (Jq.s == 0.0) continue;
-          const int j0 = rr_elem(q, r, T), j1 = rr_elem(T - 1 - q, r, T);
-          const double2 v0 = a.V[row * T + j0], v1 = a.V[row * T + j1];
-          const double2 qph = make_double2(Jq.px, -Jq.py);
-          const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
-          const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
-          a.V[row * T + j0] = zadd(make_double2(v0.x * Jq.c, v0.y * Jq.c), zmul(v1, q10));
-          a.V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
+          jacobi_vrow(a.V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), Jq);
         }
       }
       grid.sync();
@@ -253,6 +275,80 @@ __global__ void k_pca_select(PcaArgs a) {
     if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
 }
 
+// Short windows (T <= 64): one CTA per window, C and V in shared memory, the same
+// float64 cyclic Jacobi with CTA barriers, then the selection of the sub-basis.
+template <int T>
+__global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
+  extern __shared__ double2 jsm[];
+  double2* C = jsm;
+  double2* V = jsm + T * T;
+  __shared__ Rot rot[T / 2];
+  __shared__ unsigned cnt;
+  __shared__ double cmax;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  constexpr int NP = T / 2;
+  const double2* Cg = a.C + size_t(w) * T * T;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    C[e] = Cg[e];
+    V[e] = make_double2(e / T == e % T ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < T; ++i) m = fmax(m, C[i * T + i].x);
+    cmax = m;
+  }
+  int sweeps = 0;
+  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    if (tid == 0) cnt = 0;
+    __syncthreads();
+    for (int r = 0; r < T - 1; ++r) {
+      if (tid < NP) {
+        const int i = rr_elem(tid, r, T), j = rr_elem(T - 1 - tid, r, T);
+        Rot q;
+        if (jacobi_rot(C[i * T + i].x, C[j * T + j].x, C[i * T + j], a.tol, a.tol_abs * cmax, q)) atomicAdd(&cnt, 1u);
+        rot[tid] = q;
+      }
+      __syncthreads();
+      for (int e = tid; e < NP * NP + T * NP; e += blockDim.x) {
+        if (e < NP * NP) {
+          const int p = e / NP, q = e % NP;
+          if (rot[p].s == 0.0 && rot[q].s == 0.0) continue;
+          jacobi_block(C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
+                       rr_elem(T - 1 - q, r, T), rot[p], rot[q], p == q);
+        } else {
+          const int f = e - NP * NP, row = f / NP, q = f % NP;
+          if (rot[q].s == 0.0) continue;
+          jacobi_vrow(V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[q]);
+        }
+      }
+      __syncthreads();
+    }
+    sweeps = sweep + 1;
+    const unsigned n = cnt;  // every thread reads it after the last barrier
+    __syncthreads();
+    if (n == 0) break;
+  }
+  if (tid == 0 && w == int(a.nwin) - 1) a.counters[2] = unsigned(sweeps);
+  // rank (descending, ties by index), eigenvalues and the sub-basis lo..hi
+  double* lam = a.lam + size_t(w) * T;
+  float2* Vs = a.Vs + size_t(w) * T * a.Mpad;
+  for (int i = tid; i < T; i += blockDim.x) {
+    const double li = C[i * T + i].x;
+    int rank = 0;
+    for (int j = 0; j < T; ++j) {
+      const double lj = C[j * T + j].x;
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    lam[rank] = li;
+    const int m = rank - int(a.lo - 1);
+    if (m >= 0 && m < int(a.M))
+      for (int t = 0; t < T; ++t) Vs[size_t(t) * a.Mpad + m] = make_float2(float(V[t * T + i].x), float(V[t * T + i].y));
+  }
+  for (int e = tid; e < T * int(a.Mpad); e += blockDim.x)
+    if (e % int(a.Mpad) >= int(a.M)) Vs[e] = make_float2(0.f, 0.f);
+}
+
 // ---------------------------------------------------------------- projection
 
 constexpr int PRJ_PB = 64;  // pixels per CTA
@@ -276,11 +372,11 @@ __global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
     for (int t0 = 0; t0 < a.T; t0 += PRJ_KS) {
       for (int e = tid; e < PRJ_KS * PRJ_PB; e += 256) {
         const int k = e / PRJ_PB, px = e % PRJ_PB;
-        Xs[k][px] = frame_ptr(a.tq, t0 + k, hw)[pb + px];
+        Xs[k][px] = win_frame(a, blockIdx.y, t0 + k, hw)[pb + px];
       }
       for (int e = tid; e < PRJ_KS * PRJ_MB; e += 256) {
         const int k = e / PRJ_MB, m = e % PRJ_MB;
-        Vss[k][m] = a.Vs[size_t(t0 + k) * a.Mpad + m0 + m];
+        Vss[k][m] = a.Vs[(size_t(blockIdx.y) * a.T + t0 + k) * a.Mpad + m0 + m];
       }
       __syncthreads();
 #pragma unroll 4
@@ -311,7 +407,7 @@ __global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
   if (tid < PRJ_PB) {
     float s = 0.f;
     for (int g = 0; g < 16; ++g) s += Er[g][tid];
-    out[pb + tid] = s;
+    out[size_t(blockIdx.y) * hw + pb + tid] = s;
   }
 }
 
@@ -325,7 +421,7 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
   if (a.T % TS || TS % 16 || hw % PRJ_PB || a.T % PRJ_KS) return cudaErrorInvalidValue;
   const int nT = a.T / TS;
-  const dim3 g1(nT * (nT + 1) / 2, a.nchunks);
+  const dim3 g1(nT * (nT + 1) / 2, a.nchunks, a.nwin);
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
   if (e0 != cudaSuccess) return e0;
   if (ev) cudaEventRecord(ev[0], s);
@@ -351,7 +447,7 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   if (e != cudaSuccess) return e;
   k_pca_select<<<1, 256, 0, s>>>(a);
   if (ev) cudaEventRecord(ev[2], s);
-  k_project<<<unsigned(hw / PRJ_PB), 256, 0, s>>>(a, out);
+  k_project<<<dim3(unsigned(hw / PRJ_PB), 1), 256, 0, s>>>(a, out);
   if (ev) cudaEventRecord(ev[3], s);
   *launches += 3;
   return cudaGetLastError();

@@ -29,7 +29,12 @@ def gpu_pca(frames, p):
         assert wf == H * W
         out = torch.zeros(n * wf, dtype=torch.float32, device="cuda")
         assert r.push(to_device(frames)) == hv.HV_OK
-        nw = r.render(out)
+        nw = 0
+        while True:
+            k = r.render(out[nw * wf:])
+            nw += k
+            if k == 0:
+                break
         torch.cuda.synchronize()
         lam = hv.hv_pca_eigenvalues(r.h, p["T"])
         return out.cpu().numpy()[: nw * wf].reshape(nw, H, W), lam
@@ -108,6 +113,22 @@ def pca_scene_window():
 
 @pytest.mark.parametrize("precision,tol", [("fp32", IMAGE_TOL), ("split_bf16", IMAGE_TOL),
                                            ("bf16", 5e-2)])
+def test_pca_batched_many_windows():
+    """Short windows are batched: all windows of one render in one launch per kernel
+    (one CTA per window for the FP64 Jacobi), overlapping and non-overlapping."""
+    for (H, W, T, S, n) in [(64, 64, 32, 32, 32 * 40 + 5), (32, 32, 64, 16, 64 + 16 * 70)]:
+        fr = synth.random_frames(n, H, W, 12, seed=n)
+        p = oracle_params(spatial="fresnel", z_m=0.3, temporal="pca", T=T, stride=S, pca_lo=2,
+                          pca_hi=12, H=H, W=W)
+        img, lam = gpu_pca(fr, p)
+        ref = oracle_windows(fr, p)
+        assert img.shape[0] == len(ref) > 32
+        for w in range(len(ref)):
+            e = rel_l2(img[w], ref[w]["E"])
+            assert e <= IMAGE_TOL, (w, e)
+        assert np.max(np.abs(lam - ref[-1]["lam"])) <= LAM_TOL * ref[-1]["lam"][0]
+
+
 def test_pca_scene_window_full_size(pca_scene_window, precision, tol):
     """One window of the PCA workload: 512x512 12-bit frames, ASP z = 0.40 m,
     T = 256, energy over eigenvectors 2..64 (every pixel), per covariance precision."""
