@@ -111,8 +111,6 @@ def pca_scene_window():
     return fr, p, oracle_windows(fr, p)[0]
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", IMAGE_TOL), ("split_bf16", IMAGE_TOL),
-                                           ("bf16", 5e-2)])
 def test_pca_batched_many_windows():
     """Short windows are batched: all windows of one render in one launch per kernel
     (one CTA per window for the FP64 Jacobi), overlapping and non-overlapping."""
@@ -129,6 +127,8 @@ def test_pca_batched_many_windows():
         assert np.max(np.abs(lam - ref[-1]["lam"])) <= LAM_TOL * ref[-1]["lam"][0]
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", IMAGE_TOL), ("split_bf16", IMAGE_TOL),
+                                           ("bf16", 5e-2)])
 def test_pca_scene_window_full_size(pca_scene_window, precision, tol):
     """One window of the PCA workload: 512x512 12-bit frames, ASP z = 0.40 m,
     T = 256, energy over eigenvectors 2..64 (every pixel), per covariance precision."""
