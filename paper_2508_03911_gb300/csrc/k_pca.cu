@@ -6,13 +6,17 @@
 //   C = V diag(lam) V^H            (cyclic complex Jacobi, float64)
 //   E(p) = sum_{j = lo..hi} |(X v_j)_p|^2, eigenvectors ranked by descending lam.
 //
-// Kernels (one window at a time, all on the handle's stream):
+// Kernels (all on the handle's stream; windows of T <= 64 frames are batched,
+// blockIdx.z / blockIdx.y / blockIdx.x selecting the window where noted):
 //   k_cov_fp32     split-K covariance: each CTA multiplies a 64 x 64 tile of the
 //                  upper triangle over one pixel chunk (float32 FMA), partials
 //                  written per chunk (deterministic, no atomics)
 //   k_cov_reduce   sums the chunk partials in float64 -> C (full Hermitian), V = I
 //   k_jacobi       cooperative launch over all SMs: parallel cyclic (round-robin)
 //                  two-sided Jacobi in float64 until a sweep makes no rotation
+//                  (T > 64, one window)
+//   k_jacobi_small the same Jacobi for T <= 64, one CTA per window, C and V in
+//                  shared memory, selection of the sub-basis fused
 //   k_pca_select   ranks eigenvalues (descending) and gathers the sub-basis
 //   k_project      Y = X V_s for 64-pixel tiles and E(p) = sum_j |Y_pj|^2
 #include <cooperative_groups.h>
@@ -411,6 +415,15 @@ __global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
   }
 }
 
+template <int T>
+static cudaError_t launch_jacobi_small(const PcaArgs& a, cudaStream_t s) {
+  const size_t smem = size_t(2) * T * T * sizeof(double2);  // C and V
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k_jacobi_small<T><<<a.nwin, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 size_t pca_partials_floats2(uint32_t T, uint32_t nchunks) {
   const uint32_t TS = T < uint32_t(COV_TS) ? T : COV_TS, nT = T / TS;
   return size_t(nchunks) * (nT * (nT + 1) / 2) * TS * TS;
@@ -436,20 +449,29 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   if (ev) cudaEventRecord(ev[1], s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0);
+  if (a.T == 32) {
+    e = launch_jacobi_small<32>(a, s);
+  } else if (a.T == 64) {
+    e = launch_jacobi_small<64>(a, s);
+  } else {
+    if (a.nwin != 1) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    k_pca_select<<<1, 256, 0, s>>>(a);
+    ++*launches;
+  }
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  void* args[] = {&a};
-  e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), args, 0, s);
-  if (e != cudaSuccess) return e;
-  k_pca_select<<<1, 256, 0, s>>>(a);
   if (ev) cudaEventRecord(ev[2], s);
-  k_project<<<dim3(unsigned(hw / PRJ_PB), 1), 256, 0, s>>>(a, out);
+  k_project<<<dim3(unsigned(hw / PRJ_PB), a.nwin), 256, 0, s>>>(a, out);
   if (ev) cudaEventRecord(ev[3], s);
-  *launches += 3;
+  *launches += 2;
   return cudaGetLastError();
 }
 
