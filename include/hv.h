@@ -208,6 +208,66 @@ hv_status hv_synchronize(hv_handle* h);
 /* Free every resource of the handle. NULL is accepted (no-op). */
 hv_status hv_close(hv_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Groups: several handles (streams of uneven frame sizes, window lengths and
+ * transforms) stepped together. The paper runs one camera stream through the
+ * pipeline of Sec. III-B (ingest, spatial demodulation, time queue, temporal
+ * analysis); a group runs that pipeline for every member in one launch.
+ *
+ * With use_graph = 1, each hv_render_group call captures the whole batch
+ * into one CUDA graph: every member's frame copies and kernels on its own
+ * branch, the branches running concurrently. The graph is then launched once
+ * on the group's stream. The executable graph is kept and updated in place
+ * while the batch keeps its shape; a batch of another shape re-instantiates
+ * it. With use_graph = 0, the same work is issued directly on each member's
+ * stream (the plain form).
+ * ------------------------------------------------------------------------ */
+typedef struct hv_group hv_group;
+
+/* Counters of a group. */
+typedef struct {
+  uint64_t steps;                /* hv_render_group calls that launched work     */
+  uint64_t graph_launches;       /* graph launches (use_graph = 1)               */
+  uint64_t graph_instantiations; /* executable graphs built from scratch         */
+  uint64_t graph_updates;        /* executable graphs updated in place           */
+  uint64_t kernel_launches;      /* kernels enqueued by the members, all steps   */
+  double capture_us_last;        /* host time of the last capture + update       */
+} hv_group_stats;
+
+/* Creates a group over n >= 1 open handles (all on the same device, each with
+ * settings, each appearing once). `stream` (cudaStream_t or NULL) is the
+ * group's stream: graphs launch on it, and it is ordered after the members'
+ * earlier work. The group does not own the handles; close it before them.
+ * Errors: HV_ERR_ARG (NULL, n = 0, a repeated handle, another device),
+ * HV_ERR_CUDA. */
+hv_status hv_group_open(hv_handle* const* handles, uint32_t n, void* stream, int use_graph, hv_group** out);
+
+/* One batch for every member i: copies n_frames[i] raw frames from the
+ * device pointer frames[i] (NULL when n_frames[i] = 0) into the member's
+ * input queue, then renders every complete window of member i into the
+ * device buffer outs[i] (capacity out_capacity_floats[i] floats), as
+ * hv_push_frames + hv_render would. n_windows[i] receives the windows
+ * rendered. Work is asynchronous: it completes on the group's stream, which
+ * every member's stream then waits for.
+ *
+ * Pending settings are applied first (this may synchronise and autotune). A
+ * member with profiling on, with PCA over T > 64 frames (its cooperative
+ * eigensolver launch), or whose copies would overflow its input queue,
+ * makes the call fail before any work is issued.
+ * Errors: HV_ERR_ARG, HV_ERR_STATE, HV_ERR_QUEUE_FULL, HV_ERR_UNSUPPORTED,
+ * HV_ERR_CUDA (the text is on hv_group_last_error). */
+hv_status hv_render_group(hv_group* g, const void* const* frames, const uint32_t* n_frames, float* const* outs,
+                          const size_t* out_capacity_floats, uint32_t* n_windows);
+
+/* Counters of the group. */
+hv_status hv_group_get_stats(const hv_group* g, hv_group_stats* s);
+
+/* Text of the group's last error. */
+const char* hv_group_last_error(const hv_group* g);
+
+/* Waits for the group's work, frees the graph and the group (NULL: no-op). */
+hv_status hv_group_close(hv_group* g);
+
 /* Maximum n * width * height of one hv_spatial_static call (12 frames of
  * 256 x 256, or 3 of 512 x 512). */
 #define HV_STATIC_MAX_PIXELS 786432u

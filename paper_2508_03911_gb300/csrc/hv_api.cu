@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,6 +70,20 @@ struct hv_handle {
   hv_profile prof_acc{};
   std::vector<cudaEvent_t> pca_ev;   // groups of 4 per recorded PCA window
   size_t pca_ev_used = 0;
+};
+
+// A group of handles stepped together (hv_render_group).
+struct hv_group {
+  std::vector<hv_handle*> hs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool use_graph = false;
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+  std::vector<cudaEvent_t> ev_pre, ev_join;  // per member
+  cudaGraphExec_t exec = nullptr;
+  hv_group_stats st{};
+  std::string err;
 };
 
 namespace {
@@ -560,6 +575,132 @@ hv_status tune_spatial(hv_handle* h) {
   return HV_OK;
 }
 
+// Copies n frames from device memory into the input ring on the handle's stream
+// (one copy, or two where the ring wraps). The caller has checked the capacity.
+hv_status enqueue_push_device(hv_handle* h, const void* frames, uint32_t n) {
+  const hv_params& p = h->pending ? h->pend : h->cur;
+  const size_t fb = size_t(p.width) * p.height * (h->bits / 8);
+  const uint32_t slot = uint32_t(h->pushed % h->cap);
+  const uint32_t n1 = std::min(n, h->cap - slot);
+  const char* src = static_cast<const char*>(frames);
+  char* ring = static_cast<char*>(h->raw);
+  HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyDeviceToDevice, h->stream));
+  if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyDeviceToDevice, h->stream));
+  h->pushed += n;
+  h->st.frames_pushed += n;
+  return HV_OK;
+}
+
+// Number of complete windows that one render can emit into cap_floats floats.
+uint32_t windows_ready(const hv_handle* h, size_t cap_floats) {
+  const uint32_t T = h->T, S = h->S;
+  uint64_t avail = 0;
+  if (h->pushed >= h->next_win + T) avail = (h->pushed - h->next_win - T) / S + 1;
+  const uint64_t by_q = (h->Q - T) / S + 1;
+  const uint64_t by_out = cap_floats / h->win_floats;
+  return uint32_t(std::min({avail, by_q, by_out}));
+}
+
+// Enqueues the spatial transform of the frames these nw windows still need and
+// the temporal analysis of the windows into dst (device memory), all on the
+// handle's stream. Makes no synchronising call unless profiling is on, so it
+// may run inside a stream capture (capturing = true; profiling must be off).
+hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing) {
+  const bool none = h->cur.temporal == HV_TEMPORAL_NONE;
+  const uint32_t T = h->T, S = h->S;
+  hv_status s = HV_OK;
+  const uint64_t prop_before = h->st.frames_propagated;
+  s = prof_mark(h, 0);
+  if (s != HV_OK) return s;
+  // spatial transform of every frame of these windows not yet in the queue: one
+  // contiguous range when windows overlap or touch (S <= T), else per window
+  if (S <= T) {
+    const uint64_t lo = std::max(h->next_win, h->propagated);
+    const uint64_t hi = h->next_win + uint64_t(nw - 1) * S + T;
+    if (lo < hi) {
+      s = propagate(h, lo, hi);
+      if (s != HV_OK) return s;
+      h->propagated = hi;
+    }
+  } else {
+    for (uint32_t w = 0; w < nw; ++w) {
+      const uint64_t a = h->next_win + uint64_t(w) * S;
+      const uint64_t lo = std::max(a, h->propagated);
+      if (lo < a + T) {
+        s = propagate(h, lo, a + T);
+        if (s != HV_OK) return s;
+        h->propagated = a + T;
+      }
+    }
+  }
+  s = prof_mark(h, 1);
+  if (s != HV_OK) return s;
+  int launches = 0;
+  cudaError_t e;
+  const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
+  if (none) {
+    e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
+  } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
+    e = cudaSuccess;
+    for (uint32_t w = 0; w < nw && e == cudaSuccess;) {
+      const uint32_t k = h->pca_batched ? std::min<uint32_t>(nw - w, 128) : 1;
+      h->pca.nwin = k;
+      h->pca.wstride = S;
+      h->pca.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
+      h->pca_last_nwin = k;
+      cudaEvent_t* ev = nullptr;
+      if (h->prof) {
+        if (h->pca_ev_used + 4 > h->pca_ev.size()) {
+          s = prof_flush(h);
+          if (s != HV_OK) return s;
+        }
+        ev = &h->pca_ev[h->pca_ev_used];
+        h->pca_ev_used += 4;
+      }
+      e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
+      w += k;
+      if (h->prof && e == cudaSuccess) {
+        unsigned sw = 0;  // sweeps of this window (synchronous read; profiling only)
+        HV_CU(h, cudaMemcpyAsync(&sw, h->pca.counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        HV_CU(h, cudaStreamSynchronize(h->stream));
+        h->prof_acc.pca_sweeps += sw;
+      }
+    }
+    h->pca_has_lam = true;
+  } else {
+    StftArgs sa{};
+    sa.W = h->W;
+    sa.H = h->H;
+    sa.T = T;
+    sa.S = S;
+    sa.nwin = nw;
+    sa.tq = tq;
+    sa.tw_t = h->tw + tw_offset(T);
+    sa.klo = h->klo;
+    sa.khi = h->khi;
+    sa.fscale = float(h->cur.fs_hz / double(T) / 1000.0);
+    sa.mask = h->cur.moments_mask;
+    sa.nout = h->nout;
+    sa.out = dst;
+    e = launch_stft(sa, h->stream, &launches);
+  }
+  h->st.kernel_launches += launches;
+  if (e != cudaSuccess) return cuda_fail(h, e, "temporal transform launch");
+  s = prof_mark(h, 2);
+  if (s != HV_OK) return s;
+  if (h->prof) {
+    h->prof_acc.renders += 1;
+    h->prof_acc.frames += h->st.frames_propagated - prop_before;
+    h->prof_acc.windows += nw;
+  }
+  // an event recorded inside a stream capture cannot be waited on from outside the
+  // graph: the group step records it after launching the graph instead
+  if (!capturing) HV_CU(h, cudaEventRecord(h->ev_consumed, h->stream));
+  h->next_win += uint64_t(nw) * S;
+  h->st.windows_rendered += nw;
+  return HV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -650,15 +791,13 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
     return fail(h, HV_ERR_QUEUE_FULL, "input queue full");
   }
   HV_CU(h, cudaSetDevice(h->device));
+  if (mem_kind == HV_MEM_DEVICE) return enqueue_push_device(h, frames, n);
   const size_t fb = size_t(p.width) * p.height * (h->bits / 8);
   const uint32_t slot = uint32_t(h->pushed % h->cap);
   const uint32_t n1 = std::min(n, h->cap - slot);
   const char* src = static_cast<const char*>(frames);
   char* ring = static_cast<char*>(h->raw);
-  if (mem_kind == HV_MEM_DEVICE) {
-    HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyDeviceToDevice, h->stream));
-    if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyDeviceToDevice, h->stream));
-  } else {
+  {
     // copy stream: wait until the slots being overwritten have been consumed
     HV_CU(h, cudaStreamWaitEvent(h->copy_stream, h->ev_consumed, 0));
     HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyHostToDevice, h->copy_stream));
@@ -695,13 +834,7 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
   HV_CU(h, cudaSetDevice(h->device));
   hv_status s = apply_pending(h);
   if (s != HV_OK) return s;
-  const bool none = h->cur.temporal == HV_TEMPORAL_NONE;
-  const uint32_t T = h->T, S = h->S;
-  uint64_t avail = 0;
-  if (h->pushed >= h->next_win + T) avail = (h->pushed - h->next_win - T) / S + 1;
-  const uint64_t by_q = (h->Q - T) / S + 1;
-  const uint64_t by_out = out ? cap_floats / h->win_floats : 0;
-  const uint32_t nw = uint32_t(std::min({avail, by_q, by_out}));
+  const uint32_t nw = out ? windows_ready(h, cap_floats) : 0;
   if (nw == 0) return HV_OK;
   float* dst = out;
   if (out_kind == HV_MEM_HOST) {
@@ -709,93 +842,8 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
     if (s != HV_OK) return s;
     dst = h->staging;
   }
-  const uint64_t prop_before = h->st.frames_propagated;
-  s = prof_mark(h, 0);
+  s = enqueue_windows(h, dst, nw, false);
   if (s != HV_OK) return s;
-  // spatial transform of every frame of these windows not yet in the queue: one
-  // contiguous range when windows overlap or touch (S <= T), else per window
-  if (S <= T) {
-    const uint64_t lo = std::max(h->next_win, h->propagated);
-    const uint64_t hi = h->next_win + uint64_t(nw - 1) * S + T;
-    if (lo < hi) {
-      s = propagate(h, lo, hi);
-      if (s != HV_OK) return s;
-      h->propagated = hi;
-    }
-  } else {
-    for (uint32_t w = 0; w < nw; ++w) {
-      const uint64_t a = h->next_win + uint64_t(w) * S;
-      const uint64_t lo = std::max(a, h->propagated);
-      if (lo < a + T) {
-        s = propagate(h, lo, a + T);
-        if (s != HV_OK) return s;
-        h->propagated = a + T;
-      }
-    }
-  }
-  s = prof_mark(h, 1);
-  if (s != HV_OK) return s;
-  int launches = 0;
-  cudaError_t e;
-  const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
-  if (none) {
-    e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
-  } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
-    e = cudaSuccess;
-    for (uint32_t w = 0; w < nw && e == cudaSuccess;) {
-      const uint32_t k = h->pca_batched ? std::min<uint32_t>(nw - w, 128) : 1;
-      h->pca.nwin = k;
-      h->pca.wstride = S;
-      h->pca.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
-      h->pca_last_nwin = k;
-      cudaEvent_t* ev = nullptr;
-      if (h->prof) {
-        if (h->pca_ev_used + 4 > h->pca_ev.size()) {
-          s = prof_flush(h);
-          if (s != HV_OK) return s;
-        }
-        ev = &h->pca_ev[h->pca_ev_used];
-        h->pca_ev_used += 4;
-      }
-      e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
-      w += k;
-      if (h->prof && e == cudaSuccess) {
-        unsigned sw = 0;  // sweeps of this window (synchronous read; profiling only)
-        HV_CU(h, cudaMemcpyAsync(&sw, h->pca.counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
-        HV_CU(h, cudaStreamSynchronize(h->stream));
-        h->prof_acc.pca_sweeps += sw;
-      }
-    }
-    h->pca_has_lam = true;
-  } else {
-    StftArgs sa{};
-    sa.W = h->W;
-    sa.H = h->H;
-    sa.T = T;
-    sa.S = S;
-    sa.nwin = nw;
-    sa.tq = tq;
-    sa.tw_t = h->tw + tw_offset(T);
-    sa.klo = h->klo;
-    sa.khi = h->khi;
-    sa.fscale = float(h->cur.fs_hz / double(T) / 1000.0);
-    sa.mask = h->cur.moments_mask;
-    sa.nout = h->nout;
-    sa.out = dst;
-    e = launch_stft(sa, h->stream, &launches);
-  }
-  h->st.kernel_launches += launches;
-  if (e != cudaSuccess) return cuda_fail(h, e, "temporal transform launch");
-  s = prof_mark(h, 2);
-  if (s != HV_OK) return s;
-  if (h->prof) {
-    h->prof_acc.renders += 1;
-    h->prof_acc.frames += h->st.frames_propagated - prop_before;
-    h->prof_acc.windows += nw;
-  }
-  HV_CU(h, cudaEventRecord(h->ev_consumed, h->stream));
-  h->next_win += uint64_t(nw) * S;
-  h->st.windows_rendered += nw;
   if (out_kind == HV_MEM_HOST) {
     HV_CU(h, cudaMemcpyAsync(out, dst, size_t(nw) * h->win_floats * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     HV_CU(h, cudaStreamSynchronize(h->stream));
@@ -890,6 +938,198 @@ hv_status hv_close(hv_handle* h) {
   delete h;
   return HV_OK;
 }
+
+// ---------------------------------------------------------------------- groups
+
+static hv_status gfail(hv_group* g, hv_status s, const std::string& msg) {
+  g->err = msg;
+  return s;
+}
+
+#define HV_GCU(g, call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return gfail(g, HV_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+hv_status hv_group_close(hv_group* g) {
+  if (!g) return HV_OK;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_done) cudaEventDestroy(g->ev_done);
+  for (auto e : g->ev_pre)
+    if (e) cudaEventDestroy(e);
+  for (auto e : g->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return HV_OK;
+}
+
+hv_status hv_group_open(hv_handle* const* handles, uint32_t n, void* stream, int use_graph, hv_group** out) {
+  if (!out) return HV_ERR_ARG;
+  *out = nullptr;
+  if (!handles || n == 0) return HV_ERR_ARG;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!handles[i] || handles[i]->device != handles[0]->device) return HV_ERR_ARG;
+    for (uint32_t j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return HV_ERR_ARG;
+  }
+  hv_group* g = new hv_group();
+  g->hs.assign(handles, handles + n);
+  g->device = handles[0]->device;
+  g->use_graph = use_graph != 0;
+  auto bail = [&](cudaError_t e) {
+    hv_group_close(g);
+    (void)e;
+    return HV_ERR_CUDA;
+  };
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return bail(e);
+  if (stream) {
+    g->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(e);
+    g->own_stream = true;
+  }
+  e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming);
+  g->ev_pre.assign(n, nullptr);
+  g->ev_join.assign(n, nullptr);
+  for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&g->ev_pre[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) return bail(e);
+  *out = g;
+  return HV_OK;
+}
+
+hv_status hv_render_group(hv_group* g, const void* const* frames, const uint32_t* n_frames, float* const* outs,
+                          const size_t* out_capacity_floats, uint32_t* n_windows) {
+  if (!g) return HV_ERR_ARG;
+  if (!outs || !out_capacity_floats || !n_windows) return gfail(g, HV_ERR_ARG, "NULL argument");
+  const uint32_t n = uint32_t(g->hs.size());
+  HV_GCU(g, cudaSetDevice(g->device));
+  // 1. settle every member's settings and check the batch before issuing work
+  for (uint32_t i = 0; i < n; ++i) {
+    hv_handle* h = g->hs[i];
+    n_windows[i] = 0;
+    if (!h->has_params && !h->pending) return gfail(g, HV_ERR_STATE, "member " + std::to_string(i) + ": no settings");
+    hv_status s = apply_pending(h);
+    if (s != HV_OK) return gfail(g, s, "member " + std::to_string(i) + ": " + h->err);
+    if (h->prof) return gfail(g, HV_ERR_STATE, "member " + std::to_string(i) + ": profiling is on");
+    if (h->cur.temporal == HV_TEMPORAL_PCA && h->T > 64)
+      return gfail(g, HV_ERR_UNSUPPORTED, "member " + std::to_string(i) + ": PCA over T > 64 frames");
+    const uint32_t nf = n_frames ? n_frames[i] : 0;
+    if (nf && (!frames || !frames[i])) return gfail(g, HV_ERR_ARG, "member " + std::to_string(i) + ": frames is NULL");
+    if (h->pushed + nf - h->next_win > h->cap) {
+      h->st.frames_rejected += nf;
+      return gfail(g, HV_ERR_QUEUE_FULL, "member " + std::to_string(i) + ": input queue full");
+    }
+  }
+  // 2. the group's stream follows every member's earlier work
+  for (uint32_t i = 0; i < n; ++i) {
+    HV_GCU(g, cudaEventRecord(g->ev_pre[i], g->hs[i]->stream));
+    HV_GCU(g, cudaStreamWaitEvent(g->stream, g->ev_pre[i], 0));
+  }
+  const bool graph = g->use_graph;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (graph) {
+    HV_GCU(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(g->ev_fork, g->stream);
+    if (e != cudaSuccess) {
+      cudaGraph_t dead = nullptr;
+      cudaStreamEndCapture(g->stream, &dead);
+      if (dead) cudaGraphDestroy(dead);
+      return gfail(g, HV_ERR_CUDA, std::string("fork event: ") + cudaGetErrorString(e));
+    }
+  }
+  // 3. every member's copies and kernels, each on its own stream (one graph branch)
+  uint64_t launches_before = 0;
+  for (auto* h : g->hs) launches_before += h->st.kernel_launches;
+  hv_status s = HV_OK;
+  for (uint32_t i = 0; i < n && s == HV_OK; ++i) {
+    hv_handle* h = g->hs[i];
+    if (graph) {
+      cudaError_t e = cudaStreamWaitEvent(h->stream, g->ev_fork, 0);
+      if (e != cudaSuccess) {
+        s = cuda_fail(h, e, "join member stream");
+        break;
+      }
+    }
+    const uint32_t nf = n_frames ? n_frames[i] : 0;
+    if (nf) s = enqueue_push_device(h, frames[i], nf);
+    if (s != HV_OK) break;
+    const uint32_t nw = outs[i] ? windows_ready(h, out_capacity_floats[i]) : 0;
+    if (nw) s = enqueue_windows(h, outs[i], nw, graph);
+    if (s != HV_OK) break;
+    n_windows[i] = nw;
+    cudaError_t e = cudaEventRecord(g->ev_join[i], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_join[i], 0);
+    if (e != cudaSuccess) s = cuda_fail(h, e, "join event");
+  }
+  uint64_t launches_after = 0;
+  for (auto* h : g->hs) launches_after += h->st.kernel_launches;
+  g->st.kernel_launches += launches_after - launches_before;
+  if (graph) {
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g->stream, &gr);
+    if (s != HV_OK || ec != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      if (s == HV_OK) return gfail(g, HV_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ec));
+      for (auto* h : g->hs)
+        if (!h->err.empty()) return gfail(g, s, h->err);
+      return gfail(g, s, "capture failed");
+    }
+    if (g->exec) {
+      cudaGraphExecUpdateResultInfo info{};
+      if (cudaGraphExecUpdate(g->exec, gr, &info) == cudaSuccess) {
+        ++g->st.graph_updates;
+      } else {
+        cudaGetLastError();  // clear the update's error; the graph is rebuilt below
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+      }
+    }
+    if (!g->exec) {
+      const cudaError_t ei = cudaGraphInstantiate(&g->exec, gr, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        g->exec = nullptr;
+        return gfail(g, HV_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+      }
+      ++g->st.graph_instantiations;
+    }
+    cudaGraphDestroy(gr);
+    g->st.capture_us_last = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    HV_GCU(g, cudaGraphLaunch(g->exec, g->stream));
+    ++g->st.graph_launches;
+  } else if (s != HV_OK) {
+    for (auto* h : g->hs)
+      if (!h->err.empty()) return gfail(g, s, h->err);
+    return gfail(g, s, "enqueue failed");
+  }
+  // 4. members' later work (pushes, renders) follows the batch
+  HV_GCU(g, cudaEventRecord(g->ev_done, g->stream));
+  for (auto* h : g->hs) {
+    HV_GCU(g, cudaStreamWaitEvent(h->stream, g->ev_done, 0));
+    if (graph) HV_GCU(g, cudaEventRecord(h->ev_consumed, h->stream));
+  }
+  ++g->st.steps;
+  return HV_OK;
+}
+
+hv_status hv_group_get_stats(const hv_group* g, hv_group_stats* s) {
+  if (!g || !s) return HV_ERR_ARG;
+  *s = g->st;
+  return HV_OK;
+}
+
+const char* hv_group_last_error(const hv_group* g) { return g ? g->err.c_str() : ""; }
 
 const char* hv_last_error(const hv_handle* h) { return h ? h->err.c_str() : g_open_err.c_str(); }
 

@@ -73,6 +73,12 @@ class hv_tuning(C.Structure):
                 ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 12)]
 
 
+class hv_group_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("steps", "graph_launches", "graph_instantiations",
+                                          "graph_updates", "kernel_launches")] + \
+               [("capture_us_last", C.c_double)]
+
+
 class HvError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -107,6 +113,12 @@ def lib() -> C.CDLL:
         "hv_profile_read": ([C.c_void_p, P(hv_profile)], C.c_int),
         "hv_close": ([C.c_void_p], C.c_int),
         "hv_last_error": ([C.c_void_p], C.c_char_p),
+        "hv_group_open": ([P(C.c_void_p), C.c_uint32, C.c_void_p, C.c_int, P(C.c_void_p)], C.c_int),
+        "hv_render_group": ([C.c_void_p, P(C.c_void_p), P(C.c_uint32), P(C.c_void_p), P(C.c_size_t),
+                             P(C.c_uint32)], C.c_int),
+        "hv_group_get_stats": ([C.c_void_p, P(hv_group_stats)], C.c_int),
+        "hv_group_last_error": ([C.c_void_p], C.c_char_p),
+        "hv_group_close": ([C.c_void_p], C.c_int),
         "hv_version": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -259,6 +271,61 @@ def hv_last_error(h=None) -> str:
 
 def hv_version() -> str:
     return lib().hv_version().decode()
+
+
+# ------------------------------------------------------------------ groups
+
+def _gcheck(g, status):
+    if status != HV_OK:
+        raise HvError(status, lib().hv_group_last_error(g).decode(errors="replace"))
+    return status
+
+
+def hv_group_open(handles, stream=None, use_graph=True) -> C.c_void_p:
+    """Group over open handles; `stream` is a cudaStream_t handle (int) or None."""
+    arr = (C.c_void_p * len(handles))(*[C.c_void_p(h.value if isinstance(h, C.c_void_p) else h)
+                                        for h in handles])
+    g = C.c_void_p()
+    s = lib().hv_group_open(arr, len(handles), C.c_void_p(stream or 0), int(use_graph), C.byref(g))
+    if s != HV_OK:
+        raise HvError(s, "hv_group_open failed")
+    return g
+
+
+def hv_render_group(g, frames, outs) -> list[int]:
+    """One batch: frames[i] (device tensor (n, H, W) or None) pushed to member i,
+    then its complete windows rendered into the device tensor outs[i]. Returns
+    the windows rendered per member."""
+    n = len(outs)
+    fp = (C.c_void_p * n)()
+    nf = (C.c_uint32 * n)()
+    op = (C.c_void_p * n)()
+    cap = (C.c_size_t * n)()
+    for i in range(n):
+        if frames is not None and frames[i] is not None:
+            ptr, kind, _ = _ptr_kind(frames[i])
+            if kind != HV_MEM_DEVICE:
+                raise ValueError("group frames must be device memory")
+            fp[i] = ptr
+            nf[i] = frames[i].shape[0]
+        ptr, kind, nbytes = _ptr_kind(outs[i])
+        if kind != HV_MEM_DEVICE:
+            raise ValueError("group outputs must be device memory")
+        op[i] = ptr
+        cap[i] = nbytes // 4
+    nw = (C.c_uint32 * n)()
+    _gcheck(g, lib().hv_render_group(g, fp, nf, op, cap, nw))
+    return list(nw)
+
+
+def hv_group_get_stats(g) -> dict:
+    st = hv_group_stats()
+    _gcheck(g, lib().hv_group_get_stats(g, C.byref(st)))
+    return {n: getattr(st, n) for n, _ in hv_group_stats._fields_}
+
+
+def hv_group_close(g):
+    lib().hv_group_close(g)
 
 
 class Renderer:
