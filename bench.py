@@ -86,6 +86,20 @@ WORKLOADS = {
         moments=(), temporal="pca", pca=(2, 64), batch=1024, batches=1, pool=256,
         scene="scene_pca"),
 }
+# Batched uneven streams: (side N, window T, spatial transform); u16 12-bit frames, S = T,
+# STFT M0/M1/M2 over 1-35 kHz at fs = 71.4 kHz, 4 windows per member and batch.
+GROUP_MEMBERS = [(128, 32, "fresnel"), (128, 128, "asp"), (256, 512, "asp"), (256, 32, "fresnel"),
+                 (512, 128, "asp"), (512, 32, "fresnel"), (1024, 128, "asp"), (1024, 32, "fresnel")]
+GROUP_WINDOWS = 4
+WORKLOADS["group_uneven_8"] = dict(
+    desc="8 streams stepped together by hv_render_group: 128^2/T32/Fresnel, 128^2/T128/ASP, "
+         "256^2/T512/ASP, 256^2/T32/Fresnel, 512^2/T128/ASP, 512^2/T32/Fresnel, "
+         "1024^2/T128/ASP, 1024^2/T32/Fresnel; uint16 12-bit frames (seeded uniform, 128-frame pool "
+         "per stream tiled on the device), S = T, STFT M0/M1/M2 over 1-35 kHz at fs = 71.4 kHz, "
+         "4 windows per stream per batch (4,096 frames, 1.95 GB raw); one batch per step",
+    N=0, bits=12, spatial="mixed", z=0.0, T=0, S=0, fs=71400.0, band=(0, 0),
+    moments=("M0", "M1", "M2"), batch=sum(GROUP_WINDOWS * t for _, t, _ in GROUP_MEMBERS), batches=1,
+    pool=0, scene="random", group=True)
 DEFAULT = "stream_fresnel_256_t512_s64"
 METRIC = "raw frames/s rendered"
 
@@ -481,9 +495,35 @@ def cpu_baseline(w):
                       f"{dt:.1f} s on 1 host core"}
 
 
+def group_oracle_sample():
+    """FP64 oracle on one window of each group member with N <= 256 and T <= 128."""
+    from oracle import hv_oracle as O
+    n_tot, t_tot = 0, 0.0
+    for i, (N, T, sp) in enumerate(GROUP_MEMBERS):
+        if N > 256 or T > 128:
+            continue
+        q = group_member_params(N, T, sp)
+        fr = synth.random_frames(T, N, N, 12, seed=1003 + i)
+        p = dict(spatial=sp, z_m=q["z"], lambda_m=852e-9, pitch_x_m=20e-6, pitch_y_m=20e-6,
+                 fftshift=1, temporal="stft", T=T, stride=T, fs_hz=q["fs"], band_lo_bin=q["band"][0],
+                 band_hi_bin=q["band"][1], moments=q["moments"])
+        t0 = time.perf_counter()
+        O.render(fr, p)
+        t_tot += time.perf_counter() - t0
+        n_tot += T
+    return n_tot / t_tot, n_tot, t_tot
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return None
+    if w.get("group"):
+        vals = []
+        for i in range(args.warmup + args.steps):
+            fps, n, _ = group_oracle_sample()
+            if i >= args.warmup:
+                vals.append(fps)
+        return float(np.median(vals)), n
     fps_list = []
     n = w["T"] + w["S"] if w["S"] < w["T"] else w["T"]
     for i in range(args.warmup + args.steps):
@@ -492,6 +532,144 @@ def run_reference(args, w, rank):
             fps_list.append(n / dt / 1.0)
     value = float(np.median(fps_list))
     return value, n
+
+
+# ------------------------------------------------------- batched streams
+
+def group_member_params(N, T, spatial):
+    return dict(spatial=spatial, z=0.25 if spatial == "fresnel" else 0.30, T=T, S=T, fs=71400.0,
+                band=(math.ceil(1000.0 * T / 71400.0 - 1e-12), math.floor(35000.0 * T / 71400.0 + 1e-12)),
+                moments=("M0", "M1", "M2"))
+
+
+def group_bytes_per_batch():
+    """Algorithmic bytes of one batch: raw 2 B/px + 16 B/px through the time queue per
+    frame, and the moment images once per window."""
+    tot = 0.0
+    for N, T, _ in GROUP_MEMBERS:
+        hw = N * N
+        tot += GROUP_WINDOWS * T * hw * (2 + 16) + GROUP_WINDOWS * 3 * hw * 4
+    return tot
+
+
+def run_group(args, use_graph, tuned, quick=False):
+    """K steps of one hv_render_group batch each (every member: 4 windows of frames
+    pushed from a device pool, then rendered)."""
+    import torch
+
+    from paper_2508_03911_gb300 import hv
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    rs, pools, outs = [], [], []
+    for i, (N, T, sp) in enumerate(GROUP_MEMBERS):
+        q = group_member_params(N, T, sp)
+        nb = GROUP_WINDOWS * T
+        r = hv.Renderer(N, N, 16, 2 * nb)
+        r.set_params(N, N, spatial=sp, z=q["z"], T=T, stride=T, fs=q["fs"], band=q["band"],
+                     moments=q["moments"], tuned=tuned)
+        base = synth.random_frames(min(nb, 128), N, N, 12, seed=1003 + i).view(np.int16)
+        pool = torch.from_numpy(base).to(dev).repeat(max(1, nb // base.shape[0]), 1, 1)[:nb].contiguous()
+        rs.append(r)
+        pools.append(pool)
+        outs.append(torch.empty(GROUP_WINDOWS * r.window_floats(), dtype=torch.float32, device=dev))
+    g = hv.hv_group_open([r.h for r in rs], stream=stream.cuda_stream, use_graph=use_graph)
+    frames_per_batch = sum(p.shape[0] for p in pools)
+
+    def step(events=None):
+        if events is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        nw = hv.hv_render_group(g, pools, outs)
+        assert nw == [GROUP_WINDOWS] * len(rs), nw
+        if events is not None:
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            events.append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(None) if not quick else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.6)
+    st0 = hv.hv_group_get_stats(g)
+    lat = []
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark("t0")
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(lat)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark("t1")
+    st1 = hv.hv_group_get_stats(g)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    clk = clocks.stop() if clocks else None
+    value = args.steps * frames_per_batch / (elapsed_ms / 1e3)
+    hv.hv_group_close(g)
+    for r in rs:
+        r.close()
+    return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, clocks=clk,
+                launches=st1["kernel_launches"] - st0["kernel_launches"], stats=st1,
+                frames_per_batch=frames_per_batch)
+
+
+def group_config(name, frames_per_batch):
+    return {"workload": name, "description": WORKLOADS[name]["desc"],
+            "members": [{"N": N, "T": T, "S": T, "spatial": sp} for N, T, sp in GROUP_MEMBERS],
+            "frames_per_step": frames_per_batch,
+            "l2": "inputs larger than L2: each batch reads 1.95 GB of raw frames",
+            "parallelism": "replicas x1"}
+
+
+def main_group(args):
+    """Batched uneven streams: tuned form (autotuned spatial kernels, one graph per
+    batch) and plain form (multi-pass kernels, launches issued per member)."""
+    w = WORKLOADS[args.workload]
+    plain = run_group(args, use_graph=False, tuned=0, quick=True)
+    res = run_group(args, use_graph=True, tuned=1)
+    peaks = load_peaks()
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    lat = res["lat_ms"]
+    gbs = group_bytes_per_batch() * args.steps / (res["elapsed_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(res["value"], 1), "unit": "frames/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(res["elapsed_ms"] / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": group_config(args.workload, res["frames_per_batch"]),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "per batch (all 8 streams): hv_render_group, CUDA events"},
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbs / hbm, 4), "traffic": None,
+                     "kernel": "whole batch (all members' kernels; algorithmic bytes 18 B/px/frame "
+                               "+ 12 B/px/window)",
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": None,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "form": "tuned",
+        "forms": {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),
+                  "plain_p99_ms": float(np.percentile(plain["lat_ms"], 99))},
+        "graph": {k: res["stats"][k] for k in ("graph_launches", "graph_instantiations",
+                                               "graph_updates", "capture_us_last")},
+    }
+    if not args.no_cpu_baseline:
+        fps, n, dt = group_oracle_sample()
+        line["cpu_baseline"] = {"value": round(fps, 2), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one window of each member with N <= 256 and T <= 128 "
+                                          f"({n} frames), FP64 numpy oracle, {dt:.1f} s on 1 host core"}
+    print(json.dumps(line), flush=True)
+
 
 
 # ------------------------------------------------------------------ main
@@ -512,6 +690,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if WORKLOADS[args.workload].get("group") and args.impl == "hv":
+        main_group(args)
+        return
     w = dict(WORKLOADS[args.workload])
     if args.precision:
         w["precision"] = args.precision
@@ -525,6 +706,8 @@ def main():
               "batch_frames": w["batch"], "precision": w.get("precision", "fp32"),
               "l2": "inputs larger than L2: each step streams >10 GB through the time queue",
               "parallelism": f"replicas x{args.gpus}"}
+    if w.get("group"):
+        config = group_config(args.workload, w["batch"])
 
     if args.impl == "reference":
         res = run_reference(args, w, rank)
@@ -536,8 +719,11 @@ def main():
                     "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                     "cpu_baseline": {"value": round(value, 3), "unit": "frames/s", "cores": 1,
                                      "kind": "oracle",
-                                     "sample": f"each step: first {n} frames of the workload "
-                                               "through the FP64 numpy oracle on 1 host core"},
+                                     "sample": (f"each step: one window of each member with N <= 256 "
+                                                f"and T <= 128 ({n} frames) through the FP64 numpy "
+                                                "oracle on 1 host core") if w.get("group") else
+                                               (f"each step: first {n} frames of the workload "
+                                                "through the FP64 numpy oracle on 1 host core")},
                     "e2e": {"value": round(value, 3), "unit": "frames/s", "h2d_bytes_per_step": 0,
                             "d2h_bytes_per_step": 0}}
             print(json.dumps(line), flush=True)
