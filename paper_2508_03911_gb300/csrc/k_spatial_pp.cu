@@ -1,15 +1,23 @@
-// k_spatial_pp.cu -- the multi-pass spatial transform (same passes and layouts as
-// k_spatial.cu, Sec. III-B.1) as persistent kernels that prefetch.
+// k_spatial_pp.cu -- the spatial transform (Sec. III-B.1) as persistent kernels, one
+// per pass, that prefetch their next work item and keep the integer work per
+// pixel small.
 //
-// A CTA stays resident and loops over work items (frame, strip of 16 lines).
-// While it transforms one item, the input of its next item streams into the
-// other buffer with cp.async, so global-load latency overlaps the FFT stages
-// instead of stalling every short-lived CTA at its start:
-//   P1  raw strip (uint8/uint16 rows) -> staging buffer; conversion (+ chirp)
-//       into the FFT buffer; column FFT; transposed store -> S1[x][ky]
-//   P2a S1 strip -> FFT buffer; row FFT, x H, row IFFT; transposed store -> S2
-//   P3a S2 strip -> FFT buffer; column IFFT -> time queue
-//   P2f S1 strip -> FFT buffer; row FFT; transposed store -> time queue
+// A CTA stays resident and loops over work items (frame, strip of 16 lines of
+// the pass). While it transforms one item, the input of its next item streams
+// into a second buffer with cp.async. Each pass reads its input in whatever
+// order makes the global loads coalesced and writes its output straight from
+// the registers of the last FFT stage; the intermediate layouts are chosen so
+// that those stores are coalesced too (lanes of a warp hold 16 neighbouring
+// lines):
+//   P1  column FFT (length H) of 16 columns: the first FFT stage reads the raw
+//       strip (uint8/uint16, staged by cp.async) and converts it in registers
+//       (Fresnel: times the chirp) -> S1[ky][x]
+//   P2a row FFT (length W) of 16 rows ky of S1, x H^T (1/(WH) and the optional
+//       high-pass folded in), row IFFT -> S2[x][ky]
+//   P3a column IFFT (length H) of 16 columns x of S2 -> time queue [y][x]
+//   P2f row FFT of 16 rows ky of S1 -> time queue [ky][kx] (through shared memory:
+//       the natural layout needs lanes along kx)
+// Twiddles of the pass length are copied to shared memory once per CTA.
 #include "fft_dev.cuh"
 #include "hv_internal.h"
 #include "../../include/hv.h"
@@ -24,10 +32,12 @@ enum { PK_P1 = 0, PK_P2A = 1, PK_P3A = 2, PK_P2F = 3 };
 template <int L>
 struct PpCfg {
   static constexpr int BT = PP_BT;
-  static constexpr int NT = FftThreads<L, BT>::value;
+  static constexpr int NT = FftThreads<L, BT>::value;  // = L for 64 <= L <= 512
   static constexpr int LD = BT + 1;
   static constexpr size_t BUF = size_t(L) * LD * sizeof(float2);
-  static constexpr size_t RAW = size_t(L) * BT * 2;  // one uint16 strip
+  static constexpr size_t RAW = size_t(L) * BT * 2;    // one uint16 strip
+  static constexpr size_t TW = size_t(L) * sizeof(float2);
+  static_assert(NT == L, "one thread per element of a line");
 };
 
 __device__ __forceinline__ void cpa8(void* s, const void* g) {
@@ -43,136 +53,232 @@ __device__ __forceinline__ void cpa16(void* s, const void* g) {
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ------------------------------------------------ stage inputs and epilogues
+
+// Element t of line b from the FFT buffer.
 template <int LD>
-struct MulHt {  // bin k of line b times the transposed transfer function
-  float2* buf;
-  const float2* ht;
-  uint32_t H, b0;
-  __device__ __forceinline__ void operator()(int b, int k, float2 v) const {
-    buf[k * LD + b] = cmul(v, __ldg(&ht[size_t(k) * H + b0 + b]));
+struct SmemSrc {
+  static constexpr bool kAliasesBuf = true;
+  const float2* buf;
+  __device__ __forceinline__ float2 operator()(int t, int b) const { return buf[t * LD + b]; }
+};
+
+// Element t (row y) of column b from a staged raw strip [y][16], converted to
+// complex; with the Fresnel chirp cy[y] * cx (cx: this thread's column factor).
+template <bool U8, bool CHIRP>
+struct RawSrc {
+  static constexpr bool kAliasesBuf = false;
+  const unsigned char* raw;
+  const float2* cy;
+  float2 cx;
+  __device__ __forceinline__ float2 operator()(int t, int b) const {
+    const float v = U8 ? float(raw[t * PP_BT + b]) : float(reinterpret_cast<const uint16_t*>(raw)[t * PP_BT + b]);
+    if constexpr (CHIRP) return cscale(cmul(cy[t], cx), v);
+    return make_float2(v, 0.f);
   }
 };
 
-struct ToGlobal {
+// Bin k of line b straight to global memory at out[k * stride + b].
+struct GlobalOut {
+  static constexpr bool kSyncFirst = false;
   float2* out;
-  uint32_t ld, b0;
-  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(k) * ld + b0 + b] = v; }
+  uint32_t stride;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(k) * stride + b] = v; }
 };
 
-// Prefetch the input of item (frame i, lines b0 .. b0+BT) of pass PK into dst.
-template <int L, int PK>
-__device__ __forceinline__ void prefetch(const SpatialArgs& a, int i, int b0, void* dst) {
+// Bin k of line b times the transposed transfer function, back to the buffer.
+template <int LD>
+struct MulHtSmem {
+  static constexpr bool kSyncFirst = true;
+  float2* buf;
+  const float2* ht;  // ht[k * H + line] of this strip's first line
+  uint32_t H;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const {
+    buf[k * LD + b] = cmul(v, __ldg(&ht[size_t(k) * H + b]));
+  }
+};
+
+template <int LD>
+struct ToSmem {
+  static constexpr bool kSyncFirst = true;
+  float2* buf;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { buf[k * LD + b] = v; }
+};
+
+// One Stockham stage of span NS over the PP_BT lines (thread layout and index
+// rules of fft_dev.cuh), and recursively the rest. The first stage reads
+// through `src`, later ones the buffer; twiddles come from the shared table
+// tws[e] = exp(-2 pi i e / L). The last stage hands bin k of line b to epi.
+template <int L, int NS, int DIR, class Src, class Epi>
+__device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const float2* tws, const Epi& epi) {
   using C = PpCfg<L>;
-  if constexpr (PK == PK_P1) {
-    const int bpp = a.in_kind == IN_U8 ? 1 : 2;
-    const int chunks = C::BT * bpp / 16;  // 16-byte pieces per row segment
-    const size_t rslot = (a.raw.slot0 + uint32_t(i)) % a.raw.cap;
-    const unsigned char* src = static_cast<const unsigned char*>(a.raw.base) +
-                               (rslot * size_t(a.W) * L + b0) * bpp;
-    unsigned char* d = static_cast<unsigned char*>(dst);
-    for (int e = threadIdx.x; e < L * chunks; e += C::NT) {
-      const int y = e / chunks, q = e % chunks;
-      cpa16(d + (y * C::BT * bpp) + q * 16, src + size_t(y) * a.W * bpp + q * 16);
+  constexpr int NT = C::NT, BT = C::BT, LD = C::LD;
+  constexpr int REM = L / NS;
+  constexpr int R = BlockRadix<REM, L, BT, NT>::value;
+  constexpr int NB = L / R;
+  static_assert((BT * NB) % NT == 0, "thread count must divide the butterflies");
+  constexpr int ITEMS = BT * NB / NT;
+  constexpr bool LAST = NS * R == L;
+  float2 v[ITEMS][R];
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    const int idx = threadIdx.x + it * NT;
+    const int b = idx % BT, j = idx / BT;
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[it][m] = src(j + m * NB, b);
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int m = 1; m < R; ++m) {
+        float2 w = tws[jm * m * (L / (NS * R))];
+        if constexpr (DIR > 0) w.y = -w.y;
+        v[it][m] = cmul(v[it][m], w);
+      }
+    }
+    dft<R, DIR>(v[it]);
+  }
+  if constexpr (LAST) {
+    if constexpr (Epi::kSyncFirst) __syncthreads();  // every read of buf is done
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int idx = threadIdx.x + it * NT;
+      const int b = idx % BT, j = idx / BT;
+#pragma unroll
+      for (int m = 0; m < R; ++m) epi(b, j + m * NB, v[it][m]);
     }
   } else {
-    // complex strip: element (t, b) of the pass at src[t * ld + b0 + b]
-    const float2* src;
-    uint32_t ld;
-    if constexpr (PK == PK_P3A) {
-      src = a.scratch2 + size_t(i) * a.W * L;
-      ld = a.W;
-    } else {
-      src = a.scratch1 + size_t(i) * a.H * L;
-      ld = a.H;
+    if constexpr (Src::kAliasesBuf) __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int idx = threadIdx.x + it * NT;
+      const int b = idx % BT, j = idx / BT;
+      const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[(base + m * NS) * LD + b] = v[it][m];
     }
-    float2* d = static_cast<float2*>(dst);
-    for (int e = threadIdx.x; e < L * C::BT; e += C::NT) {
-      const int b = e % C::BT, t = e / C::BT;
-      cpa8(&d[t * C::LD + b], &src[size_t(t) * ld + b0 + b]);
-    }
+    __syncthreads();
+    SmemSrc<LD> s{buf};
+    pp_stages<L, NS * R, DIR>(s, buf, tws, epi);
+  }
+}
+
+// ------------------------------------------------------------- prefetch
+
+// Raw strip of pass P1: rows 0..H-1, columns s0..s0+15 of frame i -> raw_s[y][16].
+template <int L>
+__device__ __forceinline__ void prefetch_raw(const SpatialArgs& a, int i, int s0, unsigned char* dst) {
+  const int bpp = a.in_kind == IN_U8 ? 1 : 2;  // 16-byte pieces per row segment
+  const size_t rslot = (a.raw.slot0 + uint32_t(i)) % a.raw.cap;
+  const unsigned char* src = static_cast<const unsigned char*>(a.raw.base) + (rslot * size_t(a.W) * L + s0) * bpp;
+  const size_t row = size_t(a.W) * bpp;
+  for (int e = threadIdx.x; e < L * bpp; e += PpCfg<L>::NT) {
+    const int y = e / bpp, q = e % bpp;
+    cpa16(dst + (y * PP_BT * bpp) + q * 16, src + y * row + q * 16);
   }
   cpa_commit();
 }
 
+// Complex strip: line b of the strip is src[b * L + t], t = 0..L-1 -> buf[t][b].
+template <int L>
+__device__ __forceinline__ void prefetch_lines(const float2* src, float2* dst) {
+  using C = PpCfg<L>;
+  const int t = threadIdx.x;  // NT == L
+#pragma unroll
+  for (int b = 0; b < C::BT; ++b) cpa8(&dst[t * C::LD + b], &src[b * L + t]);
+  cpa_commit();
+}
+
+// ---------------------------------------------------------------- kernel
+
 template <int L, int PK>
-__global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 3 : 1)) k_pass_pp(SpatialArgs a, int nitems, int nstrips) {
+__global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
+    k_pass_pp(SpatialArgs a, int nitems, int strip_log2) {
   using C = PpCfg<L>;
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* tws = reinterpret_cast<float2*>(smem);
+  float2* cys = reinterpret_cast<float2*>(smem + C::TW);  // P1 Fresnel: chirp along y
+  unsigned char* body = smem + (PK == PK_P1 ? 2 * C::TW : C::TW);
+  float2* buf0 = reinterpret_cast<float2*>(body);
   // P1: one FFT buffer and two raw staging buffers; other passes: two FFT buffers
-  float2* buf1 = reinterpret_cast<float2*>(smem + C::BUF);
-  unsigned char* raw0 = smem + C::BUF;
-  unsigned char* raw1 = smem + C::BUF + C::RAW;
+  float2* buf1 = reinterpret_cast<float2*>(body + C::BUF);
+  unsigned char* raw0 = body + C::BUF;
+  unsigned char* raw1 = body + C::BUF + C::RAW;
   const int tid = threadIdx.x;
+  const int smask = (1 << strip_log2) - 1;
+  const bool fresnel = a.spatial == HV_SPATIAL_FRESNEL;
+  const bool u8 = a.in_kind == IN_U8;
+  // the pass length: P1 and P3a run along y (length H), P2a and P2f along x
+  const float2* twg = (PK == PK_P1 || PK == PK_P3A) ? a.tw_h : a.tw_w;
+  for (int e = tid; e < L; e += C::NT) {
+    tws[e] = __ldg(&twg[e]);
+    if (PK == PK_P1 && fresnel) cys[e] = __ldg(&a.chirp_y[e]);
+  }
+  // lines per frame of the other axis: W columns (P1, P3a) or H rows (P2a, P2f)
+  const uint32_t LO = (PK == PK_P1 || PK == PK_P3A) ? a.W : a.H;
+
+  auto issue = [&](int it, int cur) {
+    const int i = it >> strip_log2, s0 = (it & smask) * C::BT;
+    if constexpr (PK == PK_P1) {
+      prefetch_raw<L>(a, i, s0, cur == 0 ? raw0 : raw1);
+    } else {
+      const float2* base = PK == PK_P3A ? a.scratch2 : a.scratch1;
+      prefetch_lines<L>(base + size_t(i) * L * LO + size_t(s0) * L, cur == 0 ? buf0 : buf1);
+    }
+  };
 
   int item = blockIdx.x;
-  if (item < nitems) prefetch<L, PK>(a, item / nstrips, (item % nstrips) * C::BT, PK == PK_P1 ? (void*)raw0 : (void*)buf0);
+  if (item < nitems) issue(item, 0);
   for (int k = 0; item < nitems; ++k, item += gridDim.x) {
     const int cur = k & 1;
-    const int i = item / nstrips, b0 = (item % nstrips) * C::BT;
+    const int i = item >> strip_log2, s0 = (item & smask) * C::BT;
     cpa_wait_all();
     __syncthreads();  // this item's input resident; the other buffer is free
-    float2* buf = (PK == PK_P1 || cur == 0) ? buf0 : buf1;
-    if constexpr (PK == PK_P1) {
-      const unsigned char* raw = cur == 0 ? raw0 : raw1;
-      const bool chirp = a.spatial == HV_SPATIAL_FRESNEL;
-      const bool u8 = a.in_kind == IN_U8;
-      for (int e = tid; e < L * C::BT; e += C::NT) {
-        const int b = e % C::BT, y = e / C::BT;
-        const float v = u8 ? float(raw[y * C::BT + b]) : float(reinterpret_cast<const uint16_t*>(raw)[y * C::BT + b]);
-        float2 u = make_float2(v, 0.f);
-        if (chirp) u = cscale(cmul(__ldg(&a.chirp_y[y]), __ldg(&a.chirp_x[b0 + b])), v);
-        buf[y * C::LD + b] = u;
-      }
-      __syncthreads();
-    }
     const int nxt = item + gridDim.x;
-    if (nxt < nitems) {
-      void* dst = PK == PK_P1 ? (void*)(cur == 0 ? raw1 : raw0) : (void*)(cur == 0 ? buf1 : buf0);
-      prefetch<L, PK>(a, nxt / nstrips, (nxt % nstrips) * C::BT, dst);
-    }
-    StoreSmem<C::LD> st{buf};
+    if (nxt < nitems) issue(nxt, cur ^ 1);
     if constexpr (PK == PK_P1) {
-      fft_lines<L, -1, C::BT, C::NT, C::LD>(buf, a.tw_h, st);
-      __syncthreads();
-      float2* s1 = a.scratch1 + size_t(i) * a.W * L;
-      for (int e = tid; e < L * C::BT; e += C::NT) {
-        const int kk = e % L, b = e / L;
-        s1[size_t(b0 + b) * L + kk] = buf[kk * C::LD + b];
+      // S1[ky][x]: bin ky of column s0 + b at s1[ky * W + s0 + b]
+      const GlobalOut out{a.scratch1 + size_t(i) * a.H * a.W + s0, a.W};
+      const unsigned char* raw = cur == 0 ? raw0 : raw1;
+      const int b = tid % C::BT;
+      if (fresnel) {
+        const float2 cx = __ldg(&a.chirp_x[s0 + b]);
+        if (u8) pp_stages<L, 1, -1>(RawSrc<true, true>{raw, cys, cx}, buf0, tws, out);
+        else pp_stages<L, 1, -1>(RawSrc<false, true>{raw, cys, cx}, buf0, tws, out);
+      } else {
+        if (u8) pp_stages<L, 1, -1>(RawSrc<true, false>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
+        else pp_stages<L, 1, -1>(RawSrc<false, false>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
       }
     } else if constexpr (PK == PK_P2A) {
-      MulHt<C::LD> mul{buf, a.asp_ht, a.H, uint32_t(b0)};
-      fft_lines<L, -1, C::BT, C::NT, C::LD>(buf, a.tw_w, mul);
+      float2* buf = cur == 0 ? buf0 : buf1;
+      const SmemSrc<C::LD> src{buf};
+      pp_stages<L, 1, -1>(src, buf, tws, MulHtSmem<C::LD>{buf, a.asp_ht + s0, a.H});
       __syncthreads();
-      fft_lines<L, +1, C::BT, C::NT, C::LD>(buf, a.tw_w, st);
-      __syncthreads();
-      float2* s2 = a.scratch2 + size_t(i) * a.H * L;
-      for (int e = tid; e < L * C::BT; e += C::NT) {
-        const int x = e % L, b = e / L;
-        s2[size_t(b0 + b) * L + x] = buf[x * C::LD + b];
-      }
+      // S2[x][ky]: sample x of row s0 + b at s2[x * H + s0 + b]
+      pp_stages<L, 1, +1>(src, buf, tws, GlobalOut{a.scratch2 + size_t(i) * a.H * a.W + s0, a.H});
     } else if constexpr (PK == PK_P3A) {
+      float2* buf = cur == 0 ? buf0 : buf1;
       const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
-      ToGlobal out{static_cast<float2*>(a.tq.base) + tslot * size_t(a.W) * L, a.W, uint32_t(b0)};
-      fft_lines<L, +1, C::BT, C::NT, C::LD>(buf, a.tw_h, out);
+      // time queue [y][x]: sample y of column s0 + b at tq[y * W + s0 + b]
+      pp_stages<L, 1, +1>(SmemSrc<C::LD>{buf}, buf, tws,
+                          GlobalOut{static_cast<float2*>(a.tq.base) + tslot * size_t(a.W) * a.H + s0, a.W});
     } else {
-      fft_lines<L, -1, C::BT, C::NT, C::LD>(buf, a.tw_w, st);
+      float2* buf = cur == 0 ? buf0 : buf1;
+      pp_stages<L, 1, -1>(SmemSrc<C::LD>{buf}, buf, tws, ToSmem<C::LD>{buf});
       __syncthreads();
+      // time queue [ky][kx]: bin kx of row s0 + b; lanes along kx for the store
       const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
-      float2* out = static_cast<float2*>(a.tq.base) + tslot * size_t(a.H) * L;
-      for (int e = tid; e < L * C::BT; e += C::NT) {
-        const int kk = e % L, b = e / L;
-        out[size_t(b0 + b) * L + kk] = buf[kk * C::LD + b];
-      }
+      float2* out = static_cast<float2*>(a.tq.base) + tslot * size_t(a.H) * a.W + size_t(s0) * a.W;
+#pragma unroll
+      for (int b = 0; b < C::BT; ++b) out[size_t(b) * a.W + tid] = buf[tid * C::LD + b];
     }
   }
   cpa_wait_all();
 }
 
 template <int L, int PK>
-static cudaError_t launch_pp(const SpatialArgs& a, int nstrips, cudaStream_t s) {
+static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t s) {
   using C = PpCfg<L>;
-  const size_t smem = PK == PK_P1 ? C::BUF + 2 * C::RAW : 2 * C::BUF;
+  const size_t smem = (PK == PK_P1 ? 2 * C::TW + C::BUF + 2 * C::RAW : C::TW + 2 * C::BUF);
   auto kern = k_pass_pp<L, PK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -181,26 +287,28 @@ static cudaError_t launch_pp(const SpatialArgs& a, int nstrips, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int nitems = int(a.n) * nstrips;
+  int strip_log2 = 0;
+  while ((uint32_t(PP_BT) << strip_log2) < lines) ++strip_log2;
+  const int nitems = int(a.n) << strip_log2;
   int grid = per_sm * nsm;
   if (grid > nitems) grid = nitems;
   if (grid < 1) grid = 1;
-  kern<<<grid, C::NT, smem, s>>>(a, nitems, nstrips);
+  kern<<<grid, C::NT, smem, s>>>(a, nitems, strip_log2);
   return cudaGetLastError();
 }
 
 template <int LH, int LW>
 static cudaError_t pp_fixed(const SpatialArgs& a, cudaStream_t s, int* launches) {
-  cudaError_t e = launch_pp<LH, PK_P1>(a, int(a.W / PP_BT), s);
+  cudaError_t e = launch_pp<LH, PK_P1>(a, a.W, s);
   if (e != cudaSuccess) return e;
   ++*launches;
   if (a.spatial == HV_SPATIAL_ASP) {
-    e = launch_pp<LW, PK_P2A>(a, int(a.H / PP_BT), s);
+    e = launch_pp<LW, PK_P2A>(a, a.H, s);
     if (e != cudaSuccess) return e;
-    e = launch_pp<LH, PK_P3A>(a, int(a.W / PP_BT), s);
+    e = launch_pp<LH, PK_P3A>(a, a.W, s);
     *launches += 2;
   } else {
-    e = launch_pp<LW, PK_P2F>(a, int(a.H / PP_BT), s);
+    e = launch_pp<LW, PK_P2F>(a, a.H, s);
     ++*launches;
   }
   return e;
