@@ -184,3 +184,93 @@ def random_frames(n, H, W, bits, seed) -> np.ndarray:
     hi = (1 << bits)
     dt = np.uint8 if bits <= 8 else np.uint16
     return rng.integers(0, hi, size=(n, H, W), dtype=np.int64).astype(dt)
+
+
+# ------------------------------------------------ autofocus holograms
+
+AF_Z_RANGE = (0.10, 0.60)
+
+
+def _pixel_point_field(N, pitch, lam, z, ipx, ipy, amps):
+    """Sum of converging spherical waves a_m exp(-i k r_m) z / r_m from scatterers at
+    pixel centres (column ipx, row ipy of the sensor grid). Every scatterer's wave
+    is a shifted copy of one point-spread function, tabulated once on the 2N x 2N
+    grid of pixel offsets (phase k (r - z) in float64 from rho^2 / (r + z), the
+    exponential in complex64; the common factor exp(-i k z) is dropped)."""
+    k = 2.0 * np.pi / lam
+    d = (np.arange(2 * N) - N) * pitch
+    rho2 = d[None, :] ** 2 + d[:, None] ** 2
+    r = np.sqrt(rho2 + z * z)
+    ph = np.mod(k * rho2 / (r + z), 2.0 * np.pi).astype(np.float32)
+    psf = np.empty(ph.shape, dtype=np.complex64)
+    psf.real = np.cos(ph)
+    psf.imag = -np.sin(ph)
+    psf *= (z / r).astype(np.float32)
+    out = np.zeros((N, N), dtype=np.complex64)
+    for px, py, am in zip(ipx, ipy, amps):
+        out += np.complex64(am) * psf[N - py:2 * N - py, N - px:2 * N - px]
+    return out.astype(np.complex128)
+
+
+def autofocus_hologram(N, seed, index, z=None, n_pts=24, radius_px=32.0, pitch=20e-6, lam=852e-9,
+                       bits=12, ref_ratio=10.0, mean_fraction=0.30):
+    """One off-axis hologram of a sparse point-scatterer object for the autofocus
+    workload, and the object distance z it was recorded at.
+
+    The object: n_pts scatterers at pixel centres in a disk of radius radius_px
+    pixels (a fixed physical size, whatever N), amplitudes 0.25 or 1 (30 % bright: amplitude
+    structure, so that the in-focus image has contrast) with uniform random
+    phases, at z ~ U[0.10, 0.60] m unless z is given. Sensor field, reference,
+    scaling and Poisson noise follow the stream scenes of this module. Hologram
+    `index` of set `seed` depends only on (seed, index).
+    """
+    rng = np.random.Generator(np.random.PCG64([seed, index]))
+    if z is None:
+        z = AF_Z_RANGE[0] + (AF_Z_RANGE[1] - AF_Z_RANGE[0]) * rng.random()
+    rad = radius_px * np.sqrt(rng.random(n_pts))
+    ang = 2.0 * np.pi * rng.random(n_pts)
+    ipx = np.rint(N / 2 + rad * np.cos(ang)).astype(np.int64)
+    ipy = np.rint(N / 2 + rad * np.sin(ang)).astype(np.int64)
+    amp = (0.25 + 0.75 * (rng.random(n_pts) < 0.3)) * np.exp(2j * np.pi * rng.random(n_pts))
+    f = _pixel_point_field(N, pitch, lam, z, ipx, ipy, amp)
+    f /= np.sqrt(np.mean(np.abs(f) ** 2))
+    c = np.arange(N)
+    ref = np.sqrt(ref_ratio) * np.exp(1j * 2.0 * np.pi * (c[None, :] + c[:, None]) / 4.0)
+    inten = np.abs(ref + f) ** 2
+    full = (1 << bits) - 1
+    inten *= mean_fraction * full / inten.mean()
+    inten = rng.poisson(inten).astype(np.float64)
+    np.clip(inten, 0, full, out=inten)
+    return inten.astype(np.uint16 if bits > 8 else np.uint8), float(z)
+
+
+def _af_chunk(args):
+    N, seed, lo, hi = args
+    fr = np.empty((hi - lo, N, N), dtype=np.uint16)
+    zs = np.empty(hi - lo)
+    for i in range(lo, hi):
+        fr[i - lo], zs[i - lo] = autofocus_hologram(N, seed, i)
+    return lo, fr, zs
+
+
+def autofocus_set(n, N=256, seed=1004, workers=1):
+    """Holograms 0..n-1 of set `seed` (uint16, (n, N, N)) and their distances z.
+    workers > 1 spreads the work over a spawn-started process pool (start it
+    before any CUDA call: a forked child of a CUDA process can hang)."""
+    frames = np.empty((n, N, N), dtype=np.uint16)
+    zs = np.empty(n)
+    step = max(1, min(256, -(-n // max(1, workers * 4))))
+    jobs = [(N, seed, lo, min(n, lo + step)) for lo in range(0, n, step)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for lo, fr, z in pool.imap_unordered(_af_chunk, jobs):
+                frames[lo:lo + len(z)] = fr
+                zs[lo:lo + len(z)] = z
+    else:
+        for job in jobs:
+            lo, fr, z = _af_chunk(job)
+            frames[lo:lo + len(z)] = fr
+            zs[lo:lo + len(z)] = z
+    return frames, zs
+
