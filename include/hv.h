@@ -209,6 +209,35 @@ hv_status hv_synchronize(hv_handle* h);
 hv_status hv_close(hv_handle* h);
 
 /* ------------------------------------------------------------------------
+ * Autofocus. The paper propagates to a distance the user sets (Sec. III-B.1);
+ * these calls give the plain focus search (a sweep of distances scored by a
+ * focus metric) and the input of the small network that replaces it
+ * (include/hv_af.h). Both use the handle's frame size, pixel depth,
+ * wavelength and pitches (its current settings) and its scratch buffers;
+ * sides must be powers of two in [64, 512]. Frames are raw device frames
+ * [n][height][width] (uint8 or uint16 by pixel_bits). Work is queued on the
+ * handle's stream.
+ * ------------------------------------------------------------------------ */
+
+/* Plain z-sweep: for each of the nz distances z[j] (host array, metres), the
+ * angular-spectrum propagation of the hologram with its mean removed (the
+ * transfer function's DC bin set to zero), then the Tamura coefficient
+ * sqrt(sigma / mu) of the amplitude |U| over the frame (population sigma; 0
+ * when mu = 0). metric: device float array [n][nz]. The distances' transfer
+ * functions are built on the host in float64 and cached until the distances or
+ * the optics change. Errors: HV_ERR_ARG (NULL, n = 0, nz not in [1, 1024]),
+ * HV_ERR_STATE (no settings), HV_ERR_UNSUPPORTED (frame size), HV_ERR_NOMEM,
+ * HV_ERR_CUDA. */
+hv_status hv_focus_sweep(hv_handle* h, const void* frames, uint32_t n, const double* z, uint32_t nz, float* metric);
+
+/* Network input of each frame: the magnitude of the centred 2-D spectrum of
+ * the mean-removed hologram, averaged over 2 x 2 bins, log(1 + .), standardised
+ * to zero mean and unit population deviation over the frame. out: device array
+ * [n][height/2][width/2] of bfloat16 (raw 16-bit patterns, rounded to nearest,
+ * ties to even). Errors as hv_focus_sweep. */
+hv_status hv_af_features(hv_handle* h, const void* frames, uint32_t n, void* out_bf16);
+
+/* ------------------------------------------------------------------------
  * Groups: several handles (streams of uneven frame sizes, window lengths and
  * transforms) stepped together. The paper runs one camera stream through the
  * pipeline of Sec. III-B (ingest, spatial demodulation, time queue, temporal

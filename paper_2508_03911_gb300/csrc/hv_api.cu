@@ -70,6 +70,12 @@ struct hv_handle {
   hv_profile prof_acc{};
   std::vector<cudaEvent_t> pca_ev;   // groups of 4 per recorded PCA window
   size_t pca_ev_used = 0;
+  // focus sweep: transfer functions of the swept distances (DC bin zero), cached
+  float2* sw_tables = nullptr;
+  size_t sw_bytes = 0;
+  std::vector<double> sw_key;        // W, H, lambda, pitches, then the distances
+  double* sw_acc = nullptr;
+  size_t sw_acc_bytes = 0;
 };
 
 // A group of handles stepped together (hv_render_group).
@@ -933,9 +939,128 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->asp_ht);
   dfree(h->staging);
   if (h->pca_ws) cudaFree(h->pca_ws);
+  if (h->sw_tables) cudaFree(h->sw_tables);
+  if (h->sw_acc) cudaFree(h->sw_acc);
   if (h->raw) cudaFree(h->raw);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+  return HV_OK;
+}
+
+// ------------------------------------------------------------- autofocus
+
+// Frames [n][H][W] in device memory as a ring for the pass kernels.
+static SpatialArgs af_args(const hv_handle* h, const void* frames, uint32_t n) {
+  SpatialArgs sa{};
+  sa.spatial = HV_SPATIAL_ASP;  // no chirp in the column pass
+  sa.in_kind = h->bits == 8 ? IN_U8 : IN_U16;
+  sa.W = h->W;
+  sa.H = h->H;
+  sa.raw = RingRef{const_cast<void*>(frames), n, 0};
+  sa.scratch1 = h->s1;
+  sa.scratch2 = h->s2;
+  sa.tw_w = h->tw + tw_offset(h->W);
+  sa.tw_h = h->tw + tw_offset(h->H);
+  return sa;
+}
+
+static hv_status af_prepare(hv_handle* h, const void* frames, uint32_t n, uint32_t chunk) {
+  if (!frames || n == 0) return fail(h, HV_ERR_ARG, "frames is NULL or n = 0");
+  if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "no settings");
+  HV_CU(h, cudaSetDevice(h->device));
+  hv_status s = apply_pending(h);
+  if (s != HV_OK) return s;
+  SpatialArgs probe{};
+  probe.spatial = HV_SPATIAL_ASP;
+  probe.W = h->W;
+  probe.H = h->H;
+  if (!spatial_pp_supported(probe)) return fail(h, HV_ERR_UNSUPPORTED, "autofocus needs sides in [64, 512]");
+  const size_t need = size_t(chunk) * h->W * h->H * sizeof(float2);
+  s = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need);
+  if (s == HV_OK) s = ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need);
+  return s;
+}
+
+hv_status hv_focus_sweep(hv_handle* h, const void* frames, uint32_t n, const double* z, uint32_t nz, float* metric) {
+  if (!h) return HV_ERR_ARG;
+  if (!z || !metric || nz == 0 || nz > 1024) return fail(h, HV_ERR_ARG, "bad distances or output");
+  const uint32_t chunk = 64;
+  hv_status s = af_prepare(h, frames, n, std::min(n, chunk));
+  if (s != HV_OK) return s;
+  const uint32_t W = h->W, H = h->H;
+  const hv_params& p = h->cur;
+  // transfer functions H_j (transposed [kx][ky], 1/(W H) folded in, DC bin zero)
+  std::vector<double> key = {double(W), double(H), p.lambda_m, p.pitch_x_m, p.pitch_y_m};
+  key.insert(key.end(), z, z + nz);
+  if (key != h->sw_key) {
+    const size_t per = size_t(W) * H;
+    s = ensure(h, reinterpret_cast<void**>(&h->sw_tables), &h->sw_bytes, per * nz * sizeof(float2));
+    if (s != HV_OK) return s;
+    std::vector<float2> host(per * nz);
+    const double k = 2.0 * M_PI / p.lambda_m, scale = 1.0 / (double(W) * double(H));
+    for (uint32_t kx = 0; kx < W; ++kx) {
+      const double fx = 2.0 * M_PI * (kx < W / 2 ? double(kx) : double(kx) - W) / (W * p.pitch_x_m);
+      for (uint32_t ky = 0; ky < H; ++ky) {
+        const double fy = 2.0 * M_PI * (ky < H / 2 ? double(ky) : double(ky) - H) / (H * p.pitch_y_m);
+        const double kz2 = k * k - fx * fx - fy * fy;
+        for (uint32_t j = 0; j < nz; ++j) {
+          float2 v = make_float2(0.f, 0.f);
+          if (kz2 >= 0 && (kx | ky)) {
+            const double ph = z[j] * std::sqrt(kz2);
+            v = make_float2(float(std::cos(ph) * scale), float(std::sin(ph) * scale));
+          }
+          host[j * per + size_t(kx) * H + ky] = v;
+        }
+      }
+    }
+    HV_CU(h, cudaMemcpyAsync(h->sw_tables, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                             h->stream));
+    HV_CU(h, cudaStreamSynchronize(h->stream));
+    h->sw_key = key;
+  }
+  s = ensure(h, reinterpret_cast<void**>(&h->sw_acc), &h->sw_acc_bytes, size_t(n) * nz * 2 * sizeof(double));
+  if (s != HV_OK) return s;
+  HV_CU(h, cudaMemsetAsync(h->sw_acc, 0, size_t(n) * nz * 2 * sizeof(double), h->stream));
+  for (uint32_t a = 0; a < n; a += chunk) {
+    SpatialArgs sa = af_args(h, frames, n);
+    sa.raw.slot0 = a;
+    sa.n = std::min(chunk, n - a);
+    cudaError_t e = launch_pp_pass(sa, PASS_COL_FFT, h->stream);
+    for (uint32_t j = 0; j < nz && e == cudaSuccess; ++j) {
+      sa.asp_ht = h->sw_tables + size_t(j) * W * H;
+      e = launch_pp_pass(sa, PASS_ROW_ASP, h->stream);
+      sa.tam_acc = h->sw_acc + (size_t(a) * nz + j) * 2;
+      sa.tam_stride = nz * 2;
+      if (e == cudaSuccess) e = launch_pp_pass(sa, PASS_COL_IFFT_TAMURA, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "focus sweep passes");
+    h->st.kernel_launches += 1 + 2 * nz;
+  }
+  cudaError_t e = launch_tamura_finish(h->sw_acc, n * nz, W * H, metric, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tamura");
+  h->st.kernel_launches += 1;
+  return HV_OK;
+}
+
+hv_status hv_af_features(hv_handle* h, const void* frames, uint32_t n, void* out_bf16) {
+  if (!h) return HV_ERR_ARG;
+  if (!out_bf16) return fail(h, HV_ERR_ARG, "output is NULL");
+  const uint32_t chunk = 64;
+  hv_status s = af_prepare(h, frames, n, std::min(n, chunk));
+  if (s != HV_OK) return s;
+  const size_t cells = size_t(h->W / 2) * (h->H / 2);
+  for (uint32_t a = 0; a < n; a += chunk) {
+    SpatialArgs sa = af_args(h, frames, n);
+    sa.raw.slot0 = a;
+    sa.n = std::min(chunk, n - a);
+    sa.tq = RingRef{h->s2, sa.n, 0};  // spectra [ky][kx] of this chunk
+    cudaError_t e = launch_pp_pass(sa, PASS_COL_FFT, h->stream);
+    if (e == cudaSuccess) e = launch_pp_pass(sa, PASS_ROW_FFT, h->stream);
+    if (e == cudaSuccess)
+      e = launch_af_features(h->s2, sa.n, h->W, h->H, static_cast<uint16_t*>(out_bf16) + a * cells, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "feature passes");
+    h->st.kernel_launches += 3;
+  }
   return HV_OK;
 }
 

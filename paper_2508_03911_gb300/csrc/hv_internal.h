@@ -33,12 +33,23 @@ struct SpatialArgs {
   const float2* chirp_y;// along y (length H)
   int use_cluster;      // 1: whole-frame cluster kernel when the size allows it
   int use_pp;           // 1: persistent prefetching multi-pass kernels when the size allows
+  double* tam_acc;      // focus sweep: frame i adds (sum |u|, sum |u|^2) at tam_acc + i * tam_stride
+  uint32_t tam_stride;
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);
 bool spatial_pp_supported(const SpatialArgs& a);
 cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launches);
 cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* launches);
+
+// Single passes of the persistent multi-pass transform (sides 64..512):
+//   PASS_COL_FFT   raw -> column FFT (chirped when spatial is Fresnel) -> scratch1 [ky][x]
+//   PASS_ROW_ASP   scratch1 -> row FFT, x asp_ht, row IFFT -> scratch2 [x][ky]
+//   PASS_COL_IFFT  scratch2 -> column IFFT -> tq ring [y][x]
+//   PASS_ROW_FFT   scratch1 -> row FFT -> tq ring [ky][kx]
+//   PASS_COL_IFFT_TAMURA  scratch2 -> column IFFT -> (sum |u|, sum |u|^2) per frame
+enum { PASS_COL_FFT = 0, PASS_ROW_ASP = 1, PASS_COL_IFFT = 2, PASS_ROW_FFT = 3, PASS_COL_IFFT_TAMURA = 4 };
+cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s);
 
 // STFT band moments of nwin windows (Sec. III-B.1), time-queue ring -> images.
 struct StftArgs {
@@ -86,6 +97,13 @@ uint32_t cov_tc_tiles(uint32_t T, uint8_t* ti, uint8_t* tj);
 cudaError_t launch_cov_tc(PcaArgs& a, cudaStream_t s, int* launches);
 // ev (optional, 4 events): before covariance, after covariance, after eigensolver, after projection
 cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev);
+
+// Autofocus: Tamura coefficients from per-(frame, distance) amplitude sums, and the
+// network input (2 x 2 binned log-magnitude spectrum, standardised, bfloat16)
+// from n unshifted spectra [ky][kx].
+cudaError_t launch_tamura_finish(const double* acc, uint32_t count, uint32_t pixels, float* metric, cudaStream_t s);
+cudaError_t launch_af_features(const float2* spec, uint32_t n, uint32_t W, uint32_t H, void* out_bf16,
+                               cudaStream_t s);
 
 // Copy propagated frames out as interleaved complex images.
 cudaError_t launch_copy_frames(const RingRef& tq, uint32_t n, uint32_t hw, float* out,

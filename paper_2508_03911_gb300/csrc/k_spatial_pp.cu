@@ -17,6 +17,8 @@
 //   P3a column IFFT (length H) of 16 columns x of S2 -> time queue [y][x]
 //   P2f row FFT of 16 rows ky of S1 -> time queue [ky][kx] (through shared memory:
 //       the natural layout needs lanes along kx)
+//   P3t as P3a, but instead of storing the field it adds sum |u| and sum |u|^2 of
+//       the strip to the frame's two float64 accumulators (focus sweep)
 // Twiddles of the pass length are copied to shared memory once per CTA.
 #include "fft_dev.cuh"
 #include "hv_internal.h"
@@ -27,7 +29,8 @@ namespace hv {
 namespace {
 
 constexpr int PP_BT = 16;
-enum { PK_P1 = 0, PK_P2A = 1, PK_P3A = 2, PK_P2F = 3 };
+enum { PK_P1 = PASS_COL_FFT, PK_P2A = PASS_ROW_ASP, PK_P3A = PASS_COL_IFFT, PK_P2F = PASS_ROW_FFT,
+       PK_P3T = PASS_COL_IFFT_TAMURA };
 
 template <int L>
 struct PpCfg {
@@ -84,6 +87,17 @@ struct GlobalOut {
   float2* out;
   uint32_t stride;
   __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(k) * stride + b] = v; }
+};
+
+// Sum of |v| and |v|^2 over the bins this thread holds (Tamura accumulation).
+struct AmpSums {
+  static constexpr bool kSyncFirst = false;
+  float* s;  // s[0] += |v|, s[1] += |v|^2
+  __device__ __forceinline__ void operator()(int, int, float2 v) const {
+    const float q = fmaf(v.x, v.x, v.y * v.y);
+    s[0] += sqrtf(q);
+    s[1] += q;
+  }
 };
 
 // Bin k of line b times the transposed transfer function, back to the buffer.
@@ -208,20 +222,20 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
   const bool fresnel = a.spatial == HV_SPATIAL_FRESNEL;
   const bool u8 = a.in_kind == IN_U8;
   // the pass length: P1 and P3a run along y (length H), P2a and P2f along x
-  const float2* twg = (PK == PK_P1 || PK == PK_P3A) ? a.tw_h : a.tw_w;
+  const float2* twg = (PK == PK_P1 || PK == PK_P3A || PK == PK_P3T) ? a.tw_h : a.tw_w;
   for (int e = tid; e < L; e += C::NT) {
     tws[e] = __ldg(&twg[e]);
     if (PK == PK_P1 && fresnel) cys[e] = __ldg(&a.chirp_y[e]);
   }
   // lines per frame of the other axis: W columns (P1, P3a) or H rows (P2a, P2f)
-  const uint32_t LO = (PK == PK_P1 || PK == PK_P3A) ? a.W : a.H;
+  const uint32_t LO = (PK == PK_P1 || PK == PK_P3A || PK == PK_P3T) ? a.W : a.H;
 
   auto issue = [&](int it, int cur) {
     const int i = it >> strip_log2, s0 = (it & smask) * C::BT;
     if constexpr (PK == PK_P1) {
       prefetch_raw<L>(a, i, s0, cur == 0 ? raw0 : raw1);
     } else {
-      const float2* base = PK == PK_P3A ? a.scratch2 : a.scratch1;
+      const float2* base = (PK == PK_P3A || PK == PK_P3T) ? a.scratch2 : a.scratch1;
       prefetch_lines<L>(base + size_t(i) * L * LO + size_t(s0) * L, cur == 0 ? buf0 : buf1);
     }
   };
@@ -261,6 +275,28 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
       // time queue [y][x]: sample y of column s0 + b at tq[y * W + s0 + b]
       pp_stages<L, 1, +1>(SmemSrc<C::LD>{buf}, buf, tws,
                           GlobalOut{static_cast<float2*>(a.tq.base) + tslot * size_t(a.W) * a.H + s0, a.W});
+    } else if constexpr (PK == PK_P3T) {
+      float2* buf = cur == 0 ? buf0 : buf1;
+      float acc[2] = {0.f, 0.f};
+      pp_stages<L, 1, +1>(SmemSrc<C::LD>{buf}, buf, tws, AmpSums{acc});
+      // block sums: warp shuffles, then one partial per warp in shared memory
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+      }
+      __shared__ float red[2][C::NT / 32];
+      if ((tid & 31) == 0) {
+        red[0][tid >> 5] = acc[0];
+        red[1][tid >> 5] = acc[1];
+      }
+      __syncthreads();
+      if (tid < 2) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < C::NT / 32; ++w) t += red[tid][w];
+        atomicAdd(&a.tam_acc[size_t(i) * a.tam_stride + tid], double(t));
+      }
     } else {
       float2* buf = cur == 0 ? buf0 : buf1;
       pp_stages<L, 1, -1>(SmemSrc<C::LD>{buf}, buf, tws, ToSmem<C::LD>{buf});
@@ -325,7 +361,34 @@ static cudaError_t pp_w(const SpatialArgs& a, cudaStream_t s, int* launches) {
   return cudaErrorInvalidValue;
 }
 
+template <int PK>
+static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
+  // pass length and number of lines: columns (length H, W lines) or rows (length W, H lines)
+  const bool cols = PK == PK_P1 || PK == PK_P3A || PK == PK_P3T;
+  const uint32_t L = cols ? a.H : a.W, lines = cols ? a.W : a.H;
+  switch (L) {
+    case 64: return launch_pp<64, PK>(a, lines, s);
+    case 128: return launch_pp<128, PK>(a, lines, s);
+    case 256: return launch_pp<256, PK>(a, lines, s);
+    case 512: return launch_pp<512, PK>(a, lines, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (!spatial_pp_supported(a)) return cudaErrorInvalidValue;
+  switch (pass) {
+    case PASS_COL_FFT: return pass_by_len<PK_P1>(a, s);
+    case PASS_ROW_ASP: return pass_by_len<PK_P2A>(a, s);
+    case PASS_COL_IFFT: return pass_by_len<PK_P3A>(a, s);
+    case PASS_ROW_FFT: return pass_by_len<PK_P2F>(a, s);
+    case PASS_COL_IFFT_TAMURA: return pass_by_len<PK_P3T>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 bool spatial_pp_supported(const SpatialArgs& a) {
   auto ok = [](uint32_t v) { return v >= 64 && v <= 512; };  // two strip buffers must fit

@@ -119,6 +119,9 @@ def lib() -> C.CDLL:
         "hv_group_get_stats": ([C.c_void_p, P(hv_group_stats)], C.c_int),
         "hv_group_last_error": ([C.c_void_p], C.c_char_p),
         "hv_group_close": ([C.c_void_p], C.c_int),
+        "hv_focus_sweep": ([C.c_void_p, C.c_void_p, C.c_uint32, P(C.c_double), C.c_uint32, C.c_void_p],
+                           C.c_int),
+        "hv_af_features": ([C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p], C.c_int),
         "hv_version": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -271,6 +274,36 @@ def hv_last_error(h=None) -> str:
 
 def hv_version() -> str:
     return lib().hv_version().decode()
+
+
+# --------------------------------------------------------------- autofocus
+
+def hv_focus_sweep(h, frames, z, metric):
+    """Tamura coefficient of every (frame, distance): frames a device tensor
+    (n, H, W), z a sequence of distances, metric a float32 device tensor (n, nz)."""
+    ptr, kind, _ = _ptr_kind(frames)
+    mptr, mkind, mbytes = _ptr_kind(metric)
+    if kind != HV_MEM_DEVICE or mkind != HV_MEM_DEVICE:
+        raise ValueError("frames and metric must be device memory")
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    n = frames.shape[0]
+    if mbytes < n * zz.size * 4:
+        raise ValueError("metric too small")
+    _check(h, lib().hv_focus_sweep(h, C.c_void_p(ptr), n, zz.ctypes.data_as(C.POINTER(C.c_double)),
+                                   zz.size, C.c_void_p(mptr)))
+
+
+def hv_af_features(h, frames, out):
+    """Network inputs (n, H/2, W/2) as bfloat16 bit patterns into the device tensor out
+    (torch.int16 or torch.bfloat16, n * H/2 * W/2 elements)."""
+    ptr, kind, _ = _ptr_kind(frames)
+    optr, okind, obytes = _ptr_kind(out)
+    if kind != HV_MEM_DEVICE or okind != HV_MEM_DEVICE:
+        raise ValueError("frames and out must be device memory")
+    n, H, W = frames.shape
+    if obytes < n * (H // 2) * (W // 2) * 2:
+        raise ValueError("out too small")
+    _check(h, lib().hv_af_features(h, C.c_void_p(ptr), n, C.c_void_p(optr)))
 
 
 # ------------------------------------------------------------------ groups
