@@ -100,6 +100,17 @@ WORKLOADS["group_uneven_8"] = dict(
     N=0, bits=12, spatial="mixed", z=0.0, T=0, S=0, fs=71400.0, band=(0, 0),
     moments=("M0", "M1", "M2"), batch=sum(GROUP_WINDOWS * t for _, t, _ in GROUP_MEMBERS), batches=1,
     pool=0, scene="random", group=True)
+WORKLOADS["autofocus_256"] = dict(
+    desc="learned autofocus on 256x256 uint16 (12-bit) holograms of point-scatterer objects at "
+         "z ~ U[0.10, 0.60] m (seed 1005): network input (2x2-binned log-magnitude spectrum, "
+         "128x128 bfloat16) and CNN inference (4 conv 3x3 stride 2, 16/32/64/64 channels, average "
+         "pool, MLP 64-32-1; He-uniform weights: throughput does not depend on them); the plain "
+         "64-distance ASP + Tamura sweep timed beside it; 512 holograms per step",
+    N=256, bits=12, spatial="asp", z=0.0, T=0, S=0, fs=0.0, band=(0, 0), moments=(), batch=512,
+    batches=1, pool=512, scene="autofocus", autofocus=True)
+# conv: 2 * CI * 9 * CO * HO * WO per layer; dense 2 * 64 * 32 + 2 * 32
+AF_FLOPS = (2 * 1 * 9 * 16 * 64 * 64 + 2 * 16 * 9 * 32 * 32 * 32 + 2 * 32 * 9 * 64 * 16 * 16
+            + 2 * 64 * 9 * 64 * 8 * 8 + 2 * 64 * 32 + 2 * 32)
 DEFAULT = "stream_fresnel_256_t512_s64"
 METRIC = "raw frames/s rendered"
 
@@ -672,6 +683,158 @@ def main_group(args):
 
 
 
+# ------------------------------------------------------------- autofocus
+
+def main_autofocus(args):
+    """Features + network inference per hologram (the learned path), the plain sweep
+    beside it, end to end from pinned host frames, and the oracle on a sample."""
+    import torch
+
+    from paper_2508_03911_gb300 import af, hv
+    from paper_2508_03911_gb300 import autofocus as AF
+    w = WORKLOADS[args.workload]
+    B = w["batch"]
+    frames, _ = synth.autofocus_set(B, N=256, seed=1005, workers=min(16, os.cpu_count() or 1))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    r = hv.Renderer(256, 256, 16, B, stream=stream.cuda_stream)
+    r.set_params(256, 256, spatial="asp", z=0.3, T=16, stride=16, band=(1, 7))
+    net = af.Autofocus(B, stream=stream.cuda_stream)
+    net.set_params(AF.he_uniform(1))
+    fr = torch.from_numpy(frames.view(np.int16)).to(dev)
+    feats = torch.empty((B, 1, 128, 128), dtype=torch.bfloat16, device=dev)
+    z = torch.empty(B, dtype=torch.float32, device=dev)
+    metric = torch.empty((B, AF.NZ), dtype=torch.float32, device=dev)
+    zs = AF.z_grid()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        hv.hv_af_features(r.h, fr, feats)
+        if ev is not None:
+            ev[1].record(stream)
+        net.forward(feats, z)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        hv.hv_focus_sweep(r.h, fr, zs, metric)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(None)
+    clocks.start()
+    time.sleep(0.6)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    s0 = r.stats()["kernel_launches"]
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    ms = t0.elapsed_time(t1)
+    feat_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    net_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    launches = (r.stats()["kernel_launches"] - s0) + args.steps * 5  # network: 4 convolutions + head
+    # the plain sweep on the same holograms
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(max(1, args.steps // 2)):
+        hv.hv_focus_sweep(r.h, fr, zs, metric)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    clk = clocks.stop()
+    # end to end: pinned host holograms in, distances out
+    host = torch.from_numpy(frames.view(np.int16)).pin_memory()
+    zh = torch.empty(B, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    for _ in range(args.steps):
+        fr.copy_(host, non_blocking=True)
+        step()
+        zh.copy_(z, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - tt) / args.steps
+    value = B * args.steps / (ms / 1e3)
+    tflops = AF_FLOPS * B / (net_ms / 1e3) / 1e12
+    line = {
+        "metric": "holograms/s focused", "value": round(value, 1), "unit": "holograms/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": w["desc"], "frame": [256, 256],
+                   "pixel_bits": 12, "holograms_per_step": B, "network_input": [128, 128],
+                   "l2": "inputs below L2 size (64 MB of frames): the same batch each step",
+                   "parallelism": "replicas x1"},
+        "roofline": {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+                     "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                     "kernel": "CNN forward (4 bf16 convolutions with float32 accumulation + head)",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "flops_per_hologram": AF_FLOPS},
+        "stage_ms_per_step": {"features": round(feat_ms, 4), "network": round(net_ms, 4)},
+        "sweep": {"holograms_per_s": round(B / (sweep_ms / 1e3), 1), "ms_per_step": round(sweep_ms, 4),
+                  "distances": AF.NZ, "speedup_of_network": round(sweep_ms / (ms / args.steps), 2)},
+        "e2e": {"value": round(B / e2e_s, 1), "unit": "holograms/s",
+                "h2d_bytes_per_step": int(host.numel() * 2), "d2h_bytes_per_step": int(B * 4)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    net.close()
+    r.close()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = autofocus_oracle_sample(frames[:8])
+    print(json.dumps(line), flush=True)
+
+
+def autofocus_oracle_sample(frames):
+    """The FP64 oracle's network input and forward pass on a few holograms."""
+    from oracle import af_oracle as A
+    from paper_2508_03911_gb300 import autofocus as AF
+    flat = AF.he_uniform(1).astype(np.float64)
+    t0 = time.perf_counter()
+    x = np.stack([A.features(f) for f in frames])[:, None]
+    A.forward(flat, x)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(frames) / dt, 2), "unit": "holograms/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(frames)} holograms: FP64 features + CNN forward, {dt:.1f} s on 1 host core"}
+
+
+
+def main_autofocus_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    frames, _ = synth.autofocus_set(4, N=256, seed=1005)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v = autofocus_oracle_sample(frames)
+        if i >= args.warmup:
+            vals.append(v["value"])
+    value = float(np.median(vals))
+    w = WORKLOADS[args.workload]
+    line = {"impl": "reference", "metric": "holograms/s focused", "value": round(value, 3),
+            "unit": "holograms/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "frame": [256, 256],
+                       "pixel_bits": 12, "holograms_per_step": w["batch"], "network_input": [128, 128],
+                       "l2": "inputs below L2 size (64 MB of frames): the same batch each step",
+                       "parallelism": "replicas x1"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "holograms/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: 4 holograms through the FP64 oracle's features and "
+                                       "CNN forward on 1 host core"},
+            "e2e": {"value": round(value, 3), "unit": "holograms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -692,6 +855,12 @@ def main():
         args.warmup = 3
     if WORKLOADS[args.workload].get("group") and args.impl == "hv":
         main_group(args)
+        return
+    if WORKLOADS[args.workload].get("autofocus"):
+        if args.impl == "hv":
+            main_autofocus(args)
+        else:
+            main_autofocus_reference(args)
         return
     w = dict(WORKLOADS[args.workload])
     if args.precision:
