@@ -289,3 +289,54 @@ def tamura(img: np.ndarray) -> float:
     if mu == 0:
         return 0.0
     return math.sqrt(a.std() / mu)
+
+# ----------------------------------------------------------- post-processing
+
+
+def gaussian_kernel(size: int, sigma: float) -> np.ndarray:
+    """size x size kernel exp(-(dx^2 + dy^2) / (2 sigma^2)), dx, dy in -(size//2)..size//2,
+    normalised to sum 1."""
+    r = np.arange(size) - size // 2
+    g = np.exp(-(r[None, :] ** 2 + r[:, None] ** 2) / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def convolve_periodic(img: np.ndarray, kern: np.ndarray) -> np.ndarray:
+    """out[y, x] = sum_{a, b} kern[a, b] img[(y + a - K//2) mod H, (x + b - K//2) mod W].
+
+    READING: the paper convolves rendered images with a given kernel (Sec. III-B,
+    post-processing) without naming the boundary; the image is taken as periodic,
+    as a Fourier-domain convolution of the same size computes it. The kernel is
+    applied as a correlation (not flipped), so a user kernel acts as written.
+    """
+    K = kern.shape[0]
+    out = np.zeros(img.shape, dtype=np.float64)
+    for a in range(K):
+        for b in range(K):
+            out += kern[a, b] * np.roll(img, shift=(K // 2 - a, K // 2 - b), axis=(0, 1))
+    return out
+
+
+def postprocess(images: np.ndarray, kern=None, renormalize=False, accumulate=1) -> np.ndarray:
+    """Post-processing of one stream of rendered images (Sec. III-B): convolution,
+    then re-normalisation, then the moving average of the accumulation buffer.
+
+    images: (n, H, W), in rendering order. READINGS: re-normalisation divides an
+    image by its spatial mean (0 where the mean is 0); the accumulation buffer of
+    size A outputs, for image t, the mean of images max(0, t - A + 1) .. t after
+    the steps above.
+    """
+    out = []
+    for img in np.asarray(images, dtype=np.float64):
+        v = convolve_periodic(img, np.asarray(kern, dtype=np.float64)) if kern is not None else img.copy()
+        if renormalize:
+            m = v.mean()
+            v = v / m if m != 0 else np.zeros_like(v)
+        out.append(v)
+    out = np.stack(out) if out else np.zeros((0,) + tuple(np.shape(images)[1:]))
+    acc = np.empty_like(out)
+    for t in range(out.shape[0]):
+        lo = max(0, t - accumulate + 1)
+        acc[t] = out[lo:t + 1].mean(axis=0)
+    return acc
+
