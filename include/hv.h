@@ -209,6 +209,40 @@ hv_status hv_synchronize(hv_handle* h);
 hv_status hv_close(hv_handle* h);
 
 /* ------------------------------------------------------------------------
+ * Post-processing of rendered images (Sec. III-B, "post processing and image
+ * accumulation"): each rendered image (every moment of STFT, the energy of
+ * PCA) is, in this order,
+ *   1. convolved with a K x K kernel, the image taken as periodic:
+ *      out[y][x] = sum_{a,b} k[a][b] img[(y + a - K/2) mod H][(x + b - K/2) mod W]
+ *      (the kernel applied as written, not flipped);
+ *   2. re-normalised: divided by its spatial mean (0 where the mean is 0);
+ *   3. accumulated: replaced by the mean of the last A images of the same
+ *      output (the same moment of the previous windows), fewer while fewer
+ *      exist.
+ * Not applicable to HV_TEMPORAL_NONE.
+ * ------------------------------------------------------------------------ */
+#define HV_POST_MAX_KERNEL 31u
+#define HV_POST_MAX_ACCUMULATE 64u
+
+typedef struct {
+  uint32_t struct_size;  /* sizeof(hv_post)                                               */
+  uint32_t kernel_size;  /* K: 0 (no convolution) or odd, 1 .. HV_POST_MAX_KERNEL          */
+  const float* kernel;   /* host, K * K row-major weights (copied by the call); NULL: the
+                            Gaussian exp(-(dx^2 + dy^2) / (2 sigma^2)) normalised to sum 1 */
+  float gauss_sigma;     /* sigma of that Gaussian (> 0 when kernel is NULL and K > 0)     */
+  int32_t renormalize;   /* 1: step 2 on; 0: off                                          */
+  uint32_t accumulate;   /* A, 1 .. HV_POST_MAX_ACCUMULATE (1: no accumulation)            */
+  uint32_t reserved;
+} hv_post;
+
+/* Post-processing settings: validated now, applied at the start of the next
+ * hv_render (like hv_set_params); applying them, or new settings, restarts
+ * the accumulation history. K = 0, renormalize = 0 and A = 1 turn it off.
+ * Errors: HV_ERR_ARG (bad fields); HV_ERR_UNSUPPORTED from hv_render when the
+ * temporal analysis is HV_TEMPORAL_NONE and post-processing is on. */
+hv_status hv_set_postprocess(hv_handle* h, const hv_post* p);
+
+/* ------------------------------------------------------------------------
  * Autofocus. The paper propagates to a distance the user sets (Sec. III-B.1);
  * these calls give the plain focus search (a sweep of distances scored by a
  * focus metric) and the input of the small network that replaces it

@@ -76,6 +76,18 @@ struct hv_handle {
   std::vector<double> sw_key;        // W, H, lambda, pitches, then the distances
   double* sw_acc = nullptr;
   size_t sw_acc_bytes = 0;
+  // post-processing: settings (current, pending), kernel weights, image ring
+  hv_post post_cur{}, post_pend{};
+  std::vector<float> post_k_cur, post_k_pend;
+  bool post_pending = false, post_active = false, post_dirty = true;
+  float* post_kdev = nullptr;
+  size_t post_kdev_bytes = 0;
+  float* post_ring = nullptr;
+  size_t post_ring_bytes = 0;
+  double* post_sums = nullptr;
+  size_t post_sums_bytes = 0;
+  uint32_t post_R = 0;
+  uint64_t post_count = 0;
 };
 
 // A group of handles stepped together (hv_render_group).
@@ -407,6 +419,7 @@ hv_status apply_pending(hv_handle* h) {
   h->cur = p;
   h->has_params = true;
   h->pending = false;
+  h->post_dirty = true;  // ring sizes depend on the settings
   h->W = W;
   h->H = H;
   h->T = d.T;
@@ -581,6 +594,51 @@ hv_status tune_spatial(hv_handle* h) {
   return HV_OK;
 }
 
+// Applies pending post-processing settings, and (re)sizes the image ring when
+// they or the compute settings changed; the accumulation history restarts then.
+hv_status post_apply(hv_handle* h) {
+  if (h->post_pending) {
+    h->post_cur = h->post_pend;
+    h->post_k_cur = h->post_k_pend;
+    h->post_pending = false;
+    h->post_dirty = true;
+  }
+  if (!h->post_dirty) return HV_OK;
+  const hv_post& q = h->post_cur;
+  h->post_active = q.struct_size != 0 && (q.kernel_size > 0 || q.renormalize || q.accumulate > 1);
+  h->post_count = 0;
+  if (h->post_active) {
+    if (h->cur.temporal == HV_TEMPORAL_NONE)
+      return fail(h, HV_ERR_UNSUPPORTED, "post-processing needs rendered images (STFT or PCA)");
+    const uint32_t by_q = (h->Q - h->T) / h->S + 1;  // most windows one render emits
+    h->post_R = q.accumulate - 1 + by_q;
+    const size_t hw = size_t(h->W) * h->H;
+    hv_status s = ensure(h, reinterpret_cast<void**>(&h->post_ring), &h->post_ring_bytes,
+                         size_t(h->post_R) * h->nout * hw * sizeof(float));
+    if (s == HV_OK)
+      s = ensure(h, reinterpret_cast<void**>(&h->post_sums), &h->post_sums_bytes,
+                 size_t(h->post_R) * h->nout * sizeof(double));
+    if (s == HV_OK && q.kernel_size > 0) {
+      s = ensure(h, reinterpret_cast<void**>(&h->post_kdev), &h->post_kdev_bytes,
+                 h->post_k_cur.size() * sizeof(float));
+      if (s == HV_OK) {
+        HV_CU(h, cudaMemcpyAsync(h->post_kdev, h->post_k_cur.data(), h->post_k_cur.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, h->stream));
+        HV_CU(h, cudaStreamSynchronize(h->stream));
+      }
+    }
+    if (s != HV_OK) return s;
+  }
+  h->post_dirty = false;
+  return HV_OK;
+}
+
+// Settings and post-processing settings in force for the next windows.
+hv_status settle(hv_handle* h) {
+  hv_status s = apply_pending(h);
+  return s == HV_OK ? post_apply(h) : s;
+}
+
 // Copies n frames from device memory into the input ring on the handle's stream
 // (one copy, or two where the ring wraps). The caller has checked the capacity.
 hv_status enqueue_push_device(hv_handle* h, const void* frames, uint32_t n) {
@@ -689,6 +747,22 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
     sa.nout = h->nout;
     sa.out = dst;
     e = launch_stft(sa, h->stream, &launches);
+  }
+  if (e == cudaSuccess && h->post_active) {
+    PostArgs pa{};
+    pa.W = h->W;
+    pa.H = h->H;
+    pa.nout = h->nout;
+    pa.K = int(h->post_cur.kernel_size);
+    pa.kern = h->post_kdev;
+    pa.renorm = h->post_cur.renormalize ? 1 : 0;
+    pa.A = h->post_cur.accumulate;
+    pa.R = h->post_R;
+    pa.count = h->post_count;
+    pa.ring = h->post_ring;
+    pa.sums = h->post_sums;
+    e = launch_post(dst, nw, pa, h->stream, &launches);
+    h->post_count += nw;
   }
   h->st.kernel_launches += launches;
   if (e != cudaSuccess) return cuda_fail(h, e, "temporal transform launch");
@@ -838,7 +912,7 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
   if (out_kind != HV_MEM_HOST && out_kind != HV_MEM_DEVICE) return fail(h, HV_ERR_ARG, "bad mem_kind");
   if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "no settings");
   HV_CU(h, cudaSetDevice(h->device));
-  hv_status s = apply_pending(h);
+  hv_status s = settle(h);
   if (s != HV_OK) return s;
   const uint32_t nw = out ? windows_ready(h, cap_floats) : 0;
   if (nw == 0) return HV_OK;
@@ -940,10 +1014,48 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->staging);
   if (h->pca_ws) cudaFree(h->pca_ws);
   if (h->sw_tables) cudaFree(h->sw_tables);
+  if (h->post_kdev) cudaFree(h->post_kdev);
+  if (h->post_ring) cudaFree(h->post_ring);
+  if (h->post_sums) cudaFree(h->post_sums);
   if (h->sw_acc) cudaFree(h->sw_acc);
   if (h->raw) cudaFree(h->raw);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+  return HV_OK;
+}
+
+hv_status hv_set_postprocess(hv_handle* h, const hv_post* p) {
+  if (!h || !p) return fail(h, HV_ERR_ARG, "NULL argument");
+  if (p->struct_size != sizeof(hv_post)) return fail(h, HV_ERR_ARG, "hv_post.struct_size mismatch");
+  const uint32_t K = p->kernel_size;
+  if (K > HV_POST_MAX_KERNEL || (K > 0 && K % 2 == 0)) return fail(h, HV_ERR_ARG, "kernel_size must be 0 or odd <= 31");
+  if (p->accumulate < 1 || p->accumulate > HV_POST_MAX_ACCUMULATE)
+    return fail(h, HV_ERR_ARG, "accumulate must be in [1, 64]");
+  if (p->renormalize != 0 && p->renormalize != 1) return fail(h, HV_ERR_ARG, "renormalize must be 0 or 1");
+  std::vector<float> k(size_t(K) * K);
+  if (K > 0) {
+    if (p->kernel) {
+      std::memcpy(k.data(), p->kernel, k.size() * sizeof(float));
+    } else {
+      if (!(p->gauss_sigma > 0.f) || !std::isfinite(p->gauss_sigma))
+        return fail(h, HV_ERR_ARG, "gauss_sigma must be > 0 without a kernel");
+      // exp(-(dx^2 + dy^2) / (2 sigma^2)), normalised to sum 1, in float64
+      std::vector<double> g(k.size());
+      double tot = 0.0;
+      const double s2 = 2.0 * double(p->gauss_sigma) * double(p->gauss_sigma);
+      const int c = int(K / 2);
+      for (int a = 0; a < int(K); ++a)
+        for (int b = 0; b < int(K); ++b) {
+          g[a * K + b] = std::exp(-double((a - c) * (a - c) + (b - c) * (b - c)) / s2);
+          tot += g[a * K + b];
+        }
+      for (size_t e = 0; e < k.size(); ++e) k[e] = float(g[e] / tot);
+    }
+  }
+  h->post_pend = *p;
+  h->post_pend.kernel = nullptr;  // the weights live in post_k_pend
+  h->post_k_pend = std::move(k);
+  h->post_pending = true;
   return HV_OK;
 }
 
@@ -1144,7 +1256,7 @@ hv_status hv_render_group(hv_group* g, const void* const* frames, const uint32_t
     hv_handle* h = g->hs[i];
     n_windows[i] = 0;
     if (!h->has_params && !h->pending) return gfail(g, HV_ERR_STATE, "member " + std::to_string(i) + ": no settings");
-    hv_status s = apply_pending(h);
+    hv_status s = settle(h);
     if (s != HV_OK) return gfail(g, s, "member " + std::to_string(i) + ": " + h->err);
     if (h->prof) return gfail(g, HV_ERR_STATE, "member " + std::to_string(i) + ": profiling is on");
     if (h->cur.temporal == HV_TEMPORAL_PCA && h->T > 64)

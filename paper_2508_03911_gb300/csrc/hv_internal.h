@@ -105,6 +105,22 @@ cudaError_t launch_tamura_finish(const double* acc, uint32_t count, uint32_t pix
 cudaError_t launch_af_features(const float2* spec, uint32_t n, uint32_t W, uint32_t H, void* out_bf16,
                                cudaStream_t s);
 
+// Post-processing of rendered images [window][nout][H][W] (Sec. III-B): periodic
+// K x K convolution into ring slot (count + window) mod R, per-image float64 sums
+// when re-normalising, then each image replaced in place by the mean of its last
+// min(A, count + window + 1) ring slots. H, W multiples of 16.
+struct PostArgs {
+  uint32_t W, H, nout;
+  int K;                // 0 (no convolution) or odd
+  const float* kern;    // device K * K weights
+  int renorm;
+  uint32_t A, R;
+  uint64_t count;       // images of each output already in the ring
+  float* ring;          // [R][nout][H][W]
+  double* sums;         // [R][nout]
+};
+cudaError_t launch_post(float* images, uint32_t nwin, const PostArgs& a, cudaStream_t s, int* launches);
+
 // Copy propagated frames out as interleaved complex images.
 cudaError_t launch_copy_frames(const RingRef& tq, uint32_t n, uint32_t hw, float* out,
                                cudaStream_t s, int* launches);

@@ -73,6 +73,12 @@ class hv_tuning(C.Structure):
                 ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 12)]
 
 
+class hv_post(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kernel_size", C.c_uint32), ("kernel", C.c_void_p),
+                ("gauss_sigma", C.c_float), ("renormalize", C.c_int32), ("accumulate", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
 class hv_group_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("steps", "graph_launches", "graph_instantiations",
                                           "graph_updates", "kernel_launches")] + \
@@ -119,6 +125,7 @@ def lib() -> C.CDLL:
         "hv_group_get_stats": ([C.c_void_p, P(hv_group_stats)], C.c_int),
         "hv_group_last_error": ([C.c_void_p], C.c_char_p),
         "hv_group_close": ([C.c_void_p], C.c_int),
+        "hv_set_postprocess": ([C.c_void_p, P(hv_post)], C.c_int),
         "hv_focus_sweep": ([C.c_void_p, C.c_void_p, C.c_uint32, P(C.c_double), C.c_uint32, C.c_void_p],
                            C.c_int),
         "hv_af_features": ([C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p], C.c_int),
@@ -274,6 +281,18 @@ def hv_last_error(h=None) -> str:
 
 def hv_version() -> str:
     return lib().hv_version().decode()
+
+
+def hv_set_postprocess(h, kernel=None, kernel_size=None, sigma=0.0, renormalize=False, accumulate=1):
+    """Post-processing of rendered images: a K x K kernel (array) or a Gaussian of
+    `sigma` with `kernel_size`, re-normalisation, moving average over `accumulate`."""
+    k = None
+    if kernel is not None:
+        k = np.ascontiguousarray(kernel, dtype=np.float32)
+        kernel_size = k.shape[0]
+    p = hv_post(C.sizeof(hv_post), int(kernel_size or 0), C.c_void_p(k.ctypes.data if k is not None else 0),
+                float(sigma), int(bool(renormalize)), int(accumulate), 0)
+    _check(h, lib().hv_set_postprocess(h, C.byref(p)))
 
 
 # --------------------------------------------------------------- autofocus
