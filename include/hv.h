@@ -93,7 +93,7 @@ typedef struct {
   uint32_t pca_lo, pca_hi;    /* PCA: eigenvectors ranked pca_lo..pca_hi (1-based,
                                  inclusive, descending eigenvalue)                     */
   int32_t precision;          /* PCA covariance arithmetic, HV_PREC_*                  */
-  int32_t tuned;              /* 1 = tuned form (graph replay, fused kernels)          */
+  int32_t tuned;              /* 1 = tuned form (spatial kernels chosen by timing)    */
   uint32_t spatial_chunk;     /* frames per spatial launch (0 = automatic)             */
   uint32_t spatial_kernel;    /* HV_SK_*: which spatial kernels (default automatic):
                                  multi-pass (one strip per CTA), persistent multi-pass
@@ -140,8 +140,11 @@ hv_status hv_get_params(const hv_handle* h, hv_params* p);
 /* Enqueue n raw frames (width x height of the current settings, or of max size
  * when none are set) into the input ring (Sec. III-A): `frames` is a host
  * pointer (mem_kind HV_MEM_HOST; copied before return, the caller may reuse it)
- * or a device pointer (HV_MEM_DEVICE; copied on the handle's stream, so it must
- * stay valid until that stream passes this point). Frames are uint8 or uint16
+ * or a device pointer (HV_MEM_DEVICE; copied on the handle's stream, so the
+ * frames must be completely written before that stream reaches the copy -- work
+ * of another stream that produces them must be ordered before it, e.g. by
+ * giving the handle the producer's stream in hv_open or by synchronising -- and
+ * must stay valid until the stream passes it). Frames are uint8 or uint16
  * by pixel_bits, row-major, frames contiguous. All-or-nothing: if the ring
  * cannot take all n frames, nothing is copied and HV_ERR_QUEUE_FULL is returned
  * (backpressure; frames are never dropped). */
@@ -241,6 +244,53 @@ typedef struct {
  * Errors: HV_ERR_ARG (bad fields); HV_ERR_UNSUPPORTED from hv_render when the
  * temporal analysis is HV_TEMPORAL_NONE and post-processing is on. */
 hv_status hv_set_postprocess(hv_handle* h, const hv_post* p);
+
+/* ------------------------------------------------------------------------
+ * .holo files (the paper's "Holofile system" section): a 64-byte header, the
+ * frames as one binary stream, and an optional JSON footer with the rendering
+ * settings used while recording. Header fields, at byte offsets:
+ *   0 "HOLO" magic (4 bytes), 4 version (uint16, 7), 6 bits per pixel (uint16,
+ *   a multiple of 8), 8 width (uint32), 12 height (uint32), 16 number of images
+ *   (uint32), 20 total data size in bytes (uint64), 28 endianness of the data
+ *   (uint8: 0 little, 1 big), 29 data type (uint8: 0 raw, 1 processed), 30..63
+ *   zero padding. Header integers are little-endian.
+ * These calls are host code: they need no GPU unless a destination is device
+ * memory. Paths are NUL-terminated file names.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint16_t version;        /* 7                                     */
+  uint16_t bits_per_pixel; /* 8, 16, 32, ...                        */
+  uint32_t width, height;
+  uint32_t n_images;
+  uint64_t data_bytes;     /* n_images * width * height * bits / 8  */
+  uint8_t endianness;      /* 0 little, 1 big                       */
+  uint8_t data_type;       /* 0 raw, 1 processed                    */
+  uint8_t reserved[6];
+} hv_holo_header;
+
+/* Parses and checks the header: magic, version 7, bits a multiple of 8,
+ * data_bytes equal to the frames' size and within the file. Errors:
+ * HV_ERR_ARG (NULL, unreadable or malformed file), HV_ERR_UNSUPPORTED (another
+ * version). */
+hv_status hv_holo_read_header(const char* path, hv_holo_header* hdr);
+
+/* Reads frames first .. first + n - 1 into dst: host memory (mem_kind
+ * HV_MEM_HOST) or device memory (HV_MEM_DEVICE, copied through a pinned buffer
+ * on `stream`, a cudaStream_t or NULL; the call returns after the copies
+ * complete). Big-endian pixels are byte-swapped to the host's order. Errors:
+ * HV_ERR_ARG (range past the last frame, short file, NULL), HV_ERR_CUDA. */
+hv_status hv_holo_read_frames(const char* path, uint64_t first, uint32_t n, void* dst, int mem_kind,
+                              void* stream);
+
+/* The footer (the bytes after the frames, JSON text) into buf with a NUL
+ * terminator; *len = its length (0 when there is none). buf may be NULL to
+ * query the length. Errors: HV_ERR_ARG (file, or cap <= *len with buf). */
+hv_status hv_holo_read_footer(const char* path, char* buf, size_t cap, size_t* len);
+
+/* Writes a .holo file: the header from hdr (version, data_bytes and padding are
+ * filled in; endianness must be 0, data written as given), n_images frames from
+ * host memory, and footer_json (may be NULL) after them. Errors: HV_ERR_ARG. */
+hv_status hv_holo_write(const char* path, const hv_holo_header* hdr, const void* frames, const char* footer_json);
 
 /* ------------------------------------------------------------------------
  * Autofocus. The paper propagates to a distance the user sets (Sec. III-B.1);

@@ -79,6 +79,12 @@ class hv_post(C.Structure):
                 ("reserved", C.c_uint32)]
 
 
+class hv_holo_header(C.Structure):
+    _fields_ = [("version", C.c_uint16), ("bits_per_pixel", C.c_uint16), ("width", C.c_uint32),
+                ("height", C.c_uint32), ("n_images", C.c_uint32), ("data_bytes", C.c_uint64),
+                ("endianness", C.c_uint8), ("data_type", C.c_uint8), ("reserved", C.c_uint8 * 6)]
+
+
 class hv_group_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("steps", "graph_launches", "graph_instantiations",
                                           "graph_updates", "kernel_launches")] + \
@@ -126,6 +132,10 @@ def lib() -> C.CDLL:
         "hv_group_last_error": ([C.c_void_p], C.c_char_p),
         "hv_group_close": ([C.c_void_p], C.c_int),
         "hv_set_postprocess": ([C.c_void_p, P(hv_post)], C.c_int),
+        "hv_holo_read_header": ([C.c_char_p, P(hv_holo_header)], C.c_int),
+        "hv_holo_read_frames": ([C.c_char_p, C.c_uint64, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+        "hv_holo_read_footer": ([C.c_char_p, C.c_char_p, C.c_size_t, P(C.c_size_t)], C.c_int),
+        "hv_holo_write": ([C.c_char_p, P(hv_holo_header), C.c_void_p, C.c_char_p], C.c_int),
         "hv_focus_sweep": ([C.c_void_p, C.c_void_p, C.c_uint32, P(C.c_double), C.c_uint32, C.c_void_p],
                            C.c_int),
         "hv_af_features": ([C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p], C.c_int),
@@ -293,6 +303,43 @@ def hv_set_postprocess(h, kernel=None, kernel_size=None, sigma=0.0, renormalize=
     p = hv_post(C.sizeof(hv_post), int(kernel_size or 0), C.c_void_p(k.ctypes.data if k is not None else 0),
                 float(sigma), int(bool(renormalize)), int(accumulate), 0)
     _check(h, lib().hv_set_postprocess(h, C.byref(p)))
+
+
+# -------------------------------------------------------------- .holo files
+
+def _holo_check(s, what):
+    if s != HV_OK:
+        raise HvError(s, what)
+
+
+def holo_read_header(path) -> dict:
+    h = hv_holo_header()
+    _holo_check(lib().hv_holo_read_header(os.fsencode(path), C.byref(h)), f"cannot read the header of {path}")
+    return {n: getattr(h, n) for n, _ in hv_holo_header._fields_ if n != "reserved"}
+
+
+def holo_read_frames(path, first, out, stream=None):
+    """Frames first .. first + len(out) - 1 into `out` (numpy array or torch tensor,
+    host or device, shape (n, H, W) of the file's pixel type)."""
+    ptr, kind, _ = _ptr_kind(out)
+    _holo_check(lib().hv_holo_read_frames(os.fsencode(path), first, out.shape[0], C.c_void_p(ptr), kind,
+                                          C.c_void_p(stream or 0)), f"cannot read frames of {path}")
+
+
+def holo_read_footer(path) -> str:
+    n = C.c_size_t(0)
+    _holo_check(lib().hv_holo_read_footer(os.fsencode(path), None, 0, C.byref(n)), f"cannot read {path}")
+    buf = C.create_string_buffer(n.value + 1)
+    _holo_check(lib().hv_holo_read_footer(os.fsencode(path), buf, n.value + 1, C.byref(n)), f"cannot read {path}")
+    return buf.value.decode()
+
+
+def holo_write(path, frames: np.ndarray, footer=None, data_type=0):
+    """Write frames (n, H, W) uint8/uint16/float32 host array and an optional JSON footer."""
+    a = np.ascontiguousarray(frames)
+    h = hv_holo_header(7, a.dtype.itemsize * 8, a.shape[2], a.shape[1], a.shape[0], a.nbytes, 0, data_type)
+    _holo_check(lib().hv_holo_write(os.fsencode(path), C.byref(h), C.c_void_p(a.ctypes.data),
+                                    footer.encode() if footer is not None else None), f"cannot write {path}")
 
 
 # --------------------------------------------------------------- autofocus

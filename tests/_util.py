@@ -40,8 +40,25 @@ def images_from(out: np.ndarray, n_win: int, p: dict) -> np.ndarray:
     return out[: n_win * n_img * H * W].reshape(n_win, n_img, H, W)
 
 
+# Device copies handed to the library: its copies run on the handle's own stream,
+# so each tensor must be complete before they run and must outlive them. Kept
+# until the end of the test (conftest releases them after a device synchronise).
+_KEEP = []
+
+
 def to_device(frames: np.ndarray):
-    """Raw frames as a CUDA tensor with the same bytes (uint16 travels as int16)."""
+    """Raw frames as a CUDA tensor with the same bytes (uint16 travels as int16),
+    complete on the device when this returns and kept alive for the test."""
     import torch
     a = frames.view(np.int16) if frames.dtype == np.uint16 else frames
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    torch.cuda.synchronize()
+    _KEEP.append(t)
+    return t
+
+
+def release_device_buffers():
+    import sys
+    if _KEEP and "torch" in sys.modules:
+        sys.modules["torch"].cuda.synchronize()
+    _KEEP.clear()
