@@ -78,6 +78,7 @@ struct PcaArgs {
   double tol, tol_abs;  // Jacobi skip thresholds (relative, and x largest diagonal)
   float2* partials;     // nwin x nchunks x upper tiles x TS x TS
   double2* C;           // nwin x T x T
+  double2* C2;          // T x T second copy (large-T path: the rounds alternate between C and C2)
   double2* V;           // T x T (large-T path)
   double* rot;          // T/2 rotations (4 doubles each)
   unsigned* counters;   // 4 counters followed by one double (largest diagonal)

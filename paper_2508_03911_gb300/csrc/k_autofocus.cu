@@ -51,12 +51,14 @@ __global__ void __launch_bounds__(FT_NT) k_af_features(const float2* spec, uint3
   const uint32_t f = blockIdx.x;
   const float2* F = spec + size_t(f) * W * H;
   const uint32_t cw = W / 2, ncell = (W / 2) * (H / 2);
-  double s1 = 0.0, s2 = 0.0;
+  // a thread's few cells summed in float32 (values below ~20), the block in float64
+  float f1 = 0.f, f2 = 0.f;
   for (uint32_t e = threadIdx.x; e < ncell; e += FT_NT) {
-    const double v = cell_value(F, W, H, e / cw, e % cw);
-    s1 += v;
-    s2 += v * v;
+    const float v = cell_value(F, W, H, e / cw, e % cw);
+    f1 += v;
+    f2 = fmaf(v, v, f2);
   }
+  double s1 = f1, s2 = f2;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);

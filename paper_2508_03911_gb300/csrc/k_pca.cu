@@ -169,11 +169,12 @@ __device__ __forceinline__ bool jacobi_rot(double al, double be, double2 g, doub
 }
 
 // B <- Jp^H B Jq for the 2 x 2 block of rows (i0, i1) and columns (j0, j1) of the
-// row-major T x T matrix C; `own` marks the pair's own diagonal block.
-__device__ __forceinline__ void jacobi_block(double2* C, int T, int i0, int i1, int j0, int j1, const Rot& Jp,
-                                             const Rot& Jq, bool own) {
-  const double2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1];
-  const double2 b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
+// row-major T x T matrix, read from Cs and written to Cd (may be the same);
+// `own` marks the pair's own diagonal block.
+__device__ __forceinline__ void jacobi_block(const double2* Cs, double2* C, int T, int i0, int i1, int j0, int j1,
+                                             const Rot& Jp, const Rot& Jq, bool own) {
+  const double2 b00 = Cs[i0 * T + j0], b01 = Cs[i0 * T + j1];
+  const double2 b10 = Cs[i1 * T + j0], b11 = Cs[i1 * T + j1];
   const double2 qph = make_double2(Jq.px, -Jq.py);  // conj(ph_q)
   const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
   const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
@@ -210,34 +211,41 @@ __device__ __forceinline__ void jacobi_vrow(double2* V, int T, int row, int j0, 
   V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
 }
 
+// Cooperative cyclic Jacobi over all SMs with one grid barrier per round: every
+// CTA computes the rotations of all pairs itself (a deterministic function of
+// the current matrix, so all CTAs agree), then updates its share of the 2 x 2
+// blocks from one copy of C into the other (every entry is rewritten each round,
+// so the copies can alternate) and its share of the rows of V in place. The
+// rotation count of a sweep, identical in every CTA, ends the loop without a
+// further barrier.
 __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int T = a.T, NP = T / 2;
+  __shared__ Rot rot[256];
+  __shared__ unsigned cnt;
   const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const size_t gsz = size_t(gridDim.x) * blockDim.x;
-  Rot* rot = reinterpret_cast<Rot*>(a.rot);
+  const double floor_abs = a.tol_abs * a.cmax[0];
+  double2* Cs = a.C;
+  double2* Cd = a.C2;
+  int sweeps = 0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
-    if (gtid == 0) a.counters[sweep & 1] = 0;  // reset the other parity's counter
+    if (threadIdx.x == 0) cnt = 0;
     for (int r = 0; r < T - 1; ++r) {
-      // phase 1: rotation of each pair from the current C
-      for (size_t p = gtid; p < size_t(NP); p += gsz) {
-        const int i = rr_elem(int(p), r, T), j = rr_elem(T - 1 - int(p), r, T);
+      __syncthreads();  // rot of the previous round fully used; cnt reset visible
+      for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        const int i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
         Rot q;
-        if (jacobi_rot(a.C[i * T + i].x, a.C[j * T + j].x, a.C[i * T + j], a.tol, a.tol_abs * a.cmax[0], q))
-          atomicAdd(&a.counters[(sweep & 1) ^ 1], 1u);
+        if (jacobi_rot(Cs[i * T + i].x, Cs[j * T + j].x, Cs[i * T + j], a.tol, floor_abs, q)) atomicAdd(&cnt, 1u);
         rot[p] = q;
       }
-      grid.sync();
-      // phase 2: C <- J^H C J on 2 x 2 blocks (pairs p, q), V <- V J
+      __syncthreads();
       const size_t nblk = size_t(NP) * NP;
       for (size_t e = gtid; e < nblk + size_t(T) * NP; e += gsz) {
         if (e < nblk) {
           const int p = int(e / NP), q = int(e % NP);
-          const Rot& Jp = rot[p];
-          const Rot& Jq = rot[q];
-          if (Jp.s == 0.0 && Jq.s == 0.0) continue;
-          jacobi_block(a.C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
-                       rr_elem(T - 1 - q, r, T), Jp, Jq, p == q);
+          jacobi_block(Cs, Cd, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
+                       rr_elem(T - 1 - q, r, T), rot[p], rot[q], p == q);
         } else {
           const size_t f = e - nblk;
           const int row = int(f / NP), q = int(f % NP);
@@ -247,13 +255,20 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
         }
       }
       grid.sync();
+      double2* t = Cs;
+      Cs = Cd;
+      Cd = t;
     }
-    // a sweep without any rotation: converged (every block reads the same count)
-    const unsigned n = *reinterpret_cast<volatile unsigned*>(&a.counters[(sweep & 1) ^ 1]);
-    grid.sync();
-    if (gtid == 0) a.counters[2] = unsigned(sweep + 1);  // sweeps performed
+    sweeps = sweep + 1;
+    __syncthreads();
+    const unsigned n = cnt;  // a sweep without any rotation: converged (same in every CTA)
+    __syncthreads();         // every thread has read cnt before the next sweep resets it
     if (n == 0) break;
   }
+  // the eigenvalues (diagonal) into a.C, where the selection reads them
+  if (Cs != a.C)
+    for (size_t i = gtid; i < size_t(T); i += gsz) a.C[i * T + i] = Cs[i * T + i];
+  if (gtid == 0) a.counters[2] = unsigned(sweeps);
 }
 
 // Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
@@ -318,7 +333,7 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
         if (e < NP * NP) {
           const int p = e / NP, q = e % NP;
           if (rot[p].s == 0.0 && rot[q].s == 0.0) continue;
-          jacobi_block(C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
+          jacobi_block(C, C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
                        rr_elem(T - 1 - q, r, T), rot[p], rot[q], p == q);
         } else {
           const int f = e - NP * NP, row = f / NP, q = f % NP;
