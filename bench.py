@@ -236,6 +236,25 @@ class ClockSampler:
                 "samples_in_timed_region": len(inside)}
 
 
+# ------------------------------------------------------------- replicas
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (the job ends when its slowest replica does);
+    x itself without a process group."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, units_per_step: int, seconds: float) -> float:
+    """Whole-job throughput: every replica processes units_per_step per step (weak
+    scaling), the job takes the slowest replica's time."""
+    return world * steps * units_per_step / seconds
+
+
 # --------------------------------------------------------------- hv arm
 
 def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
@@ -328,12 +347,9 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     elapsed_ms = t_start.elapsed_time(t_end)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     frames_per_step = B * w["batches"]
-    value = world * args.steps * frames_per_step / (elapsed_ms / 1e3)
+    value = job_value(world, args.steps, frames_per_step, elapsed_ms / 1e3)
     launches = stats1["kernel_launches"] - stats0["kernel_launches"]
     r.close()
 
@@ -370,11 +386,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         step_host(True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps * frames_per_step / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_value = job_value(world, e2e_steps, frames_per_step, e2e_s)
     r2.close()
 
     return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
@@ -563,9 +576,10 @@ def group_bytes_per_batch():
     return tot
 
 
-def run_group(args, use_graph, tuned, quick=False):
+def run_group(args, use_graph, tuned, quick=False, dist=None):
     """K steps of one hv_render_group batch each (every member: 4 windows of frames
-    pushed from a device pool, then rendered)."""
+    pushed from a device pool, then rendered); with a process group, one replica
+    per rank and the slowest rank's time."""
     import torch
 
     from paper_2508_03911_gb300 import hv
@@ -609,6 +623,8 @@ def run_group(args, use_graph, tuned, quick=False):
         time.sleep(0.6)
     st0 = hv.hv_group_get_stats(g)
     lat = []
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     if clocks:
         clocks.mark("t0")
@@ -625,7 +641,9 @@ def run_group(args, use_graph, tuned, quick=False):
     elapsed_ms = t_start.elapsed_time(t_end)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
     clk = clocks.stop() if clocks else None
-    value = args.steps * frames_per_batch / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
+    world = dist.get_world_size() if dist else 1
+    value = job_value(world, args.steps, frames_per_batch, elapsed_ms / 1e3)
     hv.hv_group_close(g)
     for r in rs:
         r.close()
@@ -639,21 +657,32 @@ def group_config(name, frames_per_batch):
             "members": [{"N": N, "T": T, "S": T, "spatial": sp} for N, T, sp in GROUP_MEMBERS],
             "frames_per_step": frames_per_batch,
             "l2": "inputs larger than L2: each batch reads 1.95 GB of raw frames",
-            "parallelism": "replicas x1"}
+            "parallelism": f"replicas x{int(os.environ.get('WORLD_SIZE', '1'))}"}
 
 
 def main_group(args):
     """Batched uneven streams: tuned form (autotuned spatial kernels, one graph per
     batch) and plain form (multi-pass kernels, launches issued per member)."""
     w = WORKLOADS[args.workload]
-    plain = run_group(args, use_graph=False, tuned=0, quick=True)
-    res = run_group(args, use_graph=True, tuned=1)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    plain = run_group(args, use_graph=False, tuned=0, quick=True, dist=dist)
+    res = run_group(args, use_graph=True, tuned=1, dist=dist)
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     peaks = load_peaks()
     hbm = (peaks or {}).get("hbm_gbs", 6800.0)
     lat = res["lat_ms"]
     gbs = group_bytes_per_batch() * args.steps / (res["elapsed_ms"] / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": round(res["value"], 1), "unit": "frames/s", "n_gpus": 1,
+        "metric": METRIC, "value": round(res["value"], 1), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(res["elapsed_ms"] / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -694,8 +723,17 @@ def main_autofocus(args):
     from paper_2508_03911_gb300 import autofocus as AF
     w = WORKLOADS[args.workload]
     B = w["batch"]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    # holograms first: the process pool starts before any CUDA call
     frames, _ = synth.autofocus_set(B, N=256, seed=1005, workers=min(16, os.cpu_count() or 1))
-    dev = torch.device("cuda", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     r = hv.Renderer(256, 256, 16, B, stream=stream.cuda_stream)
@@ -727,6 +765,8 @@ def main_autofocus(args):
     time.sleep(0.6)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     s0 = r.stats()["kernel_launches"]
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks.mark("t0")
     t0 = torch.cuda.Event(enable_timing=True)
@@ -737,7 +777,7 @@ def main_autofocus(args):
     t1.record(stream)
     torch.cuda.synchronize()
     clocks.mark("t1")
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
     feat_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     net_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     launches = (r.stats()["kernel_launches"] - s0) + args.steps * 5  # network: 4 convolutions + head
@@ -761,11 +801,11 @@ def main_autofocus(args):
         step()
         zh.copy_(z, non_blocking=True)
         stream.synchronize()
-    e2e_s = (time.perf_counter() - tt) / args.steps
-    value = B * args.steps / (ms / 1e3)
+    e2e_s = max_over_ranks((time.perf_counter() - tt) / args.steps, dist, dev)
+    value = job_value(world, args.steps, B, ms / 1e3)
     tflops = AF_FLOPS * B / (net_ms / 1e3) / 1e12
     line = {
-        "metric": "holograms/s focused", "value": round(value, 1), "unit": "holograms/s", "n_gpus": 1,
+        "metric": "holograms/s focused", "value": round(value, 1), "unit": "holograms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
@@ -781,14 +821,19 @@ def main_autofocus(args):
         "stage_ms_per_step": {"features": round(feat_ms, 4), "network": round(net_ms, 4)},
         "sweep": {"holograms_per_s": round(B / (sweep_ms / 1e3), 1), "ms_per_step": round(sweep_ms, 4),
                   "distances": AF.NZ, "speedup_of_network": round(sweep_ms / (ms / args.steps), 2)},
-        "e2e": {"value": round(B / e2e_s, 1), "unit": "holograms/s",
+        "e2e": {"value": round(world * B / e2e_s, 1), "unit": "holograms/s",
                 "h2d_bytes_per_step": int(host.numel() * 2), "d2h_bytes_per_step": int(B * 4)},
         "gpu_launches": launches,
         "clocks": clk,
     }
     net.close()
     r.close()
-    if not args.no_cpu_baseline:
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line["config"]["parallelism"] = f"replicas x{world}"
+    if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = autofocus_oracle_sample(frames[:8])
     print(json.dumps(line), flush=True)
 
