@@ -281,10 +281,12 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         if w.get("temporal") == "pca":
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], temporal="pca", T=w["T"],
                          stride=w["S"], pca=w["pca"], tuned=tuned,
-                         precision=w.get("precision", "fp32"))
+                         precision=w.get("precision", "fp32"), spatial_kernel=args.spatial_kernel,
+                         spatial_chunk=args.spatial_chunk)
         else:
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"],
-                         fs=w["fs"], band=(klo, khi), moments=w["moments"], tuned=tuned)
+                         fs=w["fs"], band=(klo, khi), moments=w["moments"], tuned=tuned,
+                         spatial_kernel=args.spatial_kernel, spatial_chunk=args.spatial_chunk)
         return r
 
     r = open_renderer()
@@ -479,9 +481,19 @@ def roofline(w, res, peaks):
     traffic = None
     if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64:
         traffic = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
+    tun = res.get("tuning") or {}
+    if (t_tm < t_sp and w["N"] == 256 and w["spatial"] == "asp" and tun.get("spatial_kernel") == 3
+            and tun.get("spatial_chunk") == 512):
+        # the three persistent passes of one 512-frame launch set, scaled to a render
+        parts = [profiled_traffic("spatial_pp_asp_256.md", ["k_spatial_pp.cu", "fft_dev.cuh"], i)
+                 for i in range(3)]
+        if all(v is not None for v in parts):
+            traffic = int(sum(parts) * frames_per_render / 512)
     if alu_frac >= hbm_frac:
         return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
                 "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic, "kernel": kern,
+                "traffic_per": "launch of the STFT kernel" if t_tm >= t_sp else
+                               "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "hbm_achieved_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4),
                 "stage_ms_per_render": {"spatial": round(t_sp, 4), "temporal": round(t_tm, 4)}}
@@ -894,7 +906,11 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default=None,
                     help="PCA covariance arithmetic (PCA workloads)")
     ap.add_argument("--form", choices=["tuned", "plain", "both"], default="both",
-                    help="tuned: whole-frame cluster kernels; plain: multi-pass kernels")
+                    help="tuned: spatial kernels chosen by the autotuner; plain: multi-pass kernels")
+    ap.add_argument("--spatial-kernel", choices=["auto", "multipass", "persistent", "cluster"], default="auto",
+                    help="fix the spatial kernels instead of autotuning them (profiling runs: the "
+                         "autotuner's timings are distorted under a profiler)")
+    ap.add_argument("--spatial-chunk", type=int, default=0, help="frames per spatial launch (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
