@@ -341,12 +341,15 @@ hv_status apply_pending(hv_handle* h) {
     const size_t hw = size_t(W) * H;
     const bool batched = d.T <= 64 && p.precision == HV_PREC_FP32;
     const uint32_t NW = batched ? 128 : 1;  // windows per launch
-    uint32_t nchunks = uint32_t(std::min<size_t>(batched ? 8 : 64, std::max<size_t>(1, hw / 1024)));
+    // batched (T <= 64): 2048-pixel chunks, one partial T x T matrix per chunk and window;
+    // otherwise up to 64 chunks of the tiled covariance
+    uint32_t nchunks = batched ? uint32_t(std::max<size_t>(1, hw / 2048))
+                               : uint32_t(std::min<size_t>(64, std::max<size_t>(1, hw / 1024)));
     uint32_t chunk = uint32_t((hw + nchunks - 1) / nchunks);
-    chunk = (chunk + 31) / 32 * 32;
+    chunk = (chunk + 63) / 64 * 64;
     nchunks = uint32_t((hw + chunk - 1) / chunk);
-    const uint32_t T = d.T, M = p.pca_hi - p.pca_lo + 1, Mpad = (M + 63) / 64 * 64;
-    const size_t b_part = pca_partials_floats2(T, nchunks) * sizeof(float2) * NW;
+    const uint32_t T = d.T, M = p.pca_hi - p.pca_lo + 1, Mpad = (M + 15) / 16 * 16;
+    const size_t b_part = (batched ? size_t(nchunks) * T * T : pca_partials_floats2(T, nchunks)) * sizeof(float2) * NW;
     const size_t b_mat = size_t(T) * T * sizeof(double2);
     const size_t b_rot = size_t(T / 2) * 4 * sizeof(double);
     const size_t b_cnt = 64;

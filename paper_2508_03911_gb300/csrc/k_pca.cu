@@ -294,75 +294,193 @@ __global__ void k_pca_select(PcaArgs a) {
     if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
 }
 
-// Short windows (T <= 64): one CTA per window, C and V in shared memory, the same
-// float64 cyclic Jacobi with CTA barriers, then the selection of the sub-basis.
+// Float32 rotation helpers of the short-window solver's first phase (same
+// formulas as the float64 ones above).
+struct RotF {
+  float c, s, px, py;
+};
+
+__device__ __forceinline__ bool jacobi_rot_f(float al, float be, float2 g, float tol, float floor_abs, RotF& q) {
+  const float ag = sqrtf(g.x * g.x + g.y * g.y);
+  q = RotF{1.f, 0.f, 1.f, 0.f};
+  if (!(ag > tol * sqrtf(fabsf(al * be)) && ag > floor_abs && ag > 0.f)) return false;
+  const float zeta = (be - al) / (2.f * ag);
+  const float t = -(zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + t * t);
+  q = RotF{c, t * c, g.x / ag, g.y / ag};
+  return true;
+}
+
+__device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1, int j0, int j1, const RotF& Jp,
+                                               const RotF& Jq, bool own) {
+  const float2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1], b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
+  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+  const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, q10)), m01 = cadd(cscale(b00, -Jq.s), cmul(b01, q11));
+  const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, q10)), m11 = cadd(cscale(b10, -Jq.s), cmul(b11, q11));
+  const float2 p01 = make_float2(Jp.px * Jp.s, Jp.py * Jp.s), p11 = make_float2(Jp.px * Jp.c, Jp.py * Jp.c);
+  float2 c00 = cadd(cscale(m00, Jp.c), cmul(p01, m10)), c01 = cadd(cscale(m01, Jp.c), cmul(p01, m11));
+  float2 c10 = cadd(cscale(m00, -Jp.s), cmul(p11, m10)), c11 = cadd(cscale(m01, -Jp.s), cmul(p11, m11));
+  if (own) {
+    c01 = make_float2(0.f, 0.f);
+    c10 = make_float2(0.f, 0.f);
+    c00.y = 0.f;
+    c11.y = 0.f;
+  }
+  C[i0 * T + j0] = c00;
+  C[i0 * T + j1] = c01;
+  C[i1 * T + j0] = c10;
+  C[i1 * T + j1] = c11;
+}
+
+__device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0, int j1, const RotF& Jq) {
+  const float2 v0 = V[row * T + j0], v1 = V[row * T + j1];
+  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+  V[row * T + j0] = cadd(cscale(v0, Jq.c), cmul(v1, q10));
+  V[row * T + j1] = cadd(cscale(v0, -Jq.s), cmul(v1, q11));
+}
+
+// One sweep's rounds of the CTA-local cyclic Jacobi on C (T x T) and V, for
+// float (RotF) or double (Rot) storage; returns the rotations performed.
+template <int T, class Real2, class R, class RotFn, class BlockFn, class RowFn>
+__device__ __forceinline__ unsigned local_sweep(Real2* C, Real2* V, R* rot, unsigned* cnt, RotFn rotfn,
+                                                BlockFn blockfn, RowFn rowfn) {
+  constexpr int NP = T / 2;
+  const int tid = threadIdx.x;
+  if (tid == 0) *cnt = 0;
+  __syncthreads();
+  for (int r = 0; r < T - 1; ++r) {
+    if (tid < NP) {
+      const int i = rr_elem(tid, r, T), j = rr_elem(T - 1 - tid, r, T);
+      if (rotfn(C[i * T + i].x, C[j * T + j].x, C[i * T + j], rot[tid])) atomicAdd(cnt, 1u);
+    }
+    __syncthreads();
+    for (int e = tid; e < NP * NP + T * NP; e += blockDim.x) {
+      if (e < NP * NP) {
+        const int p = e / NP, q = e % NP;
+        if (rot[p].s == 0 && rot[q].s == 0) continue;
+        blockfn(C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[p],
+                rot[q], p == q);
+      } else {
+        const int f = e - NP * NP, row = f / NP, q = f % NP;
+        if (rot[q].s == 0) continue;
+        rowfn(V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[q]);
+      }
+    }
+    __syncthreads();
+  }
+  const unsigned n = *cnt;
+  __syncthreads();
+  return n;
+}
+
+// Short windows (T <= 64): one CTA per window, the eigendecomposition in shared
+// memory in two phases. (1) Float32 cyclic Jacobi on a float copy of C, with the
+// rotations accumulated in Vf, until a sweep rotates nothing at 1e-6 relative.
+// (2) Float64: C' = Vf^H C Vf from the float64 C, then the float64 Jacobi
+// (float64 thresholds) on C' with V = Vf rotated further. Vf is unitary to about
+// 1e-6 only, so each eigenvalue is taken as the Rayleigh quotient
+// diag(V^H C V)_i / |v_i|^2 (second order in the vector's error) and the vectors
+// are normalised. Then the ranking and the sub-basis. GB300's float64 rate
+// makes the float32 phase about the whole cost of the first sweeps only.
 template <int T>
 __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
   extern __shared__ double2 jsm[];
-  double2* C = jsm;
-  double2* V = jsm + T * T;
+  double2* RA = jsm;            // Cf (float) in phase 1, then M = C Vf, then V (float64)
+  double2* C = jsm + T * T;     // C' (float64)
+  float2* Vf = reinterpret_cast<float2*>(jsm + 2 * T * T);
+  float2* Cf = reinterpret_cast<float2*>(RA);
   __shared__ Rot rot[T / 2];
+  __shared__ RotF rotf[T / 2];
   __shared__ unsigned cnt;
   __shared__ double cmax;
+  __shared__ float cmaxf;
   const int w = blockIdx.x, tid = threadIdx.x;
-  constexpr int NP = T / 2;
   const double2* Cg = a.C + size_t(w) * T * T;
   for (int e = tid; e < T * T; e += blockDim.x) {
-    C[e] = Cg[e];
-    V[e] = make_double2(e / T == e % T ? 1.0 : 0.0, 0.0);
+    const double2 v = Cg[e];
+    Cf[e] = make_float2(float(v.x), float(v.y));
+    Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   if (tid == 0) {
     double m = 0.0;
-    for (int i = 0; i < T; ++i) m = fmax(m, C[i * T + i].x);
+    for (int i = 0; i < T; ++i) m = fmax(m, Cg[i * T + i].x);
     cmax = m;
+    cmaxf = float(m);
   }
-  int sweeps = 0;
-  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
-    if (tid == 0) cnt = 0;
-    __syncthreads();
-    for (int r = 0; r < T - 1; ++r) {
-      if (tid < NP) {
-        const int i = rr_elem(tid, r, T), j = rr_elem(T - 1 - tid, r, T);
-        Rot q;
-        if (jacobi_rot(C[i * T + i].x, C[j * T + j].x, C[i * T + j], a.tol, a.tol_abs * cmax, q)) atomicAdd(&cnt, 1u);
-        rot[tid] = q;
-      }
-      __syncthreads();
-      for (int e = tid; e < NP * NP + T * NP; e += blockDim.x) {
-        if (e < NP * NP) {
-          const int p = e / NP, q = e % NP;
-          if (rot[p].s == 0.0 && rot[q].s == 0.0) continue;
-          jacobi_block(C, C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
-                       rr_elem(T - 1 - q, r, T), rot[p], rot[q], p == q);
-        } else {
-          const int f = e - NP * NP, row = f / NP, q = f % NP;
-          if (rot[q].s == 0.0) continue;
-          jacobi_vrow(V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[q]);
-        }
-      }
-      __syncthreads();
-    }
-    sweeps = sweep + 1;
-    const unsigned n = cnt;  // every thread reads it after the last barrier
-    __syncthreads();
+  __syncthreads();
+  // (1) float32 sweeps
+  const float ftol = 1e-6f, ffloor = 1e-7f * cmaxf;
+  int sweeps_f = 0;
+  for (int sw = 0; sw < 20; ++sw) {
+    const unsigned n = local_sweep<T>(
+        Cf, Vf, rotf, &cnt,
+        [&](float al, float be, float2 g, RotF& q) { return jacobi_rot_f(al, be, g, ftol, ffloor, q); },
+        jacobi_block_f, jacobi_vrow_f);
+    sweeps_f = sw + 1;
     if (n == 0) break;
   }
-  if (tid == 0 && w == int(a.nwin) - 1) a.counters[2] = unsigned(sweeps);
-  // rank (descending, ties by index), eigenvalues and the sub-basis lo..hi
+  // (2) C' = Vf^H (C Vf) in float64: M = C Vf into RA (Cf is dead), then C' into C
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int r = e / T, c = e % T;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < T; ++k) {
+      const float2 v = Vf[k * T + c];
+      acc = zadd(acc, zmul(Cg[r * T + k], make_double2(v.x, v.y)));
+    }
+    RA[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int r = e / T, c = e % T;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < T; ++k) {
+      const float2 v = Vf[k * T + r];
+      acc = zadd(acc, zmul(make_double2(v.x, -v.y), RA[k * T + c]));
+    }
+    C[e] = acc;
+  }
+  __syncthreads();
+  double2* V = RA;  // V = Vf in float64, rotated further below
+  for (int e = tid; e < T * T; e += blockDim.x) V[e] = make_double2(Vf[e].x, Vf[e].y);
+  for (int i = tid; i < T; i += blockDim.x) C[i * T + i].y = 0.0;
+  __syncthreads();
+  int sweeps_d = 0;
+  for (int sw = 0; sw < a.max_sweeps; ++sw) {
+    const unsigned n = local_sweep<T>(
+        C, V, rot, &cnt,
+        [&](double al, double be, double2 g, Rot& q) { return jacobi_rot(al, be, g, a.tol, a.tol_abs * cmax, q); },
+        [](double2* Cm, int TT, int i0, int i1, int j0, int j1, const Rot& Jp, const Rot& Jq, bool own) {
+          jacobi_block(Cm, Cm, TT, i0, i1, j0, j1, Jp, Jq, own);
+        },
+        jacobi_vrow);
+    sweeps_d = sw + 1;
+    if (n == 0) break;
+  }
+  if (tid == 0) atomicAdd(&a.counters[2], unsigned(sweeps_f + sweeps_d));  // summed over the launch's windows
+  // eigenvalues as Rayleigh quotients, vectors normalised; rank and sub-basis
+  __shared__ double lamv[T], inrm[T];
+  for (int i = tid; i < T; i += blockDim.x) {
+    double n2 = 0.0;
+    for (int t = 0; t < T; ++t) n2 += V[t * T + i].x * V[t * T + i].x + V[t * T + i].y * V[t * T + i].y;
+    lamv[i] = C[i * T + i].x / n2;
+    inrm[i] = 1.0 / sqrt(n2);
+  }
+  __syncthreads();
   double* lam = a.lam + size_t(w) * T;
   float2* Vs = a.Vs + size_t(w) * T * a.Mpad;
   for (int i = tid; i < T; i += blockDim.x) {
-    const double li = C[i * T + i].x;
+    const double li = lamv[i];
     int rank = 0;
     for (int j = 0; j < T; ++j) {
-      const double lj = C[j * T + j].x;
+      const double lj = lamv[j];
       rank += (lj > li) || (lj == li && j < i);
     }
     lam[rank] = li;
     const int m = rank - int(a.lo - 1);
     if (m >= 0 && m < int(a.M))
-      for (int t = 0; t < T; ++t) Vs[size_t(t) * a.Mpad + m] = make_float2(float(V[t * T + i].x), float(V[t * T + i].y));
+      for (int t = 0; t < T; ++t)
+        Vs[size_t(t) * a.Mpad + m] = make_float2(float(V[t * T + i].x * inrm[i]), float(V[t * T + i].y * inrm[i]));
   }
   for (int e = tid; e < T * int(a.Mpad); e += blockDim.x)
     if (e % int(a.Mpad) >= int(a.M)) Vs[e] = make_float2(0.f, 0.f);
@@ -370,41 +488,59 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
 
 // ---------------------------------------------------------------- projection
 
-constexpr int PRJ_PB = 64;  // pixels per CTA
-constexpr int PRJ_MB = 64;  // sub-basis columns per pass
-constexpr int PRJ_KS = 32;  // frames per smem stage
+constexpr int PRJ_KS = 16;  // frames per stage
 
+// Y = X V_s and E(p) = sum_j |Y_pj|^2. A CTA of 256 threads covers PB = 4096 / MB
+// pixels and MB sub-basis columns per pass (MB = 16, 32 or 64; the sub-basis is
+// padded to a multiple of 16); thread (tx, ty) owns pixels tx + (PB/4) i and
+// columns 4 ty .. 4 ty + 3. Stages of PRJ_KS frames of the pixel strip are
+// fetched with 16-byte cp.async into one of two buffers while the other is used.
+template <int MB>
 __global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
-  __shared__ float2 Xs[PRJ_KS][PRJ_PB + 1];
-  __shared__ float2 Vss[PRJ_KS][PRJ_MB + 1];
-  __shared__ float Er[16][PRJ_PB];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // tx: pixel group, ty: column group
+  constexpr int PB = 4096 / MB, PG = PB / 4, LDX = PB + 2;  // row stride keeps 16-byte alignment
+  extern __shared__ float2 psm[];
+  float2* Xs = psm;                      // 2 x [PRJ_KS][LDX]
+  float2* Vss = psm + 2 * PRJ_KS * LDX;  // [PRJ_KS][MB]
+  __shared__ float Er[MB / 4][PB];
+  const int tid = threadIdx.x, tx = tid % PG, ty = tid / PG;
   const size_t hw = size_t(a.W) * a.H;
-  const size_t pb = size_t(blockIdx.x) * PRJ_PB;
+  const size_t pb = size_t(blockIdx.x) * PB;
+  const int nst = int(a.T) / PRJ_KS;
+  auto issue = [&](int st, int buf) {
+    float2* d = Xs + buf * PRJ_KS * LDX;
+    for (int e = tid; e < PRJ_KS * PB / 2; e += 256) {
+      const int k = e / (PB / 2), q = e % (PB / 2);
+      const float2* src = win_frame(a, blockIdx.y, st * PRJ_KS + k, hw) + pb + 2 * q;
+      const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&d[k * LDX + 2 * q]));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
   float e_acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (uint32_t m0 = 0; m0 < a.Mpad; m0 += PRJ_MB) {
+  for (uint32_t m0 = 0; m0 < a.Mpad; m0 += MB) {
     float2 acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    for (int t0 = 0; t0 < a.T; t0 += PRJ_KS) {
-      for (int e = tid; e < PRJ_KS * PRJ_PB; e += 256) {
-        const int k = e / PRJ_PB, px = e % PRJ_PB;
-        Xs[k][px] = win_frame(a, blockIdx.y, t0 + k, hw)[pb + px];
-      }
-      for (int e = tid; e < PRJ_KS * PRJ_MB; e += 256) {
-        const int k = e / PRJ_MB, m = e % PRJ_MB;
-        Vss[k][m] = a.Vs[(size_t(blockIdx.y) * a.T + t0 + k) * a.Mpad + m0 + m];
+    issue(0, 0);
+    for (int st = 0; st < nst; ++st) {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();  // stage st resident; the other buffer and Vss free
+      if (st + 1 < nst) issue(st + 1, (st + 1) & 1);
+      for (int e = tid; e < PRJ_KS * MB; e += 256) {
+        const int k = e / MB, m = e % MB;
+        Vss[k * MB + m] = a.Vs[(size_t(blockIdx.y) * a.T + st * PRJ_KS + k) * a.Mpad + m0 + m];
       }
       __syncthreads();
+      const float2* X = Xs + (st & 1) * PRJ_KS * LDX;
 #pragma unroll 4
       for (int k = 0; k < PRJ_KS; ++k) {
         float2 x[4], v[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = Xs[k][tx + 16 * i];
+        for (int i = 0; i < 4; ++i) x[i] = X[k * LDX + tx + PG * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = Vss[k][ty * 4 + j];
+        for (int j = 0; j < 4; ++j) v[j] = Vss[k * MB + ty * 4 + j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -413,26 +549,143 @@ __global__ void __launch_bounds__(256) k_project(PcaArgs a, float* out) {
             acc[i][j].y = fmaf(x[i].x, v[j].y, fmaf(x[i].y, v[j].x, acc[i][j].y));
           }
       }
-      __syncthreads();
     }
+    __syncthreads();  // Vss and the buffers are reused by the next pass
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) e_acc[i] = fmaf(acc[i][j].x, acc[i][j].x, fmaf(acc[i][j].y, acc[i][j].y, e_acc[i]));
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) Er[ty][tx + 16 * i] = e_acc[i];
+  for (int i = 0; i < 4; ++i) Er[ty][tx + PG * i] = e_acc[i];
   __syncthreads();
-  if (tid < PRJ_PB) {
+  for (int px = tid; px < PB; px += 256) {
     float s = 0.f;
-    for (int g = 0; g < 16; ++g) s += Er[g][tid];
-    out[size_t(blockIdx.y) * hw + pb + tid] = s;
+#pragma unroll
+    for (int g = 0; g < MB / 4; ++g) s += Er[g][px];
+    out[size_t(blockIdx.y) * hw + pb + px] = s;
+  }
+}
+
+template <int MB>
+static cudaError_t launch_project(const PcaArgs& a, float* out, cudaStream_t s) {
+  constexpr int PB = 4096 / MB;
+  const size_t hw = size_t(a.W) * a.H;
+  if (hw % PB) return cudaErrorInvalidValue;
+  const size_t smem = (size_t(2) * PRJ_KS * (PB + 2) + size_t(PRJ_KS) * MB) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_project<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k_project<MB><<<dim3(unsigned(hw / PB), a.nwin), 256, smem, s>>>(a, out);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------- covariance of short windows
+//
+// T <= 64: a group of (T/4)^2 threads covers the whole T x T matrix with 4 x 4
+// complex tiles (thread (ta, tb): rows 4 ta.., columns 4 tb..); the CTA's
+// 256 / (T/4)^2 groups take alternate pixels of each staged strip. A strip is
+// SP pixels of all T frames of the window, [t][p] in shared memory (row stride
+// SP + 1), fetched with cp.async into one of two buffers while the other is
+// used. The groups' sums are added in shared memory and each CTA writes its
+// partial matrix part[window][cta][T][T]; a second kernel sums them in float64.
+constexpr int CS_SP = 64;
+
+template <int T>
+__global__ void __launch_bounds__(256) k_cov_small(PcaArgs a) {
+  constexpr int TG = T / 4, GT = TG * TG, G = 256 / GT, LDX = CS_SP + 1;
+  extern __shared__ float2 xs[];  // 2 buffers of T x LDX
+  const int tid = threadIdx.x, g = tid / GT, r = tid % GT, ta = r / TG, tb = r % TG;
+  const size_t hw = size_t(a.W) * a.H;
+  const uint32_t z = blockIdx.y;
+  const size_t p_begin = size_t(blockIdx.x) * a.chunk;
+  const size_t p_end = p_begin + a.chunk < hw ? p_begin + a.chunk : hw;
+  const int nstrips = int((p_end - p_begin + CS_SP - 1) / CS_SP);
+  auto issue = [&](int sidx, int buf) {
+    float2* d = xs + buf * T * LDX;
+    const size_t q0 = p_begin + size_t(sidx) * CS_SP;
+    for (int e = tid; e < T * CS_SP; e += 256) {
+      const int t = e / CS_SP, p = e % CS_SP;
+      if (q0 + p < p_end) {
+        const float2* src = win_frame(a, z, t, hw) + q0 + p;
+        const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(&d[t * LDX + p]));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+      } else {
+        d[t * LDX + p] = make_float2(0.f, 0.f);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  if (nstrips > 0) issue(0, 0);
+  for (int sidx = 0; sidx < nstrips; ++sidx) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // strip sidx resident, the other buffer free
+    if (sidx + 1 < nstrips) issue(sidx + 1, (sidx + 1) & 1);
+    const float2* x = xs + (sidx & 1) * T * LDX;
+#pragma unroll 4
+    for (int p = g; p < CS_SP; p += G) {
+      float2 u[4], v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) u[i] = x[(4 * ta + i) * LDX + p];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = x[(4 * tb + j) * LDX + p];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // conj(u) * v
+          acc[i][j].x = fmaf(u[i].x, v[j].x, fmaf(u[i].y, v[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(u[i].x, v[j].y, fmaf(-u[i].y, v[j].x, acc[i][j].y));
+        }
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  // groups' sums in shared memory (reusing the strip buffers: G x T x T <= 2 x T x LDX)
+  float2* red = xs;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[(size_t(g) * T + 4 * ta + i) * T + 4 * tb + j] = acc[i][j];
+  __syncthreads();
+  float2* out = a.partials + (size_t(z) * gridDim.x + blockIdx.x) * T * T;
+  for (int e = tid; e < T * T; e += 256) {
+    float2 s = red[e];
+    for (int q = 1; q < G; ++q) {
+      const float2 v = red[size_t(q) * T * T + e];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    out[e] = s;
+  }
+}
+
+// C[w] = sum over the CTAs' partials in float64 (upper triangle, mirrored).
+__global__ void k_cov_small_reduce(PcaArgs a, uint32_t nparts) {
+  const int T = a.T;
+  for (int ew = blockIdx.x * blockDim.x + threadIdx.x; ew < int(a.nwin) * T * T; ew += gridDim.x * blockDim.x) {
+    const int w = ew / (T * T), e = ew % (T * T), rr = e / T, cc = e % T;
+    if (rr > cc) continue;
+    const float2* P = a.partials + size_t(w) * nparts * T * T + e;
+    double sx = 0.0, sy = 0.0;
+    for (uint32_t k = 0; k < nparts; ++k) {
+      const float2 v = P[size_t(k) * T * T];
+      sx += v.x;
+      sy += v.y;
+    }
+    if (rr == cc) sy = 0.0;
+    double2* Cw = a.C + size_t(w) * T * T;
+    Cw[rr * T + cc] = make_double2(sx, sy);
+    Cw[cc * T + rr] = make_double2(sx, -sy);
   }
 }
 
 template <int T>
 static cudaError_t launch_jacobi_small(const PcaArgs& a, cudaStream_t s) {
-  const size_t smem = size_t(2) * T * T * sizeof(double2);  // C and V
+  const size_t smem = size_t(2) * T * T * sizeof(double2) + size_t(T) * T * sizeof(float2);  // RA, C', Vf
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   k_jacobi_small<T><<<a.nwin, 256, smem, s>>>(a);
@@ -447,13 +700,25 @@ size_t pca_partials_floats2(uint32_t T, uint32_t nchunks) {
 cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev) {
   const size_t hw = size_t(a.W) * a.H;
   const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
-  if (a.T % TS || TS % 16 || hw % PRJ_PB || a.T % PRJ_KS) return cudaErrorInvalidValue;
+  if (a.T % TS || TS % 16 || hw % 256 || a.T % PRJ_KS) return cudaErrorInvalidValue;
   const int nT = a.T / TS;
   const dim3 g1(nT * (nT + 1) / 2, a.nchunks, a.nwin);
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
   if (e0 != cudaSuccess) return e0;
   if (ev) cudaEventRecord(ev[0], s);
-  if (a.precision == HV_PREC_FP32) {
+  if (a.precision == HV_PREC_FP32 && (a.T == 32 || a.T == 64)) {
+    const size_t smem = size_t(2) * a.T * (CS_SP + 1) * sizeof(float2);
+    const dim3 gs(a.nchunks, a.nwin);
+    if (a.T == 32) {
+      cudaFuncSetAttribute(k_cov_small<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_cov_small<32><<<gs, 256, smem, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_cov_small<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      k_cov_small<64><<<gs, 256, smem, s>>>(a);
+    }
+    k_cov_small_reduce<<<unsigned((size_t(a.nwin) * a.T * a.T + 255) / 256), 256, 0, s>>>(a, a.nchunks);
+    *launches += 2;
+  } else if (a.precision == HV_PREC_FP32) {
     k_cov_fp32<<<g1, 256, 0, s>>>(a);
     k_cov_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
     *launches += 2;
@@ -484,7 +749,10 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
-  k_project<<<dim3(unsigned(hw / PRJ_PB), a.nwin), 256, 0, s>>>(a, out);
+  if (a.Mpad % 64 == 0) e = launch_project<64>(a, out, s);
+  else if (a.Mpad % 32 == 0) e = launch_project<32>(a, out, s);
+  else e = launch_project<16>(a, out, s);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], s);
   *launches += 2;
   return cudaGetLastError();
