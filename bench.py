@@ -444,8 +444,10 @@ def roofline_pca(w, res, peaks, force=None):
                 "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)",
                 "sweeps_per_window": round(sweeps, 2),
                 "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
-    else:
-        flops, byts = 0.0, P * (2 + 8.0)
+    else:  # spatial: the S new frames each window propagates
+        alg = algorithmic(w)
+        flops = alg["spatial_flops"] * w["S"]
+        byts = P * ((1 if w["bits"] <= 8 else 2) + 8.0) * w["S"]
     return {"bound": "alu", "achieved": round(flops / t / 1e12, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
             "unit": "TFLOP/s", "frac": round(flops / t / 1e12 / FP32_PEAK_TFLOPS, 4), "traffic": None,
             "kernel": kern, "hbm_achieved_gbs": round(byts / t / 1e9, 1),

@@ -590,11 +590,37 @@ static cudaError_t launch_project(const PcaArgs& a, float* out, cudaStream_t s) 
 // partial matrix part[window][cta][T][T]; a second kernel sums them in float64.
 constexpr int CS_SP = 64;
 
+// Groups of k_cov_small<T> (tiles per group: the upper triangle's for T = 32) and
+// its dynamic shared memory: two strip buffers, or the groups' partial matrices
+// at the end, whichever is larger.
+__host__ __device__ constexpr int cov_small_groups(int T) {
+  return 256 / (T == 32 ? (T / 4) * (T / 4 + 1) / 2 : (T / 4) * (T / 4));
+}
+__host__ __device__ constexpr size_t cov_small_smem(int T) {
+  const size_t strips = size_t(2) * T * (CS_SP + 1), red = size_t(cov_small_groups(T)) * T * T;
+  return (strips > red ? strips : red) * sizeof(float2);
+}
+
 template <int T>
 __global__ void __launch_bounds__(256) k_cov_small(PcaArgs a) {
-  constexpr int TG = T / 4, GT = TG * TG, G = 256 / GT, LDX = CS_SP + 1;
-  extern __shared__ float2 xs[];  // 2 buffers of T x LDX
-  const int tid = threadIdx.x, g = tid / GT, r = tid % GT, ta = r / TG, tb = r % TG;
+  // T = 32: only the 36 tiles on or above the diagonal (ta <= tb), 7 groups in 252
+  // threads; T = 64: all 256 tiles, one group (the reduction reads the upper triangle)
+  constexpr bool UPPER = T == 32;
+  constexpr int TG = T / 4, GT = UPPER ? TG * (TG + 1) / 2 : TG * TG, G = 256 / GT, LDX = CS_SP + 1;
+  static_assert(G == cov_small_groups(T), "groups");
+  extern __shared__ float2 xs[];  // cov_small_smem(T): 2 buffers of T x LDX, later G x T x T
+  const int tid = threadIdx.x, g = tid / GT, r = tid % GT;
+  const bool active = g < G;
+  int ta = r / TG, tb = r % TG;
+  if constexpr (UPPER) {  // r-th tile of the upper triangle, row by row
+    int rr = r;
+    ta = 0;
+    while (rr >= TG - ta) {
+      rr -= TG - ta;
+      ++ta;
+    }
+    tb = ta + rr;
+  }
   const size_t hw = size_t(a.W) * a.H;
   const uint32_t z = blockIdx.y;
   const size_t p_begin = size_t(blockIdx.x) * a.chunk;
@@ -627,7 +653,7 @@ __global__ void __launch_bounds__(256) k_cov_small(PcaArgs a) {
     if (sidx + 1 < nstrips) issue(sidx + 1, (sidx + 1) & 1);
     const float2* x = xs + (sidx & 1) * T * LDX;
 #pragma unroll 4
-    for (int p = g; p < CS_SP; p += G) {
+    for (int p = active ? g : CS_SP; p < CS_SP; p += G) {
       float2 u[4], v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) u[i] = x[(4 * ta + i) * LDX + p];
@@ -646,10 +672,11 @@ __global__ void __launch_bounds__(256) k_cov_small(PcaArgs a) {
   __syncthreads();
   // groups' sums in shared memory (reusing the strip buffers: G x T x T <= 2 x T x LDX)
   float2* red = xs;
+  if (active)
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) red[(size_t(g) * T + 4 * ta + i) * T + 4 * tb + j] = acc[i][j];
+      for (int j = 0; j < 4; ++j) red[(size_t(g) * T + 4 * ta + i) * T + 4 * tb + j] = acc[i][j];
   __syncthreads();
   float2* out = a.partials + (size_t(z) * gridDim.x + blockIdx.x) * T * T;
   for (int e = tid; e < T * T; e += 256) {
@@ -707,7 +734,7 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   if (e0 != cudaSuccess) return e0;
   if (ev) cudaEventRecord(ev[0], s);
   if (a.precision == HV_PREC_FP32 && (a.T == 32 || a.T == 64)) {
-    const size_t smem = size_t(2) * a.T * (CS_SP + 1) * sizeof(float2);
+    const size_t smem = cov_small_smem(int(a.T));
     const dim3 gs(a.nchunks, a.nwin);
     if (a.T == 32) {
       cudaFuncSetAttribute(k_cov_small<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
