@@ -365,18 +365,22 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     h2d = d2h = 0
 
     def step_host(count):
+        # pinned frames pushed and images read back with queued copies
+        # (HV_MEM_HOST_ASYNC): the upload of one batch overlaps the rendering of the
+        # previous one; the step ends when the handle's streams are idle
         nonlocal h2d, d2h
         for _ in range(w["batches"]):
-            assert r2.push(host_pool) == hv.HV_OK
+            assert r2.push(host_pool, async_=True) == hv.HV_OK
             n = 0
             while True:
-                k = r2.render(out_host)
+                k = r2.render(out_host, async_=True)
                 n += k
                 if k == 0:
                     break
             if count:
                 h2d += host_pool.numel() * host_pool.element_size()
                 d2h += n * wf * 4
+        r2.synchronize()
     for _ in range(max(1, args.warmup // 2)):
         step_host(False)
     torch.cuda.synchronize()

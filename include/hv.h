@@ -40,7 +40,11 @@ typedef enum {
   HV_ERR_UNSUPPORTED = -7  /* valid request this build does not implement         */
 } hv_status;
 
-enum { HV_MEM_HOST = 0, HV_MEM_DEVICE = 1 };
+/* Memory kinds of the buffers a call reads or writes. HV_MEM_HOST_ASYNC is host
+ * memory (page-locked for full speed) whose copy is only queued: the call
+ * returns before it has run, as the paper's pipeline runs asynchronously to its
+ * input and output streams (Sec. III). */
+enum { HV_MEM_HOST = 0, HV_MEM_DEVICE = 1, HV_MEM_HOST_ASYNC = 2 };
 
 /* Spatial demodulation (Sec. III-B.1; benchmarks Sec. VI-B). */
 enum { HV_SPATIAL_NONE = 0, HV_SPATIAL_ASP = 1, HV_SPATIAL_FRESNEL = 2 };
@@ -144,7 +148,11 @@ hv_status hv_get_params(const hv_handle* h, hv_params* p);
  * frames must be completely written before that stream reaches the copy -- work
  * of another stream that produces them must be ordered before it, e.g. by
  * giving the handle the producer's stream in hv_open or by synchronising -- and
- * must stay valid until the stream passes it). Frames are uint8 or uint16
+ * must stay valid until the stream passes it) or a host pointer whose copy is
+ * only queued (HV_MEM_HOST_ASYNC: on the handle's copy stream, after the ring
+ * slots it overwrites have been consumed; the buffer must stay unchanged until
+ * hv_synchronize returns or until an hv_render with HV_MEM_HOST output that
+ * renders windows using these frames returns). Frames are uint8 or uint16
  * by pixel_bits, row-major, frames contiguous. All-or-nothing: if the ring
  * cannot take all n frames, nothing is copied and HV_ERR_QUEUE_FULL is returned
  * (backpressure; frames are never dropped). */
@@ -155,7 +163,9 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
  * (order M0, M1, M2, M1N, M2N); PCA -> one float image E; TEMPORAL_NONE -> one
  * complex image per frame (2 floats per pixel). out_capacity_floats bounds the
  * write; *n_windows receives the number of windows rendered (0 is not an
- * error). out_mem_kind says whether `out` is host or device memory.
+ * error). out_mem_kind says whether `out` is host or device memory; with
+ * HV_MEM_HOST_ASYNC the device-to-host copy is queued on the handle's stream and
+ * the images are in `out` once hv_synchronize returns.
  * Errors: HV_ERR_STATE (no params), HV_ERR_ARG, HV_ERR_CUDA. */
 hv_status hv_render(hv_handle* h, float* out, size_t out_capacity_floats, int out_mem_kind,
                     uint32_t* n_windows);
@@ -205,7 +215,7 @@ hv_status hv_profile_enable(hv_handle* h, int on);
 /* Stage times recorded so far; waits for the handle's stream. */
 hv_status hv_profile_read(hv_handle* h, hv_profile* out);
 
-/* Wait for all device work of the handle. */
+/* Wait for all device work of the handle (its stream and its copy stream). */
 hv_status hv_synchronize(hv_handle* h);
 
 /* Free every resource of the handle. NULL is accepted (no-op). */

@@ -27,6 +27,12 @@ struct hv_handle {
   bool own_stream = false;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_pushed = nullptr, ev_consumed = nullptr;
+  // raw-ring consumption: event k is recorded on the stream after a spatial stage
+  // that had propagated every frame below cons_hi[k] (oldest first, circular)
+  static constexpr int NCONS = 32;
+  cudaEvent_t cons_ev[NCONS] = {};
+  uint64_t cons_hi[NCONS] = {};
+  int cons_head = 0, cons_n = 0;
   uint32_t max_w = 0, max_h = 0, bits = 8, cap = 0, tq_req = 0;
   void* raw = nullptr;
   // settings
@@ -644,6 +650,34 @@ hv_status settle(hv_handle* h) {
   return s == HV_OK ? post_apply(h) : s;
 }
 
+// Records that every raw frame below h->propagated has been read once the
+// handle's stream reaches this point (pushes that overwrite those slots wait
+// for it, and only for it).
+hv_status note_consumed(hv_handle* h) {
+  const int k = (h->cons_head + h->cons_n) % hv_handle::NCONS;
+  if (h->cons_n == hv_handle::NCONS) h->cons_head = (h->cons_head + 1) % hv_handle::NCONS;
+  else ++h->cons_n;
+  HV_CU(h, cudaEventRecord(h->cons_ev[k], h->stream));
+  h->cons_hi[k] = h->propagated;
+  return HV_OK;
+}
+
+// The copy stream waits until the raw frames that a push of n frames overwrites
+// have been consumed: the oldest recorded spatial stage that covered them.
+hv_status wait_slots_free(hv_handle* h, uint32_t n) {
+  if (h->pushed + n <= h->cap) return HV_OK;  // nothing overwritten yet
+  const uint64_t need = h->pushed + n - h->cap;  // frames below this are overwritten
+  for (int i = 0; i < h->cons_n; ++i) {
+    const int k = (h->cons_head + i) % hv_handle::NCONS;
+    if (h->cons_hi[k] >= need) {
+      HV_CU(h, cudaStreamWaitEvent(h->copy_stream, h->cons_ev[k], 0));
+      return HV_OK;
+    }
+  }
+  HV_CU(h, cudaStreamWaitEvent(h->copy_stream, h->ev_consumed, 0));  // everything rendered so far
+  return HV_OK;
+}
+
 // Copies n frames from device memory into the input ring on the handle's stream
 // (one copy, or two where the ring wraps). The caller has checked the capacity.
 hv_status enqueue_push_device(hv_handle* h, const void* frames, uint32_t n) {
@@ -704,6 +738,10 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   }
   s = prof_mark(h, 1);
   if (s != HV_OK) return s;
+  if (!capturing) {
+    s = note_consumed(h);
+    if (s != HV_OK) return s;
+  }
   int launches = 0;
   cudaError_t e;
   const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
@@ -822,6 +860,8 @@ hv_status hv_open(const hv_open_desc* desc, hv_handle** out) {
   e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pushed, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_consumed, cudaEventDisableTiming);
+  for (int i = 0; i < hv_handle::NCONS && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&h->cons_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(HV_ERR_CUDA, std::string("stream/event: ") + cudaGetErrorString(e));
   const size_t raw_bytes = size_t(h->cap) * h->max_w * h->max_h * (h->bits / 8);
   e = cudaMalloc(&h->raw, raw_bytes);
@@ -868,7 +908,8 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
   if (!h) return HV_ERR_ARG;
   if (n == 0) return HV_OK;
   if (!frames) return fail(h, HV_ERR_ARG, "frames is NULL");
-  if (mem_kind != HV_MEM_HOST && mem_kind != HV_MEM_DEVICE) return fail(h, HV_ERR_ARG, "bad mem_kind");
+  if (mem_kind != HV_MEM_HOST && mem_kind != HV_MEM_DEVICE && mem_kind != HV_MEM_HOST_ASYNC)
+    return fail(h, HV_ERR_ARG, "bad mem_kind");
   if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "hv_set_params must come first");
   const hv_params& p = h->pending ? h->pend : h->cur;
   if (h->pushed + n - h->next_win > h->cap) {
@@ -884,11 +925,12 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
   char* ring = static_cast<char*>(h->raw);
   {
     // copy stream: wait until the slots being overwritten have been consumed
-    HV_CU(h, cudaStreamWaitEvent(h->copy_stream, h->ev_consumed, 0));
+    hv_status sw = wait_slots_free(h, n);
+    if (sw != HV_OK) return sw;
     HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyHostToDevice, h->copy_stream));
     if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyHostToDevice, h->copy_stream));
     HV_CU(h, cudaEventRecord(h->ev_pushed, h->copy_stream));
-    HV_CU(h, cudaEventSynchronize(h->ev_pushed));  // host buffer consumed on return
+    if (mem_kind == HV_MEM_HOST) HV_CU(h, cudaEventSynchronize(h->ev_pushed));  // host buffer consumed on return
     HV_CU(h, cudaStreamWaitEvent(h->stream, h->ev_pushed, 0));
   }
   h->pushed += n;
@@ -914,7 +956,9 @@ hv_status hv_window_floats(const hv_handle* h, size_t* f) {
 hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, uint32_t* n_windows) {
   if (!h || !n_windows) return fail(h, HV_ERR_ARG, "NULL argument");
   *n_windows = 0;
-  if (out_kind != HV_MEM_HOST && out_kind != HV_MEM_DEVICE) return fail(h, HV_ERR_ARG, "bad mem_kind");
+  if (out_kind != HV_MEM_HOST && out_kind != HV_MEM_DEVICE && out_kind != HV_MEM_HOST_ASYNC)
+    return fail(h, HV_ERR_ARG, "bad mem_kind");
+  const bool host_out = out_kind != HV_MEM_DEVICE;
   if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "no settings");
   HV_CU(h, cudaSetDevice(h->device));
   hv_status s = settle(h);
@@ -922,16 +966,16 @@ hv_status hv_render(hv_handle* h, float* out, size_t cap_floats, int out_kind, u
   const uint32_t nw = out ? windows_ready(h, cap_floats) : 0;
   if (nw == 0) return HV_OK;
   float* dst = out;
-  if (out_kind == HV_MEM_HOST) {
+  if (host_out) {
     s = ensure(h, reinterpret_cast<void**>(&h->staging), &h->staging_bytes, size_t(nw) * h->win_floats * sizeof(float));
     if (s != HV_OK) return s;
     dst = h->staging;
   }
   s = enqueue_windows(h, dst, nw, false);
   if (s != HV_OK) return s;
-  if (out_kind == HV_MEM_HOST) {
+  if (host_out) {
     HV_CU(h, cudaMemcpyAsync(out, dst, size_t(nw) * h->win_floats * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    HV_CU(h, cudaStreamSynchronize(h->stream));
+    if (out_kind == HV_MEM_HOST) HV_CU(h, cudaStreamSynchronize(h->stream));
   }
   *n_windows = nw;
   return HV_OK;
@@ -993,6 +1037,7 @@ hv_status hv_profile_read(hv_handle* h, hv_profile* out) {
 hv_status hv_synchronize(hv_handle* h) {
   if (!h) return HV_ERR_ARG;
   HV_CU(h, cudaSetDevice(h->device));
+  HV_CU(h, cudaStreamSynchronize(h->copy_stream));
   HV_CU(h, cudaStreamSynchronize(h->stream));
   return HV_OK;
 }
@@ -1007,6 +1052,8 @@ hv_status hv_close(hv_handle* h) {
   }
   if (h->ev_pushed) cudaEventDestroy(h->ev_pushed);
   if (h->ev_consumed) cudaEventDestroy(h->ev_consumed);
+  for (auto& e : h->cons_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->pca_ev)
@@ -1359,7 +1406,10 @@ hv_status hv_render_group(hv_group* g, const void* const* frames, const uint32_t
   HV_GCU(g, cudaEventRecord(g->ev_done, g->stream));
   for (auto* h : g->hs) {
     HV_GCU(g, cudaStreamWaitEvent(h->stream, g->ev_done, 0));
-    if (graph) HV_GCU(g, cudaEventRecord(h->ev_consumed, h->stream));
+    if (graph) {
+      HV_GCU(g, cudaEventRecord(h->ev_consumed, h->stream));
+      if (note_consumed(h) != HV_OK) return gfail(g, HV_ERR_CUDA, h->err);
+    }
   }
   ++g->st.steps;
   return HV_OK;

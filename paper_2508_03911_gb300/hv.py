@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libhv.so")
 
 HV_OK, HV_ERR_ARG, HV_ERR_STATE, HV_ERR_QUEUE_FULL = 0, -1, -2, -3
 HV_ERR_NOMEM, HV_ERR_CUDA, HV_ERR_TIMEOUT, HV_ERR_UNSUPPORTED = -4, -5, -6, -7
-HV_MEM_HOST, HV_MEM_DEVICE = 0, 1
+HV_MEM_HOST, HV_MEM_DEVICE, HV_MEM_HOST_ASYNC = 0, 1, 2
 HV_SPATIAL_NONE, HV_SPATIAL_ASP, HV_SPATIAL_FRESNEL = 0, 1, 2
 HV_TEMPORAL_STFT, HV_TEMPORAL_PCA, HV_TEMPORAL_NONE = 0, 1, 2
 HV_MOM_M0, HV_MOM_M1, HV_MOM_M2, HV_MOM_M1N, HV_MOM_M2N = 1, 2, 4, 8, 16
@@ -223,10 +223,13 @@ def _ptr_kind(x):
     return x.data_ptr(), kind, x.numel() * x.element_size()
 
 
-def hv_push_frames(h, frames, n=None) -> int:
-    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). Returns the
-    status (HV_OK or HV_ERR_QUEUE_FULL); other errors raise."""
+def hv_push_frames(h, frames, n=None, async_=False) -> int:
+    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). async_: a host
+    source is only queued (HV_MEM_HOST_ASYNC; keep it unchanged until hv_synchronize).
+    Returns the status (HV_OK or HV_ERR_QUEUE_FULL); other errors raise."""
     ptr, kind, _ = _ptr_kind(frames)
+    if async_ and kind == HV_MEM_HOST:
+        kind = HV_MEM_HOST_ASYNC
     n = frames.shape[0] if n is None else n
     s = lib().hv_push_frames(h, C.c_void_p(ptr), n, kind)
     if s not in (HV_OK, HV_ERR_QUEUE_FULL):
@@ -234,9 +237,12 @@ def hv_push_frames(h, frames, n=None) -> int:
     return s
 
 
-def hv_render(h, out) -> int:
-    """Render into `out` (float32 numpy / torch, host or device). Returns windows."""
+def hv_render(h, out, async_=False) -> int:
+    """Render into `out` (float32 numpy / torch, host or device). async_: a host
+    output is only queued (valid after hv_synchronize). Returns windows."""
     ptr, kind, nbytes = _ptr_kind(out)
+    if async_ and kind == HV_MEM_HOST:
+        kind = HV_MEM_HOST_ASYNC
     n = C.c_uint32(0)
     _check(h, lib().hv_render(h, C.c_void_p(ptr), nbytes // 4, kind, C.byref(n)))
     return n.value
@@ -438,11 +444,11 @@ class Renderer:
     def set_params(self, width, height, **kw):
         hv_set_params(self.h, make_params(width, height, **kw))
 
-    def push(self, frames):
-        return hv_push_frames(self.h, frames)
+    def push(self, frames, async_=False):
+        return hv_push_frames(self.h, frames, async_=async_)
 
-    def render(self, out):
-        return hv_render(self.h, out)
+    def render(self, out, async_=False):
+        return hv_render(self.h, out, async_=async_)
 
     def window_floats(self):
         return hv_window_floats(self.h)

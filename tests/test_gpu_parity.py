@@ -261,6 +261,36 @@ def test_host_buffers_path():
     check_images(img, O.render(fr, p))
 
 
+def test_async_host_push_and_render():
+    """Host frames pushed and images read back asynchronously (HV_MEM_HOST_ASYNC)
+    through a ring smaller than the stream: slot reuse is ordered on the device."""
+    import torch
+    H = W = 64
+    T, S, n = 16, 8, 200
+    fr = synth.random_frames(n, H, W, 12, seed=8)
+    p = oracle_params(spatial="asp", T=T, stride=S, band_lo_bin=1, band_hi_bin=7, moments=("M0", "M2"),
+                      H=H, W=W)
+    src = torch.from_numpy(fr.view(np.int16)).pin_memory()
+    r = hv.Renderer(W, H, 16, 48)
+    try:
+        hv.hv_set_params(r.h, to_hv(p))
+        wf = r.window_floats()
+        out = torch.zeros(n * wf, dtype=torch.float32).pin_memory()
+        got = 0
+        for a in range(0, n, 24):
+            assert r.push(src[a:a + 24], async_=True) == hv.HV_OK
+            while True:
+                k = r.render(out[got * wf:], async_=True)
+                got += k
+                if k == 0:
+                    break
+        r.synchronize()
+    finally:
+        r.close()
+    img = images_from(out.numpy(), got, p)
+    check_images(img, O.render(fr, p))
+
+
 def test_max_window_length():
     H, W, T = 16, 32, 1024
     fr = synth.random_frames(T + 256, H, W, 12, seed=11)
