@@ -172,9 +172,8 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
   }
   if (p.spatial_kernel > HV_SK_PERSISTENT) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
   if (p.spatial_kernel == HV_SK_PERSISTENT &&
-      !(p.width >= 64 && p.width <= 512 && p.height >= 64 && p.height <= 512 &&
-        (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
-    why = "the persistent multi-pass kernels need sides in [64, 512] and ASP or Fresnel";
+      !(p.width >= 64 && p.height >= 64 && (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
+    why = "the persistent multi-pass kernels need sides in [64, 1024] and ASP or Fresnel";
     return HV_ERR_UNSUPPORTED;
   }
   if (p.spatial_kernel == HV_SK_CLUSTER &&
@@ -1138,7 +1137,7 @@ static hv_status af_prepare(hv_handle* h, const void* frames, uint32_t n, uint32
   probe.spatial = HV_SPATIAL_ASP;
   probe.W = h->W;
   probe.H = h->H;
-  if (!spatial_pp_supported(probe)) return fail(h, HV_ERR_UNSUPPORTED, "autofocus needs sides in [64, 512]");
+  if (!spatial_pp_supported(probe)) return fail(h, HV_ERR_UNSUPPORTED, "autofocus needs sides in [64, 1024]");
   const size_t need = size_t(chunk) * h->W * h->H * sizeof(float2);
   s = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need);
   if (s == HV_OK) s = ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need);

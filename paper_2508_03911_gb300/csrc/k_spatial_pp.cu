@@ -3,7 +3,7 @@
 // pixel small.
 //
 // A CTA stays resident and loops over work items (frame, strip of 16 lines of
-// the pass). While it transforms one item, the input of its next item streams
+// the pass; 8 at line length 1024). While it transforms one item, the input of its next item streams
 // into a second buffer with cp.async. Each pass reads its input in whatever
 // order makes the global loads coalesced and writes its output straight from
 // the registers of the last FFT stage; the intermediate layouts are chosen so
@@ -32,15 +32,16 @@ constexpr int PP_BT = 16;
 enum { PK_P1 = PASS_COL_FFT, PK_P2A = PASS_ROW_ASP, PK_P3A = PASS_COL_IFFT, PK_P2F = PASS_ROW_FFT,
        PK_P3T = PASS_COL_IFFT_TAMURA };
 
+// Lines per strip: 16, or 8 at L = 1024 (two buffers of 16 lines would not fit).
 template <int L>
 struct PpCfg {
-  static constexpr int BT = PP_BT;
-  static constexpr int NT = FftThreads<L, BT>::value;  // = L for 64 <= L <= 512
+  static constexpr int BT = L >= 1024 ? 8 : PP_BT;
+  static constexpr int NT = FftThreads<L, BT>::value;  // L for 64 <= L <= 512, 512 at 1024
   static constexpr int LD = BT + 1;
   static constexpr size_t BUF = size_t(L) * LD * sizeof(float2);
   static constexpr size_t RAW = size_t(L) * BT * 2;    // one uint16 strip
   static constexpr size_t TW = size_t(L) * sizeof(float2);
-  static_assert(NT == L, "one thread per element of a line");
+  static_assert(L % NT == 0 && NT % BT == 0, "threads cover the elements of a line");
 };
 
 __device__ __forceinline__ void cpa8(void* s, const void* g) {
@@ -66,16 +67,16 @@ struct SmemSrc {
   __device__ __forceinline__ float2 operator()(int t, int b) const { return buf[t * LD + b]; }
 };
 
-// Element t (row y) of column b from a staged raw strip [y][16], converted to
+// Element t (row y) of column b from a staged raw strip [y][BT], converted to
 // complex; with the Fresnel chirp cy[y] * cx (cx: this thread's column factor).
-template <bool U8, bool CHIRP>
+template <bool U8, bool CHIRP, int BT>
 struct RawSrc {
   static constexpr bool kAliasesBuf = false;
   const unsigned char* raw;
   const float2* cy;
   float2 cx;
   __device__ __forceinline__ float2 operator()(int t, int b) const {
-    const float v = U8 ? float(raw[t * PP_BT + b]) : float(reinterpret_cast<const uint16_t*>(raw)[t * PP_BT + b]);
+    const float v = U8 ? float(raw[t * BT + b]) : float(reinterpret_cast<const uint16_t*>(raw)[t * BT + b]);
     if constexpr (CHIRP) return cscale(cmul(cy[t], cx), v);
     return make_float2(v, 0.f);
   }
@@ -178,16 +179,24 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
 
 // ------------------------------------------------------------- prefetch
 
-// Raw strip of pass P1: rows 0..H-1, columns s0..s0+15 of frame i -> raw_s[y][16].
+// Raw strip of pass P1: rows 0..H-1, columns s0..s0+BT-1 of frame i -> raw_s[y][BT],
+// in 16-byte pieces (8-byte ones when a row segment is shorter: uint8 at BT = 8).
 template <int L>
 __device__ __forceinline__ void prefetch_raw(const SpatialArgs& a, int i, int s0, unsigned char* dst) {
-  const int bpp = a.in_kind == IN_U8 ? 1 : 2;  // 16-byte pieces per row segment
+  using C = PpCfg<L>;
+  const int bpp = a.in_kind == IN_U8 ? 1 : 2;
+  const int seg = C::BT * bpp;  // bytes of one row segment: 8, 16 or 32
   const size_t rslot = (a.raw.slot0 + uint32_t(i)) % a.raw.cap;
   const unsigned char* src = static_cast<const unsigned char*>(a.raw.base) + (rslot * size_t(a.W) * L + s0) * bpp;
   const size_t row = size_t(a.W) * bpp;
-  for (int e = threadIdx.x; e < L * bpp; e += PpCfg<L>::NT) {
-    const int y = e / bpp, q = e % bpp;
-    cpa16(dst + (y * PP_BT * bpp) + q * 16, src + y * row + q * 16);
+  if (seg >= 16) {
+    const int pieces = seg / 16;
+    for (int e = threadIdx.x; e < L * pieces; e += C::NT) {
+      const int y = e / pieces, q = e % pieces;
+      cpa16(dst + y * seg + q * 16, src + y * row + q * 16);
+    }
+  } else {
+    for (int y = threadIdx.x; y < L; y += C::NT) cpa8(dst + y * seg, src + y * row);
   }
   cpa_commit();
 }
@@ -196,9 +205,10 @@ __device__ __forceinline__ void prefetch_raw(const SpatialArgs& a, int i, int s0
 template <int L>
 __device__ __forceinline__ void prefetch_lines(const float2* src, float2* dst) {
   using C = PpCfg<L>;
-  const int t = threadIdx.x;  // NT == L
 #pragma unroll
-  for (int b = 0; b < C::BT; ++b) cpa8(&dst[t * C::LD + b], &src[b * L + t]);
+  for (int t = threadIdx.x; t < L; t += C::NT)
+#pragma unroll
+    for (int b = 0; b < C::BT; ++b) cpa8(&dst[t * C::LD + b], &src[b * L + t]);
   cpa_commit();
 }
 
@@ -256,11 +266,11 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
       const int b = tid % C::BT;
       if (fresnel) {
         const float2 cx = __ldg(&a.chirp_x[s0 + b]);
-        if (u8) pp_stages<L, 1, -1>(RawSrc<true, true>{raw, cys, cx}, buf0, tws, out);
-        else pp_stages<L, 1, -1>(RawSrc<false, true>{raw, cys, cx}, buf0, tws, out);
+        if (u8) pp_stages<L, 1, -1>(RawSrc<true, true, C::BT>{raw, cys, cx}, buf0, tws, out);
+        else pp_stages<L, 1, -1>(RawSrc<false, true, C::BT>{raw, cys, cx}, buf0, tws, out);
       } else {
-        if (u8) pp_stages<L, 1, -1>(RawSrc<true, false>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
-        else pp_stages<L, 1, -1>(RawSrc<false, false>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
+        if (u8) pp_stages<L, 1, -1>(RawSrc<true, false, C::BT>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
+        else pp_stages<L, 1, -1>(RawSrc<false, false, C::BT>{raw, cys, make_float2(0.f, 0.f)}, buf0, tws, out);
       }
     } else if constexpr (PK == PK_P2A) {
       float2* buf = cur == 0 ? buf0 : buf1;
@@ -304,8 +314,9 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
       // time queue [ky][kx]: bin kx of row s0 + b; lanes along kx for the store
       const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
       float2* out = static_cast<float2*>(a.tq.base) + tslot * size_t(a.H) * a.W + size_t(s0) * a.W;
+      for (int kx = tid; kx < L; kx += C::NT)
 #pragma unroll
-      for (int b = 0; b < C::BT; ++b) out[size_t(b) * a.W + tid] = buf[tid * C::LD + b];
+        for (int b = 0; b < C::BT; ++b) out[size_t(b) * a.W + kx] = buf[kx * C::LD + b];
     }
   }
   cpa_wait_all();
@@ -324,7 +335,7 @@ static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int strip_log2 = 0;
-  while ((uint32_t(PP_BT) << strip_log2) < lines) ++strip_log2;
+  while ((uint32_t(C::BT) << strip_log2) < lines) ++strip_log2;
   const int nitems = int(a.n) << strip_log2;
   int grid = per_sm * nsm;
   if (grid > nitems) grid = nitems;
@@ -357,6 +368,7 @@ static cudaError_t pp_w(const SpatialArgs& a, cudaStream_t s, int* launches) {
     case 128: return pp_fixed<LH, 128>(a, s, launches);
     case 256: return pp_fixed<LH, 256>(a, s, launches);
     case 512: return pp_fixed<LH, 512>(a, s, launches);
+    case 1024: return pp_fixed<LH, 1024>(a, s, launches);
   }
   return cudaErrorInvalidValue;
 }
@@ -371,6 +383,7 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
     case 128: return launch_pp<128, PK>(a, lines, s);
     case 256: return launch_pp<256, PK>(a, lines, s);
     case 512: return launch_pp<512, PK>(a, lines, s);
+    case 1024: return launch_pp<1024, PK>(a, lines, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -391,7 +404,7 @@ cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s) {
 }
 
 bool spatial_pp_supported(const SpatialArgs& a) {
-  auto ok = [](uint32_t v) { return v >= 64 && v <= 512; };  // two strip buffers must fit
+  auto ok = [](uint32_t v) { return v >= 64 && v <= 1024; };  // two strip buffers must fit
   return ok(a.W) && ok(a.H) && (a.spatial == HV_SPATIAL_ASP || a.spatial == HV_SPATIAL_FRESNEL);
 }
 
@@ -402,6 +415,7 @@ cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launche
     case 128: return pp_w<128>(a, s, launches);
     case 256: return pp_w<256>(a, s, launches);
     case 512: return pp_w<512>(a, s, launches);
+    case 1024: return pp_w<1024>(a, s, launches);
   }
   return cudaErrorInvalidValue;
 }

@@ -110,12 +110,15 @@ def test_cluster_spatial_field_parity(N, spatial, bits):
         assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
 
 
-@pytest.mark.parametrize("H,W,spatial", [(64, 128, "asp"), (256, 256, "fresnel"), (512, 256, "asp"),
-                                         (128, 512, "fresnel")])
-def test_persistent_multipass_parity(H, W, spatial):
-    """Persistent prefetching multi-pass kernels (frames and strips looped per CTA)."""
+@pytest.mark.parametrize("H,W,spatial,bits", [(64, 128, "asp", 12), (256, 256, "fresnel", 12),
+                                              (512, 256, "asp", 12), (128, 512, "fresnel", 12),
+                                              (1024, 1024, "asp", 12), (256, 1024, "fresnel", 8),
+                                              (1024, 64, "asp", 8)])
+def test_persistent_multipass_parity(H, W, spatial, bits):
+    """Persistent prefetching multi-pass kernels (frames and strips looped per CTA;
+    8-line strips at side 1024, 8-byte raw copies for uint8 there)."""
     n = 7
-    fr = synth.random_frames(n, H, W, 12, seed=H + 3 * W)
+    fr = synth.random_frames(n, H, W, bits, seed=H + 3 * W)
     p = oracle_params(spatial=spatial, z_m=0.3, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
                       H=H, W=W)
     img, _ = gpu_render(fr, p, extra=dict(spatial_kernel="persistent", spatial_chunk=3),
