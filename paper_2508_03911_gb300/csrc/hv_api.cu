@@ -376,7 +376,9 @@ hv_status apply_pending(hv_handle* h) {
       b_tc = cov_tc_partials_floats(ntiles, tc_nchunks) * sizeof(float);
     }
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t total = al(b_part) + (NW + 2) * al(b_mat) + al(b_rot) + al(b_cnt) + al(b_lam) + al(b_vs) + al(b_tc);
+    const size_t b_matf = size_t(T) * T * sizeof(float2);
+    const size_t total = al(b_part) + (NW + 2) * al(b_mat) + 3 * al(b_matf) + al(b_rot) + al(b_cnt) + al(b_lam) +
+                         al(b_vs) + al(b_tc);
     s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
     if (s != HV_OK) return s;
     char* b = static_cast<char*>(h->pca_ws);
@@ -404,6 +406,12 @@ hv_status apply_pending(hv_handle* h) {
     b += al(b_mat);
     a.C2 = reinterpret_cast<double2*>(b);
     b += al(b_mat);
+    a.Cf = reinterpret_cast<float2*>(b);
+    b += al(b_matf);
+    a.Cf2 = reinterpret_cast<float2*>(b);
+    b += al(b_matf);
+    a.Vf = reinterpret_cast<float2*>(b);
+    b += al(b_matf);
     a.rot = reinterpret_cast<double*>(b);
     b += al(b_rot);
     a.counters = reinterpret_cast<unsigned*>(b);

@@ -79,6 +79,9 @@ struct PcaArgs {
   float2* partials;     // nwin x nchunks x upper tiles x TS x TS
   double2* C;           // nwin x T x T
   double2* C2;          // T x T second copy (large-T path: the rounds alternate between C and C2)
+  float2* Cf;           // T x T float32 copies and rotations of the large-T path's first phase
+  float2* Cf2;
+  float2* Vf;
   double2* V;           // T x T (large-T path)
   double* rot;          // T/2 rotations (4 doubles each)
   unsigned* counters;   // 4 counters followed by one double (largest diagonal)

@@ -211,6 +211,51 @@ __device__ __forceinline__ void jacobi_vrow(double2* V, int T, int row, int j0, 
   V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
 }
 
+// Float32 rotation helpers of the float32 phases (same
+// formulas as the float64 ones above).
+struct RotF {
+  float c, s, px, py;
+};
+
+__device__ __forceinline__ bool jacobi_rot_f(float al, float be, float2 g, float tol, float floor_abs, RotF& q) {
+  const float ag = sqrtf(g.x * g.x + g.y * g.y);
+  q = RotF{1.f, 0.f, 1.f, 0.f};
+  if (!(ag > tol * sqrtf(fabsf(al * be)) && ag > floor_abs && ag > 0.f)) return false;
+  const float zeta = (be - al) / (2.f * ag);
+  const float t = -(zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float c = 1.f / sqrtf(1.f + t * t);
+  q = RotF{c, t * c, g.x / ag, g.y / ag};
+  return true;
+}
+
+__device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1, int j0, int j1, const RotF& Jp,
+                                               const RotF& Jq, bool own) {
+  const float2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1], b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
+  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+  const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, q10)), m01 = cadd(cscale(b00, -Jq.s), cmul(b01, q11));
+  const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, q10)), m11 = cadd(cscale(b10, -Jq.s), cmul(b11, q11));
+  const float2 p01 = make_float2(Jp.px * Jp.s, Jp.py * Jp.s), p11 = make_float2(Jp.px * Jp.c, Jp.py * Jp.c);
+  float2 c00 = cadd(cscale(m00, Jp.c), cmul(p01, m10)), c01 = cadd(cscale(m01, Jp.c), cmul(p01, m11));
+  float2 c10 = cadd(cscale(m00, -Jp.s), cmul(p11, m10)), c11 = cadd(cscale(m01, -Jp.s), cmul(p11, m11));
+  if (own) {
+    c01 = make_float2(0.f, 0.f);
+    c10 = make_float2(0.f, 0.f);
+    c00.y = 0.f;
+    c11.y = 0.f;
+  }
+  C[i0 * T + j0] = c00;
+  C[i0 * T + j1] = c01;
+  C[i1 * T + j0] = c10;
+  C[i1 * T + j1] = c11;
+}
+
+__device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0, int j1, const RotF& Jq) {
+  const float2 v0 = V[row * T + j0], v1 = V[row * T + j1];
+  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+  V[row * T + j0] = cadd(cscale(v0, Jq.c), cmul(v1, q10));
+  V[row * T + j1] = cadd(cscale(v0, -Jq.s), cmul(v1, q11));
+}
+
 // Cooperative cyclic Jacobi over all SMs with one grid barrier per round: every
 // CTA computes the rotations of all pairs itself (a deterministic function of
 // the current matrix, so all CTAs agree), then updates its share of the 2 x 2
@@ -271,15 +316,124 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
   if (gtid == 0) a.counters[2] = unsigned(sweeps);
 }
 
+// First phase of the large-window eigensolver: the same cooperative cyclic
+// Jacobi in float32 (on a quarter of the SMs: the arithmetic is cheap, so the
+// grid barrier sets the pace of a round, and a smaller grid makes it cheaper),
+// Cf alternating with Cf2, rotations accumulated in Vf, until a sweep rotates
+// nothing at 1e-6 relative.
+__global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int T = a.T, NP = T / 2;
+  __shared__ RotF rot[256];
+  __shared__ unsigned cnt;
+  const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t gsz = size_t(gridDim.x) * blockDim.x;
+  for (size_t e = gtid; e < size_t(T) * T; e += gsz) {
+    const double2 v = a.C[e];
+    a.Cf[e] = make_float2(float(v.x), float(v.y));
+    a.Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
+  }
+  grid.sync();
+  const float ftol = 1e-6f, ffloor = 1e-7f * float(a.cmax[0]);
+  float2* Cs = a.Cf;
+  float2* Cd = a.Cf2;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    if (threadIdx.x == 0) cnt = 0;
+    for (int r = 0; r < T - 1; ++r) {
+      __syncthreads();
+      for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        const int i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
+        RotF q;
+        if (jacobi_rot_f(Cs[i * T + i].x, Cs[j * T + j].x, Cs[i * T + j], ftol, ffloor, q)) atomicAdd(&cnt, 1u);
+        rot[p] = q;
+      }
+      __syncthreads();
+      const size_t nblk = size_t(NP) * NP;
+      for (size_t e = gtid; e < nblk + size_t(T) * NP; e += gsz) {
+        if (e < nblk) {
+          const int p = int(e / NP), q = int(e % NP);
+          const int i0 = rr_elem(p, r, T), i1 = rr_elem(T - 1 - p, r, T), j0 = rr_elem(q, r, T),
+                    j1 = rr_elem(T - 1 - q, r, T);
+          // copy the 2 x 2 block into the other buffer, then rotate it there
+          Cd[i0 * T + j0] = Cs[i0 * T + j0];
+          Cd[i0 * T + j1] = Cs[i0 * T + j1];
+          Cd[i1 * T + j0] = Cs[i1 * T + j0];
+          Cd[i1 * T + j1] = Cs[i1 * T + j1];
+          if (rot[p].s != 0.f || rot[q].s != 0.f) jacobi_block_f(Cd, T, i0, i1, j0, j1, rot[p], rot[q], p == q);
+        } else {
+          const size_t f = e - nblk;
+          const int row = int(f / NP), q = int(f % NP);
+          if (rot[q].s == 0.f) continue;
+          jacobi_vrow_f(a.Vf, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[q]);
+        }
+      }
+      grid.sync();
+      float2* t = Cs;
+      Cs = Cd;
+      Cd = t;
+    }
+    sweeps = sweep + 1;
+    __syncthreads();
+    const unsigned n = cnt;
+    __syncthreads();
+    if (n == 0) break;
+  }
+  if (gtid == 0) a.counters[1] = unsigned(sweeps);
+}
+
+// out = op(A) B for T x T complex matrices: A float64 (op = identity) or the
+// float32 Vf (op = conjugate transpose, transA = 1); B float64 or Vf as float64.
+// 16 x 16 output tiles, 16-wide k stages in shared memory, float64 accumulation.
+__global__ void __launch_bounds__(256) k_gemm_c64(int T, const double2* A, const float2* Af, int transA,
+                                                  const double2* B, const float2* Bf, double2* out) {
+  __shared__ double2 As[16][17], Bs[16][17];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < T; k0 += 16) {
+    // A element (r, k): A[r][k], or conj(Vf[k][r]) when transposed
+    const int ar = blockIdx.y * 16 + ty, ak = k0 + tx;
+    if (transA) {
+      const float2 v = Af[size_t(ak) * T + ar];
+      As[ty][tx] = make_double2(v.x, -v.y);
+    } else {
+      As[ty][tx] = A[size_t(ar) * T + ak];
+    }
+    const int bk = k0 + ty, bc = blockIdx.x * 16 + tx;
+    if (Bf) {
+      const float2 v = Bf[size_t(bk) * T + bc];
+      Bs[ty][tx] = make_double2(v.x, v.y);
+    } else {
+      Bs[ty][tx] = B[size_t(bk) * T + bc];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) acc = zadd(acc, zmul(As[ty][k], Bs[k][tx]));
+    __syncthreads();
+  }
+  out[size_t(r) * T + c] = acc;
+}
+
 // Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
 // sub-basis columns lo..hi of V as float32.
+// The eigenvalues are Rayleigh quotients diag(V^H C V)_i / |v_i|^2 (the columns of
+// V are unitary only to the float32 phase's accuracy), the vectors normalised.
 __global__ void k_pca_select(PcaArgs a) {
   const int T = a.T;
+  __shared__ double lamv[512], inrm[512];
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    const double li = a.C[i * T + i].x;
+    double n2 = 0.0;
+    for (int t = 0; t < T; ++t) n2 += a.V[t * T + i].x * a.V[t * T + i].x + a.V[t * T + i].y * a.V[t * T + i].y;
+    lamv[i] = a.C[i * T + i].x / n2;
+    inrm[i] = 1.0 / sqrt(n2);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    const double li = lamv[i];
     int rank = 0;
     for (int j = 0; j < T; ++j) {
-      const double lj = a.C[j * T + j].x;
+      const double lj = lamv[j];
       rank += (lj > li) || (lj == li && j < i);
     }
     a.lam[rank] = li;
@@ -287,56 +441,11 @@ __global__ void k_pca_select(PcaArgs a) {
     if (m >= 0 && m < int(a.M))
       for (int t = 0; t < T; ++t) {
         const double2 v = a.V[t * T + i];
-        a.Vs[size_t(t) * a.Mpad + m] = make_float2(float(v.x), float(v.y));
+        a.Vs[size_t(t) * a.Mpad + m] = make_float2(float(v.x * inrm[i]), float(v.y * inrm[i]));
       }
   }
   for (int e = threadIdx.x; e < T * int(a.Mpad); e += blockDim.x)
     if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
-}
-
-// Float32 rotation helpers of the short-window solver's first phase (same
-// formulas as the float64 ones above).
-struct RotF {
-  float c, s, px, py;
-};
-
-__device__ __forceinline__ bool jacobi_rot_f(float al, float be, float2 g, float tol, float floor_abs, RotF& q) {
-  const float ag = sqrtf(g.x * g.x + g.y * g.y);
-  q = RotF{1.f, 0.f, 1.f, 0.f};
-  if (!(ag > tol * sqrtf(fabsf(al * be)) && ag > floor_abs && ag > 0.f)) return false;
-  const float zeta = (be - al) / (2.f * ag);
-  const float t = -(zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-  const float c = 1.f / sqrtf(1.f + t * t);
-  q = RotF{c, t * c, g.x / ag, g.y / ag};
-  return true;
-}
-
-__device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1, int j0, int j1, const RotF& Jp,
-                                               const RotF& Jq, bool own) {
-  const float2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1], b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
-  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
-  const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, q10)), m01 = cadd(cscale(b00, -Jq.s), cmul(b01, q11));
-  const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, q10)), m11 = cadd(cscale(b10, -Jq.s), cmul(b11, q11));
-  const float2 p01 = make_float2(Jp.px * Jp.s, Jp.py * Jp.s), p11 = make_float2(Jp.px * Jp.c, Jp.py * Jp.c);
-  float2 c00 = cadd(cscale(m00, Jp.c), cmul(p01, m10)), c01 = cadd(cscale(m01, Jp.c), cmul(p01, m11));
-  float2 c10 = cadd(cscale(m00, -Jp.s), cmul(p11, m10)), c11 = cadd(cscale(m01, -Jp.s), cmul(p11, m11));
-  if (own) {
-    c01 = make_float2(0.f, 0.f);
-    c10 = make_float2(0.f, 0.f);
-    c00.y = 0.f;
-    c11.y = 0.f;
-  }
-  C[i0 * T + j0] = c00;
-  C[i0 * T + j1] = c01;
-  C[i1 * T + j0] = c10;
-  C[i1 * T + j1] = c11;
-}
-
-__device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0, int j1, const RotF& Jq) {
-  const float2 v0 = V[row * T + j0], v1 = V[row * T + j1];
-  const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
-  V[row * T + j0] = cadd(cscale(v0, Jq.c), cmul(v1, q10));
-  V[row * T + j1] = cadd(cscale(v0, -Jq.s), cmul(v1, q11));
 }
 
 // One sweep's rounds of the CTA-local cyclic Jacobi on C (T x T) and V, for
@@ -710,6 +819,15 @@ __global__ void k_cov_small_reduce(PcaArgs a, uint32_t nparts) {
   }
 }
 
+// V = Vf in float64; the diagonal of C' made exactly real.
+__global__ void k_vf_to_v(PcaArgs a) {
+  const int T = a.T;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T * T; e += gridDim.x * blockDim.x) {
+    a.V[e] = make_double2(a.Vf[e].x, a.Vf[e].y);
+    if (e / T == e % T) a.C[e].y = 0.0;
+  }
+}
+
 template <int T>
 static cudaError_t launch_jacobi_small(const PcaArgs& a, cudaStream_t s) {
   const size_t smem = size_t(2) * T * T * sizeof(double2) + size_t(T) * T * sizeof(float2);  // RA, C', Vf
@@ -769,10 +887,23 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), args, 0, s);
+    // (1) float32 sweeps on a quarter of the SMs
+    const int nf = nsm / 4 > 0 ? nsm / 4 : 1;
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_f32), dim3(nf), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    // (2) C' = Vf^H (C Vf) and V = Vf in float64
+    const dim3 gg(a.T / 16, a.T / 16);
+    k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), a.C, nullptr, 0, nullptr, a.Vf, a.C2);     // M = C Vf
+    k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), nullptr, a.Vf, 1, a.C2, nullptr, a.C);     // C' = Vf^H M
+    k_vf_to_v<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+    // (3) at most two float64 sweeps on C' (off-diagonals ~1e-6 relative -> ~1e-12)
+    PcaArgs b = a;
+    b.max_sweeps = 2;
+    void* bargs[] = {&b};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), bargs, 0, s);
     if (e != cudaSuccess) return e;
     k_pca_select<<<1, 256, 0, s>>>(a);
-    ++*launches;
+    *launches += 5;
   }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
