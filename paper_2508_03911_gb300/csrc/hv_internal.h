@@ -76,6 +76,8 @@ struct PcaArgs {
   uint32_t lo, M, Mpad; // sub-basis: ranks lo .. lo+M-1 (1-based), padded to 64
   int max_sweeps;
   double tol, tol_abs;  // Jacobi skip thresholds (relative, and x largest diagonal)
+  double stop_rel;      // > 0: a float64 sweep whose off-diagonal entries are all below
+                        // stop_rel x trace ends the iteration (refinement after float32)
   float2* partials;     // nwin x nchunks x upper tiles x TS x TS
   double2* C;           // nwin x T x T
   double2* C2;          // T x T second copy (large-T path: the rounds alternate between C and C2)

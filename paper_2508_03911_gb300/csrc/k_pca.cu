@@ -271,17 +271,27 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
   const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const size_t gsz = size_t(gridDim.x) * blockDim.x;
   const double floor_abs = a.tol_abs * a.cmax[0];
+  // optional early end: every off-diagonal entry met in a sweep below stop_rel x trace
+  __shared__ unsigned long long offbits;
+  double trace = 0.0;
+  if (a.stop_rel > 0.0)
+    for (int i = 0; i < T; ++i) trace += a.C[size_t(i) * T + i].x;
   double2* Cs = a.C;
   double2* Cd = a.C2;
   int sweeps = 0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) cnt = 0;
+    if (threadIdx.x == 0) {
+      cnt = 0;
+      offbits = 0ull;
+    }
     for (int r = 0; r < T - 1; ++r) {
       __syncthreads();  // rot of the previous round fully used; cnt reset visible
       for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         const int i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
         Rot q;
-        if (jacobi_rot(Cs[i * T + i].x, Cs[j * T + j].x, Cs[i * T + j], a.tol, floor_abs, q)) atomicAdd(&cnt, 1u);
+        const double2 g = Cs[i * T + j];
+        if (jacobi_rot(Cs[i * T + i].x, Cs[j * T + j].x, g, a.tol, floor_abs, q)) atomicAdd(&cnt, 1u);
+        atomicMax(&offbits, static_cast<unsigned long long>(__double_as_longlong(sqrt(g.x * g.x + g.y * g.y))));
         rot[p] = q;
       }
       __syncthreads();
@@ -306,14 +316,16 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
     }
     sweeps = sweep + 1;
     __syncthreads();
-    const unsigned n = cnt;  // a sweep without any rotation: converged (same in every CTA)
-    __syncthreads();         // every thread has read cnt before the next sweep resets it
-    if (n == 0) break;
+    // a sweep without any rotation, or below the early-end bound: converged (same in every CTA)
+    const bool done = cnt == 0 || (a.stop_rel > 0.0 && __longlong_as_double(static_cast<long long>(offbits)) <=
+                                                          a.stop_rel * trace);
+    __syncthreads();  // every thread has read cnt and offbits before the next sweep resets them
+    if (done) break;
   }
   // the eigenvalues (diagonal) into a.C, where the selection reads them
   if (Cs != a.C)
     for (size_t i = gtid; i < size_t(T); i += gsz) a.C[i * T + i] = Cs[i * T + i];
-  if (gtid == 0) a.counters[2] = unsigned(sweeps);
+  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // float32 phase's sweeps plus these
 }
 
 // First phase of the large-window eigensolver: the same cooperative cyclic
@@ -334,18 +346,28 @@ __global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
     a.Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
   }
   grid.sync();
-  const float ftol = 1e-6f, ffloor = 1e-7f * float(a.cmax[0]);
+  // scales: the trace (>= the largest eigenvalue); float32 rounding leaves
+  // off-diagonal entries near 6e-8 of the largest eigenvalue
+  float trace = 0.f;
+  for (int i = 0; i < T; ++i) trace += float(a.C[size_t(i) * T + i].x);
+  const float ftol = 1e-6f, ffloor = 2e-7f * trace;
+  __shared__ unsigned offbits;  // largest |C_ij| met in the sweep (non-negative float bits)
   float2* Cs = a.Cf;
   float2* Cd = a.Cf2;
   int sweeps = 0;
   for (int sweep = 0; sweep < 20; ++sweep) {
-    if (threadIdx.x == 0) cnt = 0;
+    if (threadIdx.x == 0) {
+      cnt = 0;
+      offbits = 0;
+    }
     for (int r = 0; r < T - 1; ++r) {
       __syncthreads();
       for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         const int i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
         RotF q;
-        if (jacobi_rot_f(Cs[i * T + i].x, Cs[j * T + j].x, Cs[i * T + j], ftol, ffloor, q)) atomicAdd(&cnt, 1u);
+        const float2 g = Cs[i * T + j];
+        if (jacobi_rot_f(Cs[i * T + i].x, Cs[j * T + j].x, g, ftol, ffloor, q)) atomicAdd(&cnt, 1u);
+        atomicMax(&offbits, __float_as_uint(sqrtf(g.x * g.x + g.y * g.y)));
         rot[p] = q;
       }
       __syncthreads();
@@ -375,11 +397,208 @@ __global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
     }
     sweeps = sweep + 1;
     __syncthreads();
-    const unsigned n = cnt;
+    const bool done = cnt == 0 || __uint_as_float(offbits) <= 1e-6f * trace;  // same in every CTA
     __syncthreads();
-    if (n == 0) break;
+    if (done) break;
   }
-  if (gtid == 0) a.counters[1] = unsigned(sweeps);
+  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));
+}
+
+// The float32 phase on one thread-block cluster (JC CTAs, the matrix in their
+// shared memory; T = 128 or 256). CTA `rank` owns rows rank R .. rank R + R - 1 of
+// C (two buffers: a round reads one and writes the other) and of Vf. A round of
+// the round-robin schedule: (1) the owner of each pair's first row computes the
+// pair's rotation (the partner's diagonal entry read from its owner's shared
+// memory) and writes it into every CTA's rotation table; (2) after a cluster
+// barrier, every CTA forms its new rows: the left rotation mixes a row with its
+// partner row (local or remote), the right rotations mix the columns of each
+// pair within the row; Vf rows rotate in place; a second barrier ends the round.
+// Every CTA counts the rotations of its complete table, so all agree when a sweep
+// rotates nothing.
+constexpr int JC = 16;
+
+// position of index i in round r of the round-robin arrangement (inverse of rr_elem)
+__device__ __forceinline__ int rr_pos(int i, int r, int T) {
+  return i == 0 ? 0 : ((i - 1 - r) % (T - 1) + (T - 1)) % (T - 1) + 1;
+}
+
+constexpr int JC_NT = 512;
+
+template <int T>
+__global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
+  constexpr int R = T / JC, NP = T / 2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = int(cl.block_rank()), tid = threadIdx.x, row0 = rank * R;
+  extern __shared__ float4 jcs[];
+  float2* C0 = reinterpret_cast<float2*>(jcs);  // buffer b at C0 + b R T
+  float2* Vr = C0 + 2 * R * T;                  // own rows of Vf
+  float2* Pr = Vr + R * T;                      // partner rows of the round
+  RotF* rot = reinterpret_cast<RotF*>(Pr + R * T);
+  __shared__ int pos_of[T], elem_at[T];
+  __shared__ float gabs[NP];     // |C_ij| of each pair when its rotation was decided
+  __shared__ float tr_part[JC];  // diagonal sums of the CTAs
+  __shared__ unsigned s_nrot;
+  __shared__ float s_offmax;
+  for (int e = tid; e < R * T; e += JC_NT) {
+    const int li = e / T, c = e % T;
+    const double2 v = a.C[size_t(row0 + li) * T + c];
+    C0[e] = make_float2(float(v.x), float(v.y));
+    Vr[e] = make_float2(row0 + li == c ? 1.f : 0.f, 0.f);
+  }
+  if (tid == 0) {  // the trace: every CTA's diagonal sum, written into every CTA
+    float t = 0.f;
+    for (int li = 0; li < R; ++li) t += float(a.C[size_t(row0 + li) * T + row0 + li].x);
+    for (int c = 0; c < JC; ++c) cl.map_shared_rank(tr_part, c)[rank] = t;
+  }
+  cl.sync();
+  float trace = 0.f;
+  for (int c = 0; c < JC; ++c) trace += tr_part[c];
+  // scales: the trace (>= the largest eigenvalue); float32 rounding leaves
+  // off-diagonal entries near 6e-8 of the largest eigenvalue
+  const float ftol = 1e-6f, ffloor = 2e-7f * trace;
+  int sweeps = 0, cur = 0;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    unsigned nrot = 0;   // warp 0's running totals of the sweep
+    float offmax = 0.f;
+    for (int r = 0; r < T - 1; ++r) {
+      float2* Cs = C0 + cur * R * T;
+      float2* Cd = C0 + (cur ^ 1) * R * T;
+      for (int x = tid; x < T; x += JC_NT) {
+        elem_at[x] = rr_elem(x, r, T);
+        pos_of[x] = rr_pos(x, r, T);
+      }
+      __syncthreads();
+      // (1) rotations of the pairs whose first row is ours, into every CTA's table
+      for (int li = tid; li < R; li += JC_NT) {
+        const int i = row0 + li, k = pos_of[i];
+        if (k >= NP) continue;  // i is the second row of its pair
+        const int j = elem_at[T - 1 - k];
+        const float2* Cj = cl.map_shared_rank(Cs, j / R);
+        RotF q;
+        const float2 g = Cs[li * T + j];
+        jacobi_rot_f(Cs[li * T + i].x, Cj[(j % R) * T + j].x, g, ftol, ffloor, q);
+        const float ag = sqrtf(g.x * g.x + g.y * g.y);
+        for (int c = 0; c < JC; ++c) {
+          cl.map_shared_rank(rot, c)[k] = q;
+          cl.map_shared_rank(gabs, c)[k] = ag;
+        }
+      }
+      // partner rows into local memory (Cs does not change during the round): all
+      // of a thread's remote loads issued before any local store
+      {
+        constexpr int PER = R * T / JC_NT;
+        float2 tmp[PER];
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+          const int e = tid + it * JC_NT, li = e / T, c = e % T;
+          const int j = elem_at[T - 1 - pos_of[row0 + li]];
+          tmp[it] = cl.map_shared_rank(Cs, j / R)[(j % R) * T + c];
+        }
+#pragma unroll
+        for (int it = 0; it < PER; ++it) Pr[tid + it * JC_NT] = tmp[it];
+      }
+      cl.sync();
+      // (2) new rows: left rotation with the partner row, then the column pairs
+      for (int e = tid; e < R * NP; e += JC_NT) {
+        const int li = e / NP, q = e % NP;
+        const int i = row0 + li, k = pos_of[i];
+        const int p = k < NP ? k : T - 1 - k;
+        const RotF Jp = rot[p], Jq = rot[q];
+        const int ca = elem_at[q], cb = elem_at[T - 1 - q];
+        // Jp^H = [[c, ph s], [-s, ph c]] on (first, second) rows
+        const float2 ph = make_float2(Jp.px, Jp.py);
+        const float2 ia = Cs[li * T + ca], ib = Cs[li * T + cb], ja = Pr[li * T + ca], jb = Pr[li * T + cb];
+        float2 xa, xb;
+        if (k < NP) {  // i first
+          xa = cadd(cscale(ia, Jp.c), cmul(cscale(ph, Jp.s), ja));
+          xb = cadd(cscale(ib, Jp.c), cmul(cscale(ph, Jp.s), jb));
+        } else {       // i second
+          xa = cadd(cscale(ja, -Jp.s), cmul(cscale(ph, Jp.c), ia));
+          xb = cadd(cscale(jb, -Jp.s), cmul(cscale(ph, Jp.c), ib));
+        }
+        // right: (xa, xb) <- (xa c + xb conj(ph_q) s, -xa s + xb conj(ph_q) c)
+        const float2 qph = make_float2(Jq.px, -Jq.py);
+        float2 ya = cadd(cscale(xa, Jq.c), cmul(xb, cscale(qph, Jq.s)));
+        float2 yb = cadd(cscale(xa, -Jq.s), cmul(xb, cscale(qph, Jq.c)));
+        if (q == p && Jp.s != 0.f) {  // the pair's own block: exactly diagonal, real diagonal
+          if (i == ca) {
+            ya.y = 0.f;
+            yb = make_float2(0.f, 0.f);
+          } else {
+            yb.y = 0.f;
+            ya = make_float2(0.f, 0.f);
+          }
+        }
+        Cd[li * T + ca] = ya;
+        Cd[li * T + cb] = yb;
+        if (Jq.s != 0.f) {  // Vf rows: right rotation of the column pair q, in place
+          const float2 va = Vr[li * T + ca], vb = Vr[li * T + cb];
+          Vr[li * T + ca] = cadd(cscale(va, Jq.c), cmul(vb, cscale(qph, Jq.s)));
+          Vr[li * T + cb] = cadd(cscale(va, -Jq.s), cmul(vb, cscale(qph, Jq.c)));
+        }
+      }
+      if (tid < 32)  // the table is the same in every CTA
+        for (int p = tid; p < NP; p += 32) {
+          nrot += rot[p].s != 0.f;
+          offmax = fmaxf(offmax, gabs[p]);
+        }
+      cl.sync();
+      cur ^= 1;
+    }
+    sweeps = sweep + 1;
+    if (tid < 32) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+        offmax = fmaxf(offmax, __shfl_xor_sync(0xffffffffu, offmax, o));
+      }
+      if (tid == 0) {
+        s_nrot = nrot;
+        s_offmax = offmax;
+      }
+    }
+    __syncthreads();
+    const bool done = s_nrot == 0 || s_offmax <= 1e-6f * trace;
+    __syncthreads();  // s_nrot / s_offmax read by every thread before the next sweep writes them
+    if (done) break;  // the float64 phase takes it from 1e-6 of the trace
+  }
+  for (int e = tid; e < R * T; e += JC_NT) a.Vf[size_t(row0) * T + e] = Vr[e];
+  if (rank == 0 && tid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));
+}
+
+template <int T>
+static cudaError_t launch_jacobi_cluster(const PcaArgs& a, cudaStream_t s, bool* ok) {
+  *ok = false;
+  constexpr int R = T / JC;
+  const size_t smem = size_t(4) * R * T * sizeof(float2) + size_t(T / 2) * sizeof(RotF);
+  auto kern = k_jacobi_cluster<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;  // not available: the caller uses the cooperative kernel
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(JC);
+  cfg.blockDim = dim3(JC_NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = JC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e == cudaSuccess) *ok = true;
+  return e;
 }
 
 // out = op(A) B for T x T complex matrices: A float64 (op = identity) or the
@@ -511,15 +730,21 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
     Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
+  __shared__ double trace_s;
   if (tid == 0) {
-    double m = 0.0;
-    for (int i = 0; i < T; ++i) m = fmax(m, Cg[i * T + i].x);
+    double m = 0.0, t = 0.0;
+    for (int i = 0; i < T; ++i) {
+      m = fmax(m, Cg[i * T + i].x);
+      t += Cg[i * T + i].x;
+    }
     cmax = m;
     cmaxf = float(m);
+    trace_s = t;
   }
   __syncthreads();
-  // (1) float32 sweeps
-  const float ftol = 1e-6f, ffloor = 1e-7f * cmaxf;
+  // (1) float32 sweeps until one rotates nothing at 1e-6 (relative, and of the
+  // largest diagonal entry)
+  const float ftol = 1e-6f, ffloor = 1e-6f * cmaxf;
   int sweeps_f = 0;
   for (int sw = 0; sw < 20; ++sw) {
     const unsigned n = local_sweep<T>(
@@ -554,17 +779,27 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
   for (int e = tid; e < T * T; e += blockDim.x) V[e] = make_double2(Vf[e].x, Vf[e].y);
   for (int i = tid; i < T; i += blockDim.x) C[i * T + i].y = 0.0;
   __syncthreads();
+  // float64 sweeps until one rotates nothing or meets no off-diagonal entry above
+  // 1e-12 of the trace
+  __shared__ unsigned long long offbits64;
+  const double trace64 = trace_s;
   int sweeps_d = 0;
   for (int sw = 0; sw < a.max_sweeps; ++sw) {
+    if (tid == 0) offbits64 = 0ull;
     const unsigned n = local_sweep<T>(
         C, V, rot, &cnt,
-        [&](double al, double be, double2 g, Rot& q) { return jacobi_rot(al, be, g, a.tol, a.tol_abs * cmax, q); },
+        [&](double al, double be, double2 g, Rot& q) {
+          atomicMax(&offbits64, static_cast<unsigned long long>(__double_as_longlong(sqrt(g.x * g.x + g.y * g.y))));
+          return jacobi_rot(al, be, g, a.tol, a.tol_abs * cmax, q);
+        },
         [](double2* Cm, int TT, int i0, int i1, int j0, int j1, const Rot& Jp, const Rot& Jq, bool own) {
           jacobi_block(Cm, Cm, TT, i0, i1, j0, j1, Jp, Jq, own);
         },
         jacobi_vrow);
     sweeps_d = sw + 1;
-    if (n == 0) break;
+    const bool done = n == 0 || __longlong_as_double(static_cast<long long>(offbits64)) <= 1e-12 * trace64;
+    __syncthreads();
+    if (done) break;
   }
   if (tid == 0) atomicAdd(&a.counters[2], unsigned(sweeps_f + sweeps_d));  // summed over the launch's windows
   // eigenvalues as Rayleigh quotients, vectors normalised; rank and sub-basis
@@ -887,18 +1122,27 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     void* args[] = {&a};
-    // (1) float32 sweeps on a quarter of the SMs
-    const int nf = nsm / 4 > 0 ? nsm / 4 : 1;
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_f32), dim3(nf), dim3(256), args, 0, s);
+    // (1) float32 sweeps: on one 16-CTA cluster (T = 128, 256), else cooperative on a
+    // quarter of the SMs
+    bool on_cluster = false;
+    if (a.T == 256) e = launch_jacobi_cluster<256>(a, s, &on_cluster);
+    else if (a.T == 128) e = launch_jacobi_cluster<128>(a, s, &on_cluster);
     if (e != cudaSuccess) return e;
+    if (!on_cluster) {
+      const int nf = nsm / 4 > 0 ? nsm / 4 : 1;
+      e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_f32), dim3(nf), dim3(256), args, 0, s);
+      if (e != cudaSuccess) return e;
+    }
     // (2) C' = Vf^H (C Vf) and V = Vf in float64
     const dim3 gg(a.T / 16, a.T / 16);
     k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), a.C, nullptr, 0, nullptr, a.Vf, a.C2);     // M = C Vf
     k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), nullptr, a.Vf, 1, a.C2, nullptr, a.C);     // C' = Vf^H M
     k_vf_to_v<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
-    // (3) at most two float64 sweeps on C' (off-diagonals ~1e-6 relative -> ~1e-12)
+    // (3) float64 sweeps on C' (off-diagonals ~1e-6 of the trace) until every entry met
+    // in a sweep is below 1e-12 of it (usually two)
     PcaArgs b = a;
-    b.max_sweeps = 2;
+    b.max_sweeps = 4;
+    b.stop_rel = 1e-12;
     void* bargs[] = {&b};
     e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), bargs, 0, s);
     if (e != cudaSuccess) return e;
