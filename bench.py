@@ -439,14 +439,19 @@ def roofline_pca(w, res, peaks, force=None):
     elif kern == "projection":
         flops, byts = 8.0 * P * T * M, 8.0 * P * T
     elif kern == "jacobi_fp64":
+        # float64 work of the refinement sweeps over the whole eigensolver time (the
+        # float32 sweeps before them run on one 16-SM cluster, bound by barriers)
         sweeps = prof["pca_sweeps"] / nwin
-        flops, byts = sweeps * (T - 1) * (T // 2) ** 2 * 96.0 + sweeps * (T - 1) * T * (T // 2) * 32.0, 0.0
+        sweeps32 = prof.get("pca_sweeps_f32", 0) / nwin
+        per_sweep = (T - 1) * (T // 2) ** 2 * 96.0 + (T - 1) * T * (T // 2) * 32.0
+        flops, byts = sweeps * per_sweep, 0.0
         fp64_peak = 1.25
         return {"bound": "alu", "achieved": round(flops / t / 1e12, 4), "peak": fp64_peak,
                 "unit": "TFLOP/s (FP64)", "frac": round(flops / t / 1e12 / fp64_peak, 4),
-                "traffic": None, "kernel": "k_jacobi (FP64 cyclic Jacobi)",
+                "traffic": None, "kernel": "eigensolver (FP32 cyclic Jacobi, then FP64 refinement)",
                 "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)",
-                "sweeps_per_window": round(sweeps, 2),
+                "sweeps_per_window": round(sweeps, 2), "fp32_sweeps_per_window": round(sweeps32, 2),
+                "fp32_flops_per_window": round(sweeps32 * per_sweep),
                 "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
     else:  # spatial: the S new frames each window propagates
         alg = algorithmic(w)

@@ -774,10 +774,11 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
       e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
       w += k;
       if (h->prof && e == cudaSuccess) {
-        unsigned sw = 0;  // sweeps of this window (synchronous read; profiling only)
-        HV_CU(h, cudaMemcpyAsync(&sw, h->pca.counters + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        unsigned sw[2] = {0, 0};  // float32, float64 sweeps of the launch (synchronous read; profiling only)
+        HV_CU(h, cudaMemcpyAsync(sw, h->pca.counters + 1, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         HV_CU(h, cudaStreamSynchronize(h->stream));
-        h->prof_acc.pca_sweeps += sw;
+        h->prof_acc.pca_sweeps_f32 += sw[0];
+        h->prof_acc.pca_sweeps += sw[1];
       }
     }
     h->pca_has_lam = true;

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
   // the eigenvalues (diagonal) into a.C, where the selection reads them
   if (Cs != a.C)
     for (size_t i = gtid; i < size_t(T); i += gsz) a.C[i * T + i] = Cs[i * T + i];
-  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // float32 phase's sweeps plus these
+  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // float64 sweeps
 }
 
 // First phase of the large-window eigensolver: the same cooperative cyclic
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
     __syncthreads();
     if (done) break;
   }
-  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));
+  if (gtid == 0) atomicAdd(&a.counters[1], unsigned(sweeps));  // float32 sweeps
 }
 
 // The float32 phase on one thread-block cluster (JC CTAs, the matrix in their
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
     if (done) break;  // the float64 phase takes it from 1e-6 of the trace
   }
   for (int e = tid; e < R * T; e += JC_NT) a.Vf[size_t(row0) * T + e] = Vr[e];
-  if (rank == 0 && tid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));
+  if (rank == 0 && tid == 0) atomicAdd(&a.counters[1], unsigned(sweeps));  // float32 sweeps
 }
 
 template <int T>
@@ -801,7 +801,10 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
     __syncthreads();
     if (done) break;
   }
-  if (tid == 0) atomicAdd(&a.counters[2], unsigned(sweeps_f + sweeps_d));  // summed over the launch's windows
+  if (tid == 0) {  // summed over the launch's windows
+    atomicAdd(&a.counters[1], unsigned(sweeps_f));
+    atomicAdd(&a.counters[2], unsigned(sweeps_d));
+  }
   // eigenvalues as Rayleigh quotients, vectors normalised; rank and sub-basis
   __shared__ double lamv[T], inrm[T];
   for (int i = tid; i < T; i += blockDim.x) {

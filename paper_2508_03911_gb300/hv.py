@@ -65,7 +65,7 @@ class hv_profile(C.Structure):
     _fields_ = [("spatial_ms", C.c_double), ("temporal_ms", C.c_double), ("renders", C.c_uint64),
                 ("frames", C.c_uint64), ("windows", C.c_uint64), ("pca_cov_ms", C.c_double),
                 ("pca_eig_ms", C.c_double), ("pca_proj_ms", C.c_double),
-                ("pca_sweeps", C.c_uint64)]
+                ("pca_sweeps", C.c_uint64), ("pca_sweeps_f32", C.c_uint64)]
 
 
 class hv_tuning(C.Structure):
