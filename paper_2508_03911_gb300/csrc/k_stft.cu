@@ -17,16 +17,24 @@
 namespace hv {
 
 // ------------------------------------------------------------------------
-// Kernel layout: 8 warps per CTA; each pixel's FFT is carried by LP lanes of one
+// Kernel layout: 8 pixels per CTA; each pixel's FFT is carried by LP lanes of one
 // warp (LP = 32 for T >= 256, fewer for short windows, a warp then holding
-// 32 / LP pixels). A pixel's samples sit in a shared ring of RS = T + min(S, T)
-// slots, so the S frames that the next window adds are fetched with cp.async
-// while the current window is transformed (S < T: frame o of the launch in slot
-// o mod RS; S >= T: windows alternate between the two halves). The FFT is a
-// Stockham pass sequence private to the warp (only __syncwarp between stages)
-// through a padded work row, index i at i + i/16, which keeps the stage
-// accesses of a pixel at two wavefronts. When the band lies below T/2 the last
-// stage only forms the lower half of its outputs.
+// PW = 32 / LP pixels). A warp runs on its own: it fetches its pixels' frames,
+// transforms them and writes their moments with only __syncwarp between steps,
+// so the warps of a CTA never wait on one another inside the window loop.
+//
+// Ring of a pixel (RS = T + min(S, T) slots of shared memory):
+//  - overlapping windows (S < T): slots [0, T) hold the current window, frame o
+//    of the launch at slot o mod T, and slots [T, T + S) stage the S frames the
+//    next window adds (cp.async, in flight while the current window is
+//    transformed). At the start of a window the staged frames move into the
+//    slots of the S frames that left. The FFT reads slots 0 .. T-1 in order: a
+//    circular shift of the window, which leaves every |S_k|^2 unchanged, so the
+//    loads need no wrap-around.
+//  - S >= T: windows alternate between the halves [0, T) and [T, 2T).
+// The FFT is a Stockham pass sequence through a padded work row (index i at
+// i + i/16, two wavefronts per stage access of a pixel). When the band lies
+// below T/2 the last stage only forms the lower half of its outputs.
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -37,20 +45,55 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
 
+// Band moments of one lane in units of bins. Its bins are k = kb + m NB (kb =
+// jl + LP it for its butterflies it); the signed frequency index of bin k is
+// kb + NB m' with m' = m below T/2 and m - R above. Per butterfly the lane sums
+// P, m' P and m'^2 P over its in-band m (constant weights), and folds them into
+// sum k' P and sum k'^2 P once.
 struct MomAcc {
-  uint32_t klo, khi;
-  float fscale;
-  float m0, m1, m2;
-  template <int T>
-  __device__ __forceinline__ void add(int k, float2 v) {
-    if (uint32_t(k) - klo <= khi - klo) {
-      const float P = fmaf(v.x, v.x, v.y * v.y);
-      const float f = float(k < T / 2 ? k : k - T) * fscale;
-      m0 += P;
-      m1 = fmaf(f, P, m1);
-      m2 = fmaf(f, f * P, m2);
-    }
+  uint32_t band;     // bit it R + m set: bin (it, m) of the last stage lies in [klo, khi]
+  float m0, m1, m2;  // sum P, sum k' P, sum k'^2 P
+};
+
+// Radix plan of the time FFT: two register-heavy stages where the length allows
+// it (one exchange through shared memory), else radix 8, 4, 2.
+template <int T>
+struct WarpPlan {
+  static constexpr int R1 = T == 1024 ? 32 : (T >= 128 ? 16 : RadixOf<T>::value);
+  static constexpr int R2 = T == 128 ? 8 : (T == 256 ? 16 : (T >= 512 ? 32 : 0));
+  static constexpr int RMAX = R1 > R2 ? R1 : R2;
+  template <int NS>
+  __host__ __device__ static constexpr int radix() {
+    if constexpr (R2 != 0) return NS == 1 ? R1 : R2;
+    else return RadixOf<T / NS>::value;
   }
+  // radix of the last stage
+  __host__ __device__ static constexpr int last() {
+    if (R2 != 0) return R2;
+    int ns = 1, r = 2;
+    while (ns < T) {
+      const int rem = T / ns;
+      r = rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2);
+      ns *= r;
+    }
+    return r;
+  }
+};
+
+// Lanes per pixel: every stage's butterflies spread evenly over LP lanes (at
+// most 32); a warp then holds 32 / LP pixels.
+template <int T>
+struct WarpLayout {
+  static constexpr int NBMIN = T / WarpPlan<T>::RMAX;
+  static constexpr int LP = NBMIN < 32 ? NBMIN : 32;
+  static constexpr int PW = 32 / LP;                                  // pixels per warp
+  static constexpr int NW = PW >= 8 ? 1 : 8 / PW;                     // warps per CTA
+  static constexpr int NT = 32 * NW;
+  static constexpr int BT = NW * PW;                                  // pixels per CTA (>= 8)
+  static constexpr int WLD = T + T / 16;                              // work row stride
+  static constexpr int RL = WarpPlan<T>::last();                      // last-stage radix
+  static constexpr int ITL = T / RL / LP;                             // last-stage butterflies per lane
+  static_assert(ITL * RL <= 32, "band bits of a lane");
 };
 
 // Lower half X_0 .. X_{R/2-1} of an R-point forward DFT.
@@ -65,8 +108,19 @@ __device__ __forceinline__ void dft_lower(float2* v) {
     }
     dft<16, -1>(e);
     dft<16, -1>(o);
+    // X_k = E_k + w32^k O_k with the twiddle product fused into the sum
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = cadd(e[k], tw32<-1>(o[k], k));
+    for (int k = 0; k < 16; ++k) {
+      if (k == 0) {
+        v[0] = cadd(e[0], o[0]);
+      } else if (k == 8) {
+        v[8] = cadd(e[8], mul_i<-1>(o[8]));
+      } else {
+        const float2 w = tw32<-1>(make_float2(1.f, 0.f), k);  // constants after unrolling
+        v[k] = make_float2(fmaf(o[k].x, w.x, fmaf(-o[k].y, w.y, e[k].x)),
+                           fmaf(o[k].x, w.y, fmaf(o[k].y, w.x, e[k].y)));
+      }
+    }
   } else if constexpr (R == 16) {
     dft<16, -1>(v);
   } else if constexpr (R == 2) {
@@ -89,39 +143,35 @@ __device__ __forceinline__ void dft_lower(float2* v) {
   }
 }
 
-// Radix plan of the time FFT: two register-heavy stages where the length allows
-// it (one exchange through shared memory), else radix 8, 4, 2.
-template <int T>
-struct WarpPlan {
-  static constexpr int R1 = T == 1024 ? 32 : (T >= 128 ? 16 : RadixOf<T>::value);
-  static constexpr int R2 = T == 128 ? 8 : (T == 256 ? 16 : (T >= 512 ? 32 : 0));
-  static constexpr int RMAX = R1 > R2 ? R1 : R2;
-  template <int NS>
-  __host__ __device__ static constexpr int radix() {
-    if constexpr (R2 != 0) return NS == 1 ? R1 : R2;
-    else return RadixOf<T / NS>::value;
+// Moment sums of butterfly it of the last stage (outputs m < MO in registers).
+template <int R, int NB, int MO>
+__device__ __forceinline__ void add_moments(const float2* v, int it, float kb, MomAcc& acc) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int m = 0; m < MO; ++m) {
+    if (acc.band & (1u << (it * R + m))) {
+      const float P = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+      const float mm = float(m < R / 2 ? m : m - R);
+      s0 += P;
+      if (m != 0) {
+        s1 = fmaf(mm, P, s1);
+        s2 = fmaf(mm * mm, P, s2);
+      }
+    }
   }
-};
-
-// Lanes per pixel: every stage's butterflies spread evenly over LP lanes (at
-// most 32); a warp then holds 32 / LP pixels.
-template <int T>
-struct WarpLayout {
-  static constexpr int NBMIN = T / WarpPlan<T>::RMAX;
-  static constexpr int LP = NBMIN < 32 ? NBMIN : 32;
-  static constexpr int PW = 32 / LP;                                  // pixels per warp
-  static constexpr int NW = PW >= 8 ? 1 : 8 / PW;                     // warps per CTA
-  static constexpr int NT = 32 * NW;
-  static constexpr int BT = NW * PW;                                  // pixels per CTA (>= 8)
-  static constexpr int WLD = T + T / 16;                              // work row stride
-};
+  // k' = kb + NB m': sum k' P = kb s0 + NB s1, sum k'^2 P = kb^2 s0 + 2 kb NB s1 + NB^2 s2
+  acc.m0 += s0;
+  acc.m1 = fmaf(kb, s0, fmaf(float(NB), s1, acc.m1));
+  acc.m2 = fmaf(kb * kb, s0, fmaf(2.f * float(NB) * kb, s1, fmaf(float(NB * NB), s2, acc.m2)));
+}
 
 // Stockham stages of one pixel's length-T forward FFT, carried by the LP lanes
-// of its group (jl = lane within the group): stage 1 reads the ring, later
-// stages the pixel's work row; the last stage feeds the moment accumulator.
+// of its group (jl = lane within the group): stage 1 reads the window (T
+// samples from `win`, in order), later stages the pixel's work row; the last
+// stage feeds the moment sums.
 template <int T, int NS, int LP>
-__device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, float2* work,
-                                         const float2* tw, int jl, MomAcc& acc, bool lower) {
+__device__ __forceinline__ void warp_fft(const float2* win, float2* work, const float2* tw, int jl,
+                                         MomAcc& acc, bool lower) {
   constexpr int R = WarpPlan<T>::template radix<NS>();
   constexpr int NB = T / R;
   static_assert(NB % LP == 0, "lanes per pixel must divide the butterflies");
@@ -133,13 +183,8 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int t = j + m * NB;
-      if constexpr (NS == 1) {
-        int sl = rbase + t;
-        if (sl >= RS) sl -= RS;
-        v[it][m] = ring[sl];
-      } else {
-        v[it][m] = work[wpad(t)];
-      }
+      if constexpr (NS == 1) v[it][m] = win[t];
+      else v[it][m] = work[wpad(t)];
     }
     if constexpr (NS > 1) {
       // stage table: entry (m, jm) at (NS - R1) + (m - 1) NS + jm, contiguous in jm
@@ -150,19 +195,18 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
     }
   }
   if constexpr (NS * R == T) {
+    const float kb0 = float(jl);
     if (lower) {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
         dft_lower<R>(v[it]);
-#pragma unroll
-        for (int m = 0; m < R / 2; ++m) acc.add<T>(jl + LP * it + m * NB, v[it][m]);
+        add_moments<R, NB, R / 2>(v[it], it, kb0 + float(LP * it), acc);
       }
     } else {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
         dft<R, -1>(v[it]);
-#pragma unroll
-        for (int m = 0; m < R; ++m) acc.add<T>(jl + LP * it + m * NB, v[it][m]);
+        add_moments<R, NB, R>(v[it], it, kb0 + float(LP * it), acc);
       }
     }
   } else {
@@ -177,7 +221,7 @@ __device__ __forceinline__ void warp_fft(const float2* ring, int rbase, int RS, 
       for (int m = 0; m < R; ++m) work[wpad(base + m * NS)] = v[it][m];
     }
     __syncwarp();
-    warp_fft<T, NS * R, LP>(ring, rbase, RS, work, tw, jl, acc, lower);
+    warp_fft<T, NS * R, LP>(win, work, tw, jl, acc, lower);
   }
 }
 
@@ -191,37 +235,37 @@ __host__ __device__ constexpr size_t warp_smem(uint32_t S) {
 template <int T>
 __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
   using Lw = WarpLayout<T>;
-  constexpr int BT = Lw::BT, NT = Lw::NT, LP = Lw::LP, PW = Lw::PW;
+  constexpr int NT = Lw::NT, LP = Lw::LP, PW = Lw::PW;
   extern __shared__ float2 smem[];
-  const int S = int(a.S);
-  const int RS = T + (S < T ? S : T);
-  const int RLD = RS + 1;
+  const uint32_t S = a.S;
+  const bool overlap = S < uint32_t(T);
+  const int RLD = T + int(overlap ? S : T) + 1;
   float2* ring = smem;
-  float2* tw = ring + BT * RLD;
+  float2* tw = ring + Lw::BT * RLD;
   float2* work = tw + T;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pl = lane / LP, jl = lane % LP;  // pixel within the warp, lane within the pixel
   const int px = warp * PW + pl;             // pixel within the CTA
   const size_t HW = size_t(a.W) * a.H;
-  const uint32_t p0 = blockIdx.x * BT;
+  const uint32_t p0 = blockIdx.x * Lw::BT;
   const float2* tq = static_cast<const float2*>(a.tq.base);
+  const uint32_t cap = a.tq.cap;
   const bool lower = a.khi < uint32_t(T / 2);
+  // the warp's pixels and its lanes' share of a fetch: pixel fb, frames ff + k 32/PW
+  float2* wring = ring + warp * PW * RLD;
+  const int fb = lane % PW, ff = lane / PW;
+  const float2* src = tq + p0 + warp * PW + fb;
 
-  auto fetch = [&](int w) {  // issue the loads of window w's new frames
-    int o0, n, s0;
-    if (w == 0) {
-      o0 = 0; n = T; s0 = 0;
-    } else if (S < T) {
-      o0 = w * S + T - S; n = S; s0 = o0 % RS;
-    } else {
-      o0 = w * S; n = T; s0 = (w & 1) * T;
-    }
-    for (int idx = tid; idx < n * BT; idx += NT) {
-      const int b = idx % BT, f = idx / BT;
-      int sl = s0 + f;
-      if (sl >= RS) sl -= RS;
-      const size_t g = (size_t(a.tq.slot0) + uint32_t(o0 + f)) % a.tq.cap;
-      cp_async8(&ring[b * RLD + sl], &tq[g * HW + p0 + b]);
+  // cp.async of n frames starting at frame o0 of the launch into slots s0 + f of
+  // the warp's pixels (the launch's frames fit the queue: o0 + n <= cap)
+  auto fetch = [&](uint32_t o0, int n, int s0) {
+    uint32_t g = a.tq.slot0 + o0 + uint32_t(ff);
+    if (g >= cap) g -= cap;
+    if (g >= cap) g -= cap;
+    for (int f = ff; f < n; f += 32 / PW) {
+      cp_async8(&wring[fb * RLD + s0 + f], &src[size_t(g) * HW]);
+      g += 32 / PW;
+      if (g >= cap) g -= cap;
     }
     cp_async_commit();
   };
@@ -241,14 +285,41 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_
       NS *= R;
     }
   }
-  fetch(0);
+  // in-band bits of the lane's last-stage bins
+  uint32_t band = 0;
+  {
+    constexpr int RL = Lw::RL, NBL = T / RL;
+#pragma unroll
+    for (int it = 0; it < Lw::ITL; ++it)
+#pragma unroll
+      for (int m = 0; m < RL; ++m) {
+        const uint32_t k = uint32_t(jl + LP * it + m * NBL);
+        if (k - a.klo <= a.khi - a.klo) band |= 1u << (it * RL + m);
+      }
+  }
+  fetch(0, T, 0);
+  if (overlap && a.nwin > 1) fetch(T, int(S), T);  // window 1's new frames, staged
+  __syncthreads();                                 // twiddles
   for (uint32_t w = 0; w < a.nwin; ++w) {
     cp_async_wait_all();
-    __syncthreads();
-    if (w + 1 < a.nwin) fetch(int(w) + 1);
-    const int rbase = S < T ? int((size_t(w) * S) % RS) : int(w & 1) * T;
-    MomAcc acc{a.klo, a.khi, a.fscale, 0.f, 0.f, 0.f};
-    warp_fft<T, 1, LP>(ring + px * RLD, rbase, RS, work + px * Lw::WLD, tw, jl, acc, lower);
+    __syncwarp();
+    const float2* win;
+    if (overlap) {
+      if (w > 0) {
+        // staged frames of window w -> slots of the frames that left
+        const uint32_t d = (w - 1) * S;
+        for (int f = ff; f < int(S); f += 32 / PW)
+          wring[fb * RLD + int((d + uint32_t(f)) & uint32_t(T - 1))] = wring[fb * RLD + T + f];
+        __syncwarp();
+        if (w + 1 < a.nwin) fetch((w + 1) * S + uint32_t(T) - S, int(S), T);
+      }
+      win = ring + px * RLD;
+    } else {
+      if (w + 1 < a.nwin) fetch((w + 1) * S, T, int((w + 1) & 1) * T);
+      win = ring + px * RLD + int(w & 1) * T;
+    }
+    MomAcc acc{band, 0.f, 0.f, 0.f};
+    warp_fft<T, 1, LP>(win, work + px * Lw::WLD, tw, jl, acc, lower);
 #pragma unroll
     for (int o = LP / 2; o > 0; o >>= 1) {  // reduce within the pixel's lane group
       acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
@@ -256,15 +327,16 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_
       acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
     }
     if (jl == 0) {
+      const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
       float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
       int q = 0;
       if (a.mask & HV_MOM_M0) o[HW * q++] = acc.m0;
-      if (a.mask & HV_MOM_M1) o[HW * q++] = acc.m1;
-      if (a.mask & HV_MOM_M2) o[HW * q++] = acc.m2;
+      if (a.mask & HV_MOM_M1) o[HW * q++] = m1;
+      if (a.mask & HV_MOM_M2) o[HW * q++] = m2;
       const double d0 = acc.m0;
-      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(acc.m1) / d0) : 0.f;
+      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(m1) / d0) : 0.f;
       if (a.mask & HV_MOM_M2N) {
-        const double r = d0 > 0.0 ? double(acc.m2) / d0 : 0.0;
+        const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
         o[HW * q++] = float(sqrt(r > 0.0 ? r : 0.0));
       }
     }
@@ -276,6 +348,8 @@ static cudaError_t launch_warp(const StftArgs& a, cudaStream_t s) {
   using Lw = WarpLayout<T>;
   const size_t hw = size_t(a.W) * a.H;
   if (hw % Lw::BT) return cudaErrorInvalidValue;
+  // every frame of the launch is resident in the queue (no slot reduction beyond one wrap)
+  if (a.tq.slot0 >= a.tq.cap || uint64_t(a.nwin - 1) * a.S + uint64_t(T) > a.tq.cap) return cudaErrorInvalidValue;
   const size_t smem = warp_smem<T>(a.S);
   cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
