@@ -216,7 +216,10 @@ hv_status hv_profile_enable(hv_handle* h, int on);
 /* Stage times recorded so far; waits for the handle's stream. */
 hv_status hv_profile_read(hv_handle* h, hv_profile* out);
 
-/* Wait for all device work of the handle (its stream and its copy stream). */
+/* Wait for all device work of the handle (its stream and its copy stream).
+ * Returns HV_ERR_CUDA if a kernel of the handle gave up a bounded wait (for
+ * staged frames or for tensor-core work, about two seconds): the flag is sticky
+ * and the images of that launch are not valid. */
 hv_status hv_synchronize(hv_handle* h);
 
 /* Free every resource of the handle. NULL is accepted (no-op). */

@@ -52,6 +52,7 @@ struct hv_handle {
   int sp_pp = 0;              // 1: persistent multi-pass kernels
   hv_tuning tuning{};
   float2* tw = nullptr;  // all twiddle tables, length 8..1024 packed
+  unsigned* dev_err = nullptr;  // sticky device flags: a kernel's bounded wait gave up
   float2* asp_ht = nullptr;
   float2* chirp = nullptr;  // [W] x factors then [H] y factors
   size_t table_bytes = 0;
@@ -428,7 +429,7 @@ hv_status apply_pending(hv_handle* h) {
     a.tc_ntiles = ntiles;
     std::memcpy(a.tc_tile_i, ti, sizeof(ti));
     std::memcpy(a.tc_tile_j, tj, sizeof(tj));
-    a.err = a.counters + 3;
+    a.err = h->dev_err;
     a.nwin = 1;
     a.wstride = d.S;
     h->pca_batched = batched;
@@ -797,6 +798,7 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
     sa.mask = h->cur.moments_mask;
     sa.nout = h->nout;
     sa.out = dst;
+    sa.err = h->dev_err;
     e = launch_stft(sa, h->stream, &launches);
   }
   if (e == cudaSuccess && h->post_active) {
@@ -881,6 +883,9 @@ hv_status hv_open(const hv_open_desc* desc, hv_handle** out) {
   e = cudaMalloc(&h->tw, tw.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMemcpy(h->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("twiddles: ") + cudaGetErrorString(e));
+  e = cudaMalloc(&h->dev_err, 16);
+  if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, 16);
+  if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("error flags: ") + cudaGetErrorString(e));
   *out = h;
   return HV_OK;
 }
@@ -1047,6 +1052,10 @@ hv_status hv_synchronize(hv_handle* h) {
   HV_CU(h, cudaSetDevice(h->device));
   HV_CU(h, cudaStreamSynchronize(h->copy_stream));
   HV_CU(h, cudaStreamSynchronize(h->stream));
+  unsigned flags = 0;
+  HV_CU(h, cudaMemcpy(&flags, h->dev_err, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (flags != 0)
+    return fail(h, HV_ERR_CUDA, "a kernel's bounded wait gave up (device flags " + std::to_string(flags) + ")");
   return HV_OK;
 }
 
@@ -1070,6 +1079,7 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->s1);
   dfree(h->s2);
   dfree(h->tw);
+  dfree(h->dev_err);
   dfree(h->asp_ht);
   dfree(h->staging);
   if (h->pca_ws) cudaFree(h->pca_ws);

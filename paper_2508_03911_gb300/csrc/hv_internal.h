@@ -62,6 +62,8 @@ struct StftArgs {
   uint32_t mask;        // HV_MOM_* bits
   uint32_t nout;        // popcount(mask)
   float* out;           // [nwin][nout][H*W]
+  unsigned* err;        // device flags: bit 1 set when a wait for staged frames gave up
+  int tma;              // set by the launcher: staged frames through a TMA tensor map
 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 

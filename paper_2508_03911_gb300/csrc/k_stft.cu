@@ -10,6 +10,11 @@
 // launch: a window only brings in its S newest frames. The frame-to-time-axis
 // transpose is that load: pixel-contiguous rows of the time queue land in a
 // per-pixel ring in shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "fft_dev.cuh"
 #include "hv_internal.h"
 #include "../../include/hv.h"
@@ -23,14 +28,20 @@ namespace hv {
 // transforms them and writes their moments with only __syncwarp between steps,
 // so the warps of a CTA never wait on one another inside the window loop.
 //
-// Ring of a pixel (RS = T + min(S, T) slots of shared memory):
+// Ring of a pixel in shared memory:
 //  - overlapping windows (S < T): slots [0, T) hold the current window, frame o
-//    of the launch at slot o mod T, and slots [T, T + S) stage the S frames the
-//    next window adds (cp.async, in flight while the current window is
-//    transformed). At the start of a window the staged frames move into the
-//    slots of the S frames that left. The FFT reads slots 0 .. T-1 in order: a
-//    circular shift of the window, which leaves every |S_k|^2 unchanged, so the
-//    loads need no wrap-around.
+//    of the launch at slot o mod T; the S frames the next window adds are staged
+//    while the current window is transformed, and at the start of a window move
+//    into the slots of the S frames that left. The FFT reads slots 0 .. T-1 in
+//    order: a circular shift of the window, which leaves every |S_k|^2
+//    unchanged, so the loads need no wrap-around. Staging:
+//      TMA path: one cp.async.bulk.tensor load per window brings the CTA's S x BT
+//      block (64-byte rows, 64-byte swizzle) into a staging tile, completing on
+//      an mbarrier; the last warp to move a window's frames out issues the next
+//      load. Each warp then reads only its own pixels' 16-byte column of the
+//      tile, conflict-free thanks to the swizzle.
+//      Fallback (S not dividing the queue, T < 64, S > 256): every warp stages
+//      its own pixels with 8-byte cp.async into slots [T, T + S) of its rows.
 //  - S >= T: windows alternate between the halves [0, T) and [T, 2T).
 // The FFT is a Stockham pass sequence through a padded work row (index i at
 // i + i/16, two wavefronts per stage access of a pixel). When the band lies
@@ -90,7 +101,6 @@ struct WarpLayout {
   static constexpr int NW = PW >= 8 ? 1 : 8 / PW;                     // warps per CTA
   static constexpr int NT = 32 * NW;
   static constexpr int BT = NW * PW;                                  // pixels per CTA (>= 8)
-  static constexpr int WLD = T + T / 16;                              // work row stride
   static constexpr int RL = WarpPlan<T>::last();                      // last-stage radix
   static constexpr int ITL = T / RL / LP;                             // last-stage butterflies per lane
   static_assert(ITL * RL <= 32, "band bits of a lane");
@@ -225,49 +235,104 @@ __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const 
   }
 }
 
+// Shared memory of the kernel (bytes): [1 KB alignment slack, staging tile]
+// (TMA path), ring rows, work rows, twiddles.
 template <int T>
-__host__ __device__ constexpr size_t warp_smem(uint32_t S) {
+struct WarpSmem {
   using Lw = WarpLayout<T>;
-  return (size_t(Lw::BT) * (T + (S < uint32_t(T) ? S : T) + 1) + T + size_t(Lw::BT) * Lw::WLD) *
-         sizeof(float2);
+  static constexpr int WLD = T + (T - 1) / 16;      // work row stride (wpad of T - 1, plus one)
+  static constexpr int NTW = T - WarpPlan<T>::R1;   // twiddle entries of stages 2 ..
+  __host__ __device__ static constexpr int rld(uint32_t S, bool tma) {
+    return S >= uint32_t(T) ? 2 * T : (tma ? T : T + int(S));
+  }
+  __host__ __device__ static constexpr size_t staging(uint32_t S, bool tma) {
+    return tma ? 1024 + size_t(S) * Lw::BT * 8 : 0;
+  }
+  __host__ __device__ static constexpr size_t bytes(uint32_t S, bool tma) {
+    return staging(S, tma) + (size_t(Lw::BT) * rld(S, tma) + size_t(Lw::BT) * WLD + NTW) * sizeof(float2);
+  }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// 2-D tiled TMA load (x innermost) completing on an mbarrier
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// Bounded wait (about 2^32 clocks) for phase `parity` of an mbarrier to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
 }
 
 template <int T>
-__global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_warp(StftArgs a) {
+__global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
+    k_stft_warp(StftArgs a, const __grid_constant__ CUtensorMap qmap) {
   using Lw = WarpLayout<T>;
-  constexpr int NT = Lw::NT, LP = Lw::LP, PW = Lw::PW;
-  extern __shared__ float2 smem[];
+  using Sm = WarpSmem<T>;
+  constexpr int NT = Lw::NT, LP = Lw::LP, PW = Lw::PW, NW = Lw::NW, BT = Lw::BT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long s_full;  // the staged frames of the next window landed
+  __shared__ unsigned s_done;                         // warps that moved a window's staged frames out
   const uint32_t S = a.S;
   const bool overlap = S < uint32_t(T);
-  const int RLD = T + int(overlap ? S : T) + 1;
-  float2* ring = smem;
-  float2* tw = ring + Lw::BT * RLD;
-  float2* work = tw + T;
+  const bool tma = a.tma != 0;  // only with overlap and BT = 8 (64-byte tile rows)
+  const int RLD = Sm::rld(S, tma);
+  const uint32_t align_pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
+  unsigned char* staging = smem_raw + align_pad;  // 1024-byte aligned (swizzle atoms)
+  float2* ring = reinterpret_cast<float2*>(smem_raw + Sm::staging(S, tma));
+  float2* work = ring + BT * RLD;
+  float2* tw = work + BT * Sm::WLD;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pl = lane / LP, jl = lane % LP;  // pixel within the warp, lane within the pixel
   const int px = warp * PW + pl;             // pixel within the CTA
   const size_t HW = size_t(a.W) * a.H;
-  const uint32_t p0 = blockIdx.x * Lw::BT;
+  const uint32_t p0 = blockIdx.x * BT;
   const float2* tq = static_cast<const float2*>(a.tq.base);
   const uint32_t cap = a.tq.cap;
   const bool lower = a.khi < uint32_t(T / 2);
-  // the warp's pixels and its lanes' share of a fetch: pixel fb, frames ff + k 32/PW
+  const uint32_t mbar = smem_addr(&s_full);
+  // the warp's pixels and its lanes' share of their frames: pixel fb, frames ff + k 32/PW
   float2* wring = ring + warp * PW * RLD;
   const int fb = lane % PW, ff = lane / PW;
   const float2* src = tq + p0 + warp * PW + fb;
 
-  // cp.async of n frames starting at frame o0 of the launch into slots s0 + f of
-  // the warp's pixels (the launch's frames fit the queue: o0 + n <= cap)
-  auto fetch = [&](uint32_t o0, int n, int s0) {
-    uint32_t g = a.tq.slot0 + o0 + uint32_t(ff);
-    if (g >= cap) g -= cap;
-    if (g >= cap) g -= cap;
+  // queue slot of frame o of the launch (o < cap: the launch's frames fit the queue)
+  auto slot_of = [&](uint32_t o) {
+    const uint32_t g = a.tq.slot0 + o;
+    return g >= cap ? g - cap : g;
+  };
+  // cp.async of n frames starting at frame o0 into slots s0 + f of the warp's pixels
+  auto fetch_warp = [&](uint32_t o0, int n, int s0) {
+    uint32_t g = slot_of(o0 + uint32_t(ff));
     for (int f = ff; f < n; f += 32 / PW) {
       cp_async8(&wring[fb * RLD + s0 + f], &src[size_t(g) * HW]);
       g += 32 / PW;
       if (g >= cap) g -= cap;
     }
     cp_async_commit();
+  };
+  // one thread: the CTA's S x BT block from frame o0 into the staging tile
+  // (S consecutive queue slots; the host guarantees they do not wrap)
+  auto fetch_tile = [&](uint32_t o0) {
+    mbar_arrive_tx(mbar, S * uint32_t(BT * 8));
+    tma_load_2d(smem_addr(staging), &qmap, int(p0), int(slot_of(o0)), mbar);
   };
 
   // per-stage twiddle tables, laid out so that a warp's reads are contiguous:
@@ -297,29 +362,68 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_
         if (k - a.klo <= a.khi - a.klo) band |= 1u << (it * RL + m);
       }
   }
-  fetch(0, T, 0);
-  if (overlap && a.nwin > 1) fetch(T, int(S), T);  // window 1's new frames, staged
-  __syncthreads();                                 // twiddles
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_done = 0;
+  }
+  __syncthreads();  // twiddles, mbarrier
+  fetch_warp(0, T, 0);
+  if (overlap && a.nwin > 1) {  // window 1's new frames
+    if (!tma) fetch_warp(uint32_t(T), int(S), T);
+    else if (tid == 0) fetch_tile(uint32_t(T));
+  }
   for (uint32_t w = 0; w < a.nwin; ++w) {
-    cp_async_wait_all();
-    __syncwarp();
     const float2* win;
     if (overlap) {
-      if (w > 0) {
-        // staged frames of window w -> slots of the frames that left
-        const uint32_t d = (w - 1) * S;
-        for (int f = ff; f < int(S); f += 32 / PW)
-          wring[fb * RLD + int((d + uint32_t(f)) & uint32_t(T - 1))] = wring[fb * RLD + T + f];
+      const uint32_t d = (w - 1) * S;  // ring slot of the first frame that left (w > 0)
+      if (!tma) {
+        cp_async_wait_all();
         __syncwarp();
-        if (w + 1 < a.nwin) fetch((w + 1) * S + uint32_t(T) - S, int(S), T);
+        if (w > 0) {
+          for (int f = ff; f < int(S); f += 32 / PW)
+            wring[fb * RLD + int((d + uint32_t(f)) & uint32_t(T - 1))] = wring[fb * RLD + T + f];
+          __syncwarp();
+          if (w + 1 < a.nwin) fetch_warp((w + 1) * S + uint32_t(T) - S, int(S), T);
+        }
+      } else if (w == 0) {
+        cp_async_wait_all();
+        __syncwarp();
+      } else {
+        if (!mbar_wait(mbar, (w - 1) & 1)) {
+          if (lane == 0) atomicOr(a.err, 2u);
+          return;
+        }
+        // pixel q of tile row f: 16-byte chunk q / 2 of the 64-byte row is stored at
+        // chunk (q / 2) ^ ((f >> 1) & 3) (64-byte swizzle), q % 2 selects its half
+        for (uint32_t e = lane; e < S * PW; e += 32) {
+          const uint32_t b = e % PW, f = e / PW, q = uint32_t(warp * PW) + b;
+          const float2 v = *reinterpret_cast<const float2*>(staging + f * 64u + 16u * ((q >> 1) ^ ((f >> 1) & 3u)) +
+                                                            8u * (q & 1u));
+          wring[int(b) * RLD + int((d + f) & uint32_t(T - 1))] = v;
+        }
+        __syncwarp();
+        // the last warp to finish issues the next window's load into the tile
+        unsigned prev = 0;
+        if (lane == 0) {
+          __threadfence_block();
+          prev = atomicAdd(&s_done, 1u);
+          __threadfence_block();
+          if (prev % NW == NW - 1 && w + 1 < a.nwin) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            fetch_tile((w + 1) * S + uint32_t(T) - S);
+          }
+        }
       }
       win = ring + px * RLD;
     } else {
-      if (w + 1 < a.nwin) fetch((w + 1) * S, T, int((w + 1) & 1) * T);
+      cp_async_wait_all();
+      __syncwarp();
+      if (w + 1 < a.nwin) fetch_warp((w + 1) * S, T, int((w + 1) & 1) * T);
       win = ring + px * RLD + int(w & 1) * T;
     }
     MomAcc acc{band, 0.f, 0.f, 0.f};
-    warp_fft<T, 1, LP>(win, work + px * Lw::WLD, tw, jl, acc, lower);
+    warp_fft<T, 1, LP>(win, work + px * Sm::WLD, tw, jl, acc, lower);
 #pragma unroll
     for (int o = LP / 2; o > 0; o >>= 1) {  // reduce within the pixel's lane group
       acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
@@ -343,18 +447,54 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1)) k_stft_
   }
 }
 
+// cuTensorMapEncodeTiled from the driver (resolved once through the runtime)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of the time queue for the staged loads: 8-byte elements, {H W
+// pixels, cap slots}, box {8 pixels, S slots}, 64-byte swizzle. False when the
+// launch does not qualify: the staged S frames of a window must be S whole
+// consecutive slots (the queue capacity, T and the first slot multiples of S).
+static bool queue_map(const StftArgs& a, int BT, CUtensorMap* map) {
+  if (BT != 8 || a.S == 0 || a.S >= a.T || a.S > 256 || a.tq.cap % a.S || a.T % a.S || a.tq.slot0 % a.S) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(a.W) * a.H, a.tq.cap};
+  const cuuint64_t strides[1] = {cuuint64_t(a.W) * a.H * 8};
+  const cuuint32_t box[2] = {8, a.S};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tq.base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int T>
-static cudaError_t launch_warp(const StftArgs& a, cudaStream_t s) {
+static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
   using Lw = WarpLayout<T>;
-  const size_t hw = size_t(a.W) * a.H;
+  const size_t hw = size_t(a0.W) * a0.H;
   if (hw % Lw::BT) return cudaErrorInvalidValue;
   // every frame of the launch is resident in the queue (no slot reduction beyond one wrap)
-  if (a.tq.slot0 >= a.tq.cap || uint64_t(a.nwin - 1) * a.S + uint64_t(T) > a.tq.cap) return cudaErrorInvalidValue;
-  const size_t smem = warp_smem<T>(a.S);
+  if (a0.tq.slot0 >= a0.tq.cap || uint64_t(a0.nwin - 1) * a0.S + uint64_t(T) > a0.tq.cap)
+    return cudaErrorInvalidValue;
+  StftArgs a = a0;
+  CUtensorMap map{};
+  a.tma = queue_map(a, Lw::BT, &map) ? 1 : 0;
+  const size_t smem = WarpSmem<T>::bytes(a.S, a.tma != 0);
   cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
   if (e != cudaSuccess) return e;
-  k_stft_warp<T><<<unsigned(hw / Lw::BT), Lw::NT, smem, s>>>(a);
+  k_stft_warp<T><<<unsigned(hw / Lw::BT), Lw::NT, smem, s>>>(a, map);
   return cudaGetLastError();
 }
 
