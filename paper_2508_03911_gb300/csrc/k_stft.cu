@@ -240,10 +240,10 @@ __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const 
 template <int T>
 struct WarpSmem {
   using Lw = WarpLayout<T>;
-  static constexpr int WLD = T + (T - 1) / 16;      // work row stride (wpad of T - 1, plus one)
+  static constexpr int WLD = T + T / 16;           // work row stride (wpad, bank skew between pixels)
   static constexpr int NTW = T - WarpPlan<T>::R1;   // twiddle entries of stages 2 ..
   __host__ __device__ static constexpr int rld(uint32_t S, bool tma) {
-    return S >= uint32_t(T) ? 2 * T : (tma ? T : T + int(S));
+    return S >= uint32_t(T) ? 2 * T + 1 : (tma ? T : T + int(S) + 1);  // +1: bank skew between pixels
   }
   __host__ __device__ static constexpr size_t staging(uint32_t S, bool tma) {
     return tma ? 1024 + size_t(S) * Lw::BT * 8 : 0;
