@@ -89,20 +89,35 @@ __device__ __forceinline__ float2 tw32(float2 v, int k) {
   return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
 }
 
+// Packed FP32x2 arithmetic (sm_100 and later): a complex addition or
+// subtraction is one instruction on the (re, im) register pair.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, exact product by -1
+}
+
 // In-register R-point DFT, X_k = sum_m v_m exp(DIR 2 pi i m k / R), R in {2, 4, 8, 16, 32}.
+// Complex sums and differences use the packed additions; products by twiddles
+// (and by +-i, a swap of the pair) stay per component.
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) {
-    float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    const float2 a = v[0], b = v[1];
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
   } else if constexpr (R == 4) {
-    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    float2 t2 = cadd(v[1], v[3]), t3 = mul_i<DIR>(csub(v[1], v[3]));
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+    const float2 t0 = padd(v[0], v[2]), t1 = psub(v[0], v[2]);
+    const float2 t2 = padd(v[1], v[3]), d = psub(v[1], v[3]);
+    v[0] = padd(t0, t2);
+    v[2] = psub(t0, t2);
+    // X1 = t1 + (DIR i) d, X3 = t1 - (DIR i) d; (DIR i) d = (-DIR d.y, DIR d.x)
+    if constexpr (DIR < 0) {
+      v[1] = make_float2(t1.x + d.y, t1.y - d.x);
+      v[3] = make_float2(t1.x - d.y, t1.y + d.x);
+    } else {
+      v[1] = make_float2(t1.x - d.y, t1.y + d.x);
+      v[3] = make_float2(t1.x + d.y, t1.y - d.x);
+    }
   } else if constexpr (R == 16) {
     // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle w16^(n2 k1), DFT4 over n2
     float2 a[4][4];
@@ -145,8 +160,8 @@ __device__ __forceinline__ void dft(float2* v) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const float2 t = tw32<DIR>(o[k], k);
-      v[k] = cadd(e[k], t);
-      v[k + 16] = csub(e[k], t);
+      v[k] = padd(e[k], t);
+      v[k + 16] = psub(e[k], t);
     }
   } else {
     static_assert(R == 8, "radix");
@@ -156,17 +171,17 @@ __device__ __forceinline__ void dft(float2* v) {
     dft<4, DIR>(o);
     const float c = 0.70710678118654752440f;
     // o_k *= exp(DIR 2 pi i k / 8)
-    float2 o1 = make_float2(c * (o[1].x - DIR * o[1].y), c * (o[1].y + DIR * o[1].x));
-    float2 o2 = mul_i<DIR>(o[2]);
-    float2 o3 = make_float2(c * (-o[3].x - DIR * o[3].y), c * (-o[3].y + DIR * o[3].x));
-    v[0] = cadd(e[0], o[0]);
-    v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);
-    v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);
-    v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);
-    v[7] = csub(e[3], o3);
+    const float2 o1 = make_float2(c * (o[1].x - DIR * o[1].y), c * (o[1].y + DIR * o[1].x));
+    const float2 o2 = mul_i<DIR>(o[2]);
+    const float2 o3 = make_float2(c * (-o[3].x - DIR * o[3].y), c * (-o[3].y + DIR * o[3].x));
+    v[0] = padd(e[0], o[0]);
+    v[4] = psub(e[0], o[0]);
+    v[1] = padd(e[1], o1);
+    v[5] = psub(e[1], o1);
+    v[2] = padd(e[2], o2);
+    v[6] = psub(e[2], o2);
+    v[3] = padd(e[3], o3);
+    v[7] = psub(e[3], o3);
   }
 }
 

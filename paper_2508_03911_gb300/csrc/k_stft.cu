@@ -106,93 +106,6 @@ struct WarpLayout {
   static_assert(ITL * RL <= 32, "band bits of a lane");
 };
 
-// Forward DFTs with packed FP32x2 arithmetic (sm_100 and later): a complex
-// addition or subtraction is one instruction on the (re, im) register pair;
-// products by twiddles stay per component. X_k = sum_m v_m exp(-2 pi i m k / R).
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, exact product by -1
-}
-
-template <int R>
-__device__ __forceinline__ void dftp(float2* v) {
-  if constexpr (R == 2) {
-    const float2 a = v[0], b = v[1];
-    v[0] = padd(a, b);
-    v[1] = psub(a, b);
-  } else if constexpr (R == 4) {
-    const float2 t0 = padd(v[0], v[2]), t1 = psub(v[0], v[2]);
-    const float2 t2 = padd(v[1], v[3]), d = psub(v[1], v[3]);
-    v[0] = padd(t0, t2);
-    v[2] = psub(t0, t2);
-    v[1] = make_float2(t1.x + d.y, t1.y - d.x);  // t1 - i d
-    v[3] = make_float2(t1.x - d.y, t1.y + d.x);  // t1 + i d
-  } else if constexpr (R == 8) {
-    float2 e[4] = {v[0], v[2], v[4], v[6]};
-    float2 o[4] = {v[1], v[3], v[5], v[7]};
-    dftp<4>(e);
-    dftp<4>(o);
-    const float c = 0.70710678118654752440f;
-    const float2 o1 = make_float2(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x));
-    const float2 o2 = mul_i<-1>(o[2]);
-    const float2 o3 = make_float2(c * (o[3].y - o[3].x), -c * (o[3].x + o[3].y));
-    v[0] = padd(e[0], o[0]);
-    v[4] = psub(e[0], o[0]);
-    v[1] = padd(e[1], o1);
-    v[5] = psub(e[1], o1);
-    v[2] = padd(e[2], o2);
-    v[6] = psub(e[2], o2);
-    v[3] = padd(e[3], o3);
-    v[7] = psub(e[3], o3);
-  } else if constexpr (R == 16) {
-    // 16 = 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle w16^(n2 k1), DFT4 over n2
-    float2 a[4][4];
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-      a[n2][0] = v[n2];
-      a[n2][1] = v[4 + n2];
-      a[n2][2] = v[8 + n2];
-      a[n2][3] = v[12 + n2];
-      dftp<4>(a[n2]);
-    }
-    a[1][1] = tw16<1, -1>(a[1][1]);
-    a[1][2] = tw16<2, -1>(a[1][2]);
-    a[1][3] = tw16<3, -1>(a[1][3]);
-    a[2][1] = tw16<2, -1>(a[2][1]);
-    a[2][2] = tw16<4, -1>(a[2][2]);
-    a[2][3] = tw16<6, -1>(a[2][3]);
-    a[3][1] = tw16<3, -1>(a[3][1]);
-    a[3][2] = tw16<6, -1>(a[3][2]);
-    a[3][3] = tw16<9, -1>(a[3][3]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
-      dftp<4>(b);
-      v[k1] = b[0];
-      v[k1 + 4] = b[1];
-      v[k1 + 8] = b[2];
-      v[k1 + 12] = b[3];
-    }
-  } else {
-    static_assert(R == 32, "radix");
-    // 32 = 2 x 16: X_k = E_k + w32^k O_k, X_{k+16} = E_k - w32^k O_k
-    float2 e[16], o[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      e[i] = v[2 * i];
-      o[i] = v[2 * i + 1];
-    }
-    dftp<16>(e);
-    dftp<16>(o);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float2 t = tw32<-1>(o[k], k);
-      v[k] = padd(e[k], t);
-      v[k + 16] = psub(e[k], t);
-    }
-  }
-}
-
 // Lower half X_0 .. X_{R/2-1} of an R-point forward DFT.
 template <int R>
 __device__ __forceinline__ void dft_lower(float2* v) {
@@ -203,8 +116,8 @@ __device__ __forceinline__ void dft_lower(float2* v) {
       e[i] = v[2 * i];
       o[i] = v[2 * i + 1];
     }
-    dftp<16>(e);
-    dftp<16>(o);
+    dft<16, -1>(e);
+    dft<16, -1>(o);
     // X_k = E_k + w32^k O_k with the twiddle product fused into the sum
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -219,7 +132,7 @@ __device__ __forceinline__ void dft_lower(float2* v) {
       }
     }
   } else if constexpr (R == 16) {
-    dftp<16>(v);
+    dft<16, -1>(v);
   } else if constexpr (R == 2) {
     v[0] = cadd(v[0], v[1]);
   } else if constexpr (R == 4) {
@@ -230,8 +143,8 @@ __device__ __forceinline__ void dft_lower(float2* v) {
   } else {
     float2 e[4] = {v[0], v[2], v[4], v[6]};
     float2 o[4] = {v[1], v[3], v[5], v[7]};
-    dftp<4>(e);
-    dftp<4>(o);
+    dft<4, -1>(e);
+    dft<4, -1>(o);
     const float c = 0.70710678118654752440f;
     v[0] = cadd(e[0], o[0]);
     v[1] = cadd(e[1], make_float2(c * (o[1].x + o[1].y), c * (o[1].y - o[1].x)));
@@ -302,13 +215,13 @@ __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const 
     } else {
 #pragma unroll
       for (int it = 0; it < IT; ++it) {
-        dftp<R>(v[it]);
+        dft<R, -1>(v[it]);
         add_moments<R, NB, R>(v[it], it, kb0 + float(LP * it), acc);
       }
     }
   } else {
 #pragma unroll
-    for (int it = 0; it < IT; ++it) dftp<R>(v[it]);
+    for (int it = 0; it < IT; ++it) dft<R, -1>(v[it]);
     __syncwarp();
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
