@@ -42,7 +42,9 @@ namespace hv {
 //      tile, conflict-free thanks to the swizzle.
 //      Fallback (S not dividing the queue, T < 64, S > 256): every warp stages
 //      its own pixels with 8-byte cp.async into slots [T, T + S) of its rows.
-//  - S >= T: windows alternate between the halves [0, T) and [T, 2T).
+//  - S >= T: windows alternate between the halves [0, T) and [T, 2T), filled by
+//    CTA-wide cp.async (whole 64-byte frame segments per warp instruction) with
+//    one CTA barrier per window.
 // The FFT is a Stockham pass sequence through a padded work row (index i at
 // i + i/16, two wavefronts per stage access of a pixel). When the band lies
 // below T/2 the last stage only forms the lower half of its outputs.
@@ -243,7 +245,7 @@ struct WarpSmem {
   static constexpr int WLD = T + T / 16;           // work row stride (wpad, bank skew between pixels)
   static constexpr int NTW = T - WarpPlan<T>::R1;   // twiddle entries of stages 2 ..
   __host__ __device__ static constexpr int rld(uint32_t S, bool tma) {
-    return S >= uint32_t(T) ? 2 * T + 1 : (tma ? T : T + int(S) + 1);  // +1: bank skew between pixels
+    return S >= uint32_t(T) ? 2 * T + 4 : (tma ? T : T + int(S) + 1);  // bank skew between pixels
   }
   __host__ __device__ static constexpr size_t staging(uint32_t S, bool tma) {
     return tma ? 1024 + size_t(S) * Lw::BT * 8 : 0;
@@ -328,6 +330,21 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
     }
     cp_async_commit();
   };
+  // CTA-wide cp.async of n frames from frame o0 into slots s0 + f of all BT
+  // pixels: a warp instruction covers 32 / BT whole frames of the CTA (full
+  // sectors); the row stride 2T + 4 keeps those stores at two wavefronts
+  auto fetch_cta = [&](uint32_t o0, int n, int s0) {
+    constexpr int FS = NT / BT;  // frames per pass of the CTA
+    const int b = tid % BT;
+    int f = tid / BT;
+    uint32_t g = slot_of(o0 + uint32_t(f));
+    for (; f < n; f += FS) {
+      cp_async8(&ring[b * RLD + s0 + f], &tq[size_t(g) * HW + p0 + b]);
+      g += FS;
+      if (g >= cap) g -= cap;
+    }
+    cp_async_commit();
+  };
   // one thread: the CTA's S x BT block from frame o0 into the staging tile
   // (S consecutive queue slots; the host guarantees they do not wrap)
   auto fetch_tile = [&](uint32_t o0) {
@@ -368,7 +385,8 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
     s_done = 0;
   }
   __syncthreads();  // twiddles, mbarrier
-  fetch_warp(0, T, 0);
+  if (overlap) fetch_warp(0, T, 0);
+  else fetch_cta(0, T, 0);
   if (overlap && a.nwin > 1) {  // window 1's new frames
     if (!tma) fetch_warp(uint32_t(T), int(S), T);
     else if (tid == 0) fetch_tile(uint32_t(T));
@@ -417,9 +435,10 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
       }
       win = ring + px * RLD;
     } else {
+      // every warp is done with window w - 1, whose half the next fetch refills
       cp_async_wait_all();
-      __syncwarp();
-      if (w + 1 < a.nwin) fetch_warp((w + 1) * S, T, int((w + 1) & 1) * T);
+      __syncthreads();
+      if (w + 1 < a.nwin) fetch_cta((w + 1) * S, T, int((w + 1) & 1) * T);
       win = ring + px * RLD + int(w & 1) * T;
     }
     MomAcc acc{band, 0.f, 0.f, 0.f};
