@@ -243,6 +243,24 @@ def test_long_window_kernel_paths(T, S, band):
     check_images(img, O.render(fr, p))
 
 
+@pytest.mark.parametrize("T,S,tq", [(512, 256, 0), (1024, 256, 0), (64, 16, 0), (128, 32, 256),
+                                    (512, 64, 1000), (256, 48, 0)])
+def test_staged_frame_paths(T, S, tq):
+    """Overlapping windows stage the S new frames of the next window: one TMA tile
+    load per CTA when S divides T, the queue capacity and the first slot (1, 2 or 4
+    pixels per warp; a small queue that wraps between launches), else per-warp
+    cp.async (queue capacity 1000 or S = 48 not dividing T)."""
+    H, W = 16, 32
+    n = T + 6 * S + 3
+    fr = synth.random_frames(n, H, W, 12, seed=T + 3 * S + tq)
+    p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=2,
+                      band_hi_bin=T // 2 - 3, moments=ALL_MOMENTS, H=H, W=W)
+    img, st = gpu_render(fr, p, tq=tq, packets=[T + S, 2 * S + 1, n - T - 3 * S - 1])
+    ref = O.render(fr, p)
+    check_images(img, ref)
+    assert st["windows_rendered"] == ref.shape[0]
+
+
 def test_streaming_packets_match_one_shot():
     """Ragged packets and renders interleaved give the windows of the whole stream."""
     H = W = 64
