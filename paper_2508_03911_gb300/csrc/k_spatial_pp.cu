@@ -15,8 +15,9 @@
 //   P2a row FFT (length W) of 16 rows ky of S1, x H^T (1/(WH) and the optional
 //       high-pass folded in), row IFFT -> S2[x][ky]
 //   P3a column IFFT (length H) of 16 columns x of S2 -> time queue [y][x]
-//   P2f row FFT of 16 rows ky of S1 -> time queue [ky][kx] (through shared memory:
-//       the natural layout needs lanes along kx)
+//   P2f row FFT of 16 rows ky of S1 -> time queue [ky][kx]; its last stage maps
+//       threads along kx (twiddles from a per-stage table), so the store of
+//       each row is coalesced straight from registers
 //   P3t as P3a, but instead of storing the field it adds sum |u| and sum |u|^2 of
 //       the strip to the frame's two float64 accumulators (focus sweep)
 // Twiddles of the pass length are copied to shared memory once per CTA.
@@ -85,6 +86,7 @@ struct RawSrc {
 // Bin k of line b straight to global memory at out[k * stride + b].
 struct GlobalOut {
   static constexpr bool kSyncFirst = false;
+  static constexpr bool kJFast = false;
   float2* out;
   uint32_t stride;
   __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(k) * stride + b] = v; }
@@ -93,6 +95,7 @@ struct GlobalOut {
 // Sum of |v| and |v|^2 over the bins this thread holds (Tamura accumulation).
 struct AmpSums {
   static constexpr bool kSyncFirst = false;
+  static constexpr bool kJFast = false;
   float* s;  // s[0] += |v|, s[1] += |v|^2
   __device__ __forceinline__ void operator()(int, int, float2 v) const {
     const float q = fmaf(v.x, v.x, v.y * v.y);
@@ -105,6 +108,7 @@ struct AmpSums {
 template <int LD>
 struct MulHtSmem {
   static constexpr bool kSyncFirst = true;
+  static constexpr bool kJFast = false;
   float2* buf;
   const float2* ht;  // ht[k * H + line] of this strip's first line
   uint32_t H;
@@ -113,19 +117,42 @@ struct MulHtSmem {
   }
 };
 
-template <int LD>
-struct ToSmem {
-  static constexpr bool kSyncFirst = true;
-  float2* buf;
-  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { buf[k * LD + b] = v; }
+// Bin k of line b straight to global memory at out[b * stride + k], with the
+// last stage's threads laid out along the bins (consecutive lanes hold
+// consecutive bins of one line, so the stores are coalesced).
+struct RowOut {
+  static constexpr bool kSyncFirst = false;
+  static constexpr bool kJFast = true;
+  float2* out;
+  uint32_t stride;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(b) * stride + k] = v; }
+};
+
+// Span NS and radix R of the last stage of the pass (the BlockRadix chain).
+template <int L, int BT, int NT>
+struct LastStage {
+  static constexpr int radix(int rem) {
+    return (rem % 16 == 0 && (BT * (L / 16)) % NT == 0 && BT * (L / 16) >= NT) ? 16
+           : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
+  }
+  static constexpr int ns() {
+    int ns = 1;
+    while (ns * radix(L / ns) < L) ns *= radix(L / ns);
+    return ns;
+  }
+  static constexpr int NS = ns();
+  static constexpr int R = L / NS;
 };
 
 // One Stockham stage of span NS over the PP_BT lines (thread layout and index
 // rules of fft_dev.cuh), and recursively the rest. The first stage reads
 // through `src`, later ones the buffer; twiddles come from the shared table
 // tws[e] = exp(-2 pi i e / L). The last stage hands bin k of line b to epi.
+// With an epilogue of kJFast, the last stage maps threads bin-fastest (b = idx / NB,
+// j = idx % NB) and takes its twiddles from twl[(m - 1) NS + j] (contiguous in j).
 template <int L, int NS, int DIR, class Src, class Epi>
-__device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const float2* tws, const Epi& epi) {
+__device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const float2* tws, const Epi& epi,
+                                          const float2* twl = nullptr) {
   using C = PpCfg<L>;
   constexpr int NT = C::NT, BT = C::BT, LD = C::LD;
   constexpr int REM = L / NS;
@@ -134,18 +161,19 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
   static_assert((BT * NB) % NT == 0, "thread count must divide the butterflies");
   constexpr int ITEMS = BT * NB / NT;
   constexpr bool LAST = NS * R == L;
+  constexpr bool JF = LAST && Epi::kJFast;
   float2 v[ITEMS][R];
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     const int idx = threadIdx.x + it * NT;
-    const int b = idx % BT, j = idx / BT;
+    const int b = JF ? idx / NB : idx % BT, j = JF ? idx % NB : idx / BT;
 #pragma unroll
     for (int m = 0; m < R; ++m) v[it][m] = src(j + m * NB, b);
     if constexpr (NS > 1) {
       const int jm = j % NS;
 #pragma unroll
       for (int m = 1; m < R; ++m) {
-        float2 w = tws[jm * m * (L / (NS * R))];
+        float2 w = JF ? twl[(m - 1) * NS + jm] : tws[jm * m * (L / (NS * R))];
         if constexpr (DIR > 0) w.y = -w.y;
         v[it][m] = cmul(v[it][m], w);
       }
@@ -157,7 +185,7 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       const int idx = threadIdx.x + it * NT;
-      const int b = idx % BT, j = idx / BT;
+      const int b = JF ? idx / NB : idx % BT, j = JF ? idx % NB : idx / BT;
 #pragma unroll
       for (int m = 0; m < R; ++m) epi(b, j + m * NB, v[it][m]);
     }
@@ -173,7 +201,7 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
     }
     __syncthreads();
     SmemSrc<LD> s{buf};
-    pp_stages<L, NS * R, DIR>(s, buf, tws, epi);
+    pp_stages<L, NS * R, DIR>(s, buf, tws, epi, twl);
   }
 }
 
@@ -221,7 +249,8 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tws = reinterpret_cast<float2*>(smem);
   float2* cys = reinterpret_cast<float2*>(smem + C::TW);  // P1 Fresnel: chirp along y
-  unsigned char* body = smem + (PK == PK_P1 ? 2 * C::TW : C::TW);
+  float2* twl = cys;                                      // P2f: last-stage twiddles by (m, j)
+  unsigned char* body = smem + ((PK == PK_P1 || PK == PK_P2F) ? 2 * C::TW : C::TW);
   float2* buf0 = reinterpret_cast<float2*>(body);
   // P1: one FFT buffer and two raw staging buffers; other passes: two FFT buffers
   float2* buf1 = reinterpret_cast<float2*>(body + C::BUF);
@@ -236,6 +265,13 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
   for (int e = tid; e < L; e += C::NT) {
     tws[e] = __ldg(&twg[e]);
     if (PK == PK_P1 && fresnel) cys[e] = __ldg(&a.chirp_y[e]);
+  }
+  if constexpr (PK == PK_P2F) {
+    using LS = LastStage<L, C::BT, C::NT>;
+    for (int e = tid; e < (LS::R - 1) * LS::NS; e += C::NT) {
+      const int m = e / LS::NS + 1, jm = e % LS::NS;
+      twl[e] = __ldg(&twg[jm * m * (L / (LS::NS * LS::R))]);
+    }
   }
   // lines per frame of the other axis: W columns (P1, P3a) or H rows (P2a, P2f)
   const uint32_t LO = (PK == PK_P1 || PK == PK_P3A || PK == PK_P3T) ? a.W : a.H;
@@ -309,14 +345,11 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
       }
     } else {
       float2* buf = cur == 0 ? buf0 : buf1;
-      pp_stages<L, 1, -1>(SmemSrc<C::LD>{buf}, buf, tws, ToSmem<C::LD>{buf});
-      __syncthreads();
-      // time queue [ky][kx]: bin kx of row s0 + b; lanes along kx for the store
+      // time queue [ky][kx]: bin kx of row s0 + b, stored from the registers of the
+      // last stage (threads along kx there)
       const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
       float2* out = static_cast<float2*>(a.tq.base) + tslot * size_t(a.H) * a.W + size_t(s0) * a.W;
-      for (int kx = tid; kx < L; kx += C::NT)
-#pragma unroll
-        for (int b = 0; b < C::BT; ++b) out[size_t(b) * a.W + kx] = buf[kx * C::LD + b];
+      pp_stages<L, 1, -1>(SmemSrc<C::LD>{buf}, buf, tws, RowOut{out, a.W}, twl);
     }
   }
   cpa_wait_all();
@@ -325,7 +358,8 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
 template <int L, int PK>
 static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t s) {
   using C = PpCfg<L>;
-  const size_t smem = (PK == PK_P1 ? 2 * C::TW + C::BUF + 2 * C::RAW : C::TW + 2 * C::BUF);
+  const size_t smem = PK == PK_P1 ? 2 * C::TW + C::BUF + 2 * C::RAW
+                                   : (PK == PK_P2F ? 2 * C::TW : C::TW) + 2 * C::BUF;
   auto kern = k_pass_pp<L, PK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
