@@ -35,6 +35,7 @@ struct SpatialArgs {
   int use_pp;           // 1: persistent prefetching multi-pass kernels when the size allows
   double* tam_acc;      // focus sweep: frame i adds (sum |u|, sum |u|^2) at tam_acc + i * tam_stride
   uint32_t tam_stride;
+  int discard_inputs;   // persistent passes: scratch1/scratch2 are read once, drop their L2 lines after staging
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);

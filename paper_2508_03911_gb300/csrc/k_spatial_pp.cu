@@ -20,7 +20,11 @@
 //       each row is coalesced straight from registers
 //   P3t as P3a, but instead of storing the field it adds sum |u| and sum |u|^2 of
 //       the strip to the frame's two float64 accumulators (focus sweep)
-// Twiddles of the pass length are copied to shared memory once per CTA.
+// Twiddles of the pass length are copied to shared memory once per CTA. In the
+// full transform the intermediates S1 and S2 are read exactly once: once a strip
+// is staged, its L2 lines are discarded (no write-back of dead data when a
+// chunk's intermediates fit in L2). Single passes (the focus sweep re-reads S1
+// for every distance) keep them.
 #include "fft_dev.cuh"
 #include "hv_internal.h"
 #include "../../include/hv.h"
@@ -295,6 +299,13 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
     __syncthreads();  // this item's input resident; the other buffer is free
     const int nxt = item + gridDim.x;
     if (nxt < nitems) issue(nxt, cur ^ 1);
+    if (PK != PK_P1 && a.discard_inputs) {
+      // the strip's intermediate is dead once staged: drop its L2 lines unwritten
+      const float2* base = (PK == PK_P3A || PK == PK_P3T) ? a.scratch2 : a.scratch1;
+      const char* st = reinterpret_cast<const char*>(base + size_t(i) * L * LO + size_t(s0) * L);
+      for (int e = tid; e < C::BT * L * 8 / 128; e += C::NT)
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(st + size_t(e) * 128) : "memory");
+    }
     if constexpr (PK == PK_P1) {
       // S1[ky][x]: bin ky of column s0 + b at s1[ky * W + s0 + b]
       const GlobalOut out{a.scratch1 + size_t(i) * a.H * a.W + s0, a.W};
@@ -442,8 +453,10 @@ bool spatial_pp_supported(const SpatialArgs& a) {
   return ok(a.W) && ok(a.H) && (a.spatial == HV_SPATIAL_ASP || a.spatial == HV_SPATIAL_FRESNEL);
 }
 
-cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launches) {
-  if (a.n == 0) return cudaSuccess;
+cudaError_t launch_spatial_pp(const SpatialArgs& a0, cudaStream_t s, int* launches) {
+  if (a0.n == 0) return cudaSuccess;
+  SpatialArgs a = a0;
+  a.discard_inputs = 1;  // the full transform reads each intermediate exactly once
   switch (a.H) {
     case 64: return pp_w<64>(a, s, launches);
     case 128: return pp_w<128>(a, s, launches);
