@@ -1227,7 +1227,9 @@ hv_status hv_focus_sweep(hv_handle* h, const void* frames, uint32_t n, const dou
 hv_status hv_af_features(hv_handle* h, const void* frames, uint32_t n, void* out_bf16) {
   if (!h) return HV_ERR_ARG;
   if (!out_bf16) return fail(h, HV_ERR_ARG, "output is NULL");
-  const uint32_t chunk = 64;
+  // frames per pass: the feature kernel runs one CTA per frame, so a chunk
+  // should cover every SM several times (512 frames: 512 MB of spectra at 256^2)
+  const uint32_t chunk = std::max<uint32_t>(64, std::min<uint32_t>(512, uint32_t((size_t(256) << 20) / (size_t(h->W) * h->H * sizeof(float2)))));
   hv_status s = af_prepare(h, frames, n, std::min(n, chunk));
   if (s != HV_OK) return s;
   const size_t cells = size_t(h->W / 2) * (h->H / 2);
