@@ -86,6 +86,11 @@ hv_status hv_af_loss_grad(hv_af* af, const void* x_bf16, const float* z_target, 
 hv_status hv_af_train_step(hv_af* af, const void* x_bf16, const float* z_target, uint32_t n,
                            const hv_af_adam* adam, float* loss);
 
+/* Waits for the network's work on its stream. Returns HV_ERR_CUDA if a
+ * tensor-core convolution gave up a bounded wait (about two seconds; the flag is
+ * sticky and the outputs of that call are not valid). */
+hv_status hv_af_synchronize(hv_af* af);
+
 /* Text of the network's last error. */
 const char* hv_af_last_error(const hv_af* af);
 

@@ -38,6 +38,7 @@ def _lib():
                                 C.c_int),
             "hv_af_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, P(hv_af_adam), C.c_void_p],
                                  C.c_int),
+            "hv_af_synchronize": ([C.c_void_p], C.c_int),
             "hv_af_last_error": ([C.c_void_p], C.c_char_p),
             "hv_af_close": ([C.c_void_p], C.c_int),
         }
@@ -98,6 +99,10 @@ class Autofocus:
         lp = _dev(loss, "loss")[0] if loss is not None else None
         opt = hv_af_adam(lr, beta1, beta2, eps)
         self._check(_lib().hv_af_train_step(self.h, xp, tp, x.shape[0], C.byref(opt), lp))
+
+    def synchronize(self):
+        """Wait for the network's work; raises if a device wait gave up."""
+        self._check(_lib().hv_af_synchronize(self.h))
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -94,6 +94,7 @@ hv_status hv_af_open(const hv_af_desc* d, hv_af** out) {
       {reinterpret_cast<void**>(&t.head), B * 130 * 4},
       {reinterpret_cast<void**>(&t.part), dw_part_floats(t.dw_chunks) * 4},
       {reinterpret_cast<void**>(&t.partb), size_t(t.dw_chunks) * 64 * 4},
+      {reinterpret_cast<void**>(&t.err), 16},
   };
   size_t total = 0;
   for (auto& p : pieces) total += (p.bytes + 255) / 256 * 256;
@@ -162,6 +163,17 @@ hv_status hv_af_train_step(hv_af* a, const void* x, const float* z_target, uint3
   const double c1 = 1.0 / (1.0 - std::pow(double(adam->beta1), double(a->step)));
   const double c2 = 1.0 / (1.0 - std::pow(double(adam->beta2), double(a->step)));
   AF_CU(a, net_adam(a->t, adam->lr, adam->beta1, adam->beta2, adam->eps, float(c1), float(c2), a->stream));
+  return HV_OK;
+}
+
+hv_status hv_af_synchronize(hv_af* a) {
+  if (!a) return HV_ERR_ARG;
+  AF_CU(a, cudaSetDevice(a->device));
+  AF_CU(a, cudaStreamSynchronize(a->stream));
+  unsigned flags = 0;
+  AF_CU(a, cudaMemcpy(&flags, a->t.err, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (flags != 0)
+    return af_fail(a, HV_ERR_CUDA, "a tensor-core convolution gave up a bounded wait (flags " + std::to_string(flags) + ")");
   return HV_OK;
 }
 

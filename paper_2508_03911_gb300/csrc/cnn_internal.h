@@ -31,7 +31,14 @@ struct Net {
   float* part;              // weight-gradient partials, dw_part_floats(dw_chunks)
   float* partb;             // [dw_chunks][64] bias-gradient partials
   uint32_t dw_chunks;       // pixel chunks of the weight-gradient reduction
+  unsigned* err;            // device flags: bit 2 set when a tensor-core convolution gave up a bounded wait
 };
+
+// y = relu(conv3x3_stride2(x, w) + b) for [n][CI][HI][HI] bfloat16 inputs on the
+// tensor cores (k_conv_tc.cu); instantiated for the network's layers 2-4.
+template <int CI, int CO, int HI>
+cudaError_t conv_tc(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, __nv_bfloat16* y,
+                    uint32_t n, unsigned* err, cudaStream_t s);
 
 // Forward pass of n inputs x (bfloat16 [n][1][128][128]). zout (optional):
 // predicted distances in metres. ztarget (optional, metres): also computes the

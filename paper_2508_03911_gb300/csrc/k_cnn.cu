@@ -7,7 +7,8 @@
 //   normalised distance (z - 0.35) / 0.25; the loss is the batch mean of the
 //   squared error.
 // Arithmetic: activations and convolution weights in bfloat16, every product
-// accumulated in float32; the dense layers, gradients and the Adam state in
+// accumulated in float32 (the forward of layers 2-4 on the tensor cores, in
+// k_conv_tc.cu; layer 1 and the backward pass here on the CUDA cores); the dense layers, gradients and the Adam state in
 // float32. Layouts: activations [n][c][h][w]; the flat float32 parameter vector
 // holds w1 [16][1][3][3], b1, w2 [32][16][3][3], b2, w3, b3, w4, b4, f1w [32][64],
 // f1b, f2w [1][32], f2b; a bfloat16 mirror of it feeds the convolutions.
@@ -411,9 +412,10 @@ cudaError_t conv_bwd(const Net& t, const float* dz, const __nv_bfloat16* x, int 
 cudaError_t net_forward(const Net& t, const void* x, uint32_t n, const float* ztarget, float* zout, cudaStream_t s) {
   const auto* xi = static_cast<const __nv_bfloat16*>(x);
   cudaError_t e = conv_fwd<1, 16, 128>(t, xi, OFF_W1, OFF_B1, t.a1, n, s);
-  if (e == cudaSuccess) e = conv_fwd<16, 32, 64>(t, t.a1, OFF_W2, OFF_B2, t.a2, n, s);
-  if (e == cudaSuccess) e = conv_fwd<32, 64, 32>(t, t.a2, OFF_W3, OFF_B3, t.a3, n, s);
-  if (e == cudaSuccess) e = conv_fwd<64, 64, 16>(t, t.a3, OFF_W4, OFF_B4, t.a4, n, s);
+  // layers 2-4 (K = 144, 288, 576): implicit GEMMs on the tensor cores
+  if (e == cudaSuccess) e = conv_tc<16, 32, 64>(t.a1, t.prm_bf + OFF_W2, t.prm + OFF_B2, t.a2, n, t.err, s);
+  if (e == cudaSuccess) e = conv_tc<32, 64, 32>(t.a2, t.prm_bf + OFF_W3, t.prm + OFF_B3, t.a3, n, t.err, s);
+  if (e == cudaSuccess) e = conv_tc<64, 64, 16>(t.a3, t.prm_bf + OFF_W4, t.prm + OFF_B4, t.a4, n, t.err, s);
   if (e != cudaSuccess) return e;
   k_head<<<n, 64, 0, s>>>(t.a4, t.prm, ztarget, n, zout, t.head, t.dbuf0);
   return cudaGetLastError();
