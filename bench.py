@@ -827,6 +827,12 @@ def main_autofocus(args):
     e2e_s = max_over_ranks((time.perf_counter() - tt) / args.steps, dist, dev)
     value = job_value(world, args.steps, B, ms / 1e3)
     tflops = AF_FLOPS * B / (net_ms / 1e3) / 1e12
+    peaks = load_peaks()
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    bf16_peak = (peaks or {}).get("bf16_tflops", 1906.8)
+    # features: raw hologram read, its spectrum written and read once, the bf16 input written
+    feat_bytes = 256 * 256 * (2 + 8 + 8) + 128 * 128 * 2
+    feat_gbs = feat_bytes * B / (feat_ms / 1e3) / 1e9
     line = {
         "metric": "holograms/s focused", "value": round(value, 1), "unit": "holograms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
@@ -836,11 +842,17 @@ def main_autofocus(args):
                    "pixel_bits": 12, "holograms_per_step": B, "network_input": [128, 128],
                    "l2": "inputs below L2 size (64 MB of frames): the same batch each step",
                    "parallelism": "replicas x1"},
-        "roofline": {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
-                     "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                     "kernel": "CNN forward (4 bf16 convolutions with float32 accumulation + head)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                     "flops_per_hologram": AF_FLOPS},
+        "roofline": {"bound": "hbm", "achieved": round(feat_gbs, 1), "peak": round(hbm, 1), "unit": "GB/s",
+                     "frac": round(feat_gbs / hbm, 4), "traffic": None,
+                     "kernel": "network input (column and row FFT passes, binned log-magnitude spectrum)",
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_hologram": feat_bytes},
+        "network_roofline": {"bound": "tensor", "achieved": round(tflops, 3), "peak": round(bf16_peak, 1),
+                             "unit": "TFLOP/s", "frac": round(tflops / bf16_peak, 4),
+                             "kernel": "CNN forward: layer 1 on CUDA cores, layers 2-4 as tcgen05 implicit GEMMs "
+                                       "(bf16, float32 accumulation) + head",
+                             "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                             "flops_per_hologram": AF_FLOPS},
         "stage_ms_per_step": {"features": round(feat_ms, 4), "network": round(net_ms, 4)},
         "sweep": {"holograms_per_s": round(B / (sweep_ms / 1e3), 1), "ms_per_step": round(sweep_ms, 4),
                   "distances": AF.NZ, "speedup_of_network": round(sweep_ms / (ms / args.steps), 2)},
