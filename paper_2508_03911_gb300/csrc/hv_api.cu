@@ -1233,15 +1233,30 @@ hv_status hv_af_features(hv_handle* h, const void* frames, uint32_t n, void* out
   hv_status s = af_prepare(h, frames, n, std::min(n, chunk));
   if (s != HV_OK) return s;
   const size_t cells = size_t(h->W / 2) * (h->H / 2);
+  // widths up to 256: the row pass forms the cells in its epilogue (no spectrum in
+  // memory); wider frames store the spectra and bin them in a second kernel
+  const bool fused = h->W <= 256;
   for (uint32_t a = 0; a < n; a += chunk) {
     SpatialArgs sa = af_args(h, frames, n);
     sa.raw.slot0 = a;
     sa.n = std::min(chunk, n - a);
-    sa.tq = RingRef{h->s2, sa.n, 0};  // spectra [ky][kx] of this chunk
+    sa.discard_inputs = 1;  // the column pass output is read once
     cudaError_t e = launch_pp_pass(sa, PASS_COL_FFT, h->stream);
-    if (e == cudaSuccess) e = launch_pp_pass(sa, PASS_ROW_FFT, h->stream);
-    if (e == cudaSuccess)
-      e = launch_af_features(h->s2, sa.n, h->W, h->H, static_cast<uint16_t*>(out_bf16) + a * cells, h->stream);
+    uint16_t* dst = static_cast<uint16_t*>(out_bf16) + a * cells;
+    if (fused) {
+      // s2 holds this chunk's cells [n][H/2][W/2] (floats), then its (sum, sum of squares)
+      sa.cells = reinterpret_cast<float*>(h->s2);
+      sa.tam_acc = reinterpret_cast<double*>(h->s2 + (size_t(sa.n) * cells + 1) / 2);
+      sa.tam_stride = 2;
+      if (e == cudaSuccess) e = cudaMemsetAsync(sa.tam_acc, 0, size_t(sa.n) * 2 * sizeof(double), h->stream);
+      if (e == cudaSuccess) e = launch_pp_pass(sa, PASS_ROW_CELLS, h->stream);
+      if (e == cudaSuccess)
+        e = launch_af_standardize(sa.cells, sa.tam_acc, 2, sa.n, uint32_t(cells), dst, h->stream);
+    } else {
+      sa.tq = RingRef{h->s2, sa.n, 0};  // spectra [ky][kx] of this chunk
+      if (e == cudaSuccess) e = launch_pp_pass(sa, PASS_ROW_FFT, h->stream);
+      if (e == cudaSuccess) e = launch_af_features(h->s2, sa.n, h->W, h->H, dst, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "feature passes");
     h->st.kernel_launches += 3;
   }

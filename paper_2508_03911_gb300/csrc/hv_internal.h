@@ -36,6 +36,7 @@ struct SpatialArgs {
   double* tam_acc;      // focus sweep: frame i adds (sum |u|, sum |u|^2) at tam_acc + i * tam_stride
   uint32_t tam_stride;
   int discard_inputs;   // persistent passes: scratch1/scratch2 are read once, drop their L2 lines after staging
+  float* cells;         // PASS_ROW_CELLS output [n][H/2][W/2]
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);
@@ -49,7 +50,12 @@ cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* la
 //   PASS_COL_IFFT  scratch2 -> column IFFT -> tq ring [y][x]
 //   PASS_ROW_FFT   scratch1 -> row FFT -> tq ring [ky][kx]
 //   PASS_COL_IFFT_TAMURA  scratch2 -> column IFFT -> (sum |u|, sum |u|^2) per frame
-enum { PASS_COL_FFT = 0, PASS_ROW_ASP = 1, PASS_COL_IFFT = 2, PASS_ROW_FFT = 3, PASS_COL_IFFT_TAMURA = 4 };
+//   PASS_ROW_CELLS scratch1 -> row FFT -> network-input cells (sides 64..256): the
+//                  centred spectrum's 2 x 2 blocks as log1p(mean |F|) (DC bin as 0)
+//                  into cells [frame][H/2][W/2], and (sum v, sum v^2) per frame
+//                  into tam_acc + frame * tam_stride
+enum { PASS_COL_FFT = 0, PASS_ROW_ASP = 1, PASS_COL_IFFT = 2, PASS_ROW_FFT = 3, PASS_COL_IFFT_TAMURA = 4,
+       PASS_ROW_CELLS = 5 };
 cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s);
 
 // STFT band moments of nwin windows (Sec. III-B.1), time-queue ring -> images.
@@ -113,6 +119,10 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
 cudaError_t launch_tamura_finish(const double* acc, uint32_t count, uint32_t pixels, float* metric, cudaStream_t s);
 cudaError_t launch_af_features(const float2* spec, uint32_t n, uint32_t W, uint32_t H, void* out_bf16,
                                cudaStream_t s);
+// The network input from the cells and per-frame sums of PASS_ROW_CELLS:
+// (v - mean) / deviation per frame, rounded to bfloat16.
+cudaError_t launch_af_standardize(const float* cells, const double* sums, uint32_t sum_stride, uint32_t n,
+                                  uint32_t ncell, void* out_bf16, cudaStream_t s);
 
 // Post-processing of rendered images [window][nout][H][W] (Sec. III-B): periodic
 // K x K convolution into ring slot (count + window) mod R, per-image float64 sums

@@ -89,7 +89,34 @@ __global__ void __launch_bounds__(FT_NT) k_af_features(const float2* spec, uint3
     o[e] = __float2bfloat16_rn((cell_value(F, W, H, e / cw, e % cw) - mean) * inv);
 }
 
+// The network input from precomputed cells, one CTA per frame: the frame's mean
+// and deviation from its float64 sums (once), then (v - mean) / deviation rounded
+// to bfloat16 (as k_af_features).
+__global__ void __launch_bounds__(FT_NT) k_af_standardize(const float* cells, const double* sums, uint32_t stride,
+                                                         uint32_t ncell, __nv_bfloat16* out) {
+  const uint32_t f = blockIdx.x;
+  __shared__ float stat[2];
+  if (threadIdx.x == 0) {
+    const double mean = sums[size_t(f) * stride] / ncell;
+    const double var = sums[size_t(f) * stride + 1] / ncell - mean * mean;
+    stat[0] = float(mean);
+    stat[1] = var > 0.0 ? float(1.0 / sqrt(var)) : 0.f;
+  }
+  __syncthreads();
+  const float m = stat[0], inv = stat[1];
+  const float* c = cells + size_t(f) * ncell;
+  __nv_bfloat16* o = out + size_t(f) * ncell;
+  for (uint32_t e = threadIdx.x; e < ncell; e += FT_NT) o[e] = __float2bfloat16_rn((c[e] - m) * inv);
+}
+
 }  // namespace
+
+cudaError_t launch_af_standardize(const float* cells, const double* sums, uint32_t sum_stride, uint32_t n,
+                                  uint32_t ncell, void* out_bf16, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_af_standardize<<<n, FT_NT, 0, s>>>(cells, sums, sum_stride, ncell, static_cast<__nv_bfloat16*>(out_bf16));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tamura_finish(const double* acc, uint32_t count, uint32_t pixels, float* metric, cudaStream_t s) {
   if (count == 0) return cudaSuccess;

@@ -35,7 +35,7 @@ namespace {
 
 constexpr int PP_BT = 16;
 enum { PK_P1 = PASS_COL_FFT, PK_P2A = PASS_ROW_ASP, PK_P3A = PASS_COL_IFFT, PK_P2F = PASS_ROW_FFT,
-       PK_P3T = PASS_COL_IFFT_TAMURA };
+       PK_P3T = PASS_COL_IFFT_TAMURA, PK_P2C = PASS_ROW_CELLS };
 
 // Lines per strip: 16, or 8 at L = 1024 (two buffers of 16 lines would not fit).
 template <int L>
@@ -130,6 +130,33 @@ struct RowOut {
   float2* out;
   uint32_t stride;
   __device__ __forceinline__ void operator()(int b, int k, float2 v) const { out[size_t(b) * stride + k] = v; }
+};
+
+// Network-input cells from bins handed out bin-fastest with 16 butterflies per
+// line (lanes 0-15: row b, lanes 16-31: row b + 1; bins j + 16 m): the 2 x 2 block
+// of unshifted bins (even ky, even kx) sits in lanes j, j ^ 1, j ^ 16, j ^ 17. The
+// lane with even j of the even row writes log1p(mean |F|) (DC bin as 0) at the
+// block's centred position and adds it to its running (sum v, sum v^2).
+struct CellsOut {
+  static constexpr bool kSyncFirst = false;
+  static constexpr bool kJFast = true;
+  float* cells;      // this frame's [H/2][W/2]
+  uint32_t ky0;      // unshifted row of the strip's first line
+  uint32_t W, H;
+  float* s;          // s[0] += v, s[1] += v^2
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const {
+    const uint32_t ky = ky0 + uint32_t(b);
+    float a = (ky | uint32_t(k)) ? sqrtf(fmaf(v.x, v.x, v.y * v.y)) : 0.f;
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    a += __shfl_xor_sync(0xffffffffu, a, 16);
+    if (((threadIdx.x & 31) & 17) == 0) {  // even bin, even row
+      const float c = log1pf(0.25f * a);
+      const uint32_t r = ((ky + H / 2) & (H - 1)) >> 1, q = ((uint32_t(k) + W / 2) & (W - 1)) >> 1;
+      cells[size_t(r) * (W / 2) + q] = c;
+      s[0] += c;
+      s[1] = fmaf(c, c, s[1]);
+    }
+  }
 };
 
 // Span NS and radix R of the last stage of the pass (the BlockRadix chain).
@@ -254,7 +281,7 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
   float2* tws = reinterpret_cast<float2*>(smem);
   float2* cys = reinterpret_cast<float2*>(smem + C::TW);  // P1 Fresnel: chirp along y
   float2* twl = cys;                                      // P2f: last-stage twiddles by (m, j)
-  unsigned char* body = smem + ((PK == PK_P1 || PK == PK_P2F) ? 2 * C::TW : C::TW);
+  unsigned char* body = smem + ((PK == PK_P1 || PK == PK_P2F || PK == PK_P2C) ? 2 * C::TW : C::TW);
   float2* buf0 = reinterpret_cast<float2*>(body);
   // P1: one FFT buffer and two raw staging buffers; other passes: two FFT buffers
   float2* buf1 = reinterpret_cast<float2*>(body + C::BUF);
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
     tws[e] = __ldg(&twg[e]);
     if (PK == PK_P1 && fresnel) cys[e] = __ldg(&a.chirp_y[e]);
   }
-  if constexpr (PK == PK_P2F) {
+  if constexpr (PK == PK_P2F || PK == PK_P2C) {
     using LS = LastStage<L, C::BT, C::NT>;
     for (int e = tid; e < (LS::R - 1) * LS::NS; e += C::NT) {
       const int m = e / LS::NS + 1, jm = e % LS::NS;
@@ -354,6 +381,28 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
         for (int w = 0; w < C::NT / 32; ++w) t += red[tid][w];
         atomicAdd(&a.tam_acc[size_t(i) * a.tam_stride + tid], double(t));
       }
+    } else if constexpr (PK == PK_P2C) {
+      float2* buf = cur == 0 ? buf0 : buf1;
+      float acc[2] = {0.f, 0.f};
+      pp_stages<L, 1, -1>(SmemSrc<C::LD>{buf}, buf, tws,
+                          CellsOut{a.cells + size_t(i) * (a.H / 2) * (a.W / 2), uint32_t(s0), a.W, a.H, acc}, twl);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+        acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+      }
+      __shared__ float redc[2][C::NT / 32];
+      if ((tid & 31) == 0) {
+        redc[0][tid >> 5] = acc[0];
+        redc[1][tid >> 5] = acc[1];
+      }
+      __syncthreads();
+      if (tid < 2) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < C::NT / 32; ++w) t += redc[tid][w];
+        atomicAdd(&a.tam_acc[size_t(i) * a.tam_stride + tid], t);
+      }
     } else {
       float2* buf = cur == 0 ? buf0 : buf1;
       // time queue [ky][kx]: bin kx of row s0 + b, stored from the registers of the
@@ -370,7 +419,7 @@ template <int L, int PK>
 static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t s) {
   using C = PpCfg<L>;
   const size_t smem = PK == PK_P1 ? 2 * C::TW + C::BUF + 2 * C::RAW
-                                   : (PK == PK_P2F ? 2 * C::TW : C::TW) + 2 * C::BUF;
+                                   : ((PK == PK_P2F || PK == PK_P2C) ? 2 * C::TW : C::TW) + 2 * C::BUF;
   auto kern = k_pass_pp<L, PK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -444,6 +493,10 @@ cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s) {
     case PASS_COL_IFFT: return pass_by_len<PK_P3A>(a, s);
     case PASS_ROW_FFT: return pass_by_len<PK_P2F>(a, s);
     case PASS_COL_IFFT_TAMURA: return pass_by_len<PK_P3T>(a, s);
+    case PASS_ROW_CELLS:
+      // the cell epilogue pairs rows and bins across lanes: 16 butterflies per line in the last stage
+      if (a.W > 256 || a.H > 1024) return cudaErrorInvalidValue;
+      return pass_by_len<PK_P2C>(a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -72,8 +72,10 @@ def gpu_features(frames):
         r.close()
 
 
-@pytest.mark.parametrize("H,W,bits", [(256, 256, 16), (64, 128, 8)])
+@pytest.mark.parametrize("H,W,bits", [(256, 256, 16), (64, 128, 8), (128, 64, 16), (64, 512, 8)])
 def test_features_match_oracle(H, W, bits):
+    """Widths up to 256 form the binned cells in the row pass's epilogue (lanes
+    pair bins and rows); 512 stores the spectra and bins them in a second kernel."""
     if H == 256:
         fr, _ = synth.autofocus_set(5, N=256, seed=1007)
     else:
