@@ -667,12 +667,54 @@ def run_group(args, use_graph, tuned, quick=False, dist=None):
     elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     world = dist.get_world_size() if dist else 1
     value = job_value(world, args.steps, frames_per_batch, elapsed_ms / 1e3)
+    e2e = None
+    if not quick and not args.no_e2e:
+        # end to end: every batch's frames copied from pinned host memory (two device
+        # pool sets, the copy of batch k + 1 overlapping the render of batch k on a
+        # copy stream), the images read back to pinned host memory, wall clock
+        hpools = [p.cpu().pin_memory() for p in pools]
+        bufs = [pools, [torch.empty_like(p) for p in pools]]
+        outs_h = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        cs = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        used = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def upload(b):
+            with torch.cuda.stream(cs):
+                for d, h in zip(bufs[b], hpools):
+                    d.copy_(h, non_blocking=True)
+            copied[b].record(cs)
+
+        K = args.steps
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        tt = time.perf_counter()
+        upload(0)
+        for k in range(K):
+            b = k & 1
+            stream.wait_event(copied[b])
+            if k + 1 < K:
+                if k >= 1:
+                    cs.wait_event(used[1 - b])
+                upload(1 - b)
+            nw = hv.hv_render_group(g, bufs[b], outs)
+            assert nw == [GROUP_WINDOWS] * len(rs), nw
+            used[b].record(stream)
+            for oh, od in zip(outs_h, outs):
+                oh.copy_(od, non_blocking=True)
+        stream.synchronize()
+        cs.synchronize()
+        e2e_s = max_over_ranks((time.perf_counter() - tt) / K, dist, dev)
+        e2e = {"value": round(world * frames_per_batch / e2e_s, 1), "unit": "frames/s",
+               "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hpools)),
+               "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs_h))}
     hv.hv_group_close(g)
     for r in rs:
         r.close()
     return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, clocks=clk,
                 launches=st1["kernel_launches"] - st0["kernel_launches"], stats=st1,
-                frames_per_batch=frames_per_batch)
+                frames_per_batch=frames_per_batch, e2e=e2e)
 
 
 def group_config(name, frames_per_batch):
@@ -717,7 +759,7 @@ def main_group(args):
                      "kernel": "whole batch (all members' kernels; algorithmic bytes 18 B/px/frame "
                                "+ 12 B/px/window)",
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
-        "e2e": None,
+        "e2e": res["e2e"],
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "form": "tuned",
@@ -814,16 +856,39 @@ def main_autofocus(args):
     torch.cuda.synchronize()
     sweep_ms = e0.elapsed_time(e1) / max(1, args.steps // 2)
     clk = clocks.stop()
-    # end to end: pinned host holograms in, distances out
+    # end to end: pinned host holograms in, distances out, wall clock; two device
+    # frame buffers, the copy of step k + 1 on a copy stream overlapping step k
     host = torch.from_numpy(frames.view(np.int16)).pin_memory()
     zh = torch.empty(B, dtype=torch.float32).pin_memory()
+    bufs = [fr, torch.empty_like(fr)]
+    cs = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def upload(b):
+        with torch.cuda.stream(cs):
+            bufs[b].copy_(host, non_blocking=True)
+        copied[b].record(cs)
+
+    def step_from(buf):
+        hv.hv_af_features(r.h, buf, feats)
+        net.forward(feats, z)
+
     torch.cuda.synchronize()
     tt = time.perf_counter()
-    for _ in range(args.steps):
-        fr.copy_(host, non_blocking=True)
-        step()
+    upload(0)
+    for k in range(args.steps):
+        b = k & 1
+        stream.wait_event(copied[b])
+        if k + 1 < args.steps:
+            if k >= 1:
+                cs.wait_event(used[1 - b])
+            upload(1 - b)
+        step_from(bufs[b])
+        used[b].record(stream)
         zh.copy_(z, non_blocking=True)
-        stream.synchronize()
+    stream.synchronize()
+    cs.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - tt) / args.steps, dist, dev)
     value = job_value(world, args.steps, B, ms / 1e3)
     tflops = AF_FLOPS * B / (net_ms / 1e3) / 1e12
