@@ -430,6 +430,20 @@ hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, uint32_t n,
  * NULL). Valid until the next call on the handle. */
 const char* hv_last_error(const hv_handle* h);
 
+/* Measured arithmetic peaks of a device: FP32 and FP64 fused multiply-add
+ * throughput (2 flop per FMA) of kernels that do nothing else, timed with CUDA
+ * events on `stream` (NULL: the legacy default stream; best of five launches,
+ * about 60 ms, synchronous).
+ * They serve as the roofline denominators of ALU-bound kernels.
+ * Errors: HV_ERR_ARG, HV_ERR_NOMEM, HV_ERR_CUDA. */
+typedef struct {
+  double fp32_tflops;
+  double fp64_tflops;
+  int sm_count;
+  int sm_clock_khz; /* maximum SM clock the device reports */
+} hv_peaks;
+hv_status hv_probe_peaks(int device, void* stream, hv_peaks* out);
+
 /* Version string of the library. */
 const char* hv_version(void);
 

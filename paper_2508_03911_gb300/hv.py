@@ -68,6 +68,11 @@ class hv_profile(C.Structure):
                 ("pca_sweeps", C.c_uint64), ("pca_sweeps_f32", C.c_uint64)]
 
 
+class hv_peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double), ("sm_count", C.c_int),
+                ("sm_clock_khz", C.c_int)]
+
+
 class hv_tuning(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("spatial_kernel", C.c_int32), ("spatial_chunk", C.c_uint32),
                 ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 12)]
@@ -140,6 +145,7 @@ def lib() -> C.CDLL:
                            C.c_int),
         "hv_af_features": ([C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p], C.c_int),
         "hv_version": ([], C.c_char_p),
+        "hv_probe_peaks": ([C.c_int, C.c_void_p, P(hv_peaks)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -297,6 +303,15 @@ def hv_last_error(h=None) -> str:
 
 def hv_version() -> str:
     return lib().hv_version().decode()
+
+
+def hv_probe_peaks(device=0, stream=None) -> dict:
+    """Measured FP32 / FP64 FMA throughput of the device (TFLOP/s)."""
+    p = hv_peaks()
+    s = lib().hv_probe_peaks(device, C.c_void_p(stream or 0), C.byref(p))
+    if s != HV_OK:
+        raise HvError(s, "hv_probe_peaks failed")
+    return {n: getattr(p, n) for n, _ in hv_peaks._fields_}
 
 
 def hv_set_postprocess(h, kernel=None, kernel_size=None, sigma=0.0, renormalize=False, accumulate=1):

@@ -400,3 +400,14 @@ def test_invalid_settings_are_rejected_and_previous_kept():
             assert ei.value.status == hv.HV_ERR_ARG
     finally:
         r.close()
+
+
+def test_probe_peaks_are_plausible():
+    """The FMA probe behind the ALU rooflines: FP32 within the unit-count bound
+    (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s, a little slack for the
+    clock) and FP64 well below it."""
+    p = hv.hv_probe_peaks(0)
+    assert p["sm_count"] > 0 and p["sm_clock_khz"] > 0
+    bound = p["sm_count"] * 128 * 2 * p["sm_clock_khz"] * 1e3 / 1e12
+    assert 0.3 * bound < p["fp32_tflops"] <= 1.05 * bound, (p, bound)
+    assert 0.0 < p["fp64_tflops"] < 0.2 * p["fp32_tflops"], p
