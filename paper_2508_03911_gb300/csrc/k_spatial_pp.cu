@@ -438,6 +438,99 @@ static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- row FFT, one warp per 2 rows
+//
+// The Fresnel row pass at L = 256 with the STFT's warp-private layout: 16 lanes
+// carry one row, so the 256-point FFT (16 x 16 Stockham) needs only __syncwarp
+// between its stages. A CTA of 8 warps stages a strip of 16 rows of S1 [ky][x]
+// with 16-byte cp.async into a row-major tile (row stride 272: index i of a row at
+// i + i/16 once the first stage has rewritten it in place), prefetching the next
+// strip into a second tile. Stage 1 reads samples jl + 16 m (consecutive lanes,
+// conflict-free) and writes its outputs back into the row at 16 jl + m (padded);
+// stage 2 reads jl + 16 m, applies w_256^(jl m) from a table laid out by (m, jl)
+// and leaves bin jl + 16 m in lane jl, stored to the time queue row (coalesced).
+constexpr int RW_L = 256, RW_BT = 16, RW_NT = 256, RW_RS = RW_L + RW_L / 16;
+
+__device__ __forceinline__ int rw_pad(int i) { return i + (i >> 4); }
+
+__global__ void __launch_bounds__(RW_NT, 3) k_row_warp(SpatialArgs a, int nitems, int strip_log2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tile0 = reinterpret_cast<float2*>(smem);
+  float2* tile1 = tile0 + RW_BT * RW_RS;
+  float2* tw2 = tile1 + RW_BT * RW_RS;  // stage 2: w_256^(j m) at (m - 1) 16 + j
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = 2 * warp + (lane >> 4), jl = lane & 15;  // row of the strip, lane within the row
+  const int smask = (1 << strip_log2) - 1;
+  for (int e = tid; e < 15 * 16; e += RW_NT) {
+    const int m = e / 16 + 1, j = e % 16;
+    tw2[e] = __ldg(&a.tw_w[j * m]);
+  }
+  auto issue = [&](int it, float2* tile) {
+    const int i = it >> strip_log2, s0 = (it & smask) * RW_BT;
+    const float2* src = a.scratch1 + (size_t(i) * a.H + s0) * RW_L;
+    for (int e = tid; e < RW_BT * RW_L / 2; e += RW_NT) {  // 16-byte pieces (2 samples)
+      const int r = e / (RW_L / 2), c = e % (RW_L / 2);
+      cpa16(tile + r * RW_RS + 2 * c, src + size_t(r) * RW_L + 2 * c);
+    }
+    cpa_commit();
+  };
+  int item = blockIdx.x;
+  if (item < nitems) issue(item, tile0);
+  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
+    float2* tile = (k & 1) ? tile1 : tile0;
+    const int i = item >> strip_log2, s0 = (item & smask) * RW_BT;
+    cpa_wait_all();
+    __syncthreads();  // this strip resident; the other tile (two strips ago) fully used
+    const int nxt = item + gridDim.x;
+    if (nxt < nitems) issue(nxt, (k & 1) ? tile0 : tile1);
+    if (a.discard_inputs) {
+      const char* st = reinterpret_cast<const char*>(a.scratch1 + (size_t(i) * a.H + s0) * RW_L);
+      for (int e = tid; e < RW_BT * RW_L * 8 / 128; e += RW_NT)
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(st + size_t(e) * 128) : "memory");
+    }
+    float2* row = tile + b * RW_RS;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = row[jl + 16 * m];
+    dft<16, -1>(v);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) row[rw_pad(16 * jl + m)] = v[m];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      v[m] = row[rw_pad(jl + 16 * m)];
+      if (m > 0) v[m] = cmul(v[m], tw2[(m - 1) * 16 + jl]);
+    }
+    dft<16, -1>(v);
+    // time queue [ky][kx]: bin kx = jl + 16 m of row s0 + b
+    const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
+    float2* out = static_cast<float2*>(a.tq.base) + (tslot * a.H + s0 + b) * size_t(RW_L);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
+  }
+  cpa_wait_all();
+}
+
+static cudaError_t launch_row_warp(const SpatialArgs& a, cudaStream_t s) {
+  const size_t smem = (2 * size_t(RW_BT) * RW_RS + 15 * 16) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_row_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_row_warp, RW_NT, smem);
+  if (e != cudaSuccess) return e;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int strip_log2 = 0;
+  while ((uint32_t(RW_BT) << strip_log2) < a.H) ++strip_log2;
+  const int nitems = int(a.n) << strip_log2;
+  int grid = per_sm * nsm;
+  if (grid > nitems) grid = nitems;
+  if (grid < 1) grid = 1;
+  k_row_warp<<<grid, RW_NT, smem, s>>>(a, nitems, strip_log2);
+  return cudaGetLastError();
+}
+
 template <int LH, int LW>
 static cudaError_t pp_fixed(const SpatialArgs& a, cudaStream_t s, int* launches) {
   cudaError_t e = launch_pp<LH, PK_P1>(a, a.W, s);
@@ -449,7 +542,8 @@ static cudaError_t pp_fixed(const SpatialArgs& a, cudaStream_t s, int* launches)
     e = launch_pp<LH, PK_P3A>(a, a.W, s);
     *launches += 2;
   } else {
-    e = launch_pp<LW, PK_P2F>(a, a.H, s);
+    // rows of 256: the warp-private row pass (H a multiple of its 16-row strips)
+    e = (LW == RW_L && a.H % RW_BT == 0) ? launch_row_warp(a, s) : launch_pp<LW, PK_P2F>(a, a.H, s);
     ++*launches;
   }
   return e;
