@@ -514,6 +514,7 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
   for (uint64_t a = f0; a < f1; a += step) {
     const uint32_t n = uint32_t(std::min<uint64_t>(step, f1 - a));
     SpatialArgs sa{};
+    sa.err = h->dev_err;
     sa.spatial = h->cur.spatial;
     sa.in_kind = h->bits == 8 ? IN_U8 : IN_U16;
     sa.W = h->W;
@@ -1134,6 +1135,7 @@ hv_status hv_set_postprocess(hv_handle* h, const hv_post* p) {
 // Frames [n][H][W] in device memory as a ring for the pass kernels.
 static SpatialArgs af_args(const hv_handle* h, const void* frames, uint32_t n) {
   SpatialArgs sa{};
+  sa.err = h->dev_err;
   sa.spatial = HV_SPATIAL_ASP;  // no chirp in the column pass
   sa.in_kind = h->bits == 8 ? IN_U8 : IN_U16;
   sa.W = h->W;

@@ -37,6 +37,7 @@ struct SpatialArgs {
   uint32_t tam_stride;
   int discard_inputs;   // persistent passes: scratch1/scratch2 are read once, drop their L2 lines after staging
   float* cells;         // PASS_ROW_CELLS output [n][H/2][W/2]
+  unsigned* err;        // device flags (bit 3: a row pass's wait for its staged strip gave up); may be NULL
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);
@@ -73,6 +74,13 @@ struct StftArgs {
   int tma;              // set by the launcher: staged frames through a TMA tensor map
 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
+
+// Encodes a 2-D tiled TMA tensor map (map: a CUtensorMap, 64-byte aligned) over
+// 8-byte elements: {inner, outer} elements, rows pitch_bytes apart, box
+// {box_inner, box_outer}, 64-byte swizzle or none. False when the driver entry
+// point is missing or the encoder rejects the shape.
+bool encode_map_2d_u64(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+                       uint32_t box_inner, uint32_t box_outer, bool swizzle64);
 
 // PCA of one window (Sec. III-B.1), time-queue ring -> energy image.
 struct PcaArgs {

@@ -25,6 +25,8 @@
 // is staged, its L2 lines are discarded (no write-back of dead data when a
 // chunk's intermediates fit in L2). Single passes (the focus sweep re-reads S1
 // for every distance) keep them.
+#include <cuda.h>
+
 #include "fft_dev.cuh"
 #include "hv_internal.h"
 #include "../../include/hv.h"
@@ -442,22 +444,42 @@ static cudaError_t launch_pp(const SpatialArgs& a, uint32_t lines, cudaStream_t 
 //
 // The Fresnel row pass at L = 256 with the STFT's warp-private layout: 16 lanes
 // carry one row, so the 256-point FFT (16 x 16 Stockham) needs only __syncwarp
-// between its stages. A CTA of 8 warps stages a strip of 16 rows of S1 [ky][x]
-// with 16-byte cp.async into a row-major tile (row stride 272: index i of a row at
-// i + i/16 once the first stage has rewritten it in place), prefetching the next
-// strip into a second tile. Stage 1 reads samples jl + 16 m (consecutive lanes,
-// conflict-free) and writes its outputs back into the row at 16 jl + m (padded);
-// stage 2 reads jl + 16 m, applies w_256^(jl m) from a table laid out by (m, jl)
-// and leaves bin jl + 16 m in lane jl, stored to the time queue row (coalesced).
-constexpr int RW_L = 256, RW_BT = 16, RW_NT = 256, RW_RS = RW_L + RW_L / 16;
+// between its stages. A CTA of 8 warps takes strips of 16 rows of S1 [ky][x]; one
+// TMA tensor load per strip (16 x 256 complex64, dense rows) lands in one of two
+// tiles and completes on the tile's mbarrier, the next strip's load in flight
+// while the current one is transformed. Stage 1 reads samples jl + 16 m
+// (consecutive lanes) and writes its output m back into the row at 16 jl +
+// (m ^ jl) (an XOR swizzle: conflict-free without padding); stage 2 reads
+// 16 m + (jl ^ m), applies w_256^(jl m) from a table laid out by (m, jl) and leaves
+// bin jl + 16 m in lane jl, stored to the time queue row (coalesced).
+constexpr int RW_L = 256, RW_BT = 16, RW_NT = 256;
 
-__device__ __forceinline__ int rw_pad(int i) { return i + (i >> 4); }
+__device__ __forceinline__ uint32_t rw_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
-__global__ void __launch_bounds__(RW_NT, 3) k_row_warp(SpatialArgs a, int nitems, int strip_log2) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Bounded wait (about 2^32 clocks) for phase `parity` of an mbarrier.
+__device__ __forceinline__ bool rw_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 32)) return false;
+  }
+}
+
+__global__ void __launch_bounds__(RW_NT, 3)
+    k_row_warp(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s1map) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[2];
   float2* tile0 = reinterpret_cast<float2*>(smem);
-  float2* tile1 = tile0 + RW_BT * RW_RS;
-  float2* tw2 = tile1 + RW_BT * RW_RS;  // stage 2: w_256^(j m) at (m - 1) 16 + j
+  float2* tile1 = tile0 + RW_BT * RW_L;
+  float2* tw2 = tile1 + RW_BT * RW_L;  // stage 2: w_256^(j m) at (m - 1) 16 + j
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = 2 * warp + (lane >> 4), jl = lane & 15;  // row of the strip, lane within the row
   const int smask = (1 << strip_log2) - 1;
@@ -465,41 +487,57 @@ __global__ void __launch_bounds__(RW_NT, 3) k_row_warp(SpatialArgs a, int nitems
     const int m = e / 16 + 1, j = e % 16;
     tw2[e] = __ldg(&a.tw_w[j * m]);
   }
-  auto issue = [&](int it, float2* tile) {
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // one thread: the strip of item `it` (rows i H + s0 .. + 15 of S1) into tile `k`
+  auto issue = [&](int it, int k) {
     const int i = it >> strip_log2, s0 = (it & smask) * RW_BT;
-    const float2* src = a.scratch1 + (size_t(i) * a.H + s0) * RW_L;
-    for (int e = tid; e < RW_BT * RW_L / 2; e += RW_NT) {  // 16-byte pieces (2 samples)
-      const int r = e / (RW_L / 2), c = e % (RW_L / 2);
-      cpa16(tile + r * RW_RS + 2 * c, src + size_t(r) * RW_L + 2 * c);
-    }
-    cpa_commit();
+    const uint32_t mb = rw_smem(&full[k]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(RW_BT * RW_L * 8)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(rw_smem(k ? tile1 : tile0)),
+        "l"(reinterpret_cast<uint64_t>(&s1map)), "r"(0), "r"(int(i * a.H + s0)), "r"(mb)
+        : "memory");
   };
   int item = blockIdx.x;
-  if (item < nitems) issue(item, tile0);
-  for (int k = 0; item < nitems; ++k, item += gridDim.x) {
-    float2* tile = (k & 1) ? tile1 : tile0;
+  if (tid == 0 && item < nitems) issue(item, 0);
+  bool ok = true;
+  for (int k = 0; item < nitems && ok; ++k, item += gridDim.x) {
+    const int cur = k & 1;
+    float2* tile = cur ? tile1 : tile0;
     const int i = item >> strip_log2, s0 = (item & smask) * RW_BT;
-    cpa_wait_all();
-    __syncthreads();  // this strip resident; the other tile (two strips ago) fully used
+    ok = rw_wait(rw_smem(&full[cur]), uint32_t(k >> 1) & 1u);
+    // every warp is done with the other tile (two strips ago) and sees this one
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
     const int nxt = item + gridDim.x;
-    if (nxt < nitems) issue(nxt, (k & 1) ? tile0 : tile1);
+    if (tid == 0 && nxt < nitems) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(nxt, cur ^ 1);
+    }
     if (a.discard_inputs) {
       const char* st = reinterpret_cast<const char*>(a.scratch1 + (size_t(i) * a.H + s0) * RW_L);
       for (int e = tid; e < RW_BT * RW_L * 8 / 128; e += RW_NT)
         asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(st + size_t(e) * 128) : "memory");
     }
-    float2* row = tile + b * RW_RS;
+    float2* row = tile + b * RW_L;
     float2 v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = row[jl + 16 * m];
     dft<16, -1>(v);
     __syncwarp();
 #pragma unroll
-    for (int m = 0; m < 16; ++m) row[rw_pad(16 * jl + m)] = v[m];
+    for (int m = 0; m < 16; ++m) row[16 * jl + (m ^ jl)] = v[m];
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      v[m] = row[rw_pad(jl + 16 * m)];
+      v[m] = row[16 * m + (jl ^ m)];
       if (m > 0) v[m] = cmul(v[m], tw2[(m - 1) * 16 + jl]);
     }
     dft<16, -1>(v);
@@ -509,11 +547,14 @@ __global__ void __launch_bounds__(RW_NT, 3) k_row_warp(SpatialArgs a, int nitems
 #pragma unroll
     for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
   }
-  cpa_wait_all();
+  if (!ok && tid == 0 && a.err) atomicOr(a.err, 8u);
 }
 
 static cudaError_t launch_row_warp(const SpatialArgs& a, cudaStream_t s) {
-  const size_t smem = (2 * size_t(RW_BT) * RW_RS + 15 * 16) * sizeof(float2);
+  const size_t smem = (2 * size_t(RW_BT) * RW_L + 15 * 16) * sizeof(float2);
+  CUtensorMap map{};
+  if (!encode_map_2d_u64(&map, a.scratch1, RW_L, uint64_t(a.n) * a.H, RW_L * 8, RW_L, RW_BT, false))
+    return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(k_row_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, nsm = 0;
@@ -527,7 +568,7 @@ static cudaError_t launch_row_warp(const SpatialArgs& a, cudaStream_t s) {
   int grid = per_sm * nsm;
   if (grid > nitems) grid = nitems;
   if (grid < 1) grid = 1;
-  k_row_warp<<<grid, RW_NT, smem, s>>>(a, nitems, strip_log2);
+  k_row_warp<<<grid, RW_NT, smem, s>>>(a, nitems, strip_log2, map);
   return cudaGetLastError();
 }
 
@@ -542,8 +583,10 @@ static cudaError_t pp_fixed(const SpatialArgs& a, cudaStream_t s, int* launches)
     e = launch_pp<LH, PK_P3A>(a, a.W, s);
     *launches += 2;
   } else {
-    // rows of 256: the warp-private row pass (H a multiple of its 16-row strips)
-    e = (LW == RW_L && a.H % RW_BT == 0) ? launch_row_warp(a, s) : launch_pp<LW, PK_P2F>(a, a.H, s);
+    // rows of 256: the warp-private row pass (H a multiple of its 16-row strips;
+    // the block-wide pass when the tensor map cannot be encoded)
+    e = (LW == RW_L && a.H % RW_BT == 0) ? launch_row_warp(a, s) : cudaErrorNotSupported;
+    if (e == cudaErrorNotSupported) e = launch_pp<LW, PK_P2F>(a, a.H, s);
     ++*launches;
   }
   return e;

@@ -487,14 +487,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // consecutive slots (the queue capacity, T and the first slot multiples of S).
 static bool queue_map(const StftArgs& a, int BT, CUtensorMap* map) {
   if (BT != 8 || a.S == 0 || a.S >= a.T || a.S > 256 || a.tq.cap % a.S || a.T % a.S || a.tq.slot0 % a.S) return false;
+  return encode_map_2d_u64(map, a.tq.base, uint64_t(a.W) * a.H, a.tq.cap, uint64_t(a.W) * a.H * 8, 8, a.S, true);
+}
+
+bool encode_map_2d_u64(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+                       uint32_t box_inner, uint32_t box_outer, bool swizzle64) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[2] = {cuuint64_t(a.W) * a.H, a.tq.cap};
-  const cuuint64_t strides[1] = {cuuint64_t(a.W) * a.H * 8};
-  const cuuint32_t box[2] = {8, a.S};
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tq.base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+  return fn(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
