@@ -243,14 +243,16 @@ float2 cis(double a) { return make_float2(float(std::cos(a)), float(std::sin(a))
 // Build ASP / Fresnel tables for p in float64 and upload them.
 hv_status build_tables(hv_handle* h, const hv_params& p) {
   const uint32_t W = p.width, H = p.height;
-  const size_t need = (size_t(W) * H + W + H) * sizeof(float2);
+  // [Hᵀ: W H][chirp x: W][chirp y: H][H row-major: W H]
+  const size_t need = (2 * size_t(W) * H + W + H) * sizeof(float2);
   if (need > h->table_bytes) {
     dfree(h->asp_ht);
     HV_CU(h, cudaMalloc(&h->asp_ht, need));
     h->table_bytes = need;
   }
   h->chirp = h->asp_ht + size_t(W) * H;
-  std::vector<float2> host(size_t(W) * H + W + H, make_float2(0.f, 0.f));
+  std::vector<float2> host(2 * size_t(W) * H + W + H, make_float2(0.f, 0.f));
+  const size_t rowmajor = size_t(W) * H + W + H;
   if (p.spatial == HV_SPATIAL_ASP) {
     // H(kx, ky) = exp(i z sqrt(k^2 - kx^2 - ky^2)), zero where evanescent; stored
     // transposed [kx][ky] with the inverse transform's 1/(W H) folded in.
@@ -272,6 +274,7 @@ hv_status build_tables(hv_handle* h, const hv_params& p) {
           v = make_float2(float(std::cos(ph) * scale), float(std::sin(ph) * scale));
         }
         host[size_t(kx) * H + ky] = v;
+        host[rowmajor + size_t(ky) * W + kx] = v;
       }
     }
   } else if (p.spatial == HV_SPATIAL_FRESNEL) {
@@ -527,6 +530,8 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.tw_w = h->tw + tw_offset(h->W);
     sa.tw_h = h->tw + tw_offset(h->H);
     sa.asp_ht = h->asp_ht;
+    // the row-major copy follows the transposed table and the two chirp vectors
+    sa.asp_h = h->cur.spatial == HV_SPATIAL_ASP ? h->asp_ht + size_t(h->W) * h->H + h->W + h->H : nullptr;
     sa.chirp_x = h->chirp;
     sa.chirp_y = h->chirp + h->W;
     sa.use_cluster = h->sp_cluster;

@@ -29,6 +29,7 @@ struct SpatialArgs {
   const float2* tw_w;   // twiddle table of length W
   const float2* tw_h;   // twiddle table of length H
   const float2* asp_ht; // ASP transfer function, transposed [kx][ky], includes 1/(W H)
+  const float2* asp_h;  // the same, row-major [ky][kx] (NULL where not built)
   const float2* chirp_x;// Fresnel chirp factors along x (length W), fftshift folded in
   const float2* chirp_y;// along y (length H)
   int use_cluster;      // 1: whole-frame cluster kernel when the size allows it

@@ -183,11 +183,13 @@ struct LastStage {
 // tws[e] = exp(-2 pi i e / L). The last stage hands bin k of line b to epi.
 // With an epilogue of kJFast, the last stage maps threads bin-fastest (b = idx / NB,
 // j = idx % NB) and takes its twiddles from twl[(m - 1) NS + j] (contiguous in j).
-template <int L, int NS, int DIR, class Src, class Epi>
+template <int L, int NS, int DIR, class Src, class Epi, int LDX = 0>
 __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const float2* tws, const Epi& epi,
                                           const float2* twl = nullptr) {
   using C = PpCfg<L>;
-  constexpr int NT = C::NT, BT = C::BT, LD = C::LD;
+  // LDX > 0: buffer row stride other than the padded one (16 for TMA-staged strips:
+  // with lines fastest, a warp's stage accesses are two contiguous 128-byte runs)
+  constexpr int NT = C::NT, BT = C::BT, LD = LDX > 0 ? LDX : C::LD;
   constexpr int REM = L / NS;
   constexpr int R = BlockRadix<REM, L, BT, NT>::value;
   constexpr int NB = L / R;
@@ -234,7 +236,7 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
     }
     __syncthreads();
     SmemSrc<LD> s{buf};
-    pp_stages<L, NS * R, DIR>(s, buf, tws, epi, twl);
+    pp_stages<L, NS * R, DIR, SmemSrc<LD>, Epi, LDX>(s, buf, tws, epi, twl);
   }
 }
 
@@ -572,12 +574,228 @@ static cudaError_t launch_row_warp(const SpatialArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ASP row pass at W = 256, warp-private like k_row_warp: forward row FFT, bins
+// times the transfer function H[ky][kx] (row-major copy, 1/(W H) folded in), then
+// the inverse row FFT, whose first stage takes the bins the forward FFT left in
+// the lane's registers (butterfly jl of the inverse is bins jl + 16 m). S2 is
+// written row-major [ky][x], coalesced.
+__global__ void __launch_bounds__(RW_NT, 3)
+    k_row_asp(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s1map) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[2];
+  float2* tile0 = reinterpret_cast<float2*>(smem);
+  float2* tile1 = tile0 + RW_BT * RW_L;
+  float2* tw2 = tile1 + RW_BT * RW_L;  // w_256^(j m) at (m - 1) 16 + j
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = 2 * warp + (lane >> 4), jl = lane & 15;
+  const int smask = (1 << strip_log2) - 1;
+  for (int e = tid; e < 15 * 16; e += RW_NT) {
+    const int m = e / 16 + 1, j = e % 16;
+    tw2[e] = __ldg(&a.tw_w[j * m]);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int it, int k) {
+    const int i = it >> strip_log2, s0 = (it & smask) * RW_BT;
+    const uint32_t mb = rw_smem(&full[k]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(RW_BT * RW_L * 8)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(rw_smem(k ? tile1 : tile0)),
+        "l"(reinterpret_cast<uint64_t>(&s1map)), "r"(0), "r"(int(i * a.H + s0)), "r"(mb)
+        : "memory");
+  };
+  int item = blockIdx.x;
+  if (tid == 0 && item < nitems) issue(item, 0);
+  bool ok = true;
+  for (int k = 0; item < nitems && ok; ++k, item += gridDim.x) {
+    const int cur = k & 1;
+    float2* tile = cur ? tile1 : tile0;
+    const int i = item >> strip_log2, s0 = (item & smask) * RW_BT;
+    ok = rw_wait(rw_smem(&full[cur]), uint32_t(k >> 1) & 1u);
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    const int nxt = item + gridDim.x;
+    if (tid == 0 && nxt < nitems) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(nxt, cur ^ 1);
+    }
+    if (a.discard_inputs) {
+      const char* st = reinterpret_cast<const char*>(a.scratch1 + (size_t(i) * a.H + s0) * RW_L);
+      for (int e = tid; e < RW_BT * RW_L * 8 / 128; e += RW_NT)
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(st + size_t(e) * 128) : "memory");
+    }
+    float2* row = tile + b * RW_L;
+    const int ky = s0 + b;
+    float2 v[16];
+    // forward row FFT
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = row[jl + 16 * m];
+    dft<16, -1>(v);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) row[16 * jl + (m ^ jl)] = v[m];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      v[m] = row[16 * m + (jl ^ m)];
+      if (m > 0) v[m] = cmul(v[m], tw2[(m - 1) * 16 + jl]);
+    }
+    dft<16, -1>(v);
+    // bins kx = jl + 16 m times H[ky][kx]
+    const float2* hrow = a.asp_h + size_t(ky) * RW_L;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], __ldg(&hrow[jl + 16 * m]));
+    // inverse row FFT: its first butterfly jl takes the inputs jl + 16 m, here already
+    dft<16, +1>(v);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) row[16 * jl + (m ^ jl)] = v[m];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      v[m] = row[16 * m + (jl ^ m)];
+      if (m > 0) {
+        float2 w = tw2[(m - 1) * 16 + jl];
+        w.y = -w.y;
+        v[m] = cmul(v[m], w);
+      }
+    }
+    dft<16, +1>(v);
+    // S2 [ky][x]: sample x = jl + 16 m of row ky
+    float2* out = a.scratch2 + (size_t(i) * a.H + ky) * RW_L;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
+  }
+  if (!ok && tid == 0 && a.err) atomicOr(a.err, 8u);
+}
+
+// Column IFFT (length L = H <= 256) of 16-column strips of a row-major S2 [ky][x]:
+// one TMA tensor load per strip (H rows x 16 columns, dense: the block-wide FFT's
+// lines-fastest layout with row stride 16), the next strip in flight; samples
+// stored to the time queue [y][x] from the last stage's registers.
+template <int L>
+__global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
+    k_col_ifft_tma(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s2map) {
+  using C = PpCfg<L>;
+  static_assert(C::BT == 16, "16-column strips");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long full[2];
+  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* buf1 = buf0 + L * 16;
+  float2* tws = buf1 + L * 16;
+  const int tid = threadIdx.x;
+  const int smask = (1 << strip_log2) - 1;
+  for (int e = tid; e < L; e += C::NT) tws[e] = __ldg(&a.tw_h[e]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int it, int k) {
+    const int i = it >> strip_log2, s0 = (it & smask) * 16;
+    const uint32_t mb = rw_smem(&full[k]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(L * 16 * 8) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(rw_smem(k ? buf1 : buf0)),
+        "l"(reinterpret_cast<uint64_t>(&s2map)), "r"(s0), "r"(int(i * L)), "r"(mb)
+        : "memory");
+  };
+  int item = blockIdx.x;
+  if (tid == 0 && item < nitems) issue(item, 0);
+  bool ok = true;
+  for (int k = 0; item < nitems && ok; ++k, item += gridDim.x) {
+    const int cur = k & 1;
+    float2* buf = cur ? buf1 : buf0;
+    const int i = item >> strip_log2, s0 = (item & smask) * 16;
+    ok = rw_wait(rw_smem(&full[cur]), uint32_t(k >> 1) & 1u);
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    const int nxt = item + gridDim.x;
+    if (tid == 0 && nxt < nitems) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(nxt, cur ^ 1);
+    }
+    if (a.discard_inputs)  // the strip's 128-byte row segments of S2 are dead once staged
+      for (int y = tid; y < L; y += C::NT)
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(a.scratch2 + (size_t(i) * L + y) * a.W + s0)
+                     : "memory");
+    const size_t tslot = (a.tq.slot0 + uint32_t(i)) % a.tq.cap;
+    // time queue [y][x]: sample y of column s0 + b at tq[y W + s0 + b]
+    pp_stages<L, 1, +1, SmemSrc<16>, GlobalOut, 16>(
+        SmemSrc<16>{buf}, buf, tws, GlobalOut{static_cast<float2*>(a.tq.base) + tslot * size_t(a.W) * L + s0, a.W});
+  }
+  if (!ok && tid == 0 && a.err) atomicOr(a.err, 8u);
+}
+
+template <int LH>
+static cudaError_t launch_asp_rows(const SpatialArgs& a, cudaStream_t s, int* launches) {
+  CUtensorMap m1{}, m2{};
+  if (!encode_map_2d_u64(&m1, a.scratch1, RW_L, uint64_t(a.n) * a.H, RW_L * 8, RW_L, RW_BT, false) ||
+      !encode_map_2d_u64(&m2, a.scratch2, RW_L, uint64_t(a.n) * a.H, RW_L * 8, 16, LH, false))
+    return cudaErrorNotSupported;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // row pass
+  {
+    const size_t smem = (2 * size_t(RW_BT) * RW_L + 15 * 16) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_row_asp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_row_asp, RW_NT, smem);
+    if (e != cudaSuccess) return e;
+    int sl = 0;
+    while ((uint32_t(RW_BT) << sl) < a.H) ++sl;
+    const int nitems = int(a.n) << sl;
+    int grid = per_sm * nsm;
+    grid = grid > nitems ? nitems : (grid < 1 ? 1 : grid);
+    k_row_asp<<<grid, RW_NT, smem, s>>>(a, nitems, sl, m1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // column IFFT
+  {
+    using C = PpCfg<LH>;
+    const size_t smem = (2 * size_t(LH) * 16 + LH) * sizeof(float2);
+    auto kern = k_col_ifft_tma<LH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, smem);
+    if (e != cudaSuccess) return e;
+    int sl = 0;
+    while ((16u << sl) < a.W) ++sl;
+    const int nitems = int(a.n) << sl;
+    int grid = per_sm * nsm;
+    grid = grid > nitems ? nitems : (grid < 1 ? 1 : grid);
+    kern<<<grid, C::NT, smem, s>>>(a, nitems, sl, m2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  *launches += 2;
+  return cudaSuccess;
+}
+
 template <int LH, int LW>
 static cudaError_t pp_fixed(const SpatialArgs& a, cudaStream_t s, int* launches) {
   cudaError_t e = launch_pp<LH, PK_P1>(a, a.W, s);
   if (e != cudaSuccess) return e;
   ++*launches;
   if (a.spatial == HV_SPATIAL_ASP) {
+    // rows of 256 with the row-major transfer function: warp-private row pass and
+    // TMA-staged column IFFT (the block-wide passes when a tensor map cannot be built)
+    if constexpr (LW == RW_L && LH <= 256) {
+      if (a.asp_h) {
+        e = launch_asp_rows<LH>(a, s, launches);
+        if (e != cudaErrorNotSupported) return e;
+      }
+    }
     e = launch_pp<LW, PK_P2A>(a, a.H, s);
     if (e != cudaSuccess) return e;
     e = launch_pp<LH, PK_P3A>(a, a.W, s);
