@@ -113,10 +113,13 @@ def test_cluster_spatial_field_parity(N, spatial, bits):
 @pytest.mark.parametrize("H,W,spatial,bits", [(64, 128, "asp", 12), (256, 256, "fresnel", 12),
                                               (512, 256, "asp", 12), (128, 512, "fresnel", 12),
                                               (1024, 1024, "asp", 12), (256, 1024, "fresnel", 8),
-                                              (1024, 64, "asp", 8)])
+                                              (1024, 64, "asp", 8), (256, 256, "asp", 12),
+                                              (64, 256, "asp", 8), (128, 256, "asp", 12),
+                                              (64, 256, "fresnel", 8), (128, 256, "fresnel", 12)])
 def test_persistent_multipass_parity(H, W, spatial, bits):
     """Persistent prefetching multi-pass kernels (frames and strips looped per CTA;
-    8-line strips at side 1024, 8-byte raw copies for uint8 there)."""
+    8-line strips at side 1024, 8-byte raw copies for uint8 there). Width 256 takes
+    the warp-private row passes (Fresnel; ASP with the TMA column IFFT for H <= 256)."""
     n = 7
     fr = synth.random_frames(n, H, W, bits, seed=H + 3 * W)
     p = oracle_params(spatial=spatial, z_m=0.3, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
@@ -411,3 +414,18 @@ def test_probe_peaks_are_plausible():
     bound = p["sm_count"] * 128 * 2 * p["sm_clock_khz"] * 1e3 / 1e12
     assert 0.3 * bound < p["fp32_tflops"] <= 1.05 * bound, (p, bound)
     assert 0.0 < p["fp64_tflops"] < 0.2 * p["fp32_tflops"], p
+
+
+@pytest.mark.parametrize("spatial,T,S", [("asp", 64, 64), ("asp", 32, 8), ("fresnel", 64, 16)])
+def test_persistent_passes_through_stft(spatial, T, S):
+    """The tuned path's spatial passes at 256 x 256 feeding the STFT: moments against
+    the oracle (u8 frames, several windows, chunks smaller than the stream)."""
+    H = W = 256
+    n = T + 3 * S
+    fr = synth.random_frames(n, H, W, 8, seed=T + S + (1 if spatial == "asp" else 2))
+    p = oracle_params(spatial=spatial, z_m=0.3, T=T, stride=S, fs_hz=20000.0, band_lo_bin=2,
+                      band_hi_bin=T // 2 - 2, moments=ALL_MOMENTS, H=H, W=W)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="persistent", spatial_chunk=48))
+    ref = O.render(fr, p)
+    check_images(img, ref)
+    assert st["windows_rendered"] == ref.shape[0]
