@@ -477,9 +477,9 @@ __device__ __forceinline__ bool rw_wait(uint32_t mbar, uint32_t parity) {
 
 __global__ void __launch_bounds__(RW_NT, 3)
     k_row_warp(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s1map) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_tma[];  // TMA destinations: 128-byte aligned
   __shared__ __align__(8) unsigned long long full[2];
-  float2* tile0 = reinterpret_cast<float2*>(smem);
+  float2* tile0 = reinterpret_cast<float2*>(smem_tma);
   float2* tile1 = tile0 + RW_BT * RW_L;
   float2* tw2 = tile1 + RW_BT * RW_L;  // stage 2: w_256^(j m) at (m - 1) 16 + j
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -581,9 +581,9 @@ static cudaError_t launch_row_warp(const SpatialArgs& a, cudaStream_t s) {
 // written row-major [ky][x], coalesced.
 __global__ void __launch_bounds__(RW_NT, 3)
     k_row_asp(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s1map) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_tma[];  // TMA destinations: 128-byte aligned
   __shared__ __align__(8) unsigned long long full[2];
-  float2* tile0 = reinterpret_cast<float2*>(smem);
+  float2* tile0 = reinterpret_cast<float2*>(smem_tma);
   float2* tile1 = tile0 + RW_BT * RW_L;
   float2* tw2 = tile1 + RW_BT * RW_L;  // w_256^(j m) at (m - 1) 16 + j
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -684,9 +684,9 @@ __global__ void __launch_bounds__(PpCfg<L>::NT, (L <= 256 ? 768 / L : 1))
     k_col_ifft_tma(SpatialArgs a, int nitems, int strip_log2, const __grid_constant__ CUtensorMap s2map) {
   using C = PpCfg<L>;
   static_assert(C::BT == 16, "16-column strips");
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_tma[];  // TMA destinations: 128-byte aligned
   __shared__ __align__(8) unsigned long long full[2];
-  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* buf0 = reinterpret_cast<float2*>(smem_tma);
   float2* buf1 = buf0 + L * 16;
   float2* tws = buf1 + L * 16;
   const int tid = threadIdx.x;
