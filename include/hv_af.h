@@ -6,7 +6,7 @@
  * autofocus. The network replaces a plain z-sweep (hv_focus_sweep in hv.h:
  * angular-spectrum propagation to 64 distances, Tamura coefficient of each
  * image, the best distance as label), which also generates its training labels
- * and judges its error.
+ * and measures its error.
  *
  * Input: the network input of hv_af_features (hv.h), bfloat16 [n][1][128][128]
  * (raw 16-bit patterns), in device memory.
