@@ -454,19 +454,30 @@ def roofline_pca(w, res, peaks, force=None):
     elif kern == "projection":
         flops, byts = 8.0 * P * T * M, 8.0 * P * T
     elif kern == "jacobi_fp64":
-        # float64 work of the refinement sweeps over the whole eigensolver time (the
-        # float32 sweeps before them run on one 16-SM cluster, bound by barriers)
         sweeps = prof["pca_sweeps"] / nwin
         sweeps32 = prof.get("pca_sweeps_f32", 0) / nwin
-        per_sweep = (T - 1) * (T // 2) ** 2 * 96.0 + (T - 1) * T * (T // 2) * 32.0
-        flops, byts = sweeps * per_sweep, 0.0
+        per_sweep32 = (T - 1) * (T // 2) ** 2 * 96.0 + (T - 1) * T * (T // 2) * 32.0
+        if T <= 64:
+            # one CTA per window: float64 work = the congruence C' = Vf^H C Vf (M = C Vf,
+            # then the upper triangle) and the rotations of V in the refinement sweeps
+            # (20 flops per row and pair); the 2 x 2 blocks of C' are float32 there
+            per_sweep = (T - 1) * (T // 2) * T * 20.0
+            flops = sweeps * per_sweep + 8.0 * T ** 3 + 4.0 * T * T * (T + 1)
+        else:
+            # float64 work of the refinement sweeps over the whole eigensolver time (the
+            # float32 sweeps before them run on one 16-SM cluster, bound by barriers)
+            flops = sweeps * per_sweep32
+        byts = 0.0
         fp64_peak = alu_peaks()["fp64_tflops"]
         return {"bound": "alu", "achieved": round(flops / t / 1e12, 4), "peak": round(fp64_peak, 3),
                 "unit": "TFLOP/s (FP64)", "frac": round(flops / t / 1e12 / fp64_peak, 4),
-                "traffic": None, "kernel": "eigensolver (FP32 cyclic Jacobi, then FP64 refinement)",
+                "traffic": None,
+                "kernel": ("eigensolver (FP32 cyclic Jacobi, then refinement: FP64 diagonal and V, "
+                           "FP32 off-diagonal)" if T <= 64 else
+                           "eigensolver (FP32 cyclic Jacobi, then FP64 refinement)"),
                 "peak_source": alu_peaks()["source"] + "; nominal GB300 FP64 1.25 TFLOP/s",
                 "sweeps_per_window": round(sweeps, 2), "fp32_sweeps_per_window": round(sweeps32, 2),
-                "fp32_flops_per_window": round(sweeps32 * per_sweep),
+                "fp32_flops_per_window": round(sweeps32 * per_sweep32),
                 "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
     else:  # spatial: the S new frames each window propagates
         alg = algorithmic(w)

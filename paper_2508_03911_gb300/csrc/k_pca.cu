@@ -667,10 +667,12 @@ __global__ void k_pca_select(PcaArgs a) {
     if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
 }
 
-// One sweep's rounds of the CTA-local cyclic Jacobi on C (T x T) and V, for
-// float (RotF) or double (Rot) storage; returns the rotations performed.
-template <int T, class Real2, class R, class RotFn, class BlockFn, class RowFn>
-__device__ __forceinline__ unsigned local_sweep(Real2* C, Real2* V, R* rot, unsigned* cnt, RotFn rotfn,
+// One sweep's rounds of the CTA-local cyclic Jacobi on C (T x T) and V. The
+// rotation of the pair (i, j) in slot k is made by rotfn(i, j, k), which stores
+// it in rc[k] (applied to C) and rv[k] (applied to V; may be the same array);
+// returns the rotations performed.
+template <int T, class CM, class VM, class RC, class RV, class RotFn, class BlockFn, class RowFn>
+__device__ __forceinline__ unsigned local_sweep(CM* C, VM* V, const RC* rc, const RV* rv, unsigned* cnt, RotFn rotfn,
                                                 BlockFn blockfn, RowFn rowfn) {
   constexpr int NP = T / 2;
   const int tid = threadIdx.x;
@@ -679,19 +681,19 @@ __device__ __forceinline__ unsigned local_sweep(Real2* C, Real2* V, R* rot, unsi
   for (int r = 0; r < T - 1; ++r) {
     if (tid < NP) {
       const int i = rr_elem(tid, r, T), j = rr_elem(T - 1 - tid, r, T);
-      if (rotfn(C[i * T + i].x, C[j * T + j].x, C[i * T + j], rot[tid])) atomicAdd(cnt, 1u);
+      if (rotfn(i, j, tid)) atomicAdd(cnt, 1u);
     }
     __syncthreads();
     for (int e = tid; e < NP * NP + T * NP; e += blockDim.x) {
       if (e < NP * NP) {
         const int p = e / NP, q = e % NP;
-        if (rot[p].s == 0 && rot[q].s == 0) continue;
-        blockfn(C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[p],
-                rot[q], p == q);
+        if (rc[p].s == 0 && rc[q].s == 0) continue;
+        blockfn(C, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rc[p],
+                rc[q], p == q);
       } else {
         const int f = e - NP * NP, row = f / NP, q = f % NP;
-        if (rot[q].s == 0) continue;
-        rowfn(V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rot[q]);
+        if (rc[q].s == 0) continue;
+        rowfn(V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rv[q]);
       }
     }
     __syncthreads();
@@ -701,15 +703,77 @@ __device__ __forceinline__ unsigned local_sweep(Real2* C, Real2* V, R* rot, unsi
   return n;
 }
 
+// Float64 rotation of the refinement sweeps with its column factors
+// q10 = conj(ph) s and q11 = conj(ph) c precomputed (J = [[c, -s], [q10, q11]]).
+struct RotV {
+  double c, s;
+  double2 q10, q11;
+};
+
+// Columns (j0, j1) of row `row` of the float64 V times Jq.
+__device__ __forceinline__ void refine_vrow(double2* V, int T, int row, int j0, int j1, const RotV& Jq) {
+  const double2 v0 = V[row * T + j0], v1 = V[row * T + j1];
+  V[row * T + j0] = make_double2(fma(Jq.c, v0.x, fma(Jq.q10.x, v1.x, -Jq.q10.y * v1.y)),
+                                 fma(Jq.c, v0.y, fma(Jq.q10.x, v1.y, Jq.q10.y * v1.x)));
+  V[row * T + j1] = make_double2(fma(-Jq.s, v0.x, fma(Jq.q11.x, v1.x, -Jq.q11.y * v1.y)),
+                                 fma(-Jq.s, v0.y, fma(Jq.q11.x, v1.y, Jq.q11.y * v1.x)));
+}
+
+// Rotation of a refinement sweep for the pair (i, j): the diagonal d in float64,
+// the off-diagonal entry g in float32 (ag = |g|). The angle (tan theta = t, the root of
+// t^2 - 2 zeta t - 1 = 0 of smaller magnitude, zeta = (d_j - d_i) / (2 |g|)) is
+// taken in float32; the float64 factors c = (1 + t^2)^(-1/2) and ph = g / |g|
+// come from the float32 inverse square roots refined by one Newton step each,
+// so that J is unitary to about 1e-13 whatever the angle's own rounding. The
+// diagonal moves by t |g| (d_i + t |g|, d_j - t |g|, the exact result of the
+// rotation that zeroes g; an angle off by a relative 1e-7 changes it only in
+// the second order and leaves 1e-7 |g| behind in the zeroed entry).
+__device__ __forceinline__ bool refine_rot(double* d, int i, int j, float2 g, float ag, float tol, float floor_abs,
+                                           RotF& qf, RotV& qv) {
+  qf = RotF{1.f, 0.f, 1.f, 0.f};
+  qv = RotV{1.0, 0.0, make_double2(0.0, 0.0), make_double2(1.0, 0.0)};
+  const double al = d[i], be = d[j];
+  if (!(ag > tol * sqrtf(fabsf(float(al))) * sqrtf(fabsf(float(be))) && ag > floor_abs && ag > 0.f)) return false;
+  const float zeta = float(be - al) / (2.f * ag);
+  const float az = fabsf(zeta);
+  const float den = az > 1e18f ? 2.f * az : az + sqrtf(fmaf(az, az, 1.f));
+  const float t = (zeta >= 0.f ? -1.f : 1.f) / den;
+  if (t == 0.f) return false;
+  const double td = t;
+  const double x = fma(td, td, 1.0);
+  double c = rsqrtf(float(x));
+  c = fma(0.5 * c, fma(-x * c, c, 1.0), c);  // c <- c (3 - x c^2) / 2
+  const double s = td * c;
+  const double gx = g.x, gy = g.y, g2 = fma(gx, gx, gy * gy);
+  double rg = 1.f / ag;
+  rg = fma(0.5 * rg, fma(-g2 * rg, rg, 1.0), rg);  // rg -> g2^(-1/2)
+  const double px = gx * rg, py = gy * rg;
+  const double tg = td * (g2 * rg);
+  d[i] = al + tg;
+  d[j] = be - tg;
+  qv = RotV{c, s, make_double2(px * s, -py * s), make_double2(px * c, -py * c)};
+  qf = RotF{float(c), float(s), float(px), float(py)};
+  return true;
+}
+
 // Short windows (T <= 64): one CTA per window, the eigendecomposition in shared
-// memory in two phases. (1) Float32 cyclic Jacobi on a float copy of C, with the
-// rotations accumulated in Vf, until a sweep rotates nothing at 1e-6 relative.
-// (2) Float64: C' = Vf^H C Vf from the float64 C, then the float64 Jacobi
-// (float64 thresholds) on C' with V = Vf rotated further. Vf is unitary to about
-// 1e-6 only, so each eigenvalue is taken as the Rayleigh quotient
-// diag(V^H C V)_i / |v_i|^2 (second order in the vector's error) and the vectors
-// are normalised. Then the ranking and the sub-basis. GB300's float64 rate
-// makes the float32 phase about the whole cost of the first sweeps only.
+// memory in two phases, on C scaled by a power of two near 1 / max C_ii (exact,
+// and no float32 overflow whatever the data's range).
+// (1) Float32 cyclic Jacobi on a float copy of C, with the rotations accumulated
+// in Vf, until a sweep rotates nothing at 1e-6 relative.
+// (2) Refinement: C' = Vf^H C Vf in float64 from the float64 C, whose
+// off-diagonal entries are then about 1e-6 of its diagonal; Jacobi sweeps on C'
+// with the diagonal d in float64, the off-diagonal entries in float32 (every
+// float32 operation of a sweep combines off-diagonal entries only, so its
+// rounding is relative to them: ~1e-7 of 1e-6, far below the float32
+// covariance's own error) and V = Vf rotated further in float64 by J unitary to
+// float64 accuracy (refine_rot), until a sweep rotates nothing at 1e-14 or meets
+// no off-diagonal entry above 1e-12 of the trace. V's columns are then
+// C-orthogonal to the refinement's accuracy; Vf is unitary to about 1e-6 only,
+// so each eigenvalue is the Rayleigh quotient d_i / |v_i|^2 and the vectors are
+// normalised. Then the ranking and the sub-basis. GB300's float64 rate is 1/64
+// of float32, which is why only the diagonal, the rotation factors and V are
+// float64.
 template <int T>
 __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
   extern __shared__ double2 jsm[];
@@ -717,44 +781,50 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
   double2* C = jsm + T * T;     // C' (float64)
   float2* Vf = reinterpret_cast<float2*>(jsm + 2 * T * T);
   float2* Cf = reinterpret_cast<float2*>(RA);
-  __shared__ Rot rot[T / 2];
+  float2* Co = Vf;              // the refinement's float32 off-diagonal entries (Vf is dead by then)
+  __shared__ RotV rotv[T / 2];
   __shared__ RotF rotf[T / 2];
-  __shared__ unsigned cnt;
-  __shared__ double cmax;
-  __shared__ float cmaxf;
+  __shared__ double d[T];
+  __shared__ unsigned cnt, offbits;
+  __shared__ double scale_s, cmax_s, trace_s;
   const int w = blockIdx.x, tid = threadIdx.x;
   const double2* Cg = a.C + size_t(w) * T * T;
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const double2 v = Cg[e];
-    Cf[e] = make_float2(float(v.x), float(v.y));
-    Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
-  }
-  __syncthreads();
-  __shared__ double trace_s;
   if (tid == 0) {
     double m = 0.0, t = 0.0;
     for (int i = 0; i < T; ++i) {
       m = fmax(m, Cg[i * T + i].x);
       t += Cg[i * T + i].x;
     }
-    cmax = m;
-    cmaxf = float(m);
-    trace_s = t;
+    int ex = 0;
+    frexp(m, &ex);
+    scale_s = m > 0.0 ? ldexp(1.0, -ex) : 1.0;  // scaled max C_ii in [0.5, 1)
+    cmax_s = m * scale_s;
+    trace_s = t * scale_s;
+  }
+  __syncthreads();
+  const double scale = scale_s, cmax = cmax_s;  // of the scaled C
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const double2 v = Cg[e];
+    Cf[e] = make_float2(float(v.x * scale), float(v.y * scale));
+    Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   // (1) float32 sweeps until one rotates nothing at 1e-6 (relative, and of the
   // largest diagonal entry)
-  const float ftol = 1e-6f, ffloor = 1e-6f * cmaxf;
+  const float ftol = 1e-6f, ffloor = 1e-6f * float(cmax);
   int sweeps_f = 0;
   for (int sw = 0; sw < 20; ++sw) {
     const unsigned n = local_sweep<T>(
-        Cf, Vf, rotf, &cnt,
-        [&](float al, float be, float2 g, RotF& q) { return jacobi_rot_f(al, be, g, ftol, ffloor, q); },
+        Cf, Vf, rotf, rotf, &cnt,
+        [&](int i, int j, int k) {
+          return jacobi_rot_f(Cf[i * T + i].x, Cf[j * T + j].x, Cf[i * T + j], ftol, ffloor, rotf[k]);
+        },
         jacobi_block_f, jacobi_vrow_f);
     sweeps_f = sw + 1;
     if (n == 0) break;
   }
-  // (2) C' = Vf^H (C Vf) in float64: M = C Vf into RA (Cf is dead), then C' into C
+  // (2) C' = Vf^H (C Vf) in float64 (scaled): M = C Vf into RA (Cf is dead), then
+  // the upper triangle of C' into C
   for (int e = tid; e < T * T; e += blockDim.x) {
     const int r = e / T, c = e % T;
     double2 acc = make_double2(0.0, 0.0);
@@ -762,42 +832,50 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
       const float2 v = Vf[k * T + c];
       acc = zadd(acc, zmul(Cg[r * T + k], make_double2(v.x, v.y)));
     }
-    RA[e] = acc;
+    RA[e] = make_double2(acc.x * scale, acc.y * scale);
   }
   __syncthreads();
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const int r = e / T, c = e % T;
+  for (int u = tid; u < T * (T + 1) / 2; u += blockDim.x) {
+    int r = 0, rem = u;
+    while (rem >= T - r) {
+      rem -= T - r;
+      ++r;
+    }
+    const int c = r + rem;
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < T; ++k) {
       const float2 v = Vf[k * T + r];
       acc = zadd(acc, zmul(make_double2(v.x, -v.y), RA[k * T + c]));
     }
-    C[e] = acc;
+    C[r * T + c] = acc;
   }
   __syncthreads();
   double2* V = RA;  // V = Vf in float64, rotated further below
   for (int e = tid; e < T * T; e += blockDim.x) V[e] = make_double2(Vf[e].x, Vf[e].y);
-  for (int i = tid; i < T; i += blockDim.x) C[i * T + i].y = 0.0;
+  __syncthreads();  // Vf read for the last time: its storage takes the off-diagonal entries
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int r = e / T, c = e % T;
+    const double2 v = C[(r < c ? r : c) * T + (r < c ? c : r)];
+    Co[e] = r == c ? make_float2(float(v.x), 0.f) : make_float2(float(v.x), r < c ? float(v.y) : -float(v.y));
+    if (r == c) d[r] = v.x;
+  }
   __syncthreads();
-  // float64 sweeps until one rotates nothing or meets no off-diagonal entry above
-  // 1e-12 of the trace
-  __shared__ unsigned long long offbits64;
   const double trace64 = trace_s;
+  const float rtol = float(a.tol), rfloor = float(a.tol_abs * cmax);
   int sweeps_d = 0;
   for (int sw = 0; sw < a.max_sweeps; ++sw) {
-    if (tid == 0) offbits64 = 0ull;
+    if (tid == 0) offbits = 0u;
     const unsigned n = local_sweep<T>(
-        C, V, rot, &cnt,
-        [&](double al, double be, double2 g, Rot& q) {
-          atomicMax(&offbits64, static_cast<unsigned long long>(__double_as_longlong(sqrt(g.x * g.x + g.y * g.y))));
-          return jacobi_rot(al, be, g, a.tol, a.tol_abs * cmax, q);
+        Co, V, rotf, rotv, &cnt,
+        [&](int i, int j, int k) {
+          const float2 g = Co[i * T + j];
+          const float ag = hypotf(g.x, g.y);
+          atomicMax(&offbits, __float_as_uint(ag));  // non-negative floats order like their bits
+          return refine_rot(d, i, j, g, ag, rtol, rfloor, rotf[k], rotv[k]);
         },
-        [](double2* Cm, int TT, int i0, int i1, int j0, int j1, const Rot& Jp, const Rot& Jq, bool own) {
-          jacobi_block(Cm, Cm, TT, i0, i1, j0, j1, Jp, Jq, own);
-        },
-        jacobi_vrow);
+        jacobi_block_f, refine_vrow);
     sweeps_d = sw + 1;
-    const bool done = n == 0 || __longlong_as_double(static_cast<long long>(offbits64)) <= 1e-12 * trace64;
+    const bool done = n == 0 || double(__uint_as_float(offbits)) <= 1e-12 * trace64;
     __syncthreads();
     if (done) break;
   }
@@ -810,7 +888,7 @@ __global__ void __launch_bounds__(256) k_jacobi_small(PcaArgs a) {
   for (int i = tid; i < T; i += blockDim.x) {
     double n2 = 0.0;
     for (int t = 0; t < T; ++t) n2 += V[t * T + i].x * V[t * T + i].x + V[t * T + i].y * V[t * T + i].y;
-    lamv[i] = C[i * T + i].x / n2;
+    lamv[i] = d[i] / (n2 * scale);
     inrm[i] = 1.0 / sqrt(n2);
   }
   __syncthreads();
