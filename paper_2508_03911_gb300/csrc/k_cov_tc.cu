@@ -183,7 +183,9 @@ __global__ void __launch_bounds__(TC_NT, 1) k_cov_tc(PcaArgs a) {
       const int w = e >> 5, l = e & 31;
       const int f = 4 * w + (l & 3), kb = l >> 2;
       const int frame = isA ? ti * 64 + f : tj * BF + f;
-      const float2* fp = static_cast<const float2*>(a.tq.base) + ((size_t(a.tq.slot0) + frame) % a.tq.cap) * hw;
+      uint32_t slot = a.tq.slot0 + uint32_t(frame);  // slot0 < cap, frame < T <= cap (checked by launch_pca)
+      if (slot >= a.tq.cap) slot -= a.tq.cap;
+      const float2* fp = static_cast<const float2*>(a.tq.base) + size_t(slot) * hw;
       convert8(fp, p0 + kb * 8, p_end, f, kb, isA ? a_hi : b_hi, split ? (isA ? a_lo : b_lo) : nullptr);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

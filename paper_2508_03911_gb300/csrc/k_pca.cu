@@ -34,8 +34,12 @@ namespace hv {
 constexpr int COV_TS = 64;   // output tile (frames x frames)
 constexpr int COV_KS = 32;   // pixels per smem stage
 
+// Frame t of the ring from slot0 on. slot0 < cap and t < cap (launch_pca checks
+// both for every window of a launch), so one conditional subtraction wraps it.
 __device__ __forceinline__ const float2* frame_ptr(const RingRef& r, uint32_t t, size_t hw) {
-  return static_cast<const float2*>(r.base) + ((size_t(r.slot0) + t) % r.cap) * hw;
+  uint32_t slot = r.slot0 + t;
+  if (slot >= r.cap) slot -= r.cap;
+  return static_cast<const float2*>(r.base) + size_t(slot) * hw;
 }
 
 // Frame t of window w (windows start S frames apart).
@@ -1162,6 +1166,8 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   const size_t hw = size_t(a.W) * a.H;
   const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
   if (a.T % TS || TS % 16 || hw % 256 || a.T % PRJ_KS) return cudaErrorInvalidValue;
+  if (a.nwin == 0 || a.tq.slot0 >= a.tq.cap || uint64_t(a.nwin - 1) * a.wstride + a.T > a.tq.cap)
+    return cudaErrorInvalidValue;  // the frame addressing (frame_ptr) relies on both
   const int nT = a.T / TS;
   const dim3 g1(nT * (nT + 1) / 2, a.nchunks, a.nwin);
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
