@@ -436,10 +436,11 @@ def roofline_pca(w, res, peaks, force=None):
         entry["covariance"] = sub
         return entry
     if kern == "covariance" and w.get("precision", "fp32") != "fp32":
-        # tensor cores: algorithmic flops of the real Gram matrix G = Y Y^T (2T x 2T, K = P),
-        # times the products per step (3 for split-BF16), against the measured bf16 peak
+        # tensor cores: algorithmic flops of the symmetric half of the real Gram matrix
+        # G = Y Y^T (2T x 2T, K = P), times the products per step (3 for split-BF16),
+        # against the measured bf16 peak
         nprod = 3 if w["precision"] == "split_bf16" else 1
-        flops = 2.0 * (2 * T) * (2 * T) * P * nprod
+        flops = 1.0 * (2 * T) * (2 * T + 1) * P * nprod
         peak = (peaks or {}).get("bf16_tflops", 1906.8)
         tf = flops / t / 1e12
         return {"bound": "tensor", "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
@@ -450,31 +451,27 @@ def roofline_pca(w, res, peaks, force=None):
                 "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
                 "stage_ms_per_window": {k: round(v, 4) for k, v in st.items()}}
     if kern == "covariance":
-        flops, byts = 8.0 * P * T * T, 8.0 * P * T
+        # the Hermitian half (T (T + 1) / 2 entries, 8 flops per pixel each)
+        flops, byts = 4.0 * P * T * (T + 1), 8.0 * P * T
     elif kern == "projection":
         flops, byts = 8.0 * P * T * M, 8.0 * P * T
     elif kern == "jacobi_fp64":
         sweeps = prof["pca_sweeps"] / nwin
         sweeps32 = prof.get("pca_sweeps_f32", 0) / nwin
         per_sweep32 = (T - 1) * (T // 2) ** 2 * 96.0 + (T - 1) * T * (T // 2) * 32.0
-        if T <= 64:
-            # one CTA per window: float64 work = the congruence C' = Vf^H C Vf (M = C Vf,
-            # then the upper triangle) and the rotations of V in the refinement sweeps
-            # (20 flops per row and pair); the 2 x 2 blocks of C' are float32 there
-            per_sweep = (T - 1) * (T // 2) * T * 20.0
-            flops = sweeps * per_sweep + 8.0 * T ** 3 + 4.0 * T * T * (T + 1)
-        else:
-            # float64 work of the refinement sweeps over the whole eigensolver time (the
-            # float32 sweeps before them run on one 16-SM cluster, bound by barriers)
-            flops = sweeps * per_sweep32
+        # float64 work over the whole eigensolver time: the congruence C' = Vf^H C Vf
+        # (M = C Vf, then the upper triangle for T <= 64 or all of it) and the rotations
+        # of V in the refinement sweeps (20 flops per row and pair); the 2 x 2 blocks of
+        # C' are float32 there, and the float32 sweeps before them are bound by barriers
+        per_sweep = (T - 1) * (T // 2) * T * 20.0
+        congruence = 8.0 * T ** 3 + (4.0 * T * T * (T + 1) if T <= 64 else 8.0 * T ** 3)
+        flops = sweeps * per_sweep + congruence
         byts = 0.0
         fp64_peak = alu_peaks()["fp64_tflops"]
         return {"bound": "alu", "achieved": round(flops / t / 1e12, 4), "peak": round(fp64_peak, 3),
                 "unit": "TFLOP/s (FP64)", "frac": round(flops / t / 1e12 / fp64_peak, 4),
                 "traffic": None,
-                "kernel": ("eigensolver (FP32 cyclic Jacobi, then refinement: FP64 diagonal and V, "
-                           "FP32 off-diagonal)" if T <= 64 else
-                           "eigensolver (FP32 cyclic Jacobi, then FP64 refinement)"),
+                "kernel": "eigensolver (FP32 cyclic Jacobi, then refinement: FP64 diagonal and V, FP32 off-diagonal)",
                 "peak_source": alu_peaks()["source"] + "; nominal GB300 FP64 1.25 TFLOP/s",
                 "sweeps_per_window": round(sweeps, 2), "fp32_sweeps_per_window": round(sweeps32, 2),
                 "fp32_flops_per_window": round(sweeps32 * per_sweep32),

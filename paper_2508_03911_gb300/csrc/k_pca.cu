@@ -12,10 +12,14 @@
 //                  upper triangle over one pixel chunk (float32 FMA), partials
 //                  written per chunk (deterministic, no atomics)
 //   k_cov_reduce   sums the chunk partials in float64 -> C (full Hermitian), V = I
-//   k_jacobi       cooperative launch over all SMs: parallel cyclic (round-robin)
-//                  two-sided Jacobi in float64 until a sweep makes no rotation
-//                  (T > 64, one window)
-//   k_jacobi_small the same Jacobi for T <= 64, one CTA per window, C and V in
+//   k_jacobi_cluster, k_jacobi_f32
+//                  float32 phase of the long-window eigensolver (T > 64, one
+//                  window): parallel cyclic (round-robin) two-sided Jacobi on one
+//                  16-CTA cluster, or cooperative on a quarter of the SMs
+//   k_gemm_c64     float64 congruence C' = Vf^H C Vf
+//   k_jacobi_refine cooperative refinement sweeps on C' over all SMs: float64
+//                  diagonal and V, float32 off-diagonal entries
+//   k_jacobi_small both phases for T <= 64, one CTA per window, C and V in
 //                  shared memory, selection of the sub-basis fused
 //   k_pca_select   ranks eigenvalues (descending) and gathers the sub-basis
 //   k_project      Y = X V_s for 64-pixel tiles and E(p) = sum_j |Y_pj|^2
@@ -232,9 +236,10 @@ __device__ __forceinline__ bool jacobi_rot_f(float al, float be, float2 g, float
   return true;
 }
 
-__device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1, int j0, int j1, const RotF& Jp,
-                                               const RotF& Jq, bool own) {
-  const float2 b00 = C[i0 * T + j0], b01 = C[i0 * T + j1], b10 = C[i1 * T + j0], b11 = C[i1 * T + j1];
+// Float32 2 x 2 block update read from Cs and written to C (may be the same).
+__device__ __forceinline__ void jacobi_block_f2(const float2* Cs, float2* C, int T, int i0, int i1, int j0, int j1,
+                                                const RotF& Jp, const RotF& Jq, bool own) {
+  const float2 b00 = Cs[i0 * T + j0], b01 = Cs[i0 * T + j1], b10 = Cs[i1 * T + j0], b11 = Cs[i1 * T + j1];
   const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
   const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, q10)), m01 = cadd(cscale(b00, -Jq.s), cmul(b01, q11));
   const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, q10)), m11 = cadd(cscale(b10, -Jq.s), cmul(b11, q11));
@@ -253,6 +258,11 @@ __device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1,
   C[i1 * T + j1] = c11;
 }
 
+__device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1, int j0, int j1, const RotF& Jp,
+                                               const RotF& Jq, bool own) {
+  jacobi_block_f2(C, C, T, i0, i1, j0, j1, Jp, Jq, own);
+}
+
 __device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0, int j1, const RotF& Jq) {
   const float2 v0 = V[row * T + j0], v1 = V[row * T + j1];
   const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
@@ -260,76 +270,149 @@ __device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0,
   V[row * T + j1] = cadd(cscale(v0, -Jq.s), cmul(v1, q11));
 }
 
-// Cooperative cyclic Jacobi over all SMs with one grid barrier per round: every
-// CTA computes the rotations of all pairs itself (a deterministic function of
-// the current matrix, so all CTAs agree), then updates its share of the 2 x 2
-// blocks from one copy of C into the other (every entry is rewritten each round,
-// so the copies can alternate) and its share of the rows of V in place. The
-// rotation count of a sweep, identical in every CTA, ends the loop without a
-// further barrier.
-__global__ void __launch_bounds__(256) k_jacobi(PcaArgs a) {
+// Float64 rotation of the refinement sweeps with its column factors
+// q10 = conj(ph) s and q11 = conj(ph) c precomputed (J = [[c, -s], [q10, q11]]).
+struct RotV {
+  double c, s;
+  double2 q10, q11;
+};
+
+// Columns (j0, j1) of row `row` of the float64 V times Jq.
+__device__ __forceinline__ void refine_vrow(double2* V, int T, int row, int j0, int j1, const RotV& Jq) {
+  const double2 v0 = V[row * T + j0], v1 = V[row * T + j1];
+  V[row * T + j0] = make_double2(fma(Jq.c, v0.x, fma(Jq.q10.x, v1.x, -Jq.q10.y * v1.y)),
+                                 fma(Jq.c, v0.y, fma(Jq.q10.x, v1.y, Jq.q10.y * v1.x)));
+  V[row * T + j1] = make_double2(fma(-Jq.s, v0.x, fma(Jq.q11.x, v1.x, -Jq.q11.y * v1.y)),
+                                 fma(-Jq.s, v0.y, fma(Jq.q11.x, v1.y, Jq.q11.y * v1.x)));
+}
+
+// Rotation of a refinement sweep for the pair (i, j): the diagonal d in float64,
+// the off-diagonal entry g in float32 (ag = |g|). The angle (tan theta = t, the root of
+// t^2 - 2 zeta t - 1 = 0 of smaller magnitude, zeta = (d_j - d_i) / (2 |g|)) is
+// taken in float32; the float64 factors c = (1 + t^2)^(-1/2) and ph = g / |g|
+// come from the float32 inverse square roots refined by one Newton step each,
+// so that J is unitary to about 1e-13 whatever the angle's own rounding. The
+// diagonal moves by t |g| (d_i + t |g|, d_j - t |g|, the exact result of the
+// rotation that zeroes g; an angle off by a relative 1e-7 changes it only in
+// the second order and leaves 1e-7 |g| behind in the zeroed entry).
+__device__ __forceinline__ bool refine_rot(double* d, int i, int j, float2 g, float ag, float tol, float floor_abs,
+                                           RotF& qf, RotV& qv) {
+  qf = RotF{1.f, 0.f, 1.f, 0.f};
+  qv = RotV{1.0, 0.0, make_double2(0.0, 0.0), make_double2(1.0, 0.0)};
+  const double al = d[i], be = d[j];
+  if (!(ag > tol * sqrtf(fabsf(float(al))) * sqrtf(fabsf(float(be))) && ag > floor_abs && ag > 0.f)) return false;
+  const float zeta = float(be - al) / (2.f * ag);
+  const float az = fabsf(zeta);
+  const float den = az > 1e18f ? 2.f * az : az + sqrtf(fmaf(az, az, 1.f));
+  const float t = (zeta >= 0.f ? -1.f : 1.f) / den;
+  if (t == 0.f) return false;
+  const double td = t;
+  const double x = fma(td, td, 1.0);
+  double c = rsqrtf(float(x));
+  c = fma(0.5 * c, fma(-x * c, c, 1.0), c);  // c <- c (3 - x c^2) / 2
+  const double s = td * c;
+  const double gx = g.x, gy = g.y, g2 = fma(gx, gx, gy * gy);
+  double rg = 1.f / ag;
+  rg = fma(0.5 * rg, fma(-g2 * rg, rg, 1.0), rg);  // rg -> g2^(-1/2)
+  const double px = gx * rg, py = gy * rg;
+  const double tg = td * (g2 * rg);
+  d[i] = al + tg;
+  d[j] = be - tg;
+  qv = RotV{c, s, make_double2(px * s, -py * s), make_double2(px * c, -py * c)};
+  qf = RotF{float(c), float(s), float(px), float(py)};
+  return true;
+}
+
+// Refinement of the long-window eigensolver (T >= 128), cooperative over all SMs
+// with one grid barrier per round, on C' = Vf^H C Vf: the diagonal in float64 (a
+// copy in every CTA's shared memory, updated identically by every CTA), the
+// off-diagonal entries in float32 alternating between Cf and Cf2 (every entry is
+// rewritten each round), V in float64 -- the arithmetic of the short-window
+// refinement (refine_rot). Every CTA computes all rotations itself, a deterministic
+// function of the same data, so all agree; the rotation count and the largest
+// off-diagonal entry of a sweep, identical in every CTA, end the loop without a
+// further barrier. C' is scaled by a power of two near 1 / max C'_ii first; the
+// unscaled diagonal goes back into a.C for the eigenvalue selection.
+__global__ void __launch_bounds__(256) k_jacobi_refine(PcaArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int T = a.T, NP = T / 2;
-  __shared__ Rot rot[256];
-  __shared__ unsigned cnt;
+  __shared__ RotF rf[256];
+  __shared__ RotV rv[256];
+  __shared__ double d[512];
+  __shared__ unsigned cnt, offbits;
+  __shared__ double scale_s, cmax_s, trace_s;
   const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const size_t gsz = size_t(gridDim.x) * blockDim.x;
-  const double floor_abs = a.tol_abs * a.cmax[0];
-  // optional early end: every off-diagonal entry met in a sweep below stop_rel x trace
-  __shared__ unsigned long long offbits;
-  double trace = 0.0;
-  if (a.stop_rel > 0.0)
-    for (int i = 0; i < T; ++i) trace += a.C[size_t(i) * T + i].x;
-  double2* Cs = a.C;
-  double2* Cd = a.C2;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) d[i] = a.C[size_t(i) * T + i].x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0, t = 0.0;
+    for (int i = 0; i < T; ++i) {
+      m = fmax(m, d[i]);
+      t += d[i];
+    }
+    int ex = 0;
+    frexp(m, &ex);
+    scale_s = m > 0.0 ? ldexp(1.0, -ex) : 1.0;
+    cmax_s = m * scale_s;
+    trace_s = t * scale_s;
+  }
+  __syncthreads();
+  const double scale = scale_s;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) d[i] *= scale;
+  for (size_t e = gtid; e < size_t(T) * T; e += gsz) {  // Hermitian by construction
+    const int r = int(e / T), c = int(e % T);
+    const double2 v = a.C[size_t(r < c ? r : c) * T + (r < c ? c : r)];
+    a.Cf[e] = make_float2(float(v.x * scale), r == c ? 0.f : (r < c ? float(v.y * scale) : -float(v.y * scale)));
+  }
+  grid.sync();
+  const float rtol = float(a.tol), rfloor = float(a.tol_abs * cmax_s);
+  float2* Cs = a.Cf;
+  float2* Cd = a.Cf2;
   int sweeps = 0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     if (threadIdx.x == 0) {
       cnt = 0;
-      offbits = 0ull;
+      offbits = 0u;
     }
     for (int r = 0; r < T - 1; ++r) {
-      __syncthreads();  // rot of the previous round fully used; cnt reset visible
+      __syncthreads();  // rotations of the previous round fully used; cnt reset visible
       for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         const int i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
-        Rot q;
-        const double2 g = Cs[i * T + j];
-        if (jacobi_rot(Cs[i * T + i].x, Cs[j * T + j].x, g, a.tol, floor_abs, q)) atomicAdd(&cnt, 1u);
-        atomicMax(&offbits, static_cast<unsigned long long>(__double_as_longlong(sqrt(g.x * g.x + g.y * g.y))));
-        rot[p] = q;
+        const float2 g = Cs[size_t(i) * T + j];
+        const float ag = hypotf(g.x, g.y);
+        atomicMax(&offbits, __float_as_uint(ag));  // non-negative floats order like their bits
+        if (refine_rot(d, i, j, g, ag, rtol, rfloor, rf[p], rv[p])) atomicAdd(&cnt, 1u);
       }
       __syncthreads();
       const size_t nblk = size_t(NP) * NP;
       for (size_t e = gtid; e < nblk + size_t(T) * NP; e += gsz) {
         if (e < nblk) {
           const int p = int(e / NP), q = int(e % NP);
-          jacobi_block(Cs, Cd, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
-                       rr_elem(T - 1 - q, r, T), rot[p], rot[q], p == q);
+          jacobi_block_f2(Cs, Cd, T, rr_elem(p, r, T), rr_elem(T - 1 - p, r, T), rr_elem(q, r, T),
+                          rr_elem(T - 1 - q, r, T), rf[p], rf[q], p == q);
         } else {
           const size_t f = e - nblk;
           const int row = int(f / NP), q = int(f % NP);
-          const Rot& Jq = rot[q];
-          if (Jq.s == 0.0) continue;
-          jacobi_vrow(a.V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), Jq);
+          if (rf[q].s == 0.f) continue;
+          refine_vrow(a.V, T, row, rr_elem(q, r, T), rr_elem(T - 1 - q, r, T), rv[q]);
         }
       }
       grid.sync();
-      double2* t = Cs;
+      float2* t = Cs;
       Cs = Cd;
       Cd = t;
     }
     sweeps = sweep + 1;
     __syncthreads();
     // a sweep without any rotation, or below the early-end bound: converged (same in every CTA)
-    const bool done = cnt == 0 || (a.stop_rel > 0.0 && __longlong_as_double(static_cast<long long>(offbits)) <=
-                                                          a.stop_rel * trace);
+    const bool done = cnt == 0 || (a.stop_rel > 0.0 && double(__uint_as_float(offbits)) <= a.stop_rel * trace_s);
     __syncthreads();  // every thread has read cnt and offbits before the next sweep resets them
     if (done) break;
   }
-  // the eigenvalues (diagonal) into a.C, where the selection reads them
-  if (Cs != a.C)
-    for (size_t i = gtid; i < size_t(T); i += gsz) a.C[i * T + i] = Cs[i * T + i];
-  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // float64 sweeps
+  if (blockIdx.x == 0)  // the Rayleigh numerators (V^H C V)_ii, unscaled, for the selection
+    for (int i = threadIdx.x; i < T; i += blockDim.x) a.C[size_t(i) * T + i] = make_double2(d[i] / scale, 0.0);
+  if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // refinement sweeps
 }
 
 // First phase of the large-window eigensolver: the same cooperative cyclic
@@ -705,59 +788,6 @@ __device__ __forceinline__ unsigned local_sweep(CM* C, VM* V, const RC* rc, cons
   const unsigned n = *cnt;
   __syncthreads();
   return n;
-}
-
-// Float64 rotation of the refinement sweeps with its column factors
-// q10 = conj(ph) s and q11 = conj(ph) c precomputed (J = [[c, -s], [q10, q11]]).
-struct RotV {
-  double c, s;
-  double2 q10, q11;
-};
-
-// Columns (j0, j1) of row `row` of the float64 V times Jq.
-__device__ __forceinline__ void refine_vrow(double2* V, int T, int row, int j0, int j1, const RotV& Jq) {
-  const double2 v0 = V[row * T + j0], v1 = V[row * T + j1];
-  V[row * T + j0] = make_double2(fma(Jq.c, v0.x, fma(Jq.q10.x, v1.x, -Jq.q10.y * v1.y)),
-                                 fma(Jq.c, v0.y, fma(Jq.q10.x, v1.y, Jq.q10.y * v1.x)));
-  V[row * T + j1] = make_double2(fma(-Jq.s, v0.x, fma(Jq.q11.x, v1.x, -Jq.q11.y * v1.y)),
-                                 fma(-Jq.s, v0.y, fma(Jq.q11.x, v1.y, Jq.q11.y * v1.x)));
-}
-
-// Rotation of a refinement sweep for the pair (i, j): the diagonal d in float64,
-// the off-diagonal entry g in float32 (ag = |g|). The angle (tan theta = t, the root of
-// t^2 - 2 zeta t - 1 = 0 of smaller magnitude, zeta = (d_j - d_i) / (2 |g|)) is
-// taken in float32; the float64 factors c = (1 + t^2)^(-1/2) and ph = g / |g|
-// come from the float32 inverse square roots refined by one Newton step each,
-// so that J is unitary to about 1e-13 whatever the angle's own rounding. The
-// diagonal moves by t |g| (d_i + t |g|, d_j - t |g|, the exact result of the
-// rotation that zeroes g; an angle off by a relative 1e-7 changes it only in
-// the second order and leaves 1e-7 |g| behind in the zeroed entry).
-__device__ __forceinline__ bool refine_rot(double* d, int i, int j, float2 g, float ag, float tol, float floor_abs,
-                                           RotF& qf, RotV& qv) {
-  qf = RotF{1.f, 0.f, 1.f, 0.f};
-  qv = RotV{1.0, 0.0, make_double2(0.0, 0.0), make_double2(1.0, 0.0)};
-  const double al = d[i], be = d[j];
-  if (!(ag > tol * sqrtf(fabsf(float(al))) * sqrtf(fabsf(float(be))) && ag > floor_abs && ag > 0.f)) return false;
-  const float zeta = float(be - al) / (2.f * ag);
-  const float az = fabsf(zeta);
-  const float den = az > 1e18f ? 2.f * az : az + sqrtf(fmaf(az, az, 1.f));
-  const float t = (zeta >= 0.f ? -1.f : 1.f) / den;
-  if (t == 0.f) return false;
-  const double td = t;
-  const double x = fma(td, td, 1.0);
-  double c = rsqrtf(float(x));
-  c = fma(0.5 * c, fma(-x * c, c, 1.0), c);  // c <- c (3 - x c^2) / 2
-  const double s = td * c;
-  const double gx = g.x, gy = g.y, g2 = fma(gx, gx, gy * gy);
-  double rg = 1.f / ag;
-  rg = fma(0.5 * rg, fma(-g2 * rg, rg, 1.0), rg);  // rg -> g2^(-1/2)
-  const double px = gx * rg, py = gy * rg;
-  const double tg = td * (g2 * rg);
-  d[i] = al + tg;
-  d[j] = be - tg;
-  qv = RotV{c, s, make_double2(px * s, -py * s), make_double2(px * c, -py * c)};
-  qf = RotF{float(c), float(s), float(px), float(py)};
-  return true;
 }
 
 // Short windows (T <= 64): one CTA per window, the eigendecomposition in shared
@@ -1205,7 +1235,7 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_refine, 256, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     void* args[] = {&a};
@@ -1234,7 +1264,7 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     b.max_sweeps = 2;
     b.stop_rel = 1e-12;
     void* bargs[] = {&b};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(nsm), dim3(256), bargs, 0, s);
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_refine), dim3(nsm), dim3(256), bargs, 0, s);
     if (e != cudaSuccess) return e;
     k_pca_select<<<1, 256, 0, s>>>(a);
     *launches += 5;
