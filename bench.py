@@ -80,7 +80,8 @@ WORKLOADS = {
         scene="scene_stream_fresnel"),
     "pca_512_t256": dict(
         desc="512x512 uint16 (12-bit) frames, ASP z=0.40 m, PCA over windows of T=256 (stride 256): "
-             "FP32 covariance, FP64 Jacobi, energy of the projection on eigenvectors 2..64; "
+             "FP32 covariance, Jacobi eigensolver (FP32 sweeps, then refinement with FP64 diagonal and "
+             "eigenvectors), energy of the projection on eigenvectors 2..64; "
              "1,024 frames (4 windows) per step",
         N=512, bits=12, spatial="asp", z=0.40, T=256, S=256, fs=20000.0, band=(0, 0),
         moments=(), temporal="pca", pca=(2, 64), batch=1024, batches=1, pool=256,

@@ -206,7 +206,8 @@ typedef struct {
   double pca_cov_ms;          /* PCA: covariance (partials and reduction)           */
   double pca_eig_ms;          /* PCA: Jacobi eigendecomposition and selection       */
   double pca_proj_ms;         /* PCA: projection and energy                         */
-  uint64_t pca_sweeps;        /* PCA: float64 Jacobi sweeps summed over recorded windows */
+  uint64_t pca_sweeps;        /* PCA: refinement sweeps (float64 diagonal and eigenvectors,
+                                 float32 off-diagonal) summed over recorded windows */
   uint64_t pca_sweeps_f32;    /* PCA: float32 Jacobi sweeps (first phase) summed likewise */
 } hv_profile;
 

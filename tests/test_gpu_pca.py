@@ -1,5 +1,5 @@
-"""GPU parity of the PCA temporal analysis (covariance, FP64 Jacobi, projection
-energy) against the FP64 oracle.
+"""GPU parity of the PCA temporal analysis (covariance, Jacobi eigensolver with an
+FP64-accurate refinement, projection energy) against the FP64 oracle.
 
 Bars: the energy image E within relative L2 1e-4; eigenvalues within 1e-6 of
 the largest eigenvalue (absolute; the covariance is accumulated from float32
@@ -113,7 +113,7 @@ def pca_scene_window():
 
 def test_pca_batched_many_windows():
     """Short windows are batched: all windows of one render in one launch per kernel
-    (one CTA per window for the FP64 Jacobi), overlapping and non-overlapping.
+    (one CTA per window for the eigensolver), overlapping and non-overlapping.
 
     The frames come from the Doppler scene, whose spectrum separates the sub-basis
     2..3 from its neighbours by >= 1e-2 lam_1. The projector onto the sub-basis then
