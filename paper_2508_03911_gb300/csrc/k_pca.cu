@@ -801,7 +801,7 @@ __device__ __forceinline__ unsigned local_sweep(CM* C, VM* V, const RC* rc, cons
 // float32 operation of a sweep combines off-diagonal entries only, so its
 // rounding is relative to them: ~1e-7 of 1e-6, far below the float32
 // covariance's own error) and V = Vf rotated further in float64 by J unitary to
-// float64 accuracy (refine_rot), until a sweep rotates nothing at 1e-14 or meets
+// ~1e-13 (refine_rot), until a sweep rotates nothing at 1e-14 or meets
 // no off-diagonal entry above 1e-12 of the trace. V's columns are then
 // C-orthogonal to the refinement's accuracy; Vf is unitary to about 1e-6 only,
 // so each eigenvalue is the Rayleigh quotient d_i / |v_i|^2 and the vectors are
