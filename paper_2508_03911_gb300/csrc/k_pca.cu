@@ -151,76 +151,15 @@ __device__ __forceinline__ int rr_elem(int k, int r, int T) {
   return k == 0 ? 0 : ((k - 1 + r) % (T - 1)) + 1;
 }
 
-struct Rot {  // J = [[c, -s], [conj(ph) s, conj(ph) c]]
-  double c, s, px, py;
-};
-
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// Rotation J that zeroes the off-diagonal of the Hermitian 2 x 2 block
-// [[al, g], [conj(g), be]] (J = P R, P = diag(1, conj(g)/|g|), R a real rotation
-// with tan(2 theta) = 2|g| / (al - be)); identity when |g| is below either bound.
-__device__ __forceinline__ bool jacobi_rot(double al, double be, double2 g, double tol, double floor_abs,
-                                           Rot& q) {
-  const double ag = sqrt(g.x * g.x + g.y * g.y);
-  q = Rot{1.0, 0.0, 1.0, 0.0};
-  if (!(ag > tol * sqrt(fabs(al * be)) && ag > floor_abs && ag > 0.0)) return false;
-  const double zeta = (be - al) / (2.0 * ag);
-  const double t = -(zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t);
-  q = Rot{c, t * c, g.x / ag, g.y / ag};
-  return true;
-}
-
-// B <- Jp^H B Jq for the 2 x 2 block of rows (i0, i1) and columns (j0, j1) of the
-// row-major T x T matrix, read from Cs and written to Cd (may be the same);
-// `own` marks the pair's own diagonal block.
-__device__ __forceinline__ void jacobi_block(const double2* Cs, double2* C, int T, int i0, int i1, int j0, int j1,
-                                             const Rot& Jp, const Rot& Jq, bool own) {
-  const double2 b00 = Cs[i0 * T + j0], b01 = Cs[i0 * T + j1];
-  const double2 b10 = Cs[i1 * T + j0], b11 = Cs[i1 * T + j1];
-  const double2 qph = make_double2(Jq.px, -Jq.py);  // conj(ph_q)
-  const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
-  const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
-  const double2 m00 = zadd(make_double2(b00.x * Jq.c, b00.y * Jq.c), zmul(b01, q10));
-  const double2 m01 = zadd(make_double2(-b00.x * Jq.s, -b00.y * Jq.s), zmul(b01, q11));
-  const double2 m10 = zadd(make_double2(b10.x * Jq.c, b10.y * Jq.c), zmul(b11, q10));
-  const double2 m11 = zadd(make_double2(-b10.x * Jq.s, -b10.y * Jq.s), zmul(b11, q11));
-  const double2 ph = make_double2(Jp.px, Jp.py);  // Jp^H = [[c, ph s], [-s, ph c]]
-  const double2 p01 = make_double2(ph.x * Jp.s, ph.y * Jp.s);
-  const double2 p11 = make_double2(ph.x * Jp.c, ph.y * Jp.c);
-  double2 c00 = zadd(make_double2(Jp.c * m00.x, Jp.c * m00.y), zmul(p01, m10));
-  double2 c01 = zadd(make_double2(Jp.c * m01.x, Jp.c * m01.y), zmul(p01, m11));
-  double2 c10 = zadd(make_double2(-Jp.s * m00.x, -Jp.s * m00.y), zmul(p11, m10));
-  double2 c11 = zadd(make_double2(-Jp.s * m01.x, -Jp.s * m01.y), zmul(p11, m11));
-  if (own) {  // exactly diagonal, real diagonal
-    c01 = make_double2(0.0, 0.0);
-    c10 = make_double2(0.0, 0.0);
-    c00.y = 0.0;
-    c11.y = 0.0;
-  }
-  C[i0 * T + j0] = c00;
-  C[i0 * T + j1] = c01;
-  C[i1 * T + j0] = c10;
-  C[i1 * T + j1] = c11;
-}
-
-// Columns (j0, j1) of row `row` of V times Jq.
-__device__ __forceinline__ void jacobi_vrow(double2* V, int T, int row, int j0, int j1, const Rot& Jq) {
-  const double2 v0 = V[row * T + j0], v1 = V[row * T + j1];
-  const double2 qph = make_double2(Jq.px, -Jq.py);
-  const double2 q10 = make_double2(qph.x * Jq.s, qph.y * Jq.s);
-  const double2 q11 = make_double2(qph.x * Jq.c, qph.y * Jq.c);
-  V[row * T + j0] = zadd(make_double2(v0.x * Jq.c, v0.y * Jq.c), zmul(v1, q10));
-  V[row * T + j1] = zadd(make_double2(-v0.x * Jq.s, -v0.y * Jq.s), zmul(v1, q11));
-}
-
-// Float32 rotation helpers of the float32 phases (same
-// formulas as the float64 ones above).
+// Rotation J = [[c, -s], [conj(ph) s, conj(ph) c]] (c, s real, |ph| = 1) that
+// zeroes the off-diagonal of the Hermitian 2 x 2 block [[al, g], [conj(g), be]]:
+// J = P R, P = diag(1, conj(g)/|g|), R a real rotation with tan(2 theta) =
+// 2|g| / (al - be); identity when |g| is below either bound.
 struct RotF {
   float c, s, px, py;
 };
@@ -236,7 +175,9 @@ __device__ __forceinline__ bool jacobi_rot_f(float al, float be, float2 g, float
   return true;
 }
 
-// Float32 2 x 2 block update read from Cs and written to C (may be the same).
+// B <- Jp^H B Jq for the 2 x 2 block of rows (i0, i1) and columns (j0, j1) of the
+// row-major T x T matrix, read from Cs and written to C (may be the same); `own`
+// marks the pair's own diagonal block, whose off-diagonal is set to zero.
 __device__ __forceinline__ void jacobi_block_f2(const float2* Cs, float2* C, int T, int i0, int i1, int j0, int j1,
                                                 const RotF& Jp, const RotF& Jq, bool own) {
   const float2 b00 = Cs[i0 * T + j0], b01 = Cs[i0 * T + j1], b10 = Cs[i1 * T + j0], b11 = Cs[i1 * T + j1];
@@ -263,6 +204,7 @@ __device__ __forceinline__ void jacobi_block_f(float2* C, int T, int i0, int i1,
   jacobi_block_f2(C, C, T, i0, i1, j0, j1, Jp, Jq, own);
 }
 
+// Columns (j0, j1) of row `row` of V times Jq.
 __device__ __forceinline__ void jacobi_vrow_f(float2* V, int T, int row, int j0, int j1, const RotF& Jq) {
   const float2 v0 = V[row * T + j0], v1 = V[row * T + j1];
   const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
