@@ -107,7 +107,7 @@ typedef struct {
                                  propagation (Sec. VI-B.1): spatial frequencies whose
                                  radius sqrt((m/W)^2 + (n/H)^2) in cycles per pixel is
                                  below this cutoff are zeroed; 0 = off. Folded into
-                                 the transfer function. hv_spatial_static ignores it. */
+                                 the transfer function. */
 } hv_params;
 
 /* Spatial kernel selection: automatic = the autotuner's choice when tuned = 1,
@@ -407,23 +407,29 @@ hv_status hv_group_close(hv_group* g);
  * counterpart; it is the same transform as HV_TEMPORAL_NONE rendering.
  *
  * `frames`: device pointer to n raw frames (uint8 or uint16 by pixel_bits),
- * p->width x p->height, row-major, contiguous. `out`: device pointer to
- * n * width * height complex values (2 floats each, re then im). Only the
- * spatial fields of `p` are read (width, height, spatial, z_m, lambda_m,
- * pitch_x_m, pitch_y_m, fftshift). Work is queued on `stream` (NULL = the
- * default stream); the caller keeps ownership of both buffers.
+ * p->width x p->height, row-major, contiguous; 2-byte aligned for 16-bit
+ * pixels. `out`: device pointer to n * width * height complex values (2 floats
+ * each, re then im), 8-byte aligned. Only the spatial fields of `p` are read
+ * (width, height, spatial, z_m, lambda_m, pitch_x_m, pitch_y_m, fftshift,
+ * highpass_cpp). Work is queued on `stream` (NULL = the default stream); the
+ * caller keeps ownership of both buffers.
  *
  * Scratch (tables and the intermediates of the 2-D FFT passes, about 14 MiB)
  * is a file-scope __device__ array that every GPU loading the library holds
- * until exit. The first call on a device resolves that array's device address
- * (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture. Every call shares the array and leaves its
- * contents behind; nothing in it needs to start at zero. Calls whose GPU work
- * may overlap race on it, so order them on one stream or with events.
+ * until exit. The first call on a device -- and the first call after the
+ * current driver context changed, e.g. after cudaDeviceReset -- resolves that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that call before any stream capture. Every call shares the array and
+ * leaves its contents behind; nothing in it needs to start at zero. Calls
+ * whose GPU work may overlap race on it, so order them on one stream or with
+ * events.
  *
- * Errors: HV_ERR_ARG for NULL pointers, n = 0, width or height not a power of
- * two in [16, 512], n * width * height > HV_STATIC_MAX_PIXELS, or invalid
- * optics; HV_ERR_CUDA if a CUDA call fails. No error text is recorded. */
+ * Errors: HV_ERR_ARG for NULL pointers, misaligned pointers, n = 0, width or
+ * height not a power of two in [16, 512], n * width * height >
+ * HV_STATIC_MAX_PIXELS, invalid optics, or a high-pass cutoff with a transform
+ * other than ASP; HV_ERR_CUDA if a CUDA call fails, or if a CUDA error was
+ * already pending on the calling thread when the call began (it is left
+ * pending for the caller). No error text is recorded. */
 hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, uint32_t n, const hv_params* p,
                             float* out, void* stream);
 

@@ -17,9 +17,11 @@
 // and the intermediates it reads. Calls whose GPU work overlaps (different
 // streams, no ordering between them) race on the array; order them on one
 // stream or with events.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/hv.h"
@@ -42,7 +44,28 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Resolved address of the array per device, with the driver context it was
+// resolved in: a different current context (after cudaDeviceReset, or a
+// non-primary context made current by the caller) has its own copy of the
+// module, so the address is resolved again there.
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// cuCtxGetCurrent from the driver, resolved once through the runtime (no link
+// dependency on libcuda). NULL when the driver does not offer it.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
 
 __host__ __device__ size_t packed_offset(uint32_t L) {  // twiddle tables packed by increasing length from 8
   size_t off = 0;
@@ -59,6 +82,7 @@ struct TableArgs {
   int spatial, fftshift;
   uint32_t W, H;
   double z, lam, dx, dy;
+  double highpass;  // cutoff in cycles per pixel, 0 = off
 };
 
 // Twiddles, chirp factors and the transposed transfer function, in float64 on
@@ -103,8 +127,11 @@ __global__ void k_static_tables(TableArgs a) {
       const double fx = 2.0 * M_PI * mx / (a.W * a.dx);
       const double fy = 2.0 * M_PI * my / (a.H * a.dy);
       const double kz2 = k * k - fx * fx - fy * fy;
+      // the high-pass filter after propagation zeroes the spectrum below the cutoff radius
+      const double rx = mx / a.W, ry = my / a.H;
+      const bool passed = !(a.highpass > 0.0) || rx * rx + ry * ry >= a.highpass * a.highpass;
       float2 v = make_float2(0.f, 0.f);
-      if (kz2 >= 0) {
+      if (kz2 >= 0 && passed) {
         const double scale = 1.0 / (double(a.W) * double(a.H));
         double s, c;
         sincos(a.z * sqrt(kz2), &s, &c);
@@ -122,6 +149,10 @@ extern "C" hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, 
   if (!frames || !out || !p || n == 0) return HV_ERR_ARG;
   if (p->struct_size != sizeof(hv_params)) return HV_ERR_ARG;
   if (pixel_bits != 8 && pixel_bits != 16) return HV_ERR_ARG;
+  // the kernels store complex values as 8-byte pairs and read 16-bit pixels as
+  // 2-byte words: a misaligned pointer would fault on the device
+  if ((reinterpret_cast<uintptr_t>(out) & 7u) != 0) return HV_ERR_ARG;
+  if (pixel_bits == 16 && (reinterpret_cast<uintptr_t>(frames) & 1u) != 0) return HV_ERR_ARG;
   const uint32_t W = p->width, H = p->height;
   if (!pow2_in(W, 16, 512) || !pow2_in(H, 16, 512)) return HV_ERR_ARG;
   if (uint64_t(n) * W * H > HV_STATIC_MAX_PIXELS) return HV_ERR_ARG;
@@ -132,17 +163,27 @@ extern "C" hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, 
       return HV_ERR_ARG;
     if (p->spatial == HV_SPATIAL_FRESNEL && p->z_m == 0.0) return HV_ERR_ARG;
   }
+  if (!(p->highpass_cpp >= 0.0) || (p->highpass_cpp > 0.0 && p->spatial != HV_SPATIAL_ASP)) return HV_ERR_ARG;
+  // an error left pending by the caller's earlier runtime calls is theirs: report
+  // it without clearing it rather than mistake it for a failure of this call
+  if (cudaPeekAtLastError() != cudaSuccess) return HV_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HV_ERR_CUDA;
-  // Set-up, once per device with that device current: the host cannot use the
-  // array's name as a device address, so resolve the address the kernels get.
+  // Set-up, once per device (and driver context) with that device current: the
+  // host cannot use the array's name as a device address, so resolve the address
+  // the kernels get.
+  CUcontext ctx = nullptr;
+  if (CtxGetCurrentFn f = ctx_get_current()) {
+    if (f(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  }
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return HV_ERR_CUDA;
       g_scratch_addr[dev] = ptr;
+      g_scratch_ctx[dev] = ctx;
     }
     base = g_scratch_addr[dev];
   }
@@ -155,8 +196,9 @@ extern "C" hv_status hv_spatial_static(const void* frames, uint32_t pixel_bits, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   TableArgs ta{tw, chirp, htab, p->spatial, p->fftshift, W, H, p->z_m, p->lambda_m, p->pitch_x_m,
-               p->pitch_y_m};
+               p->pitch_y_m, p->highpass_cpp};
   k_static_tables<<<256, 256, 0, s>>>(ta);
+  // no error was pending before the launch, so one now is this launch's
   if (cudaGetLastError() != cudaSuccess) return HV_ERR_CUDA;
 
   SpatialArgs sa{};
