@@ -112,7 +112,7 @@ WORKLOADS["autofocus_256"] = dict(
 # conv: 2 * CI * 9 * CO * HO * WO per layer; dense 2 * 64 * 32 + 2 * 32
 AF_FLOPS = (2 * 1 * 9 * 16 * 64 * 64 + 2 * 16 * 9 * 32 * 32 * 32 + 2 * 32 * 9 * 64 * 16 * 16
             + 2 * 64 * 9 * 64 * 8 * 8 + 2 * 64 * 32 + 2 * 32)
-DEFAULT = "stream_fresnel_256_t512_s64"
+DEFAULT = "asp_stft_256_t512_s512"
 METRIC = "raw frames/s rendered"
 
 
@@ -370,10 +370,16 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     value = job_value(world, args.steps, frames_per_step, elapsed_ms / 1e3)
     launches = stats1["kernel_launches"] - stats0["kernel_launches"]
     r.close()
+    library = None
+    if not quick and not args.no_library and rank == 0:
+        library = run_library(w, args, pool_dev, stream)
 
     if args.no_e2e or quick:
-        return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
-                    clocks=clk, e2e=None, frames_per_step=frames_per_step, tuning=tuning)
+        out = dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
+                   clocks=clk, e2e=None, frames_per_step=frames_per_step, tuning=tuning)
+        if library:
+            out["library"] = library
+        return out
     # ----- end-to-end through host buffers (pinned frames in, images out)
     host_pool = pool_t.repeat(reps, 1, 1).contiguous().pin_memory()
     r2 = open_renderer()
@@ -412,11 +418,14 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     e2e_value = job_value(world, e2e_steps, frames_per_step, e2e_s)
     r2.close()
 
-    return dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
+    out = dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
                 clocks=clk, e2e=dict(value=e2e_value, unit="frames/s",
                                      h2d_bytes_per_step=h2d // e2e_steps,
                                      d2h_bytes_per_step=d2h // e2e_steps),
                 frames_per_step=frames_per_step, tuning=tuning)
+    if library:
+        out["library"] = library
+    return out
 
 
 def roofline_pca(w, res, peaks, force=None):
@@ -543,48 +552,197 @@ def roofline(w, res, peaks):
 
 
 # -------------------------------------------------------- oracle timing
+#
+# The oracle's steady-state rate on a workload. In steady state every raw frame is
+# propagated once and one window is analysed every S frames, so
+#     frames/s = 1 / (t_spatial per frame + t_window / S).
+# t_spatial is timed on a sample of frames, t_window on one window (or on a
+# fraction of its pixel rows, scaled up: the STFT is per pixel). Both steps are
+# the oracle's own functions (hv_oracle.spatial / stft_moments / pca), run in
+# worker processes started with `spawn` (safe after CUDA is in use): frames are
+# spread over the workers for the spatial step, pixel-row tiles of the window for
+# the STFT; a PCA window runs in one worker whose BLAS may use every thread it is
+# given. The propagated window sits in shared memory (no copies in the timed
+# region). Worker threads: 1 per process for the 1-core figure, else 1 per worker
+# (the PCA worker: all of them).
 
-_FRAME_CACHE = {}
+_POOLS = {}
+_WINDOWS = {}
+_FRAMES = {}
 
 
-def oracle_sample(w, n_frames):
-    """Time the FP64 oracle on the first n_frames of the workload (all complete windows)."""
+def _thread_env(n):
+    return {k: str(n) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def _oracle_pool(workers, threads):
+    """A spawned pool of `workers` processes with `threads` BLAS/OpenMP threads each."""
+    import multiprocessing as mp
+    key = (workers, threads)
+    if key not in _POOLS:
+        saved = {k: os.environ.get(k) for k in _thread_env(1)}
+        os.environ.update(_thread_env(threads))
+        try:
+            pool = mp.get_context("spawn").Pool(workers)
+            pool.map(_warm_job, range(workers))  # workers up and the oracle imported
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        _POOLS[key] = pool
+    return _POOLS[key]
+
+
+def close_oracle_pools():
+    for pool in _POOLS.values():
+        pool.terminate()
+    _POOLS.clear()
+    for shm, _ in _WINDOWS.values():
+        shm.close()
+        shm.unlink()
+    _WINDOWS.clear()
+    _FRAMES.clear()
+
+
+def _warm_job(_):
+    from oracle import hv_oracle  # noqa: F401
+    return os.getpid()
+
+
+def _shared_window(name, shape):
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)
+    return shm, np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+
+
+def _spatial_job(args):
+    """Propagate raw frames into slots of the shared window (oracle spatial step)."""
     from oracle import hv_oracle as O
-    key = (w["desc"], n_frames)
-    if key not in _FRAME_CACHE:
-        _FRAME_CACHE[key] = make_pool(w, n_frames)
-    fr = _FRAME_CACHE[key]
+    name, shape, slots, raw, p = args
+    shm, U = _shared_window(name, shape)
+    for s, fr in zip(slots, raw):
+        U[s] = O.spatial(O.convert(fr), p)
+    del U
+    shm.close()
+    return len(slots)
+
+
+def _temporal_job(args):
+    """Oracle temporal step on pixel rows r0..r1 of the shared window (STFT), or on
+    the whole window (PCA)."""
+    from oracle import hv_oracle as O
+    name, shape, r0, r1, p = args
+    shm, U = _shared_window(name, shape)
+    if p["temporal"] == "pca":
+        out = O.pca(U, p["pca_lo"], p["pca_hi"])["E"][None]
+    else:
+        m = O.stft_moments(U[:, r0:r1], p["fs_hz"], p["band_lo_bin"], p["band_hi_bin"])
+        out = np.stack([m[k] for k in O.MOMENT_ORDER if k in p["moments"]])
+    del U
+    shm.close()
+    return out.shape
+
+
+def _raw_frames(w, n):
+    key = (w["desc"], n)
+    if key not in _FRAMES:
+        _FRAMES.clear()
+        _FRAMES[key] = make_pool(w, n)
+    return _FRAMES[key]
+
+
+def oracle_rate(w, cores, n_spatial, row_frac=1.0):
+    """Steady-state oracle frames/s on `cores` cores: t_spatial per frame from n_spatial
+    frames, t_window from a row_frac fraction of one window's pixel rows (STFT; PCA takes
+    the whole window). Returns (frames/s, t_spatial per frame, t_window)."""
+    from multiprocessing import shared_memory
+    T, S, N = w["T"], w["S"], w["N"]
     p = oracle_params(w)
+    pca = p["temporal"] == "pca"
+    workers = 1 if (cores == 1) else cores
+    pool = _oracle_pool(workers, 1 if cores == 1 else 1)
+    shape = (T, N, N)
+    key = (w["desc"], T, N)
+    raw = _raw_frames(w, max(T, n_spatial))
+    if key not in _WINDOWS:
+        shm = shared_memory.SharedMemory(create=True, size=T * N * N * 16)
+        _WINDOWS[key] = (shm, False)
+    shm, filled = _WINDOWS[key]
+    if not filled:  # the window the temporal step reads (untimed)
+        per = -(-T // workers)
+        pool.map(_spatial_job, [(shm.name, shape, list(range(i, min(T, i + per))), raw[i:i + per], p)
+                                for i in range(0, T, per)])
+        _WINDOWS[key] = (shm, True)
+    # spatial step: n_spatial frames over the workers, into the window's slots (overwriting
+    # them with the same values: the sample's first T frames are the window's frames)
+    per = -(-n_spatial // workers)
+    jobs = [(shm.name, shape, [f % T for f in range(i, min(n_spatial, i + per))], raw[i:i + per], p)
+            for i in range(0, n_spatial, per)]
     t0 = time.perf_counter()
-    img = O.render(fr, p)
-    dt = time.perf_counter() - t0
-    return n_frames / dt, img.shape[0], dt
+    pool.map(_spatial_job, jobs)
+    t_sp = (time.perf_counter() - t0) / n_spatial
+    # temporal step
+    if pca:
+        pool_t = _oracle_pool(1, cores)
+        t0 = time.perf_counter()
+        pool_t.map(_temporal_job, [(shm.name, shape, 0, N, p)])
+        t_win = time.perf_counter() - t0
+    else:
+        rows = max(1, int(round(N * row_frac)))
+        per = -(-rows // workers)
+        jobs = [(shm.name, shape, r, min(rows, r + per), p) for r in range(0, rows, per)]
+        t0 = time.perf_counter()
+        pool.map(_temporal_job, jobs)
+        t_win = (time.perf_counter() - t0) * N / rows
+    return 1.0 / (t_sp + t_win / S), t_sp, t_win
 
 
-def cpu_baseline(w, budget_s=12.0, max_bytes=4 << 30):
-    """The oracle on a bounded prefix of the workload: a first sample of 3 (overlapping)
-    or 2 windows sizes a second one of about budget_s seconds, which is reported
-    (at most the step's frames, and max_bytes of propagated complex128 frames)."""
-    T, S = w["T"], w["S"]
+def host_cpu():
+    """Core count and CPU model of this host (lscpu when present)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
 
-    def frames_for(nwin):  # window k covers frames k S .. k S + T - 1
-        return T + (nwin - 1) * S
 
-    nwin0 = 3 if S < T else 2
-    n = frames_for(nwin0)
-    fps, nwin, dt = oracle_sample(w, n)
-    cap = min(w.get("batch", n) * w.get("batches", 1), max_bytes // (w["N"] * w["N"] * 16))
-    if dt < 0.67 * budget_s:
-        want = frames_for(max(nwin0, int(np.ceil(nwin0 * budget_s / max(dt, 1e-3)))))
-        want = min(want, cap)
-        if want > n:
-            _FRAME_CACHE.clear()
-            n = want
-            fps, nwin, dt = oracle_sample(w, n)
-    _FRAME_CACHE.clear()
-    return {"value": round(fps, 2), "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} frames of the workload ({nwin} windows), FP64 numpy oracle, "
-                      f"{dt:.1f} s on 1 host core"}
+# 1-core sample (shared with the reference arm, so both report the same rate)
+ONE_CORE_SPATIAL_FRAMES = 32
+ONE_CORE_ROW_FRAC = 0.25
+
+
+def cpu_baseline(w, reps=3):
+    """The oracle's steady-state rate on all host cores (the reported value) and on one
+    core (median of reps samples, the reference arm's procedure)."""
+    T, S, N = w["T"], w["S"], w["N"]
+    ncpu, model = host_cpu()
+    one = [oracle_rate(w, 1, ONE_CORE_SPATIAL_FRAMES, ONE_CORE_ROW_FRAC) for _ in range(reps)]
+    one_fps = float(np.median([r[0] for r in one]))
+    n_sp = max(T, 4 * ncpu) if ncpu > 1 else T
+    allc = oracle_rate(w, ncpu, n_sp, 1.0) if ncpu > 1 else one[0]
+    close_oracle_pools()
+    what = "PCA window" if w.get("temporal") == "pca" else "STFT + moments window"
+    return {"value": round(allc[0], 3), "unit": "frames/s", "cores": ncpu, "kind": "oracle",
+            "cpu_model": model,
+            "rule": "steady state: frames/s = 1 / (t_spatial per frame + t_window / S)",
+            "sample": (f"FP64 numpy oracle, {ncpu} spawned worker processes: spatial step timed on "
+                       f"{n_sp} frames spread over the workers ({allc[1] * 1e3:.2f} ms per frame), one "
+                       f"{what} of T = {T} frames on {N}x{N} pixels spread over them by pixel rows "
+                       f"({allc[2]:.2f} s), S = {S}"),
+            "one_core": {"value": round(one_fps, 3), "cores": 1,
+                         "sample": (f"median of {reps}: spatial step on {ONE_CORE_SPATIAL_FRAMES} frames "
+                                    f"({float(np.median([r[1] for r in one])) * 1e3:.2f} ms per frame), "
+                                    f"{what} on {int(ONE_CORE_ROW_FRAC * 100)} % of the pixel rows scaled "
+                                    f"to the window ({float(np.median([r[2] for r in one])):.2f} s), one "
+                                    "worker process with one thread")}}
 
 
 def group_oracle_sample():
@@ -607,6 +765,8 @@ def group_oracle_sample():
 
 
 def run_reference(args, w, rank):
+    """The oracle as it stands on one host core, one steady-state sample per step (the
+    procedure of cpu_baseline's 1-core figure)."""
     if rank != 0:
         return None
     if w.get("group"):
@@ -616,14 +776,121 @@ def run_reference(args, w, rank):
             if i >= args.warmup:
                 vals.append(fps)
         return float(np.median(vals)), n
-    fps_list = []
-    n = w["T"] + w["S"] if w["S"] < w["T"] else w["T"]
+    vals = []
     for i in range(args.warmup + args.steps):
-        fps, nwin, dt = oracle_sample(w, n)
+        fps, _, _ = oracle_rate(w, 1, ONE_CORE_SPATIAL_FRAMES, ONE_CORE_ROW_FRAC)
         if i >= args.warmup:
-            fps_list.append(n / dt / 1.0)
-    value = float(np.median(fps_list))
-    return value, n
+            vals.append(fps)
+    close_oracle_pools()
+    return float(np.median(vals)), ONE_CORE_SPATIAL_FRAMES
+
+
+# -------------------------------------------------- library comparison
+
+def library_tables(w, dev):
+    """Transfer function (ASP) or chirp (Fresnel, fftshift folded in as (-1)^(j+l)) of the
+    workload on the device, built in float64 by torch ops for the library route."""
+    import torch
+    N, lam, d = w["N"], 852e-9, 20e-6
+    if w["spatial"] == "asp":
+        m = torch.arange(N, device=dev, dtype=torch.float64)
+        m = torch.where(m < N // 2, m, m - N)
+        kx = 2 * math.pi * m / (N * d)
+        k = 2 * math.pi / lam
+        kz2 = k * k - kx[None, :] ** 2 - kx[:, None] ** 2
+        ph = w["z"] * torch.sqrt(torch.clamp(kz2, min=0.0))
+        h = torch.polar(torch.ones_like(ph), ph) * (kz2 >= 0)
+        return h.to(torch.complex64)
+    x = (torch.arange(N, device=dev, dtype=torch.float64) - N / 2) * d
+    j = torch.arange(N, device=dev)
+    ph = math.pi * (x[None, :] ** 2 + x[:, None] ** 2) / (lam * w["z"]) + math.pi * ((j[None, :] + j[:, None]) % 2)
+    return torch.polar(torch.ones_like(ph), ph).to(torch.complex64)
+
+
+def run_library(w, args, pool_dev, stream):
+    """The same batches through library calls, outside the library under test:
+    torch.fft (cuFFT plan-many) for FFT2 x H IFFT2 (or chirp x FFT2) in complex64,
+    then per window a time-axis FFT over the strided queue (STFT: |S|^2 band sums by
+    torch reductions) or, for PCA, C = X^H X by torch.matmul (cuBLAS complex GEMM),
+    torch.linalg.eigh (cuSOLVER) and the projection energy. CUDA events on `stream`."""
+    import torch
+    dev = pool_dev.device
+    N, T, S = w["N"], w["T"], w["S"]
+    B = pool_dev.shape[0]
+    tab = library_tables(w, dev)
+    q = torch.empty((B, N, N), dtype=torch.complex64, device=dev)
+    klo, khi = band_bins(w)
+    pca = w.get("temporal") == "pca"
+    if not pca:
+        kk = torch.arange(klo, khi + 1, device=dev, dtype=torch.float32)
+        kk = torch.where(kk < (T + 1) // 2, kk, kk - T)
+        fk = (kk * w["fs"] / T / 1000.0)[:, None, None]
+    starts = list(range(0, B - T + 1, S))
+    nmom = max(1, len(w["moments"]))
+    img = torch.empty((len(starts), nmom, N, N), dtype=torch.float32, device=dev)
+    chunk = 512
+
+    def spatial():
+        for c in range(0, B, chunk):
+            raw = pool_dev[c:c + chunk]
+            x = (raw.to(torch.int32) & 0xFFFF).to(torch.float32) if raw.dtype == torch.int16 else raw.to(torch.float32)
+            x = torch.complex(x, torch.zeros_like(x))
+            if w["spatial"] == "asp":
+                q[c:c + chunk] = torch.fft.ifft2(torch.fft.fft2(x) * tab)
+            else:
+                q[c:c + chunk] = torch.fft.fft2(x * tab)
+
+    def temporal():
+        for i, s0 in enumerate(starts):
+            X = q[s0:s0 + T]
+            if pca:
+                Xm = X.reshape(T, N * N).transpose(0, 1)
+                C = Xm.conj().transpose(0, 1) @ Xm
+                lam, V = torch.linalg.eigh(C.to(torch.complex128))
+                lo, hi = w["pca"]
+                Vs = V.flip(-1)[:, lo - 1:hi].to(torch.complex64)
+                Y = Xm @ Vs
+                img[i, 0] = (Y.real ** 2 + Y.imag ** 2).sum(1).reshape(N, N)
+            else:
+                F = torch.fft.fft(X, dim=0)[klo:khi + 1]
+                P = F.real ** 2 + F.imag ** 2
+                img[i, 0] = P.sum(0)
+                if nmom > 1:
+                    img[i, 1] = (fk * P).sum(0)
+                    img[i, 2] = (fk * fk * P).sum(0)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            spatial()
+            temporal()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        sp = tm = 0.0
+        reps = max(2, min(args.steps, 5))
+        for _ in range(reps):
+            ev[0].record(stream)
+            spatial()
+            ev[1].record(stream)
+            temporal()
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            sp += ev[0].elapsed_time(ev[1])
+            tm += ev[1].elapsed_time(ev[2])
+    sp /= reps
+    tm /= reps
+    # steady state: every frame propagated once, one window per S frames
+    frames = len(starts) * S
+    t_ms = sp * frames / B + tm
+    del q, img
+    torch.cuda.empty_cache()
+    return {"value": round(frames / (t_ms / 1e3), 1), "unit": "frames/s",
+            "spatial_ms_per_frame": round(sp / B, 6), "temporal_ms_per_window": round(tm / len(starts), 5),
+            "what": ("torch.fft (cuFFT plan-many) FFT2 x H IFFT2 (or chirp x FFT2) in complex64 over "
+                     f"{B} frames in launches of {chunk}, then per window " +
+                     ("C = X^H X by torch.matmul (cuBLAS complex GEMM), torch.linalg.eigh in complex128 "
+                      "(cuSOLVER), projection energy" if pca else
+                      "a time-axis FFT of the strided queue (cuFFT) and |S|^2 band sums by torch reductions") +
+                     "; steady state 1 / (t_spatial + t_window / S); same frames, not the library under test")}
 
 
 # ------------------------------------------------------- batched streams
@@ -1036,6 +1303,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--no-library", action="store_true",
+                    help="skip the cuFFT / cuBLAS comparison of the same batches")
     ap.add_argument("--precision", choices=["fp32", "bf16", "split_bf16"], default=None,
                     help="PCA covariance arithmetic (PCA workloads)")
     ap.add_argument("--form", choices=["tuned", "plain", "both"], default="both",
@@ -1085,8 +1354,11 @@ def main():
                                      "sample": (f"each step: one window of each member with N <= 256 "
                                                 f"and T <= 128 ({n} frames) through the FP64 numpy "
                                                 "oracle on 1 host core") if w.get("group") else
-                                               (f"each step: first {n} frames of the workload "
-                                                "through the FP64 numpy oracle on 1 host core")},
+                                               (f"each step: the oracle's steady-state rate 1 / (t_spatial "
+                                                f"+ t_window / S), spatial step on {n} frames, one window's "
+                                                f"temporal step on {int(ONE_CORE_ROW_FRAC * 100)} % of its "
+                                                "pixel rows scaled to the window; one worker process, one "
+                                                "thread, one host core")},
                     "e2e": {"value": round(value, 3), "unit": "frames/s", "h2d_bytes_per_step": 0,
                             "d2h_bytes_per_step": 0}}
             print(json.dumps(line), flush=True)
@@ -1137,6 +1409,11 @@ def main():
                              "plain_stage_ms_per_render": {
                                  "spatial": round(plain["prof"]["spatial_ms"] / max(1, plain["prof"]["renders"]), 4),
                                  "temporal": round(plain["prof"]["temporal_ms"] / max(1, plain["prof"]["renders"]), 4)}}
+        if "library" in res:
+            lib = res["library"]
+            lib["hbm_pct_of_measured"] = round(100 * lib["value"] * alg["frame_bytes"] / 1e9 / hbm, 2)
+            lib["library_over_hv"] = round(lib["value"] / (res["value"] / world), 4)
+            line["comparison"] = {"cufft_cublas": lib}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -1,54 +1,64 @@
-"""Host logic of bench.py that needs no GPU: the sizing of the CPU-baseline
-sample (a first sample of 2-3 windows, then one scaled to the time budget,
-capped by the step's frames and the oracle's memory)."""
-import importlib.util
+"""Host logic of bench.py that needs no GPU: the oracle's steady-state rate
+(frames/s = 1 / (t_spatial per frame + t_window / S)), measured in spawned worker
+processes on one core and on several, and the reference arm that repeats the
+1-core procedure per step."""
+import argparse
+import importlib
 import os
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+import numpy as np
 
 
 def _bench():
-    spec = importlib.util.spec_from_file_location("bench_host_mod", os.path.join(ROOT, "bench.py"))
-    m = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(m)
-    return m
+    # a module importable by name: the spawned workers unpickle its functions
+    import bench
+    return importlib.reload(bench)
 
 
-def _fake_sampler(per_window_s):
-    calls = []
-
-    def sample(w, n):
-        nwin = (n - w["T"]) // w["S"] + 1
-        calls.append(n)
-        dt = per_window_s * nwin
-        return n / dt, nwin, dt
-
-    return sample, calls
+def _tiny(b):
+    w = dict(b.WORKLOADS["tiny_asp_stft_256_t64"])
+    w.update(N=32, T=8, S=4, band=(1, 3), moments=("M0", "M1", "M2"), desc="tiny host-test stream")
+    return w
 
 
-def test_overlapping_windows_scale_to_the_budget():
+def test_steady_state_rule_and_worker_pools():
     b = _bench()
-    w = dict(b.WORKLOADS["stream_fresnel_256_t512_s64"])
-    b.oracle_sample, calls = _fake_sampler(1.0)
-    r = b.cpu_baseline(w, budget_s=12.0)
-    assert calls[0] == 512 + 2 * 64                 # 3 windows first
-    assert calls[1] == 512 + 11 * 64                # then 12 windows (~12 s)
-    assert r["sample"].startswith("first 1216 frames of the workload (12 windows)")
-    assert r["cores"] == 1 and r["kind"] == "oracle"
+    w = _tiny(b)
+    try:
+        fps, t_sp, t_win = b.oracle_rate(w, 1, 8, 0.5)
+        assert t_sp > 0 and t_win > 0
+        assert np.isclose(fps, 1.0 / (t_sp + t_win / w["S"]))
+        fps2, t_sp2, t_win2 = b.oracle_rate(w, 2, 8, 1.0)
+        assert np.isclose(fps2, 1.0 / (t_sp2 + t_win2 / w["S"]))
+    finally:
+        b.close_oracle_pools()
+    assert not b._POOLS and not b._WINDOWS
 
 
-def test_long_first_sample_is_kept():
+def test_cpu_baseline_reports_all_cores_and_one_core():
     b = _bench()
-    w = dict(b.WORKLOADS["pca_512_t256"])
-    b.oracle_sample, calls = _fake_sampler(5.0)    # 2 windows take 10 s >= 2/3 of 12 s
-    b.cpu_baseline(w, budget_s=12.0)
-    assert calls == [2 * 256]
+    w = _tiny(b)
+    r = b.cpu_baseline(w, reps=1)
+    ncpu = os.cpu_count() or 1
+    assert r["kind"] == "oracle" and r["unit"] == "frames/s"
+    assert r["cores"] == ncpu and r["value"] > 0
+    assert r["one_core"]["cores"] == 1 and r["one_core"]["value"] > 0
+    assert "t_window / S" in r["rule"]
+    assert not b._POOLS  # pools closed after the measurement
 
 
-def test_sample_is_capped_by_the_step_and_memory():
+def test_reference_arm_uses_the_one_core_procedure():
     b = _bench()
-    w = dict(b.WORKLOADS["pca_fresnel_256_t32"])
-    b.oracle_sample, calls = _fake_sampler(1e-3)   # very fast: the budget would ask for ~24k windows
-    b.cpu_baseline(w, budget_s=12.0)
-    cap_mem = (4 << 30) // (w["N"] * w["N"] * 16)
-    assert calls[-1] == min(w["batch"] * w["batches"], cap_mem)
+    w = _tiny(b)
+    seen = []
+
+    def fake_rate(w_, cores, n_sp, frac):
+        seen.append((cores, n_sp, frac))
+        return 100.0 + len(seen), 1e-3, 1e-2
+
+    b.oracle_rate = fake_rate
+    args = argparse.Namespace(warmup=2, steps=3)
+    value, n = b.run_reference(args, w, 0)
+    assert seen == [(1, b.ONE_CORE_SPATIAL_FRAMES, b.ONE_CORE_ROW_FRAC)] * 5
+    assert value == np.median([103.0, 104.0, 105.0])  # warm-up samples dropped
+    assert b.run_reference(args, w, 1) is None        # other ranks do no work
