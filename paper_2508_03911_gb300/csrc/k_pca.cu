@@ -357,6 +357,19 @@ __global__ void __launch_bounds__(256) k_jacobi_refine(PcaArgs a) {
   if (gtid == 0) atomicAdd(&a.counters[2], unsigned(sweeps));  // refinement sweeps
 }
 
+// Power of two near 1 / max_i C_ii (exact scaling): the float32 phase works on
+// C times this, so no product of two entries can overflow float32 whatever the
+// frames' range (a 16-bit full-range window of a large frame reaches diagonal
+// entries above 1e19, whose products exceed the float32 range). Every thread
+// computes the same value from the float64 diagonal.
+__device__ __forceinline__ double pow2_diag_scale(const double2* C, int T) {
+  double m = 0.0;
+  for (int i = 0; i < T; ++i) m = fmax(m, C[size_t(i) * T + i].x);
+  int ex = 0;
+  frexp(m, &ex);
+  return m > 0.0 ? ldexp(1.0, -ex) : 1.0;
+}
+
 // First phase of the large-window eigensolver: the same cooperative cyclic
 // Jacobi in float32 (on a quarter of the SMs: the arithmetic is cheap, so the
 // grid barrier sets the pace of a round, and a smaller grid makes it cheaper),
@@ -369,16 +382,17 @@ __global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
   __shared__ unsigned cnt;
   const size_t gtid = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const size_t gsz = size_t(gridDim.x) * blockDim.x;
+  const double scale = pow2_diag_scale(a.C, T);  // the rotations do not depend on it
   for (size_t e = gtid; e < size_t(T) * T; e += gsz) {
     const double2 v = a.C[e];
-    a.Cf[e] = make_float2(float(v.x), float(v.y));
+    a.Cf[e] = make_float2(float(v.x * scale), float(v.y * scale));
     a.Vf[e] = make_float2(e / T == e % T ? 1.f : 0.f, 0.f);
   }
   grid.sync();
   // scales: the trace (>= the largest eigenvalue); float32 rounding leaves
   // off-diagonal entries near 6e-8 of the largest eigenvalue
   float trace = 0.f;
-  for (int i = 0; i < T; ++i) trace += float(a.C[size_t(i) * T + i].x);
+  for (int i = 0; i < T; ++i) trace += float(a.C[size_t(i) * T + i].x * scale);
   const float ftol = 1e-6f, ffloor = 2e-7f * trace;
   __shared__ unsigned offbits;  // largest |C_ij| met in the sweep (non-negative float bits)
   float2* Cs = a.Cf;
@@ -468,15 +482,16 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
   __shared__ float tr_part[JC];  // diagonal sums of the CTAs
   __shared__ unsigned s_nrot;
   __shared__ float s_offmax;
+  const double scale = pow2_diag_scale(a.C, T);  // the same in every CTA
   for (int e = tid; e < R * T; e += JC_NT) {
     const int li = e / T, c = e % T;
     const double2 v = a.C[size_t(row0 + li) * T + c];
-    C0[e] = make_float2(float(v.x), float(v.y));
+    C0[e] = make_float2(float(v.x * scale), float(v.y * scale));
     Vr[e] = make_float2(row0 + li == c ? 1.f : 0.f, 0.f);
   }
   if (tid == 0) {  // the trace: every CTA's diagonal sum, written into every CTA
     float t = 0.f;
-    for (int li = 0; li < R; ++li) t += float(a.C[size_t(row0 + li) * T + row0 + li].x);
+    for (int li = 0; li < R; ++li) t += float(a.C[size_t(row0 + li) * T + row0 + li].x * scale);
     for (int c = 0; c < JC; ++c) cl.map_shared_rank(tr_part, c)[rank] = t;
   }
   cl.sync();

@@ -1,7 +1,9 @@
-"""What the trained network gains over the method without it: trained on the
-GPU (8,192 holograms labelled by the plain sweep, 20 epochs), it estimates the
-focus distance of unseen holograms close to the sweep's answer at a fraction of
-the sweep's cost, while a constant guess misses by ~16 sweep steps."""
+"""What the trained network gains over the method without it: trained on the GPU
+by the library's own forward, backward and Adam kernels (50,000 holograms
+labelled by the plain sweep, 40 epochs), it estimates the focus distance of
+1,000 unseen holograms within one sweep step of the sweep's answer for at least
+80 % of them (median error at most one step), at a fraction of the sweep's
+cost, while a constant guess misses by ~16 sweep steps."""
 import numpy as np
 import pytest
 
@@ -9,31 +11,34 @@ pytestmark = pytest.mark.gpu
 
 
 def test_trained_network_against_the_sweep():
+    import os
+
     import torch
 
     from paper_2508_03911_gb300 import autofocus as AF
     from paper_2508_03911_gb300 import synth
-    tr, _ = synth.autofocus_set(8192, N=256, seed=1004, workers=16)
-    te, te_z = synth.autofocus_set(256, N=256, seed=1005, workers=16)
+    workers = min(16, os.cpu_count() or 1)
+    tr, _ = synth.autofocus_set(50000, N=256, seed=1004, workers=workers)
+    te, te_z = synth.autofocus_set(1000, N=256, seed=1005, workers=workers)
     p = AF.Pipeline(max_batch=256)
     try:
         _, tr_lab, _, tr_x = p.label_and_features(tr)
+        del tr
         _, te_lab, _, te_x = p.label_and_features(te)
         # the sweep itself finds the recorded distance
         assert np.mean(np.abs(te_lab - te_z) <= AF.STEP) >= 0.97
         p.net.set_params(AF.he_uniform(1))
-        hist, _ = AF.train(p, tr_x, tr_lab, epochs=20, batch=256, lr=2e-3)
+        hist, t_train = AF.train(p, tr_x, tr_lab, epochs=40, batch=256, lr=2e-3)
         pred = p.predict(te_x)
         err = np.abs(pred - te_lab) / AF.STEP
         const = np.abs(np.mean(tr_lab) - te_lab) / AF.STEP
         t_sweep, t_net = AF.time_sweep_and_net(p, te)
-        print(f"within 1 step {np.mean(err <= 1):.3f}, MAE {err.mean():.2f} steps "
-              f"(constant guess {const.mean():.1f}); sweep {t_sweep * 1e6:.1f} us, network "
-              f"{t_net * 1e6:.1f} us per hologram")
-        assert hist[-1] < 0.01
-        assert err.mean() <= 2.0 and np.median(err) <= 1.5
-        assert np.mean(err <= 1) >= 0.4
-        assert err.mean() < 0.2 * const.mean()
+        print(f"within 1 step {np.mean(err <= 1):.3f}, median {np.median(err):.2f}, MAE "
+              f"{err.mean():.2f} steps (constant guess {const.mean():.1f}); trained in {t_train:.1f} s; "
+              f"sweep {t_sweep * 1e6:.1f} us, network {t_net * 1e6:.1f} us per hologram")
+        assert np.mean(err <= 1) >= 0.80
+        assert np.median(err) <= 1.0
+        assert err.mean() < 0.1 * const.mean()
         assert t_net < t_sweep / 4
     finally:
         p.close()

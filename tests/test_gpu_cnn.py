@@ -108,3 +108,45 @@ def test_short_training_fits_a_small_set():
         l1 = float(loss.item())
     print(f"loss {l0:.4f} -> {l1:.4f}")
     assert l1 < 0.2 * l0
+
+
+def test_bf16_network_error_against_the_unrounded_fp64_oracle():
+    """The error of the BF16 network itself: the GPU (bf16 input, bf16 convolution
+    weights, bf16 stored activations, float32 sums) against the FP64 oracle with no
+    rounding at all (float64 input, weights and activations). Stated per output:
+    forward error in metres, and the relative L2 error of every parameter
+    tensor's gradient, held to 2e-2."""
+    import torch
+    n = 8
+    rng = np.random.default_rng(11)
+    flat = A.init_params(11) + 0.02 * rng.standard_normal(A.n_params())
+    flat = flat.astype(np.float32).astype(np.float64)  # the GPU's float32 master copy
+    x = rng.standard_normal((n, 1, 128, 128))
+    z = rng.uniform(0.1, 0.6, n).astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).cuda()
+    zd = torch.from_numpy(z.astype(np.float32)).cuda()
+    with _net(n) as net:
+        net.set_params(flat)
+        out = torch.zeros(n, device="cuda")
+        net.forward(xd, out)
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.zeros(A.n_params(), device="cuda")
+        net.loss_grad(xd, zd, loss, grad)
+        net.synchronize()
+        zp = out.cpu().numpy().astype(np.float64)
+        g = grad.cpu().numpy().astype(np.float64)
+        L = float(loss.item())
+    z_ref = A.predict_z(flat, x, bf16_acts=False)
+    L_ref, g_ref = A.gradients(flat, x, z, bf16_acts=False)
+    dz = np.max(np.abs(zp - z_ref))
+    print(f"BF16 network vs FP64: forward max |dz| {dz * 1e3:.3f} mm "
+          f"(sweep step {0.5 / 63 * 1e3:.2f} mm), loss {L:.5f} vs {L_ref:.5f}")
+    assert dz <= 0.5 / 63 / 4  # well inside a quarter of a sweep step
+    assert abs(L - L_ref) <= 2e-2 * L_ref
+    o = 0
+    for name, s in A.param_shapes():
+        k = int(np.prod(s))
+        e = np.linalg.norm(g[o:o + k] - g_ref[o:o + k]) / max(np.linalg.norm(g_ref[o:o + k]), 1e-30)
+        print(f"  gradient {name}: rel L2 {e:.2e}")
+        assert e <= 2e-2, (name, e)
+        o += k

@@ -122,3 +122,57 @@ def test_group_rejects_before_issuing_work():
     finally:
         a.close()
         b.close()
+
+
+def test_group_at_the_batched_workload_shapes():
+    """Members of the batched uneven-stream workload's sizes through the graph path
+    with the autotuned kernels: 1024x1024 ASP and Fresnel members, a 256x256 member
+    with T = 512, a 512x512 member with T = 128 and two 128x128 members; 12-bit
+    frames, S = T, M0/M1/M2 over 1-35 kHz at 71.4 kHz. Two batches of one window per
+    member (the second replays the updated graph), each against the FP64 oracle.
+    (The workload's 1024x1024 ASP member has T = 128; T = 32 here keeps the FP64
+    oracle's work to seconds.)"""
+    import math
+
+    import torch
+    shapes = [(128, 32, "fresnel"), (128, 128, "asp"), (256, 512, "asp"), (512, 128, "asp"),
+              (1024, 32, "asp"), (1024, 32, "fresnel")]
+    members = []
+    for i, (N, T, sp) in enumerate(shapes):
+        band = (math.ceil(1000.0 * T / 71400.0 - 1e-12), math.floor(35000.0 * T / 71400.0 + 1e-12))
+        p = oracle_params(spatial=sp, z_m=0.25 if sp == "fresnel" else 0.30, T=T, stride=T,
+                          fs_hz=71400.0, band_lo_bin=band[0], band_hi_bin=band[1],
+                          moments=("M0", "M1", "M2"), H=N, W=N)
+        members.append((p, synth.random_frames(2 * T, N, N, 12, seed=1003 + i)))
+    rs = []
+    try:
+        for p, fr in members:
+            r = hv.Renderer(p["W"], p["H"], 16, 2 * p["T"])
+            hv.hv_set_params(r.h, to_hv(p, tuned=1))
+            rs.append(r)
+        g = hv.hv_group_open([r.h for r in rs], use_graph=True)
+        try:
+            dev = [to_device(fr) for _, fr in members]
+            outs = [torch.zeros(3 * r.window_floats(), dtype=torch.float32, device="cuda") for r in rs]
+            got = [[] for _ in rs]
+            for step in range(2):
+                frames = [d[step * p["T"]:(step + 1) * p["T"]] for d, (p, _) in zip(dev, members)]
+                nw = hv.hv_render_group(g, frames, outs)
+                assert nw == [1] * len(rs), nw
+                torch.cuda.synchronize()
+                for i in range(len(rs)):
+                    got[i].append(outs[i][: rs[i].window_floats()].cpu().numpy().copy())
+            st = hv.hv_group_get_stats(g)
+            assert st["graph_launches"] == 2 and st["graph_updates"] >= 1
+        finally:
+            hv.hv_group_close(g)
+        for i, (p, fr) in enumerate(members):
+            img = np.stack(got[i]).reshape(2, 3, p["H"], p["W"])
+            for w in range(2):
+                ref = O.render(fr[w * p["T"]:(w + 1) * p["T"]], p)[0]
+                for q in range(3):
+                    e = rel_l2(img[w, q], ref[q])
+                    assert e <= IMAGE_TOL, (shapes[i], w, q, e)
+    finally:
+        for r in rs:
+            r.close()
