@@ -218,7 +218,8 @@ def test_pca_full_range_16bit_fresnel_long_window():
         print(f"16-bit Fresnel {precision}: E rel L2 {e:.3e}, lam max err / lam1 {el:.3e}")
         assert np.all(np.isfinite(img)) and np.all(np.isfinite(lam))
         assert e <= IMAGE_TOL
-        assert el <= LAM_TOL
+        # split-BF16 covariance: the eigenvalue bar of the other split-BF16 cases
+        assert el <= (LAM_TOL if precision == "fp32" else max(LAM_TOL, IMAGE_TOL))
 
 
 def test_pca_rejects_unbuilt_precisions_and_bad_basis():
