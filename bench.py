@@ -1309,7 +1309,8 @@ def main():
                     help="PCA covariance arithmetic (PCA workloads)")
     ap.add_argument("--form", choices=["tuned", "plain", "both"], default="both",
                     help="tuned: spatial kernels chosen by the autotuner; plain: multi-pass kernels")
-    ap.add_argument("--spatial-kernel", choices=["auto", "multipass", "persistent", "cluster"], default="auto",
+    ap.add_argument("--spatial-kernel", choices=["auto", "multipass", "persistent", "cluster", "fused"],
+                    default="auto",
                     help="fix the spatial kernels instead of autotuning them (profiling runs: the "
                          "autotuner's timings are distorted under a profiler)")
     ap.add_argument("--spatial-chunk", type=int, default=0, help="frames per spatial launch (0: automatic)")
@@ -1396,13 +1397,13 @@ def main():
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "form": "plain" if args.form == "plain" else "tuned",
-            "tuning": {"spatial_kernel": {1: "multipass", 2: "cluster", 3: "persistent"}.get(
+            "tuning": {"spatial_kernel": {1: "multipass", 2: "cluster", 3: "persistent", 4: "fused"}.get(
                            res["tuning"]["spatial_kernel"], "multipass"),
                        "frames_per_launch": res["tuning"]["spatial_chunk"],
                        "candidates_us_per_frame": dict(zip(
                            ["mp16", "mp32", "mp64", "mp128", "mp256", "pp64", "pp128", "pp256",
-                            "pp512", "cluster"],
-                           [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:10]]))},
+                            "pp512", "cluster", "fused"],
+                           [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:11]]))},
         }
         if plain is not None:
             line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),

@@ -101,8 +101,10 @@ typedef struct {
   uint32_t spatial_chunk;     /* frames per spatial launch (0 = automatic)             */
   uint32_t spatial_kernel;    /* HV_SK_*: which spatial kernels (default automatic):
                                  multi-pass (one strip per CTA), persistent multi-pass
-                                 (CTAs loop over strips, prefetching the next), or the
-                                 whole-frame cluster kernel                           */
+                                 (CTAs loop over strips, prefetching the next), the
+                                 whole-frame cluster kernel, or the fused transform
+                                 (256 x 256 frames: every pass of every frame in one
+                                 persistent launch, intermediates in L2-resident rings) */
   double highpass_cpp;        /* ASP only: high-pass spatial filter applied after the
                                  propagation (Sec. VI-B.1): spatial frequencies whose
                                  radius sqrt((m/W)^2 + (n/H)^2) in cycles per pixel is
@@ -112,7 +114,7 @@ typedef struct {
 
 /* Spatial kernel selection: automatic = the autotuner's choice when tuned = 1,
  * the multi-pass kernels otherwise. */
-enum { HV_SK_AUTO = 0, HV_SK_MULTIPASS = 1, HV_SK_CLUSTER = 2, HV_SK_PERSISTENT = 3 };
+enum { HV_SK_AUTO = 0, HV_SK_MULTIPASS = 1, HV_SK_CLUSTER = 2, HV_SK_PERSISTENT = 3, HV_SK_FUSED = 4 };
 
 typedef struct {
   uint64_t frames_pushed;     /* frames accepted by hv_push_frames                     */
@@ -180,13 +182,14 @@ hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n);
  * applied by timing each candidate on the handle's own buffers. */
 typedef struct {
   int32_t tuned;                    /* 1 once the autotuner has run                   */
-  int32_t spatial_kernel;           /* HV_SK_MULTIPASS, HV_SK_CLUSTER or HV_SK_PERSISTENT */
+  int32_t spatial_kernel;           /* HV_SK_MULTIPASS, _CLUSTER, _PERSISTENT or _FUSED */
   uint32_t spatial_chunk;           /* frames per multi-pass launch                   */
   uint32_t reserved;
   float candidate_us_per_frame[12]; /* measured us per frame: multi-pass with 16, 32, 64,
                                        128, 256 frames per launch; persistent
                                        multi-pass with 64, 128, 256, 512; the cluster
-                                       kernel (0 where not applicable)                */
+                                       kernel; the fused transform (0 where not
+                                       applicable)                                    */
 } hv_tuning;
 
 /* The autotuner's choices for the applied settings. Errors: HV_ERR_STATE. */

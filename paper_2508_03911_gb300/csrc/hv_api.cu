@@ -50,6 +50,9 @@ struct hv_handle {
   uint32_t chunk = 0;
   int sp_cluster = 0;         // 1: whole-frame cluster kernel
   int sp_pp = 0;              // 1: persistent multi-pass kernels
+  int sp_fused = 0;           // 1: fused transform (s1 / s2 are rings of kFusedRing frames)
+  unsigned* fused_ctr = nullptr;  // its ticket and per-slot counters
+  size_t fused_ctr_bytes = 0;
   hv_tuning tuning{};
   float2* tw = nullptr;  // all twiddle tables, length 8..1024 packed
   unsigned* dev_err = nullptr;  // sticky device flags: a kernel's bounded wait gave up
@@ -171,7 +174,12 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     why = "unknown spatial transform";
     return HV_ERR_ARG;
   }
-  if (p.spatial_kernel > HV_SK_PERSISTENT) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.spatial_kernel > HV_SK_FUSED) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.spatial_kernel == HV_SK_FUSED &&
+      (p.width != 256 || p.height != 256 || (p.spatial != HV_SPATIAL_ASP && p.spatial != HV_SPATIAL_FRESNEL))) {
+    why = "the fused spatial transform needs 256 x 256 frames and ASP or Fresnel";
+    return HV_ERR_UNSUPPORTED;
+  }
   if (p.spatial_kernel == HV_SK_PERSISTENT &&
       !(p.width >= 64 && p.height >= 64 && (p.spatial == HV_SPATIAL_ASP || p.spatial == HV_SPATIAL_FRESNEL))) {
     why = "the persistent multi-pass kernels need sides in [64, 1024] and ASP or Fresnel";
@@ -335,7 +343,13 @@ hv_status apply_pending(hv_handle* h) {
   if (s != HV_OK) return s;
   uint32_t chunk = p.spatial_chunk ? p.spatial_chunk : std::max<uint32_t>(1, uint32_t((size_t(32) << 20) / fbytes));
   chunk = std::min<uint32_t>(chunk, 1024);
-  const size_t sbytes = size_t(chunk) * fbytes;
+  const bool fused = p.spatial_kernel == HV_SK_FUSED;
+  const size_t sbytes = size_t(fused ? std::max(chunk, kFusedRing) : chunk) * fbytes;
+  if (fused) {
+    s = ensure(h, reinterpret_cast<void**>(&h->fused_ctr), &h->fused_ctr_bytes,
+               (1 + 3 * size_t(kFusedRing)) * sizeof(unsigned));
+    if (s != HV_OK) return s;
+  }
   if (p.spatial != HV_SPATIAL_NONE) {
     s = ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, sbytes);
     if (s != HV_OK) return s;
@@ -454,6 +468,7 @@ hv_status apply_pending(hv_handle* h) {
   h->chunk = chunk;
   h->sp_cluster = p.spatial_kernel == HV_SK_CLUSTER ? 1 : 0;
   h->sp_pp = p.spatial_kernel == HV_SK_PERSISTENT ? 1 : 0;
+  h->sp_fused = fused ? 1 : 0;
   h->tuning = hv_tuning{};
   h->tuning.spatial_chunk = chunk;
   h->tuning.spatial_kernel = p.spatial_kernel == HV_SK_AUTO ? HV_SK_MULTIPASS : int32_t(p.spatial_kernel);
@@ -511,8 +526,9 @@ bool cluster_ok(const hv_handle* h) {
 }
 
 hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
-  // the cluster kernel needs no scratch: one persistent launch for all frames
-  const bool whole = h->sp_cluster && cluster_ok(h);
+  // the cluster kernel needs no scratch, the fused transform keeps its intermediates
+  // in rings: one persistent launch for all frames
+  const bool whole = (h->sp_cluster && cluster_ok(h)) || h->sp_fused;
   const uint64_t step = whole ? f1 - f0 : h->chunk;
   for (uint64_t a = f0; a < f1; a += step) {
     const uint32_t n = uint32_t(std::min<uint64_t>(step, f1 - a));
@@ -536,6 +552,9 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.chirp_y = h->chirp + h->W;
     sa.use_cluster = h->sp_cluster;
     sa.use_pp = h->sp_pp;
+    sa.use_fused = h->sp_fused;
+    sa.ring = kFusedRing;
+    sa.fused_ctr = h->fused_ctr;
     int launches = 0;
     cudaError_t e = launch_spatial(sa, h->stream, &launches);
     h->st.kernel_launches += launches;
@@ -560,24 +579,29 @@ hv_status tune_spatial(hv_handle* h) {
   cudaEvent_t e0, e1;
   HV_CU(h, cudaEventCreate(&e0));
   HV_CU(h, cudaEventCreate(&e1));
-  struct Cand { int kind; uint32_t chunk; };  // kind: 1 multi-pass, 3 persistent, 2 cluster
+  struct Cand { int kind; uint32_t chunk; };  // kind: 1 multi-pass, 3 persistent, 2 cluster, 4 fused
   static const Cand cands[] = {{1, 16}, {1, 32}, {1, 64}, {1, 128}, {1, 256},
-                               {3, 64}, {3, 128}, {3, 256}, {3, 512}, {2, 0}};
+                               {3, 64}, {3, 128}, {3, 256}, {3, 512}, {2, 0}, {4, 0}};
   SpatialArgs probe{};
   probe.spatial = h->cur.spatial;
   probe.W = h->W;
   probe.H = h->H;
   const bool pp_ok = spatial_pp_supported(probe);
+  const bool fused_ok = h->W == 256 && h->H == 256;  // ASP or Fresnel (checked above)
   float best = 1e30f;
   int best_kind = 1;
   uint32_t best_chunk = h->chunk;
-  for (int ci = 0; ci < 10; ++ci) {
+  for (int ci = 0; ci < 11; ++ci) {
     const Cand c = cands[ci];
     if (c.kind == 2 && !cluster_ok(h)) continue;
     if (c.kind == 3 && !pp_ok) continue;
-    const uint32_t ch = c.kind == 2 ? n : std::min(c.chunk, n);
+    if (c.kind == 4 && !fused_ok) continue;
+    const uint32_t ch = (c.kind == 2 || c.kind == 4) ? n : std::min(c.chunk, n);
+    if (c.kind == 4 && ensure(h, reinterpret_cast<void**>(&h->fused_ctr), &h->fused_ctr_bytes,
+                              (1 + 3 * size_t(kFusedRing)) * sizeof(unsigned)) != HV_OK)
+      continue;
     if (c.kind != 2) {
-      const size_t need = size_t(ch) * fbytes;
+      const size_t need = size_t(c.kind == 4 ? kFusedRing : ch) * fbytes;
       if (ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need) != HV_OK) continue;
       if (h->cur.spatial == HV_SPATIAL_ASP &&
           ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need) != HV_OK)
@@ -585,7 +609,8 @@ hv_status tune_spatial(hv_handle* h) {
     }
     h->sp_cluster = c.kind == 2;
     h->sp_pp = c.kind == 3;
-    h->chunk = c.kind == 2 ? h->chunk : ch;
+    h->sp_fused = c.kind == 4;
+    h->chunk = (c.kind == 2 || c.kind == 4) ? h->chunk : ch;
     const uint64_t before = h->st.frames_propagated;
     hv_status st = propagate(h, 0, n);  // warm-up
     if (st != HV_OK) return st;
@@ -604,15 +629,24 @@ hv_status tune_spatial(hv_handle* h) {
     if (us_per_frame < best) {
       best = us_per_frame;
       best_kind = c.kind;
-      best_chunk = c.kind == 2 ? best_chunk : ch;
+      best_chunk = (c.kind == 2 || c.kind == 4) ? best_chunk : ch;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->sp_cluster = best_kind == 2;
   h->sp_pp = best_kind == 3;
+  h->sp_fused = best_kind == 4;
   h->chunk = best_chunk;
-  t.spatial_kernel = best_kind == 2 ? HV_SK_CLUSTER : (best_kind == 3 ? HV_SK_PERSISTENT : HV_SK_MULTIPASS);
+  // the chosen kernels' scratch: chunk frames (multi-pass), the rings (fused)
+  if (best_kind != 2) {
+    const size_t need = size_t(best_kind == 4 ? std::max(best_chunk, kFusedRing) : best_chunk) * fbytes;
+    if (ensure(h, reinterpret_cast<void**>(&h->s1), &h->s1_bytes, need) != HV_OK ||
+        (h->cur.spatial == HV_SPATIAL_ASP && ensure(h, reinterpret_cast<void**>(&h->s2), &h->s2_bytes, need) != HV_OK))
+      return HV_ERR_NOMEM;
+  }
+  t.spatial_kernel = best_kind == 2 ? HV_SK_CLUSTER
+                     : (best_kind == 3 ? HV_SK_PERSISTENT : (best_kind == 4 ? HV_SK_FUSED : HV_SK_MULTIPASS));
   t.spatial_chunk = best_chunk;
   t.tuned = 1;
   h->tuning = t;
@@ -1086,6 +1120,7 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->s2);
   dfree(h->tw);
   dfree(h->dev_err);
+  dfree(h->fused_ctr);
   dfree(h->asp_ht);
   dfree(h->staging);
   if (h->pca_ws) cudaFree(h->pca_ws);

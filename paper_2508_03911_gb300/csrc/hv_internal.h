@@ -38,13 +38,25 @@ struct SpatialArgs {
   uint32_t tam_stride;
   int discard_inputs;   // persistent passes: scratch1/scratch2 are read once, drop their L2 lines after staging
   float* cells;         // PASS_ROW_CELLS output [n][H/2][W/2]
-  unsigned* err;        // device flags (bit 3: a row pass's wait for its staged strip gave up); may be NULL
+  unsigned* err;        // device flags (bit 3: a row pass's wait for its staged strip gave up;
+                        // bit 4: a fused-transform wait for another CTA's pass gave up); may be NULL
+  // fused transform (one persistent launch for every pass of every frame, 256 x 256):
+  // scratch1 / scratch2 are rings of `ring` frames each, fused_ctr holds
+  // 1 + 3 ring counters (ticket, then per-slot completed strips of each pass)
+  int use_fused;
+  uint32_t ring;
+  unsigned* fused_ctr;
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);
 bool spatial_pp_supported(const SpatialArgs& a);
 cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launches);
 cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* launches);
+// Fused transform: frames of 256 x 256, ASP or Fresnel; needs ring >= kFusedRing
+// frames in scratch1 (and scratch2 for ASP), fused_ctr and err.
+constexpr uint32_t kFusedRing = 64;
+bool spatial_fused_supported(const SpatialArgs& a);
+cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* launches);
 
 // Single passes of the persistent multi-pass transform (sides 64..512):
 //   PASS_COL_FFT   raw -> column FFT (chirped when spatial is Fresnel) -> scratch1 [ky][x]

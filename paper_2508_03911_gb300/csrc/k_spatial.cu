@@ -222,6 +222,7 @@ cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches) 
     ++*launches;
     return cudaGetLastError();
   }
+  if (a.use_fused && spatial_fused_supported(a)) return launch_spatial_fused(a, s, launches);
   if (a.use_cluster && spatial_cluster_supported(a)) return launch_spatial_cluster(a, s, launches);
   if (a.use_pp && spatial_pp_supported(a)) return launch_spatial_pp(a, s, launches);
   switch (a.H) {

@@ -76,9 +76,9 @@ struct SmemSrc {
 
 // Element t (row y) of column b from a staged raw strip [y][BT], converted to
 // complex; with the Fresnel chirp cy[y] * cx (cx: this thread's column factor).
-template <bool U8, bool CHIRP, int BT>
+template <bool U8, bool CHIRP, int BT, bool ALIAS = false>
 struct RawSrc {
-  static constexpr bool kAliasesBuf = false;
+  static constexpr bool kAliasesBuf = ALIAS;  // staged inside the FFT buffer: read all before writing
   const unsigned char* raw;
   const float2* cy;
   float2 cx;
@@ -183,7 +183,15 @@ struct LastStage {
 // tws[e] = exp(-2 pi i e / L). The last stage hands bin k of line b to epi.
 // With an epilogue of kJFast, the last stage maps threads bin-fastest (b = idx / NB,
 // j = idx % NB) and takes its twiddles from twl[(m - 1) NS + j] (contiguous in j).
-template <int L, int NS, int DIR, class Src, class Epi, int LDX = 0>
+// Barrier between stages: the whole CTA (BAR = 0), or named barrier BAR over the
+// pass's NT threads (warp-specialised kernels whose other warps do not take part).
+template <int BAR, int NT>
+__device__ __forceinline__ void pp_sync() {
+  if constexpr (BAR == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;\n" ::"n"(BAR), "n"(NT) : "memory");
+}
+
+template <int L, int NS, int DIR, class Src, class Epi, int LDX = 0, int BAR = 0>
 __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const float2* tws, const Epi& epi,
                                           const float2* twl = nullptr) {
   using C = PpCfg<L>;
@@ -216,7 +224,7 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
     dft<R, DIR>(v[it]);
   }
   if constexpr (LAST) {
-    if constexpr (Epi::kSyncFirst) __syncthreads();  // every read of buf is done
+    if constexpr (Epi::kSyncFirst) pp_sync<BAR, NT>();  // every read of buf is done
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       const int idx = threadIdx.x + it * NT;
@@ -225,7 +233,7 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
       for (int m = 0; m < R; ++m) epi(b, j + m * NB, v[it][m]);
     }
   } else {
-    if constexpr (Src::kAliasesBuf) __syncthreads();
+    if constexpr (Src::kAliasesBuf) pp_sync<BAR, NT>();
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       const int idx = threadIdx.x + it * NT;
@@ -234,9 +242,9 @@ __device__ __forceinline__ void pp_stages(const Src& src, float2* buf, const flo
 #pragma unroll
       for (int m = 0; m < R; ++m) buf[(base + m * NS) * LD + b] = v[it][m];
     }
-    __syncthreads();
+    pp_sync<BAR, NT>();
     SmemSrc<LD> s{buf};
-    pp_stages<L, NS * R, DIR, SmemSrc<LD>, Epi, LDX>(s, buf, tws, epi, twl);
+    pp_stages<L, NS * R, DIR, SmemSrc<LD>, Epi, LDX, BAR>(s, buf, tws, epi, twl);
   }
 }
 
@@ -837,6 +845,340 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------- fused transform, 256 x 256 frames
+//
+// Every pass of every frame of a launch in one persistent kernel. The passes
+// above each run as a launch of their own over a chunk of frames, so their
+// intermediates (S1, S2: 512 KB per frame) go through HBM once written and once
+// read. Here work items come in a fixed global order from an atomic ticket
+// counter: row r of the order holds the 16 strips of pass 1 of frame r, of pass
+// 2 of frame r - LAG and (ASP) of pass 3 of frame r - 2 LAG. S1 and S2 are rings
+// of RING frames that stay in L2. An item may start once the counters that make
+// its input complete and its output slot free have been published:
+//   pass 1 of f: the 16 row-pass items of f - RING have read S1 slot f mod RING
+//   pass 2 of f: the 16 column items of f wrote S1 slot; (ASP) the 16 column-IFFT
+//                items of f - RING have read S2 slot
+//   pass 3 of f: the 16 row-pass items of f wrote S2 slot
+// A CTA is warp-specialised: one producer warp takes the tickets, waits (bounded
+// spin on acquire loads) for each item's counters, stages its input strip into
+// one of two buffers with cp.async completing on the buffer's mbarrier, and
+// publishes every finished item (fence, atomic add on its slot counter); eight
+// consumer warps transform the staged strip while the next one streams in. Every
+// wait is on an item with a smaller ticket (RING > LAG); a producer holds at most
+// the item being staged and the one being transformed, and publishes the latter
+// from inside its own waits, so the item with the smallest unfinished ticket
+// always completes: the launch ends. Raw frames are read with an evict-first L2
+// policy and the propagated frames stored with streaming stores, so that the two
+// rings keep their L2 lines.
+constexpr int FZ_NT = 256;       // consumer threads (one pass's thread layout)
+constexpr int FZ_THREADS = FZ_NT + 32;
+constexpr int FZ_LAG = 24;
+constexpr int FZ_BAR = 1;        // named barrier of the consumer warps
+constexpr size_t FZ_FRAME = size_t(RW_L) * RW_L;  // complex values per frame
+constexpr size_t FZ_BUF = size_t(256) * 16;       // complex values per buffer
+constexpr size_t FZ_RAW = 256 * 32;               // bytes of a raw strip (uint16), in the buffer's tail
+static_assert(kFusedRing > 2 * FZ_LAG, "the rings must outlast the lag between passes");
+// shared memory: pass twiddles (256), row-FFT stage-2 twiddles (240), Fresnel
+// chirp along y (256), two buffers of 16 lines x 256 (the column passes' lines
+// fastest with row stride 16, the row tile 16 x 256; a raw strip lands in the
+// tail of its buffer and is read whole by the first FFT stage before it writes)
+constexpr size_t FZ_SMEM = (256 + 240 + 256 + 2 * FZ_BUF) * sizeof(float2);
+constexpr uint32_t FZ_STOP = 0xffffffffu;
+
+// Bin k of line b to global memory at out[k * stride + b] with a streaming store.
+struct GlobalOutCs {
+  static constexpr bool kSyncFirst = false;
+  static constexpr bool kJFast = false;
+  float2* out;
+  uint32_t stride;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { __stcs(&out[size_t(k) * stride + b], v); }
+};
+
+__device__ __forceinline__ void cpa16_hint(void* s, const void* g, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(s))),
+               "l"(g), "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+struct FzItem {
+  uint32_t pass, frame, strip;
+};
+
+__global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, uint32_t nticket) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tws = reinterpret_cast<float2*>(smem);
+  float2* tw2 = tws + 256;
+  float2* cys = tw2 + 240;
+  float2* bufs = cys + 256;  // buffer b at bufs + b FZ_BUF
+  // raw strip of buffer b: its last FZ_RAW bytes
+  auto raw_of = [&](int b) {
+    return reinterpret_cast<unsigned char*>(bufs + (b + 1) * FZ_BUF) - FZ_RAW;
+  };
+  __shared__ __align__(8) unsigned long long full[2], freed[2];
+  __shared__ FzItem desc[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool asp = a.spatial == HV_SPATIAL_ASP;
+  const bool u8 = a.in_kind == IN_U8;
+  const uint32_t npass = asp ? 3u : 2u, ipr = 16u * npass, R = a.ring;
+  for (int e = tid; e < 256; e += FZ_THREADS) {
+    tws[e] = __ldg(&a.tw_h[e]);
+    cys[e] = asp ? make_float2(1.f, 0.f) : __ldg(&a.chirp_y[e]);
+  }
+  for (int e = tid; e < 240; e += FZ_THREADS) {
+    const int m = e / 16 + 1, j = e % 16;
+    tw2[e] = __ldg(&a.tw_w[j * m]);
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      // full: 32 cp.async arrivals of the producer lanes + one arrival after the descriptor
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 33;\n" ::"r"(rw_smem(&full[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&freed[b])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  float2* const tq = static_cast<float2*>(a.tq.base);
+  unsigned* const done = a.fused_ctr + 1;  // done[pass * R + slot]
+
+  if (warp == FZ_NT / 32) {
+    // ------------------------------------------------------------ producer
+    uint64_t pol_first;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol_first));
+    bool have_pend = false, ok = true;  // lane 0: an item transformed or being transformed, not yet published
+    FzItem pend{0, 0, 0};
+    uint32_t pend_k = 0;
+    const long long limit = 1ll << 31;
+    // release-add: the consumers' stores, ordered before the producer by the buffer's
+    // mbarrier, are visible at GPU scope before the count; nothing waits on a reply
+    auto publish = [&](const FzItem& it) {
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&done[it.pass * R + it.frame % R])
+                   : "memory");
+    };
+    // lane 0 keeps the next ticket's fetch in flight while it handles the current one
+    uint32_t t_next = lane == 0 ? atomicAdd(a.fused_ctr, 1u) : 0u;
+    uint32_t k = 0;
+    for (;; ++k) {
+      uint32_t pass = 0, f = 0, strip = 0, stop = 0;
+      if (lane == 0) {
+        while (true) {
+          const uint32_t t = t_next;
+          if (t >= nticket) {
+            stop = 1;
+            break;
+          }
+          t_next = atomicAdd(a.fused_ctr, 1u);
+          const uint32_t row = t / ipr, kk = t % ipr;
+          pass = kk / 16u;
+          strip = kk % 16u;
+          const long long fl = (long long)row - (long long)pass * FZ_LAG;
+          if (fl >= 0 && fl < (long long)a.n) {
+            f = uint32_t(fl);
+            break;
+          }
+        }
+        if (!stop) {
+          // wait for the item's counters, publishing the pending item meanwhile
+          const uint32_t slot = f % R, gen = f / R;
+          const long long t0 = clock64();
+          while (true) {
+            bool ready;
+            if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 16u * gen;
+            else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 16u * (gen + 1) &&
+                                        (!asp || ld_acquire_u32(&done[2 * R + slot]) >= 16u * gen);
+            else ready = ld_acquire_u32(&done[R + slot]) >= 16u * (gen + 1);
+            if (have_pend && mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
+              publish(pend);
+              have_pend = false;
+            }
+            if (ready) break;
+            if ((*reinterpret_cast<const volatile unsigned*>(a.err) & 16u) || clock64() - t0 > limit) {
+              ok = false;
+              atomicOr(a.err, 16u);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+      }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (stop || !ok) break;
+      pass = __shfl_sync(0xffffffffu, pass, 0);
+      f = __shfl_sync(0xffffffffu, f, 0);
+      strip = __shfl_sync(0xffffffffu, strip, 0);
+      // buffer k & 1 is free: item k - 2 was transformed and published before item k - 1 was staged
+      const int b = int(k & 1);
+      const uint32_t s0 = strip * 16u, slot = f % R;
+      float2* buf = bufs + b * FZ_BUF;
+      if (lane == 0) desc[b] = FzItem{pass, f, strip};
+      if (pass == 0) {
+        const int bpp = u8 ? 1 : 2, seg = 16 * bpp, pieces = seg / 16;
+        const size_t rslot = (a.raw.slot0 + f) % a.raw.cap;
+        const unsigned char* src = static_cast<const unsigned char*>(a.raw.base) + (rslot * FZ_FRAME + s0) * bpp;
+        unsigned char* dst = raw_of(b);
+        for (int e = lane; e < 256 * pieces; e += 32) {
+          const int y = e / pieces, q = e % pieces;
+          cpa16_hint(dst + y * seg + q * 16, src + size_t(y) * 256 * bpp + q * 16, pol_first);
+        }
+      } else if (pass == 1) {
+        const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
+        for (int e = lane; e < 16 * 256 / 2; e += 32) cpa16(buf + 2 * e, src + 2 * e);
+      } else {
+        const float2* src = a.scratch2 + size_t(slot) * FZ_FRAME + s0;
+        for (int e = lane; e < 256 * 8; e += 32) {
+          const int y = e >> 3, q = e & 7;
+          cpa16(buf + y * 16 + 2 * q, src + size_t(y) * 256 + 2 * q);
+        }
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+        // publish item k - 1 once its transform is done (the consumers then start item k)
+        if (have_pend) {
+          const long long t0 = clock64();
+          while (!mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
+            if (clock64() - t0 > limit) {
+              ok = false;
+              atomicOr(a.err, 16u);
+              break;
+            }
+          }
+          if (ok) publish(pend);
+        }
+        have_pend = true;
+        pend = FzItem{pass, f, strip};
+        pend_k = k;
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+    }
+    // publish the last item, then tell the consumers to stop (item k, buffer k & 1)
+    if (lane == 0 && ok && have_pend) {
+      const long long t0 = clock64();
+      while (!mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
+        if (clock64() - t0 > limit) {
+          ok = false;
+          atomicOr(a.err, 16u);
+          break;
+        }
+      }
+      if (ok) publish(pend);
+    }
+    const int b = int(k & 1);
+    if (lane == 0) desc[b] = FzItem{FZ_STOP, 0, 0};
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+    cpa_wait_all();
+    return;
+  }
+
+  // ------------------------------------------------------------- consumers
+  const int rb = 2 * warp + (lane >> 4), jl = lane & 15;  // row pass: row of the strip, lane in the row
+  for (uint32_t k = 0;; ++k) {
+    const int b = int(k & 1);
+    if (!rw_wait(rw_smem(&full[b]), (k >> 1) & 1)) {
+      if (tid == 0) atomicOr(a.err, 16u);
+      break;
+    }
+    const FzItem it = desc[b];
+    if (it.pass == FZ_STOP) break;
+    const uint32_t pass = it.pass, f = it.frame, s0 = it.strip * 16u, slot = f % R;
+    float2* buf = bufs + b * FZ_BUF;
+    float2* s1 = a.scratch1 + size_t(slot) * FZ_FRAME;
+    float2* s2 = a.scratch2 + size_t(slot) * FZ_FRAME;
+    const size_t tslot = (a.tq.slot0 + f) % a.tq.cap;
+    if (pass == 0) {
+      // column FFT of 16 raw columns (conversion and chirp in the first stage) -> S1 [ky][x]
+      const unsigned char* raw = raw_of(b);
+      const GlobalOut out{s1 + s0, 256u};
+      if (asp) {
+        if (u8) pp_stages<256, 1, -1, RawSrc<true, false, 16, true>, GlobalOut, 16, FZ_BAR>(
+                    RawSrc<true, false, 16, true>{raw, cys, make_float2(0.f, 0.f)}, buf, tws, out);
+        else pp_stages<256, 1, -1, RawSrc<false, false, 16, true>, GlobalOut, 16, FZ_BAR>(
+                 RawSrc<false, false, 16, true>{raw, cys, make_float2(0.f, 0.f)}, buf, tws, out);
+      } else {
+        const float2 cx = __ldg(&a.chirp_x[s0 + (tid % 16)]);
+        if (u8) pp_stages<256, 1, -1, RawSrc<true, true, 16, true>, GlobalOut, 16, FZ_BAR>(
+                    RawSrc<true, true, 16, true>{raw, cys, cx}, buf, tws, out);
+        else pp_stages<256, 1, -1, RawSrc<false, true, 16, true>, GlobalOut, 16, FZ_BAR>(
+                 RawSrc<false, true, 16, true>{raw, cys, cx}, buf, tws, out);
+      }
+    } else if (pass == 1) {
+      // 16 rows ky = s0 .. s0 + 15 of S1 -> row FFT [x H, row IFFT]; the staged strip of
+      // S1 is dead: drop its L2 lines unwritten
+      asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s1 + size_t(s0) * 256 + size_t(tid) * 16) : "memory");
+      float2* rowp = buf + rb * 256;
+      const int ky = int(s0) + rb;
+      float2 v[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = rowp[jl + 16 * m];
+      dft<16, -1>(v);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 16; ++m) rowp[16 * jl + (m ^ jl)] = v[m];
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        v[m] = rowp[16 * m + (jl ^ m)];
+        if (m > 0) v[m] = cmul(v[m], tw2[(m - 1) * 16 + jl]);
+      }
+      dft<16, -1>(v);
+      if (asp) {
+        const float2* hrow = a.asp_h + size_t(ky) * 256;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], __ldg(&hrow[jl + 16 * m]));
+        dft<16, +1>(v);
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) rowp[16 * jl + (m ^ jl)] = v[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          v[m] = rowp[16 * m + (jl ^ m)];
+          if (m > 0) {
+            float2 w = tw2[(m - 1) * 16 + jl];
+            w.y = -w.y;
+            v[m] = cmul(v[m], w);
+          }
+        }
+        dft<16, +1>(v);
+        float2* out = s2 + size_t(ky) * 256;  // S2 [ky][x]
+#pragma unroll
+        for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
+      } else {
+        float2* out = tq + (tslot * 256 + size_t(ky)) * 256;  // time queue [ky][kx]
+#pragma unroll
+        for (int m = 0; m < 16; ++m) __stcs(&out[jl + 16 * m], v[m]);
+      }
+    } else {
+      // column IFFT of 16 columns x = s0 .. s0 + 15 of S2 -> time queue [y][x]
+      asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s2 + s0 + size_t(tid) * 256) : "memory");
+      pp_stages<256, 1, +1, SmemSrc<16>, GlobalOutCs, 16, FZ_BAR>(SmemSrc<16>{buf}, buf, tws,
+                                                                  GlobalOutCs{tq + tslot * FZ_FRAME + s0, 256u});
+    }
+    // every consumer is done with the buffer and has issued the item's stores
+    pp_sync<FZ_BAR, FZ_NT>();
+    if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&freed[b])) : "memory");
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pp_pass(const SpatialArgs& a, int pass, cudaStream_t s) {
@@ -873,6 +1215,35 @@ cudaError_t launch_spatial_pp(const SpatialArgs& a0, cudaStream_t s, int* launch
     case 1024: return pp_w<1024>(a, s, launches);
   }
   return cudaErrorInvalidValue;
+}
+
+bool spatial_fused_supported(const SpatialArgs& a) {
+  return a.W == RW_L && a.H == RW_L && (a.spatial == HV_SPATIAL_ASP || a.spatial == HV_SPATIAL_FRESNEL) &&
+         a.ring >= kFusedRing && a.fused_ctr && a.err && a.scratch1 &&
+         (a.spatial == HV_SPATIAL_FRESNEL || (a.scratch2 && a.asp_h));
+}
+
+cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* launches) {
+  if (a.n == 0) return cudaSuccess;
+  if (!spatial_fused_supported(a)) return cudaErrorInvalidValue;
+  const uint32_t npass = a.spatial == HV_SPATIAL_ASP ? 3u : 2u;
+  const uint64_t nt = (uint64_t(a.n) + uint64_t(npass - 1) * FZ_LAG) * 16u * npass;
+  if (nt >= (1ull << 31)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(a.fused_ctr, 0, (1 + 3 * size_t(a.ring)) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_spatial_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(FZ_SMEM));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spatial_fused, FZ_THREADS, FZ_SMEM);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  uint64_t grid = uint64_t(per_sm) * nsm;  // every CTA resident: the items' waits rely on it
+  if (grid > nt) grid = nt;
+  k_spatial_fused<<<unsigned(grid), FZ_THREADS, FZ_SMEM, s>>>(a, uint32_t(nt));
+  ++*launches;
+  return cudaGetLastError();
 }
 
 }  // namespace hv

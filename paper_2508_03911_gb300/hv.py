@@ -201,7 +201,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.precision = PRECISION[precision]
     p.tuned = int(tuned)
     p.spatial_chunk = spatial_chunk
-    p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3}[spatial_kernel]
+    p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3, "fused": 4}[spatial_kernel]
     p.highpass_cpp = highpass
     return p
 

@@ -159,8 +159,8 @@ def test_autotuned_form_matches_oracle():
         n = r.render(out)
         t = hv.hv_get_tuning(r.h)
         torch.cuda.synchronize()
-        assert t["tuned"] == 1 and t["spatial_kernel"] in (1, 2, 3)
-        assert all(v > 0 for v in t["candidate_us_per_frame"][:10])
+        assert t["tuned"] == 1 and t["spatial_kernel"] in (1, 2, 3, 4)
+        assert all(v > 0 for v in t["candidate_us_per_frame"][:11])
         img = out.cpu().numpy()[: n * 2 * N * N].reshape(n, 2, N, N)
         check_images(img, O.render(fr, p))
     finally:
@@ -429,3 +429,65 @@ def test_persistent_passes_through_stft(spatial, T, S):
     ref = O.render(fr, p)
     check_images(img, ref)
     assert st["windows_rendered"] == ref.shape[0]
+
+
+# ------------------------------------------------- fused spatial transform
+
+@pytest.mark.parametrize("spatial,bits", [("asp", 12), ("asp", 8), ("fresnel", 12), ("fresnel", 8)])
+def test_fused_spatial_field_parity(spatial, bits):
+    """The fused transform at 256 x 256: every pass of every frame in one persistent
+    launch, intermediates in rings of 64 frames. 130 frames pushed as packets of 1,
+    57 and 72 (launches of one frame and of more than two ring generations; input
+    and time-queue rings wrapping), every field against the oracle."""
+    N, n = 256, 130
+    fr = synth.random_frames(n, N, N, bits, seed=400 + bits + (1 if spatial == "asp" else 2))
+    p = oracle_params(spatial=spatial, z_m=0.27, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
+                      H=N, W=N)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="fused"), packets=[1, 57, 72], queue=100,
+                         tq=90)
+    ref = oracle_fields(fr, p)
+    assert img.shape == ref.shape
+    for i in range(n):
+        assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
+    assert st["frames_propagated"] == n
+
+
+@pytest.mark.parametrize("spatial,T,S,highpass", [("asp", 64, 64, 0.0), ("asp", 32, 8, 0.03),
+                                                  ("fresnel", 64, 16, 0.0)])
+def test_fused_passes_through_stft(spatial, T, S, highpass):
+    """The fused transform feeding the STFT: every moment against the oracle (u8
+    frames, several windows, the high-pass filter folded into H)."""
+    H = W = 256
+    n = T + 5 * S + 3
+    fr = synth.random_frames(n, H, W, 8, seed=T + S + 17)
+    p = oracle_params(spatial=spatial, z_m=0.3, T=T, stride=S, fs_hz=20000.0, band_lo_bin=2,
+                      band_hi_bin=T // 2 - 2, moments=ALL_MOMENTS, H=H, W=W, highpass=highpass)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="fused"), packets=[T + S, n - T - S])
+    ref = O.render(fr, p)
+    check_images(img, ref)
+    assert st["windows_rendered"] == ref.shape[0]
+
+
+def test_fused_rejects_other_sizes():
+    r = hv.Renderer(128, 128, 16, 8)
+    try:
+        p = oracle_params(H=128, W=128, T=8, stride=8, band_lo_bin=1, band_hi_bin=3)
+        with pytest.raises(hv.HvError) as ei:
+            hv.hv_set_params(r.h, to_hv(p, spatial_kernel="fused"))
+        assert ei.value.status == hv.HV_ERR_UNSUPPORTED
+    finally:
+        r.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("spatial", ["fresnel", "asp"])
+def test_fused_paper_scale_stream_prefix(spatial):
+    """The paper-scale stream's shape through the fused transform: 256x256 12-bit,
+    T=512 S=64, M0/M1/M2 over 1..35 kHz at fs = 71.4 kHz, the first 768 frames."""
+    sc = synth.build(synth.scene_stream_fresnel())
+    fr = synth.frames(sc, 0, 768)
+    klo, khi = O.band_bins_from_hz(1000.0, 35000.0, 71400.0, 512)
+    p = oracle_params(spatial=spatial, z_m=0.25, T=512, stride=64, fs_hz=71400.0,
+                      band_lo_bin=klo, band_hi_bin=khi, moments=("M0", "M1", "M2"), H=256, W=256)
+    img, _ = gpu_render(fr, p, extra=dict(spatial_kernel="fused"))
+    check_images(img, O.render(fr, p))
