@@ -1403,7 +1403,10 @@ def main():
                        "candidates_us_per_frame": dict(zip(
                            ["mp16", "mp32", "mp64", "mp128", "mp256", "pp64", "pp128", "pp256",
                             "pp512", "cluster", "fused"],
-                           [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:11]]))},
+                           [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:11]])),
+                       "stft_kernel": {1: "walk", 2: "window"}.get(res["tuning"].get("stft_kernel"), "walk"),
+                       "stft_candidates_us_per_window": dict(zip(
+                           ["walk", "window"], [round(v, 3) for v in res["tuning"]["stft_us_per_window"][:2]]))},
         }
         if plain is not None:
             line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),

@@ -110,6 +110,11 @@ typedef struct {
                                  radius sqrt((m/W)^2 + (n/H)^2) in cycles per pixel is
                                  below this cutoff are zeroed; 0 = off. Folded into
                                  the transfer function. */
+  int32_t stft_kernel;        /* STFT kernel for windows that do not overlap (S >= T):
+                                 0 = automatic (the autotuner's choice when tuned = 1,
+                                 else the walking kernel launched once per window),
+                                 HV_STFT_WALK or HV_STFT_WINDOW                       */
+  uint32_t reserved;
 } hv_params;
 
 /* Spatial kernel selection: automatic = the autotuner's choice when tuned = 1,
@@ -184,13 +189,20 @@ typedef struct {
   int32_t tuned;                    /* 1 once the autotuner has run                   */
   int32_t spatial_kernel;           /* HV_SK_MULTIPASS, _CLUSTER, _PERSISTENT or _FUSED */
   uint32_t spatial_chunk;           /* frames per multi-pass launch                   */
-  uint32_t reserved;
+  int32_t stft_kernel;              /* HV_STFT_WALK or HV_STFT_WINDOW                  */
   float candidate_us_per_frame[12]; /* measured us per frame: multi-pass with 16, 32, 64,
                                        128, 256 frames per launch; persistent
                                        multi-pass with 64, 128, 256, 512; the cluster
                                        kernel; the fused transform (0 where not
                                        applicable)                                    */
+  float stft_us_per_window[4];      /* measured us per window of the STFT kernels:
+                                       walking (CTAs walk every window of their
+                                       pixels), one CTA per (window, pixel tile); 0
+                                       where not applicable (the latter needs S >= T) */
 } hv_tuning;
+
+/* STFT kernels the autotuner chooses between (windows that do not overlap). */
+enum { HV_STFT_WALK = 1, HV_STFT_WINDOW = 2 };
 
 /* The autotuner's choices for the applied settings. Errors: HV_ERR_STATE. */
 hv_status hv_get_tuning(const hv_handle* h, hv_tuning* t);

@@ -51,6 +51,7 @@ struct hv_handle {
   int sp_cluster = 0;         // 1: whole-frame cluster kernel
   int sp_pp = 0;              // 1: persistent multi-pass kernels
   int sp_fused = 0;           // 1: fused transform (s1 / s2 are rings of kFusedRing frames)
+  int stft_kernel = STFT_AUTO;  // STFT kernel for windows that do not overlap (autotuner's choice)
   unsigned* fused_ctr = nullptr;  // its ticket and per-slot counters
   size_t fused_ctr_bytes = 0;
   hv_tuning tuning{};
@@ -175,6 +176,10 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     return HV_ERR_ARG;
   }
   if (p.spatial_kernel > HV_SK_FUSED) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
+  if (p.stft_kernel != 0 && p.stft_kernel != HV_STFT_WALK && p.stft_kernel != HV_STFT_WINDOW) {
+    why = "unknown stft_kernel";
+    return HV_ERR_ARG;
+  }
   if (p.spatial_kernel == HV_SK_FUSED &&
       (p.width != 256 || p.height != 256 || (p.spatial != HV_SPATIAL_ASP && p.spatial != HV_SPATIAL_FRESNEL))) {
     why = "the fused spatial transform needs 256 x 256 frames and ASP or Fresnel";
@@ -317,6 +322,7 @@ hv_status ensure(hv_handle* h, void** p, size_t* have, size_t need) {
 }
 
 hv_status tune_spatial(hv_handle* h);
+hv_status tune_temporal(hv_handle* h);
 
 // Apply the pending settings (window boundary).
 hv_status apply_pending(hv_handle* h) {
@@ -472,8 +478,16 @@ hv_status apply_pending(hv_handle* h) {
   h->tuning = hv_tuning{};
   h->tuning.spatial_chunk = chunk;
   h->tuning.spatial_kernel = p.spatial_kernel == HV_SK_AUTO ? HV_SK_MULTIPASS : int32_t(p.spatial_kernel);
+  // STFT kernel for windows that do not overlap: the caller's, the autotuner's (tuned),
+  // else the walking kernel launched once per window (the plain form)
+  h->stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? STFT_AUTO : STFT_WALK;
+  h->tuning.stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? HV_STFT_WINDOW : HV_STFT_WALK;
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
     s = tune_spatial(h);
+    if (s != HV_OK) return s;
+  }
+  if (p.tuned && p.stft_kernel == 0 && p.temporal == HV_TEMPORAL_STFT && d.S >= d.T) {
+    s = tune_temporal(h);
     if (s != HV_OK) return s;
   }
   // queue flush: the next window starts at the first unconsumed frame and is
@@ -575,7 +589,9 @@ hv_status tune_spatial(hv_handle* h) {
     return HV_OK;
   }
   const size_t fbytes = size_t(h->W) * h->H * sizeof(float2);
-  const uint32_t n = std::min<uint32_t>(512, std::min(h->Q, h->cap));
+  // frames per timed run: a render's worth where the rings allow (the fused
+  // transform's pipeline fill and drain weigh on short runs)
+  const uint32_t n = std::min<uint32_t>(2048, std::min(h->Q, h->cap));
   cudaEvent_t e0, e1;
   HV_CU(h, cudaEventCreate(&e0));
   HV_CU(h, cudaEventCreate(&e1));
@@ -650,6 +666,69 @@ hv_status tune_spatial(hv_handle* h) {
   t.spatial_chunk = best_chunk;
   t.tuned = 1;
   h->tuning = t;
+  return HV_OK;
+}
+
+// Autotuner of the STFT for windows that do not overlap (S >= T): times the
+// walking kernel (CTAs walk every window of their pixels) and the kernel with one
+// CTA per (window, pixel tile) on the handle's time queue (its contents are being
+// flushed, so any values do) and keeps the faster.
+hv_status tune_temporal(hv_handle* h) {
+  const uint32_t T = h->T, S = h->S;
+  const uint32_t nwin = std::min<uint32_t>(16, (h->Q - T) / S + 1);
+  const size_t hw = size_t(h->W) * h->H;
+  float* out = nullptr;
+  HV_CU(h, cudaMalloc(&out, size_t(nwin) * h->nout * hw * sizeof(float)));
+  cudaEvent_t e0, e1;
+  HV_CU(h, cudaEventCreate(&e0));
+  HV_CU(h, cudaEventCreate(&e1));
+  StftArgs sa{};
+  sa.W = h->W;
+  sa.H = h->H;
+  sa.T = T;
+  sa.S = S;
+  sa.nwin = nwin;
+  sa.tq = RingRef{h->tq, h->Q, 0};
+  sa.tw_t = h->tw + tw_offset(T);
+  sa.klo = h->klo;
+  sa.khi = h->khi;
+  sa.fscale = float(h->cur.fs_hz / double(T) / 1000.0);
+  sa.mask = h->cur.moments_mask;
+  sa.nout = h->nout;
+  sa.out = out;
+  sa.err = h->dev_err;
+  const int kinds[2] = {STFT_WALK, STFT_AUTO};
+  float best = 1e30f;
+  int best_kind = STFT_AUTO;
+  hv_status st = HV_OK;
+  for (int ci = 0; ci < 2 && st == HV_OK; ++ci) {
+    sa.kernel = kinds[ci];
+    int launches = 0;
+    cudaError_t e = launch_stft(sa, h->stream, &launches);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_stft(sa, h->stream, &launches);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e, "STFT autotuning");
+      break;
+    }
+    const float us = 1000.f * ms / (3.f * nwin);
+    h->tuning.stft_us_per_window[ci] = us;
+    if (us < best) {
+      best = us;
+      best_kind = kinds[ci];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (st != HV_OK) return st;
+  h->stft_kernel = best_kind;
+  h->tuning.stft_kernel = best_kind == STFT_WALK ? HV_STFT_WALK : HV_STFT_WINDOW;
+  h->tuning.tuned = 1;
   return HV_OK;
 }
 
@@ -839,7 +918,19 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
     sa.nout = h->nout;
     sa.out = dst;
     sa.err = h->dev_err;
-    e = launch_stft(sa, h->stream, &launches);
+    sa.kernel = h->stft_kernel;
+    if (h->cur.tuned || h->cur.stft_kernel != 0) {
+      e = launch_stft(sa, h->stream, &launches);
+    } else {
+      // plain form: the walking kernel, one launch per window
+      sa.nwin = 1;
+      e = cudaSuccess;
+      for (uint32_t w = 0; w < nw && e == cudaSuccess; ++w) {
+        sa.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
+        sa.out = dst + size_t(w) * h->win_floats;
+        e = launch_stft(sa, h->stream, &launches);
+      }
+    }
   }
   if (e == cudaSuccess && h->post_active) {
     PostArgs pa{};

@@ -85,7 +85,10 @@ struct StftArgs {
   float* out;           // [nwin][nout][H*W]
   unsigned* err;        // device flags: bit 1 set when a wait for staged frames gave up
   int tma;              // set by the launcher: staged frames through a TMA tensor map
+  int kernel;           // STFT_AUTO: windows that do not overlap (S >= T) one CTA per
+                        // (window, pixel tile); STFT_WALK: CTAs walk all windows of their pixels
 };
+enum { STFT_AUTO = 0, STFT_WALK = 1 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
 // Encodes a 2-D tiled TMA tensor map (map: a CUtensorMap, 64-byte aligned) over

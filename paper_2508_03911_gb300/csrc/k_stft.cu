@@ -181,9 +181,10 @@ __device__ __forceinline__ void add_moments(const float2* v, int it, float kb, M
 // of its group (jl = lane within the group): stage 1 reads the window (T
 // samples from `win`, in order), later stages the pixel's work row; the last
 // stage feeds the moment sums.
-template <int T, int NS, int LP>
+template <int T, int NS, int LP, bool WP = false>
 __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const float2* tw, int jl,
                                          MomAcc& acc, bool lower) {
+  // WP: the window itself is stored padded (sample t at t + t / 16)
   constexpr int R = WarpPlan<T>::template radix<NS>();
   constexpr int NB = T / R;
   static_assert(NB % LP == 0, "lanes per pixel must divide the butterflies");
@@ -195,7 +196,7 @@ __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const 
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int t = j + m * NB;
-      if constexpr (NS == 1) v[it][m] = win[t];
+      if constexpr (NS == 1) v[it][m] = WP ? win[wpad(t)] : win[t];
       else v[it][m] = work[wpad(t)];
     }
     if constexpr (NS > 1) {
@@ -233,7 +234,7 @@ __device__ __forceinline__ void warp_fft(const float2* win, float2* work, const 
       for (int m = 0; m < R; ++m) work[wpad(base + m * NS)] = v[it][m];
     }
     __syncwarp();
-    warp_fft<T, NS * R, LP>(win, work, tw, jl, acc, lower);
+    warp_fft<T, NS * R, LP, WP>(win, work, tw, jl, acc, lower);
   }
 }
 
@@ -466,6 +467,113 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
   }
 }
 
+// Windows that do not overlap (S >= T): one CTA per (window, tile of BT pixels),
+// so that many windows are in flight per SM instead of one CTA walking all
+// windows of its pixels. The window's T frames of the CTA's pixels land by
+// cp.async straight in the pixels' padded work rows (sample t at t + t / 16; the
+// row stride adds two more values so that the eight rows of a CTA start in
+// different banks), and the FFT runs in place there: the first stage reads the
+// whole row into registers before any lane of the pixel writes. A CTA holds one
+// window, so its shared memory is a quarter of the walking kernel's and several
+// CTAs share an SM.
+template <int T>
+struct WinCfg {
+  using Lw = WarpLayout<T>;
+  // warps per CTA: 8 for short windows (a warp's fetch covers 32 pixels, 256
+  // contiguous bytes of a frame), else the walking kernel's count
+  static constexpr int NW = T <= 128 ? 8 : Lw::NW;
+  static constexpr int NT = 32 * NW;
+  static constexpr int BT = NW * Lw::PW;  // pixels per CTA
+  // row stride (float2): the padded row, rounded to 1 mod 16 so that the rows of
+  // consecutive pixels start in consecutive bank pairs
+  static constexpr int WR = (T + T / 16 + 15) / 16 * 16 + 1;
+  static constexpr int OCC = T >= 1024 ? 1 : (T >= 512 ? 4 : (T >= 256 ? 6 : 4));
+  static constexpr size_t bytes() { return (size_t(BT) * WR + (T - WarpPlan<T>::R1)) * sizeof(float2); }
+};
+
+template <int T>
+__global__ void __launch_bounds__(WinCfg<T>::NT, WinCfg<T>::OCC) k_stft_win(StftArgs a) {
+  using Lw = WarpLayout<T>;
+  using Wc = WinCfg<T>;
+  constexpr int NT = Wc::NT, LP = Lw::LP, PW = Lw::PW, BT = Wc::BT, WR = Wc::WR;
+  extern __shared__ __align__(16) unsigned char smem_win[];
+  float2* rows = reinterpret_cast<float2*>(smem_win);
+  float2* tw = rows + BT * WR;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pl = lane / LP, jl = lane % LP;
+  const int px = warp * PW + pl;
+  const size_t HW = size_t(a.W) * a.H;
+  const uint32_t ntile = uint32_t(HW / BT);
+  const uint32_t w = blockIdx.x / ntile;
+  const uint32_t p0 = (blockIdx.x % ntile) * BT;
+  const float2* tq = static_cast<const float2*>(a.tq.base);
+  const uint32_t cap = a.tq.cap;
+  // the window's frames: queue slots slot0 + w S + f (one wrap at most)
+  {
+    constexpr int FS = NT / BT;  // frames per pass of the CTA
+    const int b = tid % BT;
+    int f = tid / BT;
+    uint32_t g = a.tq.slot0 + w * a.S + uint32_t(f);
+    while (g >= cap) g -= cap;
+    for (; f < T; f += FS) {
+      cp_async8(&rows[b * WR + wpad(f)], &tq[size_t(g) * HW + p0 + b]);
+      g += FS;
+      if (g >= cap) g -= cap;
+    }
+    cp_async_commit();
+  }
+  {  // stage twiddles (the walking kernel's table layout)
+    constexpr int R1 = WarpPlan<T>::R1;
+    int NS = R1;
+    while (NS < T) {
+      const int rem = T / NS;
+      const int R = WarpPlan<T>::R2 != 0 ? WarpPlan<T>::R2 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
+      for (int idx = tid; idx < (R - 1) * NS; idx += NT) {
+        const int m = idx / NS + 1, jm = idx % NS;
+        tw[(NS - R1) + idx] = a.tw_t[jm * m * (T / (NS * R))];
+      }
+      NS *= R;
+    }
+  }
+  uint32_t band = 0;
+  {
+    constexpr int RL = Lw::RL, NBL = T / RL;
+#pragma unroll
+    for (int it = 0; it < Lw::ITL; ++it)
+#pragma unroll
+      for (int m = 0; m < RL; ++m) {
+        const uint32_t k = uint32_t(jl + LP * it + m * NBL);
+        if (k - a.klo <= a.khi - a.klo) band |= 1u << (it * RL + m);
+      }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const bool lower = a.khi < uint32_t(T / 2);
+  MomAcc acc{band, 0.f, 0.f, 0.f};
+  float2* row = rows + px * WR;
+  warp_fft<T, 1, LP, true>(row, row, tw, jl, acc, lower);
+#pragma unroll
+  for (int o = LP / 2; o > 0; o >>= 1) {
+    acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
+    acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
+    acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
+  }
+  if (jl == 0) {
+    const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
+    float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
+    int q = 0;
+    if (a.mask & HV_MOM_M0) __stcs(&o[HW * q++], acc.m0);
+    if (a.mask & HV_MOM_M1) __stcs(&o[HW * q++], m1);
+    if (a.mask & HV_MOM_M2) __stcs(&o[HW * q++], m2);
+    const double d0 = acc.m0;
+    if (a.mask & HV_MOM_M1N) __stcs(&o[HW * q++], d0 > 0.0 ? float(double(m1) / d0) : 0.f);
+    if (a.mask & HV_MOM_M2N) {
+      const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
+      __stcs(&o[HW * q++], float(sqrt(r > 0.0 ? r : 0.0)));
+    }
+  }
+}
+
 // cuTensorMapEncodeTiled from the driver (resolved once through the runtime)
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -513,6 +621,19 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
   if (a0.tq.slot0 >= a0.tq.cap || uint64_t(a0.nwin - 1) * a0.S + uint64_t(T) > a0.tq.cap)
     return cudaErrorInvalidValue;
   StftArgs a = a0;
+  if (a.S >= uint32_t(T) && a.kernel != STFT_WALK) {
+    // one CTA per (window, pixel tile)
+    using Wc = WinCfg<T>;
+    if (hw % Wc::BT == 0) {
+      const size_t smem = Wc::bytes();
+      cudaError_t e = cudaFuncSetAttribute(k_stft_win<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      const uint64_t grid = uint64_t(a.nwin) * (hw / Wc::BT);
+      if (grid >= (1ull << 31)) return cudaErrorInvalidValue;
+      k_stft_win<T><<<unsigned(grid), Wc::NT, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   CUtensorMap map{};
   a.tma = queue_map(a, Lw::BT, &map) ? 1 : 0;
   const size_t smem = WarpSmem<T>::bytes(a.S, a.tma != 0);

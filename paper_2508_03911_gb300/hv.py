@@ -52,7 +52,7 @@ class hv_params(C.Structure):
                 ("band_lo_hz", C.c_double), ("band_hi_hz", C.c_double),
                 ("pca_lo", C.c_uint32), ("pca_hi", C.c_uint32), ("precision", C.c_int32),
                 ("tuned", C.c_int32), ("spatial_chunk", C.c_uint32), ("spatial_kernel", C.c_uint32),
-                ("highpass_cpp", C.c_double)]
+                ("highpass_cpp", C.c_double), ("stft_kernel", C.c_int32), ("reserved", C.c_uint32)]
 
 
 class hv_stats(C.Structure):
@@ -75,7 +75,8 @@ class hv_peaks(C.Structure):
 
 class hv_tuning(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("spatial_kernel", C.c_int32), ("spatial_chunk", C.c_uint32),
-                ("reserved", C.c_uint32), ("candidate_us_per_frame", C.c_float * 12)]
+                ("stft_kernel", C.c_int32), ("candidate_us_per_frame", C.c_float * 12),
+                ("stft_us_per_window", C.c_float * 4)]
 
 
 class hv_post(C.Structure):
@@ -180,7 +181,7 @@ def hv_open(max_width, max_height, pixel_bits, queue_capacity_frames, device=0,
 def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pitch_y=None,
                 fftshift=1, temporal="stft", T=64, stride=None, fs=20000.0, band=(4, 28),
                 band_hz=None, moments=("M0",), pca=(2, 64), precision="fp32", tuned=0,
-                spatial_chunk=0, spatial_kernel="auto", highpass=0.0) -> hv_params:
+                spatial_chunk=0, spatial_kernel="auto", highpass=0.0, stft_kernel="auto") -> hv_params:
     p = hv_params()
     p.struct_size = C.sizeof(hv_params)
     p.width, p.height = width, height
@@ -203,6 +204,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.spatial_chunk = spatial_chunk
     p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3, "fused": 4}[spatial_kernel]
     p.highpass_cpp = highpass
+    p.stft_kernel = {"auto": 0, "walk": 1, "window": 2}[stft_kernel]
     return p
 
 
@@ -286,7 +288,8 @@ def hv_get_tuning(h) -> dict:
     t = hv_tuning()
     _check(h, lib().hv_get_tuning(h, C.byref(t)))
     return {"tuned": t.tuned, "spatial_kernel": t.spatial_kernel, "spatial_chunk": t.spatial_chunk,
-            "candidate_us_per_frame": list(t.candidate_us_per_frame)}
+            "candidate_us_per_frame": list(t.candidate_us_per_frame), "stft_kernel": t.stft_kernel,
+            "stft_us_per_window": list(t.stft_us_per_window)}
 
 
 def hv_synchronize(h):

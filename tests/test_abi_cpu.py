@@ -52,6 +52,7 @@ def test_open_rejects_bad_descriptor_without_touching_a_device():
 
 def test_params_struct_layout():
     # offsets the C side relies on (natural alignment, doubles on 8 bytes)
-    assert ctypes.sizeof(hv.hv_params) == 136
+    assert ctypes.sizeof(hv.hv_params) == 144
     assert hv.hv_params.z_m.offset == 24 and hv.hv_params.fs_hz.offset == 72
+    assert hv.hv_params.highpass_cpp.offset == 128 and hv.hv_params.stft_kernel.offset == 136
     assert ctypes.sizeof(hv.hv_open_desc) == 40

@@ -491,3 +491,60 @@ def test_fused_paper_scale_stream_prefix(spatial):
                       band_lo_bin=klo, band_hi_bin=khi, moments=("M0", "M1", "M2"), H=256, W=256)
     img, _ = gpu_render(fr, p, extra=dict(spatial_kernel="fused"))
     check_images(img, O.render(fr, p))
+
+
+# ------------------------------------------- STFT: one CTA per (window, tile)
+
+@pytest.mark.parametrize("T,S,band", [(8, 8, (1, 3)), (32, 40, (2, 20)), (64, 64, (4, 28)),
+                                      (128, 128, (1, 63)), (256, 300, (0, 127)), (512, 512, (8, 250)),
+                                      (512, 700, (3, 400)), (1024, 1024, (10, 300))])
+def test_window_per_cta_stft(T, S, band):
+    """Windows that do not overlap through the kernel with one CTA per (window, pixel
+    tile), frames landing straight in padded rows and transformed in place: every
+    moment against the oracle, bands below and across T/2, gaps between windows."""
+    H, W = 16, 32
+    n = T + 3 * S + 5
+    fr = synth.random_frames(n, H, W, 12, seed=T + 5 * S)
+    p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=band[0],
+                      band_hi_bin=band[1], moments=ALL_MOMENTS, H=H, W=W)
+    img, st = gpu_render(fr, p, extra=dict(stft_kernel="window"), packets=[T + S, n - T - S])
+    ref = O.render(fr, p)
+    check_images(img, ref)
+    assert st["windows_rendered"] == ref.shape[0]
+
+
+def test_stft_autotuner_times_both_kernels():
+    """tuned = 1 with S = T: both STFT kernels are timed on the handle's queue and the
+    faster kept; the rendered windows are the oracle's either way."""
+    import torch
+    N, T = 64, 64
+    fr = synth.random_frames(3 * T, N, N, 12, seed=55)
+    p = oracle_params(spatial="asp", T=T, stride=T, band_lo_bin=3, band_hi_bin=40,
+                      moments=("M0", "M1", "M2"), H=N, W=N)
+    r = hv.Renderer(N, N, 16, 4 * T)
+    try:
+        hv.hv_set_params(r.h, to_hv(p, tuned=1))
+        out = torch.zeros(3 * 3 * N * N, device="cuda")
+        assert r.push(to_device(fr)) == hv.HV_OK
+        n = r.render(out)  # the settings, and the autotuner, apply here
+        torch.cuda.synchronize()
+        t = hv.hv_get_tuning(r.h)
+        assert t["stft_kernel"] in (1, 2) and t["stft_us_per_window"][0] > 0 and t["stft_us_per_window"][1] > 0
+        img = out.cpu().numpy()[: n * 3 * N * N].reshape(n, 3, N, N)
+        check_images(img, O.render(fr, p))
+    finally:
+        r.close()
+
+
+@pytest.mark.slow
+def test_window_per_cta_stft_paper_asp_shape():
+    """The paper's ASP + STFT 512/512 shape at 256 x 256 (12-bit, ASP z = 0.30 m,
+    M0/M1/M2 over 1-35 kHz at 71.4 kHz) through the fused transform and the
+    window-per-CTA STFT: two windows, every pixel."""
+    sc = synth.build(synth.scene_stream_fresnel())
+    fr = synth.frames(sc, 0, 1024)
+    klo, khi = O.band_bins_from_hz(1000.0, 35000.0, 71400.0, 512)
+    p = oracle_params(spatial="asp", z_m=0.30, T=512, stride=512, fs_hz=71400.0,
+                      band_lo_bin=klo, band_hi_bin=khi, moments=("M0", "M1", "M2"), H=256, W=256)
+    img, _ = gpu_render(fr, p, extra=dict(spatial_kernel="fused", stft_kernel="window"))
+    check_images(img, O.render(fr, p))
