@@ -105,7 +105,8 @@ WORKLOADS["autofocus_256"] = dict(
     desc="learned autofocus on 256x256 uint16 (12-bit) holograms of point-scatterer objects at "
          "z ~ U[0.10, 0.60] m (seed 1005): network input (2x2-binned log-magnitude spectrum, "
          "128x128 bfloat16) and CNN inference (4 conv 3x3 stride 2, 16/32/64/64 channels, average "
-         "pool, MLP 64-32-1; He-uniform weights: throughput does not depend on them); the plain "
+         "pool, MLP 64-32-1; trained on the GPU on 50,000 holograms labelled by the sweep unless "
+         "--af-train 0); the plain "
          "64-distance ASP + Tamura sweep timed beside it; 512 holograms per step",
     N=256, bits=12, spatial="asp", z=0.0, T=0, S=0, fs=0.0, band=(0, 0), moments=(), batch=512,
     batches=1, pool=512, scene="autofocus", autofocus=True)
@@ -1102,8 +1103,14 @@ def main_autofocus(args):
     B = w["batch"]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    # holograms first: the process pool starts before any CUDA call
-    frames, _ = synth.autofocus_set(B, N=256, seed=1005, workers=min(16, os.cpu_count() or 1))
+    # holograms first: the process pool starts before any CUDA call. The timed batch is
+    # the first B holograms of the 1,000-hologram test set (seed 1005); the network is
+    # trained on --af-train holograms of the training set (seed 1004)
+    workers = min(16, os.cpu_count() or 1)
+    te_frames, te_z = synth.autofocus_set(max(B, 1000), N=256, seed=1005, workers=workers)
+    frames = te_frames[:B]
+    tr_frames = (synth.autofocus_set(args.af_train, N=256, seed=1004, workers=workers)[0]
+                 if args.af_train > 0 else None)
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -1117,6 +1124,33 @@ def main_autofocus(args):
     r.set_params(256, 256, spatial="asp", z=0.3, T=16, stride=16, band=(1, 7))
     net = af.Autofocus(B, stream=stream.cuda_stream)
     net.set_params(AF.he_uniform(1))
+    accuracy = None
+    if tr_frames is not None:
+        # train on the GPU (the library's forward, backward and Adam kernels), labels from
+        # the plain sweep; then score the 1,000 test holograms against the sweep
+        pl = AF.Pipeline(max_batch=256)
+        try:
+            _, tr_lab, _, tr_x = pl.label_and_features(tr_frames)
+            _, te_lab, _, te_x = pl.label_and_features(te_frames)
+            pl.net.set_params(AF.he_uniform(1))
+            hist, t_train = AF.train(pl, tr_x, tr_lab, epochs=args.af_epochs, batch=256, lr=2e-3)
+            pred = pl.predict(te_x)
+            err = np.abs(pred - te_lab) / AF.STEP
+            const = np.abs(np.mean(tr_lab) - te_lab) / AF.STEP
+            accuracy = {"within_1_step_of_sweep": round(float(np.mean(err <= 1.0)), 4),
+                        "mean_steps_vs_sweep": round(float(err.mean()), 3),
+                        "median_steps_vs_sweep": round(float(np.median(err)), 3),
+                        "p90_steps_vs_sweep": round(float(np.percentile(err, 90)), 3),
+                        "sweep_within_1_step_of_recorded_z": round(float(np.mean(np.abs(te_lab - te_z) <= AF.STEP)), 4),
+                        "constant_guess_mean_steps": round(float(const.mean()), 2),
+                        "train": {"holograms": int(args.af_train), "epochs": args.af_epochs, "batch": 256,
+                                  "seconds": round(t_train, 1), "final_loss": round(float(hist[-1]), 5)},
+                        "test_holograms": int(te_frames.shape[0])}
+            net.set_params(pl.net.get_params())
+            del tr_x, te_x
+        finally:
+            pl.close()
+        del tr_frames
     fr = torch.from_numpy(frames.view(np.int16)).to(dev)
     feats = torch.empty((B, 1, 128, 128), dtype=torch.bfloat16, device=dev)
     z = torch.empty(B, dtype=torch.float32, device=dev)
@@ -1237,6 +1271,7 @@ def main_autofocus(args):
                 "h2d_bytes_per_step": int(host.numel() * 2), "d2h_bytes_per_step": int(B * 4)},
         "gpu_launches": launches,
         "clocks": clk,
+        "accuracy": accuracy,
     }
     net.close()
     r.close()
@@ -1314,6 +1349,9 @@ def main():
                     help="fix the spatial kernels instead of autotuning them (profiling runs: the "
                          "autotuner's timings are distorted under a profiler)")
     ap.add_argument("--spatial-chunk", type=int, default=0, help="frames per spatial launch (0: automatic)")
+    ap.add_argument("--af-train", type=int, default=50000,
+                    help="autofocus workload: training holograms (0: untrained weights, no accuracy block)")
+    ap.add_argument("--af-epochs", type=int, default=40, help="autofocus workload: training epochs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -399,10 +399,13 @@ hv_status apply_pending(hv_handle* h) {
       tc_nchunks = uint32_t((hw + tc_chunk - 1) / tc_chunk);
       b_tc = cov_tc_partials_floats(ntiles, tc_nchunks) * sizeof(float);
     }
+    // BF16 operand staging: 64-pixel steps x 2T rows x 64 values per part
+    const size_t stage_part = p.precision != HV_PREC_FP32 ? (hw + 63) / 64 * 64 * 2 * size_t(T) : 0;
+    const size_t b_stage = stage_part * sizeof(uint16_t) * (p.precision == HV_PREC_SPLIT_BF16 ? 2 : 1);
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
     const size_t b_matf = size_t(T) * T * sizeof(float2);
     const size_t total = al(b_part) + (NW + 2) * al(b_mat) + 3 * al(b_matf) + al(b_rot) + al(b_cnt) + al(b_lam) +
-                         al(b_vs) + al(b_tc);
+                         al(b_vs) + al(b_tc) + al(b_stage);
     s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
     if (s != HV_OK) return s;
     char* b = static_cast<char*>(h->pca_ws);
@@ -447,6 +450,9 @@ hv_status apply_pending(hv_handle* h) {
     b += al(b_vs);
     a.precision = p.precision;
     a.tc_partials = b_tc ? reinterpret_cast<float*>(b) : nullptr;
+    b += al(b_tc);
+    a.tc_stage = b_stage ? reinterpret_cast<uint16_t*>(b) : nullptr;
+    a.tc_stage_part = stage_part;
     a.tc_chunk = tc_chunk;
     a.tc_nchunks = tc_nchunks;
     a.tc_ntiles = ntiles;

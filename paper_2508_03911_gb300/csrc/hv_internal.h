@@ -127,6 +127,11 @@ struct PcaArgs {
   int precision;        // HV_PREC_*
   float* tc_partials;   // nchunks x ntiles x 128 x 256 float
   uint32_t tc_chunk, tc_nchunks, tc_ntiles;
+  // the window as BF16 operands, hi part then (split-BF16) lo part, each
+  // [64-pixel step][2T/8 row blocks][8 k blocks][8 rows][8 pixels]: every step's
+  // rows form the MMA's no-swizzle K-major core-matrix layout, contiguous
+  uint16_t* tc_stage;
+  size_t tc_stage_part;  // bf16 elements per part: steps x 2T x 64
   uint8_t tc_tile_i[32], tc_tile_j[32];
   unsigned* err;        // device error flag (bounded waits that gave up)
 };

@@ -9,16 +9,17 @@
 // N = 2 min(T, 128)) over one pixel chunk; tiles wholly below the diagonal are
 // skipped; chunk partials are summed in float64 by k_cov_tc_reduce.
 //
-// Per 64-pixel step all 512 threads load the step's frames (float2), split each
-// value v into hi = bf16(v) and lo = bf16(v - hi), and store them into shared
-// memory in the no-swizzle K-major canonical layout (8 x 16-byte core matrices,
-// element (r, k) at (r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2: leading-dimension
-// byte offset 128 along K, stride-dimension byte offset 1024 along rows). One
-// thread then issues four K = 16 MMAs per product -- hi.hi (BF16), plus hi.lo and
-// lo.hi (split-BF16) -- and commits them to the stage's mbarrier. Two stages
-// alternate, so loading step s+1 overlaps the MMAs of step s. Every mbarrier wait
-// is bounded; on timeout the kernel records an error, stops issuing, releases its
-// tensor memory and returns.
+// A first kernel converts the window once: each value v becomes hi = bf16(v) and
+// lo = bf16(v - hi), stored in a staging buffer in the no-swizzle K-major
+// canonical layout of the MMA operands (8 x 16-byte core matrices, element (r, k)
+// of a 64-pixel step at (r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes:
+// leading-dimension byte offset 128 along K, stride-dimension byte offset 1024
+// along rows), so every tile of consecutive rows of a step is one contiguous
+// chunk. The covariance kernel then streams those chunks into shared memory with
+// 1-D bulk copies (one thread, two stages on mbarriers) while another thread
+// issues four K = 16 MMAs per product -- hi.hi (BF16), plus hi.lo and lo.hi
+// (split-BF16) -- per step. Every mbarrier wait is bounded; on timeout the kernel
+// records an error, stops issuing, releases its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include "hv_internal.h"
@@ -128,26 +129,69 @@ __device__ __forceinline__ void convert8(const float2* frame, size_t p, size_t p
   }
 }
 
+// The window as BF16 operands in the staging buffer: item (step, frame, k block)
+// converts 8 pixels of one frame (zero past the last pixel) into rows 2f (re) and
+// 2f + 1 (im) of the step's core-matrix block -- the layout of an MMA tile in
+// shared memory, so a tile of consecutive rows is one contiguous chunk. A warp
+// covers 4 frames x 8 k blocks: 2 KB of reads, 1 KB contiguous per part written.
+__global__ void __launch_bounds__(256) k_cov_stage(PcaArgs a) {
+  const size_t hw = size_t(a.W) * a.H;
+  const uint32_t T = a.T;
+  const size_t nsteps = (hw + TC_KS - 1) / TC_KS;
+  const size_t total = nsteps * T * 8;
+  const bool split = a.precision == HV_PREC_SPLIT_BF16;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    const int kb = int(idx & 7);
+    const uint32_t f = uint32_t((idx >> 3) % T);
+    const size_t st = (idx >> 3) / T;
+    uint32_t slot = a.tq.slot0 + f;  // slot0 < cap, f < T <= cap
+    if (slot >= a.tq.cap) slot -= a.tq.cap;
+    const float2* fp = static_cast<const float2*>(a.tq.base) + size_t(slot) * hw;
+    unsigned char* hi = reinterpret_cast<unsigned char*>(a.tc_stage + st * 2 * T * TC_KS);
+    unsigned char* lo = split ? reinterpret_cast<unsigned char*>(a.tc_stage + a.tc_stage_part + st * 2 * T * TC_KS)
+                              : nullptr;
+    convert8(fp, st * TC_KS + size_t(kb) * 8, hw, int(f), kb, hi, lo);
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// One 128 x N tile of G over one pixel chunk. Warp 0 (one thread) streams each
+// 64-pixel step's operand tiles from the staging buffer into one of two stages
+// with 1-D bulk copies completing on the stage's `full` mbarrier; warp 1 (one
+// thread) waits for a stage, issues its MMAs and commits them to the stage's
+// `empty` mbarrier, which the copies of the stage's next step wait for.
 __global__ void __launch_bounds__(TC_NT, 1) k_cov_tc(PcaArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_ok;  // wait outcome, decided by one thread so every thread agrees
+  __shared__ int s_ok;  // outcome of the waits, one value every thread agrees on
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ti = a.tc_tile_i[blockIdx.x], tj = a.tc_tile_j[blockIdx.x];
   const int BF = int(a.T) < 128 ? int(a.T) : 128;  // frames per B block
   const int N = 2 * BF;                             // G columns per tile
-  const int B_BYTES = N * TC_KS * 2;
+  const uint32_t B_BYTES = uint32_t(N) * TC_KS * 2;
   const bool split = a.precision == HV_PREC_SPLIT_BF16;
   const size_t hw = size_t(a.W) * a.H;
   const size_t p_begin = size_t(blockIdx.y) * a.tc_chunk;
   const size_t p_end = p_begin + a.tc_chunk < hw ? p_begin + a.tc_chunk : hw;
   const int nsteps = int((p_end - p_begin + TC_KS - 1) / TC_KS);
+  const size_t step0 = p_begin / TC_KS;
+  const size_t step_elems = size_t(2) * a.T * TC_KS;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])) : "memory");
+    for (int st = 0; st < 2; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[st])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[st])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_ok = 1;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(
@@ -160,39 +204,42 @@ __global__ void __launch_bounds__(TC_NT, 1) k_cov_tc(PcaArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t id = idesc_bf16(TC_M, N);
-  bool ok = true;
 
-  for (int it = 0; it < nsteps && ok; ++it) {
-    const int s = it & 1;
-    unsigned char* st = sm + s * STAGE_BYTES;
-    unsigned char* a_hi = st;
-    unsigned char* a_lo = st + A_BYTES;
-    unsigned char* b_hi = st + 2 * A_BYTES;
-    unsigned char* b_lo = st + 2 * A_BYTES + B_BYTES_MAX;
-    if (it >= 2) {
-      if (tid == 0) s_ok = mbar_wait(smem_u32(&mbar[s]), uint32_t(((it >> 1) - 1) & 1)) ? 1 : 0;
-      __syncthreads();
-      ok = s_ok != 0;
-      if (!ok) break;
+  if (tid == 0) {
+    // copies: A rows 128 ti .., B rows N tj .. of each step, hi and (split) lo parts
+    const uint32_t bytes = (uint32_t(A_BYTES) + B_BYTES) * (split ? 2u : 1u);
+    for (int it = 0; it < nsteps; ++it) {
+      const int st = it & 1;
+      if (it >= 2 && !mbar_wait(smem_u32(&empty[st]), uint32_t(((it >> 1) - 1) & 1))) {
+        atomicOr(a.err, 1u);
+        s_ok = 0;
+        break;
+      }
+      unsigned char* stg = sm + st * STAGE_BYTES;
+      const uint32_t fb = smem_u32(&full[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
+      const uint16_t* hi = a.tc_stage + (step0 + size_t(it)) * step_elems;
+      bulk_load(smem_u32(stg), hi + size_t(ti) * TC_M * TC_KS, A_BYTES, fb);
+      bulk_load(smem_u32(stg + 2 * A_BYTES), hi + size_t(tj) * N * TC_KS, B_BYTES, fb);
+      if (split) {
+        const uint16_t* lo = hi + a.tc_stage_part;
+        bulk_load(smem_u32(stg + A_BYTES), lo + size_t(ti) * TC_M * TC_KS, A_BYTES, fb);
+        bulk_load(smem_u32(stg + 2 * A_BYTES + B_BYTES_MAX), lo + size_t(tj) * N * TC_KS, B_BYTES, fb);
+      }
     }
-    const size_t p0 = p_begin + size_t(it) * TC_KS;
-    // A: 64 frames x 8 k-blocks; B: BF frames x 8 k-blocks (lane -> frame l%4, k-block l/4)
-    for (int idx = tid; idx < 64 * 8 + BF * 8; idx += TC_NT) {
-      const bool isA = idx < 64 * 8;
-      const int e = isA ? idx : idx - 64 * 8;
-      const int w = e >> 5, l = e & 31;
-      const int f = 4 * w + (l & 3), kb = l >> 2;
-      const int frame = isA ? ti * 64 + f : tj * BF + f;
-      uint32_t slot = a.tq.slot0 + uint32_t(frame);  // slot0 < cap, frame < T <= cap (checked by launch_pca)
-      if (slot >= a.tq.cap) slot -= a.tq.cap;
-      const float2* fp = static_cast<const float2*>(a.tq.base) + size_t(slot) * hw;
-      convert8(fp, p0 + kb * 8, p_end, f, kb, isA ? a_hi : b_hi, split ? (isA ? a_lo : b_lo) : nullptr);
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    bool ok = true;
+    for (int it = 0; it < nsteps; ++it) {
+      const int st = it & 1;
+      if (!mbar_wait(smem_u32(&full[st]), uint32_t((it >> 1) & 1))) {
+        atomicOr(a.err, 1u);
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t ahi = smem_u32(a_hi), alo = smem_u32(a_lo), bhi = smem_u32(b_hi), blo = smem_u32(b_lo);
+      unsigned char* stg = sm + st * STAGE_BYTES;
+      const uint32_t ahi = smem_u32(stg), alo = smem_u32(stg + A_BYTES), bhi = smem_u32(stg + 2 * A_BYTES),
+                     blo = smem_u32(stg + 2 * A_BYTES + B_BYTES_MAX);
 #pragma unroll
       for (int k = 0; k < TC_KS / 16; ++k) {
         const uint32_t kofs = uint32_t(k * 256);  // two core matrices along K
@@ -202,19 +249,18 @@ __global__ void __launch_bounds__(TC_NT, 1) k_cov_tc(PcaArgs a) {
           mma_bf16(tmem, smem_desc(alo + kofs), smem_desc(bhi + kofs), id, 1u);
         }
       }
-      mma_commit(smem_u32(&mbar[s]));
+      mma_commit(smem_u32(&empty[st]));
     }
+    // the last commit covers every MMA issued before it
+    if (ok && nsteps > 0 &&
+        !mbar_wait(smem_u32(&empty[(nsteps - 1) & 1]), uint32_t(((nsteps - 1) >> 1) & 1))) {
+      atomicOr(a.err, 1u);
+      ok = false;
+    }
+    if (!ok) s_ok = 0;
   }
-  // the last commit covers every MMA issued before it
   __syncthreads();
-  if (tid == 0) {
-    bool fin = ok;
-    if (fin && nsteps > 0) fin = mbar_wait(smem_u32(&mbar[(nsteps - 1) & 1]), uint32_t(((nsteps - 1) >> 1) & 1));
-    s_ok = fin ? 1 : 0;
-    if (!fin) atomicOr(a.err, 1u);
-  }
-  __syncthreads();
-  ok = s_ok != 0;
+  const bool ok = s_ok != 0;
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) .. +31 (G rows), columns chunk (w / 4) of N/4
@@ -297,11 +343,16 @@ uint32_t cov_tc_tiles(uint32_t T, uint8_t* ti, uint8_t* tj) {
 }
 
 cudaError_t launch_cov_tc(PcaArgs& a, cudaStream_t s, int* launches) {
+  if (!a.tc_stage) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_cov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_cov_stage<<<unsigned(nsm) * 8, 256, 0, s>>>(a);
   k_cov_tc<<<dim3(a.tc_ntiles, a.tc_nchunks), TC_NT, TC_SMEM, s>>>(a);
   k_cov_tc_reduce<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
-  *launches += 2;
+  *launches += 3;
   return cudaGetLastError();
 }
 
