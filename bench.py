@@ -294,7 +294,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     N = w["N"]
 
     def open_renderer():
-        r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream)
+        r = hv.Renderer(N, N, 8 if w["bits"] <= 8 else 16, 2 * B, stream=stream.cuda_stream,
+                        time_queue_frames=args.tq_frames)
         if w.get("temporal") == "pca":
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], temporal="pca", T=w["T"],
                          stride=w["S"], pca=w["pca"], tuned=tuned,
@@ -303,7 +304,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
         else:
             r.set_params(N, N, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"],
                          fs=w["fs"], band=(klo, khi), moments=w["moments"], tuned=tuned,
-                         spatial_kernel=args.spatial_kernel, spatial_chunk=args.spatial_chunk)
+                         spatial_kernel=args.spatial_kernel, spatial_chunk=args.spatial_chunk,
+                         stft_kernel=args.stft_kernel if tuned else "auto")
         return r
 
     r = open_renderer()
@@ -526,21 +528,38 @@ def roofline(w, res, peaks):
     alu_frac = tflops / fp32
     hbm_frac = gbs / hbm
     traffic = None
+    traffic_per = "launch of the STFT kernel" if t_tm >= t_sp else \
+        "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)"
+    tun = res.get("tuning") or {}
     if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64:
         traffic = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
-    tun = res.get("tuning") or {}
-    if (t_tm < t_sp and w["N"] == 256 and w["spatial"] == "asp" and tun.get("spatial_kernel") == 3
-            and tun.get("spatial_chunk") == 512):
-        # the three persistent passes of one 512-frame launch set, scaled to a render
-        parts = [profiled_traffic("spatial_pp_asp_256.md", ["k_spatial_pp.cu", "fft_dev.cuh"], i)
-                 for i in range(3)]
-        if all(v is not None for v in parts):
-            traffic = int(sum(parts) * frames_per_render / 512)
+    if (t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 512
+            and tun.get("stft_kernel") == 2):
+        # window-per-CTA STFT: a 1,024-frame launch captured, traffic in proportion to the frames
+        v = profiled_traffic("stft_win_512_asp_256.md", ["k_stft.cu", "fft_dev.cuh"])
+        if v is not None:
+            traffic = int(v * frames_per_render / 1024)
+            traffic_per = "render (the STFT launch; 1,024-frame ncu capture scaled to the render's frames)"
+    if t_tm < t_sp and w["N"] == 256 and w["spatial"] == "asp":
+        kern = "k_spatial_fused (every spatial pass, one launch per render)" if tun.get("spatial_kernel") == 4 \
+            else kern
+        if tun.get("spatial_kernel") == 3 and tun.get("spatial_chunk") == 512:
+            # the three persistent passes of one 512-frame launch set, scaled to a render
+            parts = [profiled_traffic("spatial_pp_asp_256.md", ["k_spatial_pp.cu", "fft_dev.cuh"], i)
+                     for i in range(3)]
+            if all(v is not None for v in parts):
+                traffic = int(sum(parts) * frames_per_render / 512)
+        elif tun.get("spatial_kernel") == 4 and w["bits"] > 8:
+            v = profiled_traffic("spatial_fused_asp_256.md", ["k_spatial_pp.cu", "fft_dev.cuh"])
+            if v is not None:
+                traffic = int(v * frames_per_render / 1024)
+                traffic_per = ("render (the fused launch; cold-cache 1,024-frame ncu capture scaled to "
+                               "the render's frames)")
     if alu_frac >= hbm_frac:
         return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(fp32, 1),
                 "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic, "kernel": kern,
-                "traffic_per": "launch of the STFT kernel" if t_tm >= t_sp else
-                               "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)",
+                "traffic_per": traffic_per,
+                "algorithmic_bytes_per_render": int(byts),
                 "peak_source": alu_peaks()["source"] + "; derived 152 SMs x 128 FP32 lanes x 2 flop "
                                "x 2.07 GHz = 80.5",
                 "hbm_achieved_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4),
@@ -1349,6 +1368,13 @@ def main():
                     help="fix the spatial kernels instead of autotuning them (profiling runs: the "
                          "autotuner's timings are distorted under a profiler)")
     ap.add_argument("--spatial-chunk", type=int, default=0, help="frames per spatial launch (0: automatic)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="frames per push/render batch (0: the workload's; profiling runs use small ones)")
+    ap.add_argument("--batches", type=int, default=0, help="batches per step (0: the workload's)")
+    ap.add_argument("--tq-frames", type=int, default=0,
+                    help="time-queue capacity in frames (0: automatic; small for profiling runs)")
+    ap.add_argument("--stft-kernel", choices=["auto", "walk", "window"], default="auto",
+                    help="fix the STFT kernel for windows that do not overlap instead of autotuning it")
     ap.add_argument("--af-train", type=int, default=50000,
                     help="autofocus workload: training holograms (0: untrained weights, no accuracy block)")
     ap.add_argument("--af-epochs", type=int, default=40, help="autofocus workload: training epochs")
@@ -1367,6 +1393,11 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.precision:
         w["precision"] = args.precision
+    if args.batch:
+        w["batch"] = args.batch
+        w["pool"] = min(w["pool"], args.batch)
+    if args.batches:
+        w["batches"] = args.batches
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     klo, khi = band_bins(w)
@@ -1437,7 +1468,8 @@ def main():
             "form": "plain" if args.form == "plain" else "tuned",
             "tuning": {"spatial_kernel": {1: "multipass", 2: "cluster", 3: "persistent", 4: "fused"}.get(
                            res["tuning"]["spatial_kernel"], "multipass"),
-                       "frames_per_launch": res["tuning"]["spatial_chunk"],
+                       "frames_per_launch": ("every frame of a render" if res["tuning"]["spatial_kernel"] in (2, 4)
+                                             else res["tuning"]["spatial_chunk"]),
                        "candidates_us_per_frame": dict(zip(
                            ["mp16", "mp32", "mp64", "mp128", "mp256", "pp64", "pp128", "pp256",
                             "pp512", "cluster", "fused"],
