@@ -54,7 +54,7 @@ cudaError_t launch_spatial_pp(const SpatialArgs& a, cudaStream_t s, int* launche
 cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* launches);
 // Fused transform: frames of 256 x 256, ASP or Fresnel; needs ring >= kFusedRing
 // frames in scratch1 (and scratch2 for ASP), fused_ctr and err.
-constexpr uint32_t kFusedRing = 64;
+constexpr uint32_t kFusedRing = 96;
 bool spatial_fused_supported(const SpatialArgs& a);
 cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* launches);
 

@@ -872,12 +872,17 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 // rings keep their L2 lines.
 constexpr int FZ_NT = 256;       // consumer threads (one pass's thread layout)
 constexpr int FZ_THREADS = FZ_NT + 32;
-constexpr int FZ_LAG = 24;
+// rows of tickets between a frame's passes: at least the tickets in flight (3 per
+// CTA: the staged item, the transformed one, the next fetched) over the items per
+// row, so that an item's inputs are usually published when it is staged
+constexpr int FZ_LAG = 48;
 constexpr int FZ_BAR = 1;        // named barrier of the consumer warps
 constexpr size_t FZ_FRAME = size_t(RW_L) * RW_L;  // complex values per frame
 constexpr size_t FZ_BUF = size_t(256) * 16;       // complex values per buffer
 constexpr size_t FZ_RAW = 256 * 32;               // bytes of a raw strip (uint16), in the buffer's tail
-static_assert(kFusedRing > 2 * FZ_LAG, "the rings must outlast the lag between passes");
+// every wait is on a smaller ticket when the rings are longer than the lag; the
+// headroom above it keeps column items from waiting for a slot to be freed
+static_assert(kFusedRing > FZ_LAG, "the rings must outlast the lag between passes");
 // shared memory: pass twiddles (256), row-FFT stage-2 twiddles (240), Fresnel
 // chirp along y (256), two buffers of 16 lines x 256 (the column passes' lines
 // fastest with row stride 16, the row tile 16 x 256; a raw strip lands in the

@@ -436,15 +436,15 @@ def test_persistent_passes_through_stft(spatial, T, S):
 @pytest.mark.parametrize("spatial,bits", [("asp", 12), ("asp", 8), ("fresnel", 12), ("fresnel", 8)])
 def test_fused_spatial_field_parity(spatial, bits):
     """The fused transform at 256 x 256: every pass of every frame in one persistent
-    launch, intermediates in rings of 64 frames. 130 frames pushed as packets of 1,
-    57 and 72 (launches of one frame and of more than two ring generations; input
+    launch, intermediates in rings of 96 frames. 220 frames pushed as packets of 1,
+    97 and 122 (launches of one frame and of more than two ring generations; input
     and time-queue rings wrapping), every field against the oracle."""
-    N, n = 256, 130
+    N, n = 256, 220
     fr = synth.random_frames(n, N, N, bits, seed=400 + bits + (1 if spatial == "asp" else 2))
     p = oracle_params(spatial=spatial, z_m=0.27, pitch_y_m=17e-6, temporal="none", T=1, stride=1,
                       H=N, W=N)
-    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="fused"), packets=[1, 57, 72], queue=100,
-                         tq=90)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="fused"), packets=[1, 97, 122], queue=160,
+                         tq=150)
     ref = oracle_fields(fr, p)
     assert img.shape == ref.shape
     for i in range(n):
