@@ -176,7 +176,8 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
     return HV_ERR_ARG;
   }
   if (p.spatial_kernel > HV_SK_FUSED) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
-  if (p.stft_kernel != 0 && p.stft_kernel != HV_STFT_WALK && p.stft_kernel != HV_STFT_WINDOW) {
+  if (p.stft_kernel != 0 && p.stft_kernel != HV_STFT_WALK && p.stft_kernel != HV_STFT_WINDOW &&
+      p.stft_kernel != HV_STFT_WINDOW_WIDE) {
     why = "unknown stft_kernel";
     return HV_ERR_ARG;
   }
@@ -486,8 +487,9 @@ hv_status apply_pending(hv_handle* h) {
   h->tuning.spatial_kernel = p.spatial_kernel == HV_SK_AUTO ? HV_SK_MULTIPASS : int32_t(p.spatial_kernel);
   // STFT kernel for windows that do not overlap: the caller's, the autotuner's (tuned),
   // else the walking kernel launched once per window (the plain form)
-  h->stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? STFT_AUTO : STFT_WALK;
-  h->tuning.stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? HV_STFT_WINDOW : HV_STFT_WALK;
+  h->stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? STFT_AUTO
+                   : (p.stft_kernel == HV_STFT_WINDOW_WIDE ? STFT_WIDE : STFT_WALK);
+  h->tuning.stft_kernel = p.stft_kernel == 0 ? HV_STFT_WALK : p.stft_kernel;
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
     s = tune_spatial(h);
     if (s != HV_OK) return s;
@@ -703,11 +705,11 @@ hv_status tune_temporal(hv_handle* h) {
   sa.nout = h->nout;
   sa.out = out;
   sa.err = h->dev_err;
-  const int kinds[2] = {STFT_WALK, STFT_AUTO};
+  const int kinds[3] = {STFT_WALK, STFT_AUTO, STFT_WIDE};
   float best = 1e30f;
   int best_kind = STFT_AUTO;
   hv_status st = HV_OK;
-  for (int ci = 0; ci < 2 && st == HV_OK; ++ci) {
+  for (int ci = 0; ci < 3 && st == HV_OK; ++ci) {
     sa.kernel = kinds[ci];
     int launches = 0;
     cudaError_t e = launch_stft(sa, h->stream, &launches);  // warm-up
@@ -733,7 +735,8 @@ hv_status tune_temporal(hv_handle* h) {
   cudaFree(out);
   if (st != HV_OK) return st;
   h->stft_kernel = best_kind;
-  h->tuning.stft_kernel = best_kind == STFT_WALK ? HV_STFT_WALK : HV_STFT_WINDOW;
+  h->tuning.stft_kernel = best_kind == STFT_WALK ? HV_STFT_WALK
+                          : (best_kind == STFT_WIDE ? HV_STFT_WINDOW_WIDE : HV_STFT_WINDOW);
   h->tuning.tuned = 1;
   return HV_OK;
 }

@@ -86,9 +86,10 @@ struct StftArgs {
   unsigned* err;        // device flags: bit 1 set when a wait for staged frames gave up
   int tma;              // set by the launcher: staged frames through a TMA tensor map
   int kernel;           // STFT_AUTO: windows that do not overlap (S >= T) one CTA per
-                        // (window, pixel tile); STFT_WALK: CTAs walk all windows of their pixels
+                        // (window, pixel tile); STFT_WIDE: the same with twice the pixels
+                        // per CTA; STFT_WALK: CTAs walk all windows of their pixels
 };
-enum { STFT_AUTO = 0, STFT_WALK = 1 };
+enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
 // Encodes a 2-D tiled TMA tensor map (map: a CUtensorMap, 64-byte aligned) over

@@ -14,6 +14,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "fft_dev.cuh"
 #include "hv_internal.h"
@@ -476,25 +477,26 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
 // whole row into registers before any lane of the pixel writes. A CTA holds one
 // window, so its shared memory is a quarter of the walking kernel's and several
 // CTAs share an SM.
-template <int T>
+template <int T, bool WIDE = false>
 struct WinCfg {
   using Lw = WarpLayout<T>;
   // warps per CTA: 8 for short windows (a warp's fetch covers 32 pixels, 256
-  // contiguous bytes of a frame), else the walking kernel's count
-  static constexpr int NW = T <= 128 ? 8 : Lw::NW;
+  // contiguous bytes of a frame), else the walking kernel's count; WIDE doubles
+  // it (twice the pixels per CTA: longer contiguous runs of each frame)
+  static constexpr int NW = (T <= 128 ? 8 : Lw::NW) * (WIDE ? 2 : 1);
   static constexpr int NT = 32 * NW;
   static constexpr int BT = NW * Lw::PW;  // pixels per CTA
   // row stride (float2): the padded row, rounded to 1 mod 16 so that the rows of
   // consecutive pixels start in consecutive bank pairs
   static constexpr int WR = (T + T / 16 + 15) / 16 * 16 + 1;
-  static constexpr int OCC = T >= 1024 ? 1 : (T >= 512 ? 4 : (T >= 256 ? 6 : 4));
+  static constexpr int OCC = WIDE ? (T >= 512 ? 2 : 2) : (T >= 1024 ? 1 : (T >= 512 ? 4 : (T >= 256 ? 6 : 4)));
   static constexpr size_t bytes() { return (size_t(BT) * WR + (T - WarpPlan<T>::R1)) * sizeof(float2); }
 };
 
-template <int T>
-__global__ void __launch_bounds__(WinCfg<T>::NT, WinCfg<T>::OCC) k_stft_win(StftArgs a) {
+template <int T, bool WIDE>
+__global__ void __launch_bounds__(WinCfg<T, WIDE>::NT, WinCfg<T, WIDE>::OCC) k_stft_win(StftArgs a) {
   using Lw = WarpLayout<T>;
-  using Wc = WinCfg<T>;
+  using Wc = WinCfg<T, WIDE>;
   constexpr int NT = Wc::NT, LP = Lw::LP, PW = Lw::PW, BT = Wc::BT, WR = Wc::WR;
   extern __shared__ __align__(16) unsigned char smem_win[];
   float2* rows = reinterpret_cast<float2*>(smem_win);
@@ -623,16 +625,20 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
   StftArgs a = a0;
   if (a.S >= uint32_t(T) && a.kernel != STFT_WALK) {
     // one CTA per (window, pixel tile)
-    using Wc = WinCfg<T>;
-    if (hw % Wc::BT == 0) {
+    auto launch_win = [&](auto wide) -> cudaError_t {
+      constexpr bool W = decltype(wide)::value;
+      using Wc = WinCfg<T, W>;
+      if (hw % Wc::BT) return cudaErrorNotSupported;
       const size_t smem = Wc::bytes();
-      cudaError_t e = cudaFuncSetAttribute(k_stft_win<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      cudaError_t e = cudaFuncSetAttribute(k_stft_win<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
       const uint64_t grid = uint64_t(a.nwin) * (hw / Wc::BT);
       if (grid >= (1ull << 31)) return cudaErrorInvalidValue;
-      k_stft_win<T><<<unsigned(grid), Wc::NT, smem, s>>>(a);
+      k_stft_win<T, W><<<unsigned(grid), Wc::NT, smem, s>>>(a);
       return cudaGetLastError();
-    }
+    };
+    const cudaError_t e = a.kernel == STFT_WIDE ? launch_win(std::true_type{}) : launch_win(std::false_type{});
+    if (e != cudaErrorNotSupported) return e;
   }
   CUtensorMap map{};
   a.tma = queue_map(a, Lw::BT, &map) ? 1 : 0;
