@@ -98,6 +98,9 @@ cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 // point is missing or the encoder rejects the shape.
 bool encode_map_2d_u64(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
                        uint32_t box_inner, uint32_t box_outer, bool swizzle64);
+// The same for 1-, 2-, 4- or 8-byte elements, no swizzle.
+bool encode_map_2d(void* map, const void* base, int elem_bytes, uint64_t inner, uint64_t outer,
+                   uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer);
 
 // PCA of one window (Sec. III-B.1), time-queue ring -> energy image.
 struct PcaArgs {

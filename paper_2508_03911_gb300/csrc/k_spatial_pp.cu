@@ -861,7 +861,8 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 //   pass 3 of f: the 16 row-pass items of f wrote S2 slot
 // A CTA is warp-specialised: one producer warp takes the tickets, waits (bounded
 // spin on acquire loads) for each item's counters, stages its input strip into
-// one of two buffers with cp.async completing on the buffer's mbarrier, and
+// one of two buffers with one copy (a TMA tensor copy, or a 1-D bulk copy)
+// completing on the buffer's mbarrier, and
 // publishes every finished item (fence, atomic add on its slot counter); eight
 // consumer warps transform the staged strip while the next one streams in. Every
 // wait is on an item with a smaller ticket (RING > LAG); a producer holds at most
@@ -887,7 +888,7 @@ static_assert(kFusedRing > FZ_LAG, "the rings must outlast the lag between passe
 // chirp along y (256), two buffers of 16 lines x 256 (the column passes' lines
 // fastest with row stride 16, the row tile 16 x 256; a raw strip lands in the
 // tail of its buffer and is read whole by the first FFT stage before it writes)
-constexpr size_t FZ_SMEM = (256 + 240 + 256 + 2 * FZ_BUF) * sizeof(float2);
+constexpr size_t FZ_SMEM = 1024 + (256 + 240 + 256 + 2 * FZ_BUF) * sizeof(float2);  // + alignment slack
 constexpr uint32_t FZ_STOP = 0xffffffffu;
 
 // Bin k of line b to global memory at out[k * stride + b] with a streaming store.
@@ -898,13 +899,6 @@ struct GlobalOutCs {
   uint32_t stride;
   __device__ __forceinline__ void operator()(int b, int k, float2 v) const { __stcs(&out[size_t(k) * stride + b], v); }
 };
-
-__device__ __forceinline__ void cpa16_hint(void* s, const void* g, uint64_t pol) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(
-                   static_cast<unsigned>(__cvta_generic_to_shared(s))),
-               "l"(g), "l"(pol)
-               : "memory");
-}
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -926,12 +920,16 @@ struct FzItem {
   uint32_t pass, frame, strip;
 };
 
-__global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, uint32_t nticket) {
+__global__ void __launch_bounds__(FZ_THREADS, 3)
+    k_spatial_fused(SpatialArgs a, uint32_t nticket, const __grid_constant__ CUtensorMap raw_map,
+                    const __grid_constant__ CUtensorMap s2_map) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* tws = reinterpret_cast<float2*>(smem);
+  // the two buffers first, 1024-byte aligned (bulk-copy destinations), then the tables
+  unsigned char* base = smem + ((1024u - (rw_smem(smem) & 1023u)) & 1023u);
+  float2* bufs = reinterpret_cast<float2*>(base);  // buffer b at bufs + b FZ_BUF
+  float2* tws = bufs + 2 * FZ_BUF;
   float2* tw2 = tws + 256;
   float2* cys = tw2 + 240;
-  float2* bufs = cys + 256;  // buffer b at bufs + b FZ_BUF
   // raw strip of buffer b: its last FZ_RAW bytes
   auto raw_of = [&](int b) {
     return reinterpret_cast<unsigned char*>(bufs + (b + 1) * FZ_BUF) - FZ_RAW;
@@ -952,8 +950,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, 
   }
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      // full: 32 cp.async arrivals of the producer lanes + one arrival after the descriptor
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 33;\n" ::"r"(rw_smem(&full[b])) : "memory");
+      // full: the producer's arrival with the item's byte count, completed by its copy
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[b])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&freed[b])) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -1032,29 +1030,44 @@ __global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, 
       const int b = int(k & 1);
       const uint32_t s0 = strip * 16u, slot = f % R;
       float2* buf = bufs + b * FZ_BUF;
-      if (lane == 0) desc[b] = FzItem{pass, f, strip};
-      if (pass == 0) {
-        const int bpp = u8 ? 1 : 2, seg = 16 * bpp, pieces = seg / 16;
-        const size_t rslot = (a.raw.slot0 + f) % a.raw.cap;
-        const unsigned char* src = static_cast<const unsigned char*>(a.raw.base) + (rslot * FZ_FRAME + s0) * bpp;
-        unsigned char* dst = raw_of(b);
-        for (int e = lane; e < 256 * pieces; e += 32) {
-          const int y = e / pieces, q = e % pieces;
-          cpa16_hint(dst + y * seg + q * 16, src + size_t(y) * 256 * bpp + q * 16, pol_first);
-        }
-      } else if (pass == 1) {
-        const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
-        for (int e = lane; e < 16 * 256 / 2; e += 32) cpa16(buf + 2 * e, src + 2 * e);
-      } else {
-        const float2* src = a.scratch2 + size_t(slot) * FZ_FRAME + s0;
-        for (int e = lane; e < 256 * 8; e += 32) {
-          const int y = e >> 3, q = e & 7;
-          cpa16(buf + y * 16 + 2 * q, src + size_t(y) * 256 + 2 * q);
+      if (lane == 0) {
+        // one copy per item: the raw strip (256 rows x 16 pixels) and the column-IFFT
+        // strip (256 rows x 16 complex) by a TMA tensor copy, the row pass's 16 rows
+        // (contiguous) by a 1-D bulk copy. The rings were written by other CTAs'
+        // generic stores, fenced for the async proxy before their publication; this
+        // thread acquired the counters that published them.
+        desc[b] = FzItem{pass, f, strip};
+        const uint32_t fb = rw_smem(&full[b]);
+        if (pass == 0) {
+          const uint32_t bytes = 256u * 16u * (u8 ? 1u : 2u);
+          const uint32_t rslot = uint32_t((a.raw.slot0 + f) % a.raw.cap);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+              "[%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(rw_smem(raw_of(b))),
+              "l"(reinterpret_cast<uint64_t>(&raw_map)), "r"(int(s0)), "r"(int(rslot * 256u)), "r"(fb),
+              "l"(pol_first)
+              : "memory");
+        } else if (pass == 1) {
+          const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
+          asm volatile("fence.proxy.async.global;\n" ::: "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                  rw_smem(buf)),
+              "l"(src), "r"(32768u), "r"(fb)
+              : "memory");
+        } else {
+          asm volatile("fence.proxy.async.global;\n" ::: "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+              "[%4];\n" ::"r"(rw_smem(buf)),
+              "l"(reinterpret_cast<uint64_t>(&s2_map)), "r"(int(s0)), "r"(int(slot * 256u)), "r"(fb)
+              : "memory");
         }
       }
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
       if (lane == 0) {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
         // publish item k - 1 once its transform is done (the consumers then start item k)
         if (have_pend) {
           const long long t0 = clock64();
@@ -1087,10 +1100,10 @@ __global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, 
       if (ok) publish(pend);
     }
     const int b = int(k & 1);
-    if (lane == 0) desc[b] = FzItem{FZ_STOP, 0, 0};
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
-    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
-    cpa_wait_all();
+    if (lane == 0) {
+      desc[b] = FzItem{FZ_STOP, 0, 0};
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+    }
     return;
   }
 
@@ -1178,6 +1191,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3) k_spatial_fused(SpatialArgs a, 
       pp_stages<256, 1, +1, SmemSrc<16>, GlobalOutCs, 16, FZ_BAR>(SmemSrc<16>{buf}, buf, tws,
                                                                   GlobalOutCs{tq + tslot * FZ_FRAME + s0, 256u});
     }
+    // the ring stores are read back by bulk copies (the async proxy) of other CTAs
+    if (pass == 0 || (pass == 1 && asp)) asm volatile("fence.proxy.async.global;\n" ::: "memory");
     // every consumer is done with the buffer and has issued the item's stores
     pp_sync<FZ_BAR, FZ_NT>();
     if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&freed[b])) : "memory");
@@ -1239,6 +1254,15 @@ cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* laun
   e = cudaFuncSetAttribute(k_spatial_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(FZ_SMEM));
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, nsm = 0;
+  // tensor maps: the raw ring (256 x cap 256 pixels, boxes of 16 x 256) and the S2 ring
+  // (256 x ring 256 complex, boxes of 16 x 256)
+  CUtensorMap raw_map{}, s2_map{};
+  const int bpp = a.in_kind == IN_U8 ? 1 : 2;
+  if (!encode_map_2d(&raw_map, a.raw.base, bpp, RW_L, uint64_t(a.raw.cap) * RW_L, uint64_t(RW_L) * bpp, 16, 256))
+    return cudaErrorNotSupported;
+  if (a.spatial == HV_SPATIAL_ASP &&
+      !encode_map_2d(&s2_map, a.scratch2, 8, RW_L, uint64_t(a.ring) * RW_L, uint64_t(RW_L) * 8, 16, 256))
+    return cudaErrorNotSupported;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spatial_fused, FZ_THREADS, FZ_SMEM);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -1246,7 +1270,7 @@ cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* laun
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   uint64_t grid = uint64_t(per_sm) * nsm;  // every CTA resident: the items' waits rely on it
   if (grid > nt) grid = nt;
-  k_spatial_fused<<<unsigned(grid), FZ_THREADS, FZ_SMEM, s>>>(a, uint32_t(nt));
+  k_spatial_fused<<<unsigned(grid), FZ_THREADS, FZ_SMEM, s>>>(a, uint32_t(nt), raw_map, s2_map);
   ++*launches;
   return cudaGetLastError();
 }

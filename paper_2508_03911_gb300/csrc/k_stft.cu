@@ -600,6 +600,23 @@ static bool queue_map(const StftArgs& a, int BT, CUtensorMap* map) {
   return encode_map_2d_u64(map, a.tq.base, uint64_t(a.W) * a.H, a.tq.cap, uint64_t(a.W) * a.H * 8, 8, a.S, true);
 }
 
+bool encode_map_2d(void* map, const void* base, int elem_bytes, uint64_t inner, uint64_t outer,
+                   uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const CUtensorMapDataType dt = elem_bytes == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                 : elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT64;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(static_cast<CUtensorMap*>(map), dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_map_2d_u64(void* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
                        uint32_t box_inner, uint32_t box_outer, bool swizzle64) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
