@@ -859,23 +859,25 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 //   pass 2 of f: the 16 column items of f wrote S1 slot; (ASP) the 16 column-IFFT
 //                items of f - RING have read S2 slot
 //   pass 3 of f: the 16 row-pass items of f wrote S2 slot
-// A CTA is warp-specialised: one producer warp takes the tickets, waits (bounded
+// A CTA is warp-specialised: one producer thread takes the tickets, waits (bounded
 // spin on acquire loads) for each item's counters, stages its input strip into
 // one of two buffers with one copy (a TMA tensor copy, or a 1-D bulk copy)
-// completing on the buffer's mbarrier, and
-// publishes every finished item (fence, atomic add on its slot counter); eight
-// consumer warps transform the staged strip while the next one streams in. Every
-// wait is on an item with a smaller ticket (RING > LAG); a producer holds at most
-// the item being staged and the one being transformed, and publishes the latter
-// from inside its own waits, so the item with the smallest unfinished ticket
-// always completes: the launch ends. Raw frames are read with an evict-first L2
+// completing on the buffer's mbarrier, and publishes every finished item, in
+// order (release add on its slot counter); eight consumer warps transform the
+// staged strip while the next one streams in. The producer readies the following
+// item (ticket and counters) while the consumers still hold both buffers, so its
+// copy starts as soon as one frees. Every wait is on an item with a smaller
+// ticket (RING > LAG), a CTA takes its items in ticket order, and the producer
+// publishes finished items from inside each of its waits, so the item with the
+// smallest unfinished ticket always completes: the launch ends. Raw frames are read with an evict-first L2
 // policy and the propagated frames stored with streaming stores, so that the two
 // rings keep their L2 lines.
 constexpr int FZ_NT = 256;       // consumer threads (one pass's thread layout)
 constexpr int FZ_THREADS = FZ_NT + 32;
-// rows of tickets between a frame's passes: at least the tickets in flight (3 per
-// CTA: the staged item, the transformed one, the next fetched) over the items per
-// row, so that an item's inputs are usually published when it is staged
+// rows of tickets between a frame's passes: at least the tickets in flight (4 per
+// CTA: the transformed item, the staged one, the one waiting for its buffer, the
+// next fetched) over the items per row, so that an item's inputs are usually
+// published when it is staged
 constexpr int FZ_LAG = 48;
 constexpr int FZ_BAR = 1;        // named barrier of the consumer warps
 constexpr size_t FZ_FRAME = size_t(RW_L) * RW_L;  // complex values per frame
@@ -961,148 +963,136 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
   unsigned* const done = a.fused_ctr + 1;  // done[pass * R + slot]
 
   if (warp == FZ_NT / 32) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ producer (lane 0)
+    if (lane != 0) return;
     uint64_t pol_first;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol_first));
-    bool have_pend = false, ok = true;  // lane 0: an item transformed or being transformed, not yet published
-    FzItem pend{0, 0, 0};
-    uint32_t pend_k = 0;
     const long long limit = 1ll << 31;
-    // release-add: the consumers' stores, ordered before the producer by the buffer's
-    // mbarrier, are visible at GPU scope before the count; nothing waits on a reply
-    auto publish = [&](const FzItem& it) {
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&done[it.pass * R + it.frame % R])
-                   : "memory");
-    };
-    // lane 0 keeps the next ticket's fetch in flight while it handles the current one
-    uint32_t t_next = lane == 0 ? atomicAdd(a.fused_ctr, 1u) : 0u;
-    uint32_t k = 0;
-    for (;; ++k) {
-      uint32_t pass = 0, f = 0, strip = 0, stop = 0;
-      if (lane == 0) {
-        while (true) {
-          const uint32_t t = t_next;
-          if (t >= nticket) {
-            stop = 1;
-            break;
-          }
-          t_next = atomicAdd(a.fused_ctr, 1u);
-          const uint32_t row = t / ipr, kk = t % ipr;
-          pass = kk / 16u;
-          strip = kk % 16u;
-          const long long fl = (long long)row - (long long)pass * FZ_LAG;
-          if (fl >= 0 && fl < (long long)a.n) {
-            f = uint32_t(fl);
-            break;
-          }
-        }
-        if (!stop) {
-          // wait for the item's counters, publishing the pending item meanwhile
-          const uint32_t slot = f % R, gen = f / R;
-          const long long t0 = clock64();
-          while (true) {
-            bool ready;
-            if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 16u * gen;
-            else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 16u * (gen + 1) &&
-                                        (!asp || ld_acquire_u32(&done[2 * R + slot]) >= 16u * gen);
-            else ready = ld_acquire_u32(&done[R + slot]) >= 16u * (gen + 1);
-            if (have_pend && mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
-              publish(pend);
-              have_pend = false;
-            }
-            if (ready) break;
-            if ((*reinterpret_cast<const volatile unsigned*>(a.err) & 16u) || clock64() - t0 > limit) {
-              ok = false;
-              atomicOr(a.err, 16u);
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-      }
-      stop = __shfl_sync(0xffffffffu, stop, 0);
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (stop || !ok) break;
-      pass = __shfl_sync(0xffffffffu, pass, 0);
-      f = __shfl_sync(0xffffffffu, f, 0);
-      strip = __shfl_sync(0xffffffffu, strip, 0);
-      // buffer k & 1 is free: item k - 2 was transformed and published before item k - 1 was staged
-      const int b = int(k & 1);
-      const uint32_t s0 = strip * 16u, slot = f % R;
-      float2* buf = bufs + b * FZ_BUF;
-      if (lane == 0) {
-        // one copy per item: the raw strip (256 rows x 16 pixels) and the column-IFFT
-        // strip (256 rows x 16 complex) by a TMA tensor copy, the row pass's 16 rows
-        // (contiguous) by a 1-D bulk copy. The rings were written by other CTAs'
-        // generic stores, fenced for the async proxy before their publication; this
-        // thread acquired the counters that published them.
-        desc[b] = FzItem{pass, f, strip};
-        const uint32_t fb = rw_smem(&full[b]);
-        if (pass == 0) {
-          const uint32_t bytes = 256u * 16u * (u8 ? 1u : 2u);
-          const uint32_t rslot = uint32_t((a.raw.slot0 + f) % a.raw.cap);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
-          asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
-              "[%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(rw_smem(raw_of(b))),
-              "l"(reinterpret_cast<uint64_t>(&raw_map)), "r"(int(s0)), "r"(int(rslot * 256u)), "r"(fb),
-              "l"(pol_first)
-              : "memory");
-        } else if (pass == 1) {
-          const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
-          asm volatile("fence.proxy.async.global;\n" ::: "memory");
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                  rw_smem(buf)),
-              "l"(src), "r"(32768u), "r"(fb)
-              : "memory");
-        } else {
-          asm volatile("fence.proxy.async.global;\n" ::: "memory");
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
-          asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-              "[%4];\n" ::"r"(rw_smem(buf)),
-              "l"(reinterpret_cast<uint64_t>(&s2_map)), "r"(int(s0)), "r"(int(slot * 256u)), "r"(fb)
-              : "memory");
-        }
-      }
-      if (lane == 0) {
-        // publish item k - 1 once its transform is done (the consumers then start item k)
-        if (have_pend) {
-          const long long t0 = clock64();
-          while (!mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
-            if (clock64() - t0 > limit) {
-              ok = false;
-              atomicOr(a.err, 16u);
-              break;
-            }
-          }
-          if (ok) publish(pend);
-        }
-        have_pend = true;
-        pend = FzItem{pass, f, strip};
-        pend_k = k;
-      }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) break;
-    }
-    // publish the last item, then tell the consumers to stop (item k, buffer k & 1)
-    if (lane == 0 && ok && have_pend) {
+    bool stuck = false;  // a wait for the consumers gave up
+    // items are staged in order, item k into buffer k & 1; `issued` items were staged,
+    // the first `published` of them transformed and counted. The counter of item k
+    // sits at done[cnt0] or done[cnt1] (by k & 1) until it is published.
+    uint32_t issued = 0, published = 0, cnt0 = 0, cnt1 = 0;
+    // publish, in order, the items below `upto` whose transform is done; block: wait
+    // for each (false when a wait gave up). Release-add: the consumers' stores, ordered
+    // before this thread by the buffer's mbarrier, are visible at GPU scope before the
+    // count; nothing waits on a reply.
+    auto drain = [&](uint32_t upto, bool block) -> bool {
       const long long t0 = clock64();
-      while (!mbar_test(rw_smem(&freed[pend_k & 1]), (pend_k >> 1) & 1)) {
-        if (clock64() - t0 > limit) {
-          ok = false;
-          atomicOr(a.err, 16u);
+      while (published < upto) {
+        if (mbar_test(rw_smem(&freed[published & 1]), (published >> 1) & 1)) {
+          const uint32_t c = (published & 1) ? cnt1 : cnt0;
+          asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&done[c]) : "memory");
+          ++published;
+        } else if (!block) {
+          return true;
+        } else if (clock64() - t0 > limit) {
+          return false;
+        }
+      }
+      return true;
+    };
+    // the next ticket's fetch stays in flight while the current one is handled
+    uint32_t t_next = atomicAdd(a.fused_ctr, 1u);
+    // the next item with its counters satisfied, publishing finished items meanwhile;
+    // false when the tickets are used up or a wait gave up
+    auto prepare = [&](FzItem& it) -> bool {
+      uint32_t pass, f, strip;
+      while (true) {
+        const uint32_t t = t_next;
+        if (t >= nticket) return false;
+        t_next = atomicAdd(a.fused_ctr, 1u);
+        const uint32_t row = t / ipr, kk = t % ipr;
+        pass = kk / 16u;
+        strip = kk % 16u;
+        const long long fl = (long long)row - (long long)pass * FZ_LAG;
+        if (fl >= 0 && fl < (long long)a.n) {
+          f = uint32_t(fl);
           break;
         }
       }
-      if (ok) publish(pend);
+      const uint32_t slot = f % R, gen = f / R;
+      const long long t0 = clock64();
+      while (true) {
+        bool ready;
+        if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 16u * gen;
+        else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 16u * (gen + 1) &&
+                                    (!asp || ld_acquire_u32(&done[2 * R + slot]) >= 16u * gen);
+        else ready = ld_acquire_u32(&done[R + slot]) >= 16u * (gen + 1);
+        drain(issued, false);
+        if (ready) break;
+        if ((*reinterpret_cast<const volatile unsigned*>(a.err) & 16u) || clock64() - t0 > limit) {
+          atomicOr(a.err, 16u);
+          return false;
+        }
+        __nanosleep(32);
+      }
+      it = FzItem{pass, f, strip};
+      return true;
+    };
+    // the next item is ready before its buffer frees, so that its copy starts the
+    // moment the consumers are done with the item two before it
+    FzItem it{0, 0, 0};
+    bool more = prepare(it);
+    while (more) {
+      const uint32_t k = issued, b = k & 1;
+      // buffer b is free once item k - 2 is transformed (published here, in order)
+      if (k >= 2 && !drain(k - 1, true)) {
+        stuck = true;
+        atomicOr(a.err, 16u);
+        break;
+      }
+      // one copy per item: the raw strip (256 rows x 16 pixels) and the column-IFFT
+      // strip (256 rows x 16 complex) by a TMA tensor copy, the row pass's 16 rows
+      // (contiguous) by a 1-D bulk copy. The rings were written by other CTAs'
+      // generic stores, fenced for the async proxy before their publication; this
+      // thread acquired the counters that published them.
+      const uint32_t s0 = it.strip * 16u, slot = it.frame % R;
+      desc[b] = it;
+      const uint32_t fb = rw_smem(&full[b]);
+      if (it.pass == 0) {
+        const uint32_t bytes = 256u * 16u * (u8 ? 1u : 2u);
+        const uint32_t rslot = uint32_t((a.raw.slot0 + it.frame) % a.raw.cap);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+            "[%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(rw_smem(raw_of(b))),
+            "l"(reinterpret_cast<uint64_t>(&raw_map)), "r"(int(s0)), "r"(int(rslot * 256u)), "r"(fb),
+            "l"(pol_first)
+            : "memory");
+      } else if (it.pass == 1) {
+        const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                rw_smem(bufs + b * FZ_BUF)),
+            "l"(src), "r"(32768u), "r"(fb)
+            : "memory");
+      } else {
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];\n" ::"r"(rw_smem(bufs + b * FZ_BUF)),
+            "l"(reinterpret_cast<uint64_t>(&s2_map)), "r"(int(s0)), "r"(int(slot * 256u)), "r"(fb)
+            : "memory");
+      }
+      const uint32_t c = it.pass * R + slot;
+      if (b) cnt1 = c;
+      else cnt0 = c;
+      issued = k + 1;
+      more = prepare(it);
     }
-    const int b = int(k & 1);
-    if (lane == 0) {
+    // publish the rest as it finishes, then tell the consumers to stop (item `issued`,
+    // whose buffer the last drain freed); if a wait gave up, the consumers' own
+    // bounded waits end them
+    if (!stuck && drain(issued, true)) {
+      const int b = int(issued & 1);
       desc[b] = FzItem{FZ_STOP, 0, 0};
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&full[b])) : "memory");
+    } else {
+      atomicOr(a.err, 16u);
     }
     return;
   }
