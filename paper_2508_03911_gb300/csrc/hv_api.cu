@@ -764,7 +764,7 @@ hv_status post_apply(hv_handle* h) {
                          size_t(h->post_R) * h->nout * hw * sizeof(float));
     if (s == HV_OK)
       s = ensure(h, reinterpret_cast<void**>(&h->post_sums), &h->post_sums_bytes,
-                 size_t(h->post_R) * h->nout * sizeof(double));
+                 size_t(h->post_R) * h->nout * kPostSub * sizeof(double));
     if (s == HV_OK && q.kernel_size > 0) {
       s = ensure(h, reinterpret_cast<void**>(&h->post_kdev), &h->post_kdev_bytes,
                  h->post_k_cur.size() * sizeof(float));
@@ -881,6 +881,22 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   int launches = 0;
   cudaError_t e;
   const RingRef tq{h->tq, h->Q, uint32_t(h->next_win % h->Q)};
+  PostArgs pa{};
+  if (h->post_active) {
+    pa.W = h->W;
+    pa.H = h->H;
+    pa.nout = h->nout;
+    pa.K = int(h->post_cur.kernel_size);
+    pa.kern = h->post_kdev;
+    pa.renorm = h->post_cur.renormalize ? 1 : 0;
+    pa.A = h->post_cur.accumulate;
+    pa.R = h->post_R;
+    pa.count = h->post_count;
+    pa.ring = h->post_ring;
+    pa.sums = h->post_sums;
+    // without a convolution the STFT epilogue writes the image ring and its sums
+    pa.fused = !none && h->cur.temporal != HV_TEMPORAL_PCA && pa.K == 0 ? 1 : 0;
+  }
   if (none) {
     e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
   } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
@@ -928,32 +944,28 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
     sa.out = dst;
     sa.err = h->dev_err;
     sa.kernel = h->stft_kernel;
-    if (h->cur.tuned || h->cur.stft_kernel != 0) {
+    e = cudaSuccess;
+    if (pa.fused) {
+      sa.post_ring = pa.ring;
+      sa.post_R = pa.R;
+      sa.post_count = pa.count;
+      sa.post_sums = pa.renorm ? pa.sums : nullptr;
+      e = launch_post_zero(pa, nw, h->stream);
+    }
+    if (e == cudaSuccess && (h->cur.tuned || h->cur.stft_kernel != 0)) {
       e = launch_stft(sa, h->stream, &launches);
-    } else {
+    } else if (e == cudaSuccess) {
       // plain form: the walking kernel, one launch per window
       sa.nwin = 1;
-      e = cudaSuccess;
       for (uint32_t w = 0; w < nw && e == cudaSuccess; ++w) {
         sa.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
         sa.out = dst + size_t(w) * h->win_floats;
+        sa.post_count = pa.count + w;
         e = launch_stft(sa, h->stream, &launches);
       }
     }
   }
   if (e == cudaSuccess && h->post_active) {
-    PostArgs pa{};
-    pa.W = h->W;
-    pa.H = h->H;
-    pa.nout = h->nout;
-    pa.K = int(h->post_cur.kernel_size);
-    pa.kern = h->post_kdev;
-    pa.renorm = h->post_cur.renormalize ? 1 : 0;
-    pa.A = h->post_cur.accumulate;
-    pa.R = h->post_R;
-    pa.count = h->post_count;
-    pa.ring = h->post_ring;
-    pa.sums = h->post_sums;
     e = launch_post(dst, nw, pa, h->stream, &launches);
     h->post_count += nw;
   }

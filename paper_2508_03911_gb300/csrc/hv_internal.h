@@ -88,7 +88,18 @@ struct StftArgs {
   int kernel;           // STFT_AUTO: windows that do not overlap (S >= T) one CTA per
                         // (window, pixel tile); STFT_WIDE: the same with twice the pixels
                         // per CTA; STFT_WALK: CTAs walk all windows of their pixels
+  // post-processing without convolution, fused into the epilogue: when post_ring is
+  // set, the images of window w go to ring slot (post_count + w) mod post_R (layout
+  // [R][nout][H*W]) instead of out, and when post_sums is set each image's sum is
+  // added (float64 atomics) into post_sums [slot][image][kPostSub], zeroed beforehand
+  float* post_ring;
+  uint32_t post_R;
+  uint64_t post_count;
+  double* post_sums;
 };
+// float64 sums of a post-processed image are kept as kPostSub partial sums, so that
+// the CTAs that produce it add into different words
+constexpr uint32_t kPostSub = 32;
 enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
@@ -159,8 +170,9 @@ cudaError_t launch_af_standardize(const float* cells, const double* sums, uint32
 
 // Post-processing of rendered images [window][nout][H][W] (Sec. III-B): periodic
 // K x K convolution into ring slot (count + window) mod R, per-image float64 sums
-// when re-normalising, then each image replaced in place by the mean of its last
-// min(A, count + window + 1) ring slots. H, W multiples of 16.
+// when re-normalising (added by the kernel that writes the slot), then each image
+// replaced in place by the mean of its last min(A, count + window + 1) ring slots.
+// H, W multiples of 16.
 struct PostArgs {
   uint32_t W, H, nout;
   int K;                // 0 (no convolution) or odd
@@ -169,8 +181,13 @@ struct PostArgs {
   uint32_t A, R;
   uint64_t count;       // images of each output already in the ring
   float* ring;          // [R][nout][H][W]
-  double* sums;         // [R][nout]
+  double* sums;         // [R][nout][kPostSub] partial sums
+  int fused;            // the STFT epilogue already wrote the ring slots and their sums
 };
+// Zeroes the partial sums of the ring slots the next nwin windows write.
+cudaError_t launch_post_zero(const PostArgs& a, uint32_t nwin, cudaStream_t s);
+// Unfused: zeroes the slots' sums, convolves (or copies) the images into the ring
+// adding the sums, then averages; fused: averages only. `images` is the output.
 cudaError_t launch_post(float* images, uint32_t nwin, const PostArgs& a, cudaStream_t s, int* launches);
 
 // Copy propagated frames out as interleaved complex images.

@@ -5,8 +5,10 @@
 // Rendered images of one call are [window][image][H][W]. Each image, after the
 // convolution, goes to slot (count + window) mod R of a ring that keeps the last
 // R images of every output (R >= A - 1 + windows per call), with its float64 sum
-// beside it; the moving average then reads the slots it needs, so every window
-// of the call is averaged in parallel.
+// beside it (kPostSub partial sums, added by the CTAs that write the slot); the
+// moving average then reads the slots it needs, so every window of the call is
+// averaged in parallel. Without a convolution the STFT epilogue writes the slots
+// and their sums itself, and only the average runs here.
 #include "hv_internal.h"
 
 namespace hv {
@@ -16,7 +18,8 @@ namespace {
 constexpr int PT = 16;  // output tile side of the convolution
 
 // ring[slot][m][y][x] = sum_{a,b} k[a][b] img[(y + a - c) mod H][(x + b - c) mod W]
-// for image m of window w (slot = (count + w) mod R); K = 0 copies.
+// for image m of window w (slot = (count + w) mod R); K = 0 copies. Re-normalising,
+// the tile's sum goes into one of the slot image's partial sums.
 __global__ void __launch_bounds__(PT* PT) k_post_conv(const float* __restrict__ img, PostArgs a) {
   extern __shared__ float sm[];
   const int K = a.K, c = K / 2, S = PT + (K > 0 ? K - 1 : 0);
@@ -46,44 +49,45 @@ __global__ void __launch_bounds__(PT* PT) k_post_conv(const float* __restrict__ 
   }
   const uint32_t slot = uint32_t((a.count + w) % a.R);
   a.ring[(size_t(slot) * a.nout + m) * hw + size_t(ty0 + ly) * a.W + tx0 + lx] = v;
-}
-
-// sums[slot][m] = sum over the ring image (float64), one CTA per image.
-__global__ void __launch_bounds__(256) k_post_sum(PostArgs a) {
-  const uint32_t im = blockIdx.x, w = im / a.nout, m = im % a.nout;
-  const uint32_t slot = uint32_t((a.count + w) % a.R);
-  const size_t hw = size_t(a.W) * a.H;
-  const float* src = a.ring + (size_t(slot) * a.nout + m) * hw;
-  double s = 0.0;
-  for (size_t e = threadIdx.x; e < hw; e += 256) s += src[e];
+  if (a.renorm) {
+    double t = v;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double red[8];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += red[i];
-    a.sums[size_t(slot) * a.nout + m] = t;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __shared__ double red[PT * PT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int i = 0; i < PT * PT / 32; ++i) u += red[i];
+      atomicAdd(&a.sums[(size_t(slot) * a.nout + m) * kPostSub + blockIdx.x % kPostSub], u);
+    }
   }
 }
 
 // out[w][m][p] = mean over the last min(A, count + w + 1) slots of image m,
 // each divided by its mean when re-normalising.
-__global__ void k_post_avg(float* __restrict__ out, PostArgs a) {
+__global__ void __launch_bounds__(256) k_post_avg(float* __restrict__ out, PostArgs a) {
+  __shared__ double scale[64];  // hw / sum of each slot read (A <= 64)
   const uint32_t im = blockIdx.y, w = im / a.nout, m = im % a.nout;
   const size_t hw = size_t(a.W) * a.H;
   const uint64_t newest = a.count + w;
   const uint32_t n = uint32_t(newest + 1 < a.A ? newest + 1 : a.A);
+  if (a.renorm) {
+    for (uint32_t j = threadIdx.x >> 5; j < n; j += blockDim.x >> 5) {
+      const uint32_t slot = uint32_t((newest - j) % a.R);
+      double t = a.sums[(size_t(slot) * a.nout + m) * kPostSub + (threadIdx.x & 31)];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if ((threadIdx.x & 31) == 0) scale[j] = t != 0.0 ? double(hw) / t : 0.0;
+    }
+    __syncthreads();
+  }
   for (size_t p = blockIdx.x * size_t(blockDim.x) + threadIdx.x; p < hw; p += size_t(gridDim.x) * blockDim.x) {
     float acc = 0.f;
     for (uint32_t j = 0; j < n; ++j) {
       const uint32_t slot = uint32_t((newest - j) % a.R);
       float v = a.ring[(size_t(slot) * a.nout + m) * hw + p];
-      if (a.renorm) {
-        const double s = a.sums[size_t(slot) * a.nout + m];
-        v = s != 0.0 ? float(double(v) * (double(hw) / s)) : 0.f;
-      }
+      if (a.renorm) v = float(double(v) * scale[j]);
       acc += v;
     }
     out[size_t(im) * hw + p] = acc / float(n);
@@ -92,17 +96,30 @@ __global__ void k_post_avg(float* __restrict__ out, PostArgs a) {
 
 }  // namespace
 
+cudaError_t launch_post_zero(const PostArgs& a, uint32_t nwin, cudaStream_t s) {
+  if (!a.renorm || nwin == 0) return cudaSuccess;
+  // the slots (count + w) mod R of the call, w < nwin <= R: one run, or two across the wrap
+  const size_t per_slot = size_t(a.nout) * kPostSub * sizeof(double);
+  const uint32_t first = uint32_t(a.count % a.R);
+  const uint32_t run = nwin < a.R - first ? nwin : a.R - first;
+  cudaError_t e = cudaMemsetAsync(a.sums + size_t(first) * a.nout * kPostSub, 0, run * per_slot, s);
+  if (e == cudaSuccess && run < nwin) e = cudaMemsetAsync(a.sums, 0, (nwin - run) * per_slot, s);
+  return e;
+}
+
 cudaError_t launch_post(float* images, uint32_t nwin, const PostArgs& a, cudaStream_t s, int* launches) {
   if (nwin == 0) return cudaSuccess;
+  if (nwin > a.R || a.A > 64) return cudaErrorInvalidValue;
   const uint32_t nimg = nwin * a.nout;
-  const int S = PT + (a.K > 0 ? a.K - 1 : 0);
-  const size_t smem = (size_t(S) * S + size_t(a.K) * a.K) * sizeof(float);
-  k_post_conv<<<dim3((a.W / PT) * (a.H / PT), nimg), PT * PT, smem, s>>>(images, a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  *launches += 1;
-  if (a.renorm) {
-    k_post_sum<<<nimg, 256, 0, s>>>(a);
+  cudaError_t e;
+  if (!a.fused) {
+    e = launch_post_zero(a, nwin, s);
+    if (e != cudaSuccess) return e;
+    const int S = PT + (a.K > 0 ? a.K - 1 : 0);
+    const size_t smem = (size_t(S) * S + size_t(a.K) * a.K) * sizeof(float);
+    k_post_conv<<<dim3((a.W / PT) * (a.H / PT), nimg), PT * PT, smem, s>>>(images, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     *launches += 1;
   }
   const size_t hw = size_t(a.W) * a.H;

@@ -285,6 +285,55 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   }
 }
 
+// The moments of pixel `pix` for window w, from the lane group's reduced sums
+// (held by its lane jl = 0, the writer): M0, M1, M2 (bins -> kHz), then M1N and M2N
+// in float64, in that order among those the mask asks for, to out [w][image][pixel]
+// or, with post-processing fused, to the image ring slot of the window, adding
+// each image's sum over the warp's pixels into one of the slot's partial sums.
+// Called by every lane of the warp (the sums are reduced across it).
+__device__ __forceinline__ void emit_moments(const StftArgs& a, uint32_t w, size_t pix, const MomAcc& acc,
+                                             bool writer, bool streaming) {
+  const size_t HW = size_t(a.W) * a.H;
+  float v[5];
+  v[0] = acc.m0;
+  v[1] = acc.m1 * a.fscale;
+  v[2] = acc.m2 * (a.fscale * a.fscale);
+  const double d0 = acc.m0;
+  v[3] = 0.f;
+  v[4] = 0.f;
+  if (a.mask & HV_MOM_M1N) v[3] = d0 > 0.0 ? float(double(v[1]) / d0) : 0.f;
+  if (a.mask & HV_MOM_M2N) {
+    const double r = d0 > 0.0 ? double(v[2]) / d0 : 0.0;
+    v[4] = float(sqrt(r > 0.0 ? r : 0.0));
+  }
+  uint32_t slot = 0;
+  float* o;
+  if (a.post_ring) {
+    slot = uint32_t((a.post_count + w) % a.post_R);
+    o = a.post_ring + size_t(slot) * a.nout * HW + pix;
+  } else {
+    o = a.out + size_t(w) * a.nout * HW + pix;
+  }
+  const uint32_t sub = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kPostSub;
+  int q = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (!(a.mask & (1u << k))) continue;
+    if (writer) {
+      if (streaming) __stcs(&o[HW * q], v[k]);
+      else o[HW * q] = v[k];
+    }
+    if (a.post_sums) {
+      float t = writer ? v[k] : 0.f;
+#pragma unroll
+      for (int x = 16; x > 0; x >>= 1) t += __shfl_xor_sync(0xffffffffu, t, x);
+      if ((threadIdx.x & 31) == 0)
+        atomicAdd(&a.post_sums[(size_t(slot) * a.nout + q) * kPostSub + sub], double(t));
+    }
+    ++q;
+  }
+}
+
 template <int T>
 __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
     k_stft_warp(StftArgs a, const __grid_constant__ CUtensorMap qmap) {
@@ -451,20 +500,7 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
       acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
       acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
     }
-    if (jl == 0) {
-      const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
-      float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
-      int q = 0;
-      if (a.mask & HV_MOM_M0) o[HW * q++] = acc.m0;
-      if (a.mask & HV_MOM_M1) o[HW * q++] = m1;
-      if (a.mask & HV_MOM_M2) o[HW * q++] = m2;
-      const double d0 = acc.m0;
-      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(m1) / d0) : 0.f;
-      if (a.mask & HV_MOM_M2N) {
-        const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
-        o[HW * q++] = float(sqrt(r > 0.0 ? r : 0.0));
-      }
-    }
+    emit_moments(a, w, p0 + px, acc, jl == 0, false);
   }
 }
 
@@ -560,20 +596,7 @@ __global__ void __launch_bounds__(WinCfg<T, WIDE>::NT, WinCfg<T, WIDE>::OCC) k_s
     acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
     acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
   }
-  if (jl == 0) {
-    const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
-    float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
-    int q = 0;
-    if (a.mask & HV_MOM_M0) __stcs(&o[HW * q++], acc.m0);
-    if (a.mask & HV_MOM_M1) __stcs(&o[HW * q++], m1);
-    if (a.mask & HV_MOM_M2) __stcs(&o[HW * q++], m2);
-    const double d0 = acc.m0;
-    if (a.mask & HV_MOM_M1N) __stcs(&o[HW * q++], d0 > 0.0 ? float(double(m1) / d0) : 0.f);
-    if (a.mask & HV_MOM_M2N) {
-      const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
-      __stcs(&o[HW * q++], float(sqrt(r > 0.0 ? r : 0.0)));
-    }
-  }
+  emit_moments(a, w, p0 + px, acc, jl == 0, true);
 }
 
 // cuTensorMapEncodeTiled from the driver (resolved once through the runtime)

@@ -12,13 +12,13 @@ pytestmark = pytest.mark.gpu
 IMAGE_TOL = 1e-4
 
 
-def gpu_stream(frames, p, post, packets, post_at=0):
+def gpu_stream(frames, p, post, packets, post_at=0, **extra):
     """Render frames pushed in `packets`; post-processing set before packet post_at."""
     import torch
     n, H, W = frames.shape
     r = hv.Renderer(W, H, 16, n)
     try:
-        hv.hv_set_params(r.h, to_hv(p))
+        hv.hv_set_params(r.h, to_hv(p, **extra))
         wf = r.window_floats()
         out = torch.zeros(n * wf, dtype=torch.float32, device="cuda")
         nw, a = 0, 0
@@ -63,6 +63,22 @@ def test_gaussian_renorm_accumulate_stft():
     post = dict(kernel_size=5, sigma=1.2, renormalize=True, accumulate=3)
     img = gpu_stream(fr, p, post, [T + 3 * S, 2 * S, 5, 4 * S + 3, 2 * S - 5 + 3])
     check(img, oracle_post(fr, p, O.gaussian_kernel(5, 1.2), True, 3))
+
+
+@pytest.mark.parametrize("T,S,form", [(16, 16, dict(tuned=1)), (16, 16, dict(stft_kernel="window_wide")),
+                                      (16, 4, dict(tuned=1)), (16, 4, dict(tuned=0))])
+def test_renorm_accumulate_fused_into_the_stft(T, S, form):
+    """Without a convolution the STFT epilogue writes the image ring and adds each
+    image's sum itself (window-per-CTA kernels for S >= T, the walking kernel for
+    S < T, one launch per window in the plain form); every moment kind, history
+    across renders and ring wrap-around."""
+    H, W = 32, 64
+    fr = synth.random_frames(T + 13 * S + 5, H, W, 12, seed=T + S)
+    p = oracle_params(spatial="asp", T=T, stride=S, fs_hz=20000.0, band_lo_bin=1, band_hi_bin=6,
+                      moments=("M0", "M1", "M2", "M1N", "M2N"), H=H, W=W)
+    packets = [T + 2 * S, 3 * S + 1, 4 * S, 4 * S - 1 + 5]
+    img = gpu_stream(fr, p, dict(renormalize=True, accumulate=4), packets, **form)
+    check(img, oracle_post(fr, p, None, True, 4))
 
 
 def test_user_kernel_pca():
