@@ -447,138 +447,222 @@ __global__ void __launch_bounds__(256) k_jacobi_f32(PcaArgs a) {
   if (gtid == 0) atomicAdd(&a.counters[1], unsigned(sweeps));  // float32 sweeps
 }
 
-// The float32 phase on one thread-block cluster (JC CTAs, the matrix in their
-// shared memory; T = 128 or 256). CTA `rank` owns rows rank R .. rank R + R - 1 of
-// C (two buffers: a round reads one and writes the other) and of Vf. A round of
-// the round-robin schedule: (1) the owner of each pair's first row computes the
-// pair's rotation (the partner's diagonal entry read from its owner's shared
-// memory) and writes it into every CTA's rotation table; (2) after a cluster
-// barrier, every CTA forms its new rows: the left rotation mixes a row with its
-// partner row (local or remote), the right rotations mix the columns of each
-// pair within the row; Vf rows rotate in place; a second barrier ends the round.
-// Every CTA counts the rotations of its complete table, so all agree when a sweep
-// rotates nothing.
+// Both phases of the long-window eigensolver on one thread-block cluster (JC CTAs,
+// the matrix in their shared memory; T = 128 or 256). The cyclic order is the
+// round-robin one (rr_elem): in round r position k holds index rr_elem(k, r) and
+// pair p joins positions p and T-1-p; from one round to the next the index at
+// position k moves to k - 1 (position 1 to T-1, position 0 stays). CTA c owns
+// pairs c PPC .. c PPC + PPC - 1: the rows at their positions sit in its shared
+// memory (slot l for position c PPC + l, slot R-1-l for position T-1-(c PPC + l)),
+// so the left rotation of a row mixes it with a local row. Rows are double
+// buffered: round r reads buffer r & 1 and writes each new row straight into the
+// slot of its next position in buffer (r + 1) & 1 -- of the same CTA, except for
+// two rows a round that go to a neighbour's shared memory. A round: (1) every CTA
+// reads each pair's off-diagonal entry (and in the float32 phase both diagonal
+// entries) from the owners' shared memory and computes all rotations itself (a
+// deterministic function of the same data, so all CTAs agree); (2) it rotates the
+// 2 x 2 blocks of its pairs' rows (left by the pair's rotation, right by each
+// column pair's) and the column pairs of its rows of V (CTA c owns rows c R ..
+// c R + R - 1 of V, which do not move); (3) one cluster barrier. Float32 phase
+// (REFINE false): C scaled by a power of two near 1 / max C_ii, rotations
+// J = [[c, -s], [conj(ph) s, conj(ph) c]] accumulated in Vf (from the identity),
+// until a sweep rotates nothing at 1e-6 of the trace. Refinement (REFINE true) on
+// C' = Vf^H C Vf: the diagonal in float64, a copy in every CTA updated
+// identically, the off-diagonal entries in float32, the angles of refine_rot; at
+// most max_sweeps sweeps, fewer when every entry met in a sweep is below stop_rel
+// of the trace; the unscaled diagonal goes back into a.C for the eigenvalue
+// selection. Its rotations take the form J = [[c, -s u], [s conj(u), c]] (u = g / |g|;
+// the same diagonal as the form with the phase on the second column,
+// P R = diag(1, conj(u)) R, since J = P R P^H), so that their product Q = I + D stays
+// near the identity: D (|D| ~ the off-diagonal size, 1e-6 of the trace) is
+// accumulated in float32 as D <- D J + (J - I), with c - 1 = -s^2 / (1 + c), and
+// written to a.Cf; V = Vf + Vf D follows in k_vcorr, the float32 product exact to
+// ~1e-13 against the entries of V. (Owning rows rather than pairs, each round read
+// the 32 KB of partner rows through the cluster's shared-memory network, about
+// 14 bytes a clock per SM, and V rotated in float64 on 16 SMs was bound by their
+// float64 rate: 4.5 us a round against about 1 us here.)
 constexpr int JC = 16;
-
-// position of index i in round r of the round-robin arrangement (inverse of rr_elem)
-__device__ __forceinline__ int rr_pos(int i, int r, int T) {
-  return i == 0 ? 0 : ((i - 1 - r) % (T - 1) + (T - 1)) % (T - 1) + 1;
-}
-
 constexpr int JC_NT = 512;
 
-template <int T>
+template <int T, bool REFINE>
+struct JclSmem {
+  static constexpr int NP = T / 2, PPC = NP / JC, R = 2 * PPC;
+  // C buffers (2), Vf or D rows, the rotation table, (REFINE) the diagonal
+  static constexpr size_t c_bytes = size_t(R) * T * sizeof(float2);
+  static constexpr size_t bytes() { return 3 * c_bytes + NP * sizeof(RotF) + (REFINE ? T * sizeof(double) : 0); }
+};
+
+// Owner CTA and slot of position k (pairs PPC to a CTA, R = 2 PPC slots)
+__device__ __forceinline__ void jc_place(int k, int T, int PPC, int& cta, int& slot) {
+  if (k < T / 2) {
+    cta = k / PPC;
+    slot = k % PPC;
+  } else {
+    const int p = T - 1 - k;
+    cta = p / PPC;
+    slot = 2 * PPC - 1 - p % PPC;
+  }
+}
+
+template <int T, bool REFINE>
 __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
-  constexpr int R = T / JC, NP = T / 2;
+  using Sm = JclSmem<T, REFINE>;
+  constexpr int NP = Sm::NP, PPC = Sm::PPC, R = Sm::R;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = int(cl.block_rank()), tid = threadIdx.x, row0 = rank * R;
   extern __shared__ float4 jcs[];
-  float2* C0 = reinterpret_cast<float2*>(jcs);  // buffer b at C0 + b R T
-  float2* Vr = C0 + 2 * R * T;                  // own rows of Vf
-  float2* Pr = Vr + R * T;                      // partner rows of the round
-  RotF* rot = reinterpret_cast<RotF*>(Pr + R * T);
-  __shared__ int pos_of[T], elem_at[T];
-  __shared__ float gabs[NP];     // |C_ij| of each pair when its rotation was decided
-  __shared__ float tr_part[JC];  // diagonal sums of the CTAs
+  float2* C0 = reinterpret_cast<float2*>(jcs);  // buffer b at C0 + b R T, slot s at + s T
+  float2* Vr = C0 + 2 * R * T;                  // own rows of Vf (float32 phase) or of D
+  RotF* rot = reinterpret_cast<RotF*>(Vr + R * T);
+  double* d = reinterpret_cast<double*>(rot + NP);  // REFINE: the scaled diagonal
+  __shared__ float gabs[NP];  // |C_ij| of each pair when its rotation was decided
   __shared__ unsigned s_nrot;
   __shared__ float s_offmax;
+  __shared__ double s_trace;
   const double scale = pow2_diag_scale(a.C, T);  // the same in every CTA
+  // round 0: position k holds index k
   for (int e = tid; e < R * T; e += JC_NT) {
-    const int li = e / T, c = e % T;
-    const double2 v = a.C[size_t(row0 + li) * T + c];
-    C0[e] = make_float2(float(v.x * scale), float(v.y * scale));
-    Vr[e] = make_float2(row0 + li == c ? 1.f : 0.f, 0.f);
+    const int sl = e / T, c = e % T;
+    const int k = sl < PPC ? rank * PPC + sl : T - 1 - (rank * PPC + (R - 1 - sl));
+    if (REFINE) {  // Hermitian by construction: the upper triangle, a real zero diagonal
+      const double2 v = a.C[size_t(k < c ? k : c) * T + (k < c ? c : k)];
+      C0[e] = make_float2(float(v.x * scale), k == c ? 0.f : (k < c ? float(v.y * scale) : -float(v.y * scale)));
+      Vr[e] = make_float2(0.f, 0.f);  // D = 0
+    } else {
+      const double2 v = a.C[size_t(k) * T + c];
+      C0[e] = make_float2(float(v.x * scale), float(v.y * scale));
+      Vr[e] = make_float2(row0 + sl == c ? 1.f : 0.f, 0.f);
+    }
   }
-  if (tid == 0) {  // the trace: every CTA's diagonal sum, written into every CTA
-    float t = 0.f;
-    for (int li = 0; li < R; ++li) t += float(a.C[size_t(row0 + li) * T + row0 + li].x * scale);
-    for (int c = 0; c < JC; ++c) cl.map_shared_rank(tr_part, c)[rank] = t;
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < T; ++i) t += a.C[size_t(i) * T + i].x * scale;
+    s_trace = t;
   }
+  if (REFINE)
+    for (int i = tid; i < T; i += JC_NT) d[i] = a.C[size_t(i) * T + i].x * scale;
   cl.sync();
-  float trace = 0.f;
-  for (int c = 0; c < JC; ++c) trace += tr_part[c];
-  // scales: the trace (>= the largest eigenvalue); float32 rounding leaves
-  // off-diagonal entries near 6e-8 of the largest eigenvalue
-  const float ftol = 1e-6f, ffloor = 2e-7f * trace;
+  const double trace = s_trace;
+  // float32 phase: the trace bounds the largest eigenvalue; float32 rounding leaves
+  // off-diagonal entries near 6e-8 of it. Refinement: the caller's bounds, relative
+  // to the largest diagonal entry (scaled to [0.5, 1))
+  double cmax = 0.0;
+  if (REFINE)
+    for (int i = 0; i < T; ++i) cmax = fmax(cmax, a.C[size_t(i) * T + i].x * scale);
+  const float tol = REFINE ? float(a.tol) : 1e-6f;
+  const float floor_abs = REFINE ? float(a.tol_abs * cmax) : 2e-7f * float(trace);
+  const int max_sweeps = REFINE ? a.max_sweeps : 20;
+  // a thread's column pair q is the same in every round (the items are strided by JC_NT)
+  static_assert(JC_NT % NP == 0, "column pair per thread");
+  const int q = tid % NP;
   int sweeps = 0, cur = 0;
-  for (int sweep = 0; sweep < 20; ++sweep) {
-    unsigned nrot = 0;   // warp 0's running totals of the sweep
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    unsigned nrot = 0;  // warp 0's running totals of the sweep
     float offmax = 0.f;
     for (int r = 0; r < T - 1; ++r) {
-      float2* Cs = C0 + cur * R * T;
+      const float2* Cs = C0 + cur * R * T;
       float2* Cd = C0 + (cur ^ 1) * R * T;
-      for (int x = tid; x < T; x += JC_NT) {
-        elem_at[x] = rr_elem(x, r, T);
-        pos_of[x] = rr_pos(x, r, T);
+      // (1) every pair's rotation, from its owner's rows
+      if (tid < NP) {
+        const int p = tid, i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
+        const float2* own = cl.map_shared_rank(Cs, p / PPC);
+        const float2* lo = own + (p % PPC) * T;
+        const float2 g = lo[j];
+        float ci = 0.f, cj = 0.f;
+        if (!REFINE) {
+          ci = lo[i].x;
+          cj = own[(R - 1 - p % PPC) * T + j].x;
+        }
+        const float ag = sqrtf(g.x * g.x + g.y * g.y);
+        if (REFINE) {
+          RotV unused;
+          refine_rot(d, i, j, g, ag, tol, floor_abs, rot[p], unused);
+        } else {
+          jacobi_rot_f(ci, cj, g, tol, floor_abs, rot[p]);
+        }
+        gabs[p] = ag;
       }
       __syncthreads();
-      // (1) rotations of the pairs whose first row is ours, into every CTA's table
-      for (int li = tid; li < R; li += JC_NT) {
-        const int i = row0 + li, k = pos_of[i];
-        if (k >= NP) continue;  // i is the second row of its pair
-        const int j = elem_at[T - 1 - k];
-        const float2* Cj = cl.map_shared_rank(Cs, j / R);
-        RotF q;
-        const float2 g = Cs[li * T + j];
-        jacobi_rot_f(Cs[li * T + i].x, Cj[(j % R) * T + j].x, g, ftol, ffloor, q);
-        const float ag = sqrtf(g.x * g.x + g.y * g.y);
-        for (int c = 0; c < JC; ++c) {
-          cl.map_shared_rank(rot, c)[k] = q;
-          cl.map_shared_rank(gabs, c)[k] = ag;
-        }
-      }
-      // partner rows into local memory (Cs does not change during the round): all
-      // of a thread's remote loads issued before any local store
-      {
-        constexpr int PER = R * T / JC_NT;
-        float2 tmp[PER];
+      // (2) the 2 x 2 blocks (pair rows x column pair q) of the CTA's pairs, written
+      // to the slots of the rows' next positions
+      const RotF Jq = rot[q];
+      const int ca = rr_elem(q, r, T), cb = rr_elem(T - 1 - q, r, T);
+      const float2 uq = cscale(make_float2(Jq.px, Jq.py), Jq.s);  // u_q s (REFINE), ph_q s
 #pragma unroll
-        for (int it = 0; it < PER; ++it) {
-          const int e = tid + it * JC_NT, li = e / T, c = e % T;
-          const int j = elem_at[T - 1 - pos_of[row0 + li]];
-          tmp[it] = cl.map_shared_rank(Cs, j / R)[(j % R) * T + c];
+      for (int l = tid / NP; l < PPC; l += JC_NT / NP) {
+        const int p = rank * PPC + l;
+        const RotF Jp = rot[p];
+        const float2* lo = Cs + l * T;
+        const float2* hi = Cs + (R - 1 - l) * T;
+        const float2 b00 = lo[ca], b01 = lo[cb], b10 = hi[ca], b11 = hi[cb];
+        float2 c00, c01, c10, c11;
+        if (REFINE) {
+          // right by J_q = [[c, -s u], [s conj(u), c]], then left by J_p^H
+          const float2 cuq = make_float2(uq.x, -uq.y);
+          const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, cuq)), m01 = csub(cscale(b01, Jq.c), cmul(b00, uq));
+          const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, cuq)), m11 = csub(cscale(b11, Jq.c), cmul(b10, uq));
+          const float2 up = cscale(make_float2(Jp.px, Jp.py), Jp.s), cup = make_float2(up.x, -up.y);
+          c00 = cadd(cscale(m00, Jp.c), cmul(up, m10));
+          c01 = cadd(cscale(m01, Jp.c), cmul(up, m11));
+          c10 = csub(cscale(m10, Jp.c), cmul(cup, m00));
+          c11 = csub(cscale(m11, Jp.c), cmul(cup, m01));
+        } else {
+          // right by J_q = [[c, -s], [conj(ph) s, conj(ph) c]], then left by J_p^H
+          const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+          const float2 m00 = cadd(cscale(b00, Jq.c), cmul(b01, q10)), m01 = cadd(cscale(b00, -Jq.s), cmul(b01, q11));
+          const float2 m10 = cadd(cscale(b10, Jq.c), cmul(b11, q10)), m11 = cadd(cscale(b10, -Jq.s), cmul(b11, q11));
+          const float2 p01 = make_float2(Jp.px * Jp.s, Jp.py * Jp.s), p11 = make_float2(Jp.px * Jp.c, Jp.py * Jp.c);
+          c00 = cadd(cscale(m00, Jp.c), cmul(p01, m10));
+          c01 = cadd(cscale(m01, Jp.c), cmul(p01, m11));
+          c10 = cadd(cscale(m00, -Jp.s), cmul(p11, m10));
+          c11 = cadd(cscale(m01, -Jp.s), cmul(p11, m11));
         }
-#pragma unroll
-        for (int it = 0; it < PER; ++it) Pr[tid + it * JC_NT] = tmp[it];
+        if (q == p) {  // the pair's own block: exactly diagonal, real diagonal
+          c01 = make_float2(0.f, 0.f);
+          c10 = make_float2(0.f, 0.f);
+          c00.y = 0.f;
+          c11.y = 0.f;
+        }
+        // next positions of the pair's rows
+        const int klo = p, khi = T - 1 - p;
+        const int nlo = klo == 0 ? 0 : (klo == 1 ? T - 1 : klo - 1), nhi = khi - 1;
+        int cta, slot;
+        jc_place(nlo, T, PPC, cta, slot);
+        float2* dlo = (cta == rank ? Cd : cl.map_shared_rank(Cd, cta)) + slot * T;
+        jc_place(nhi, T, PPC, cta, slot);
+        float2* dhi = (cta == rank ? Cd : cl.map_shared_rank(Cd, cta)) + slot * T;
+        dlo[ca] = c00;
+        dlo[cb] = c01;
+        dhi[ca] = c10;
+        dhi[cb] = c11;
       }
-      cl.sync();
-      // (2) new rows: left rotation with the partner row, then the column pairs
-      for (int e = tid; e < R * NP; e += JC_NT) {
-        const int li = e / NP, q = e % NP;
-        const int i = row0 + li, k = pos_of[i];
-        const int p = k < NP ? k : T - 1 - k;
-        const RotF Jp = rot[p], Jq = rot[q];
-        const int ca = elem_at[q], cb = elem_at[T - 1 - q];
-        // Jp^H = [[c, ph s], [-s, ph c]] on (first, second) rows
-        const float2 ph = make_float2(Jp.px, Jp.py);
-        const float2 ia = Cs[li * T + ca], ib = Cs[li * T + cb], ja = Pr[li * T + ca], jb = Pr[li * T + cb];
-        float2 xa, xb;
-        if (k < NP) {  // i first
-          xa = cadd(cscale(ia, Jp.c), cmul(cscale(ph, Jp.s), ja));
-          xb = cadd(cscale(ib, Jp.c), cmul(cscale(ph, Jp.s), jb));
-        } else {       // i second
-          xa = cadd(cscale(ja, -Jp.s), cmul(cscale(ph, Jp.c), ia));
-          xb = cadd(cscale(jb, -Jp.s), cmul(cscale(ph, Jp.c), ib));
-        }
-        // right: (xa, xb) <- (xa c + xb conj(ph_q) s, -xa s + xb conj(ph_q) c)
-        const float2 qph = make_float2(Jq.px, -Jq.py);
-        float2 ya = cadd(cscale(xa, Jq.c), cmul(xb, cscale(qph, Jq.s)));
-        float2 yb = cadd(cscale(xa, -Jq.s), cmul(xb, cscale(qph, Jq.c)));
-        if (q == p && Jp.s != 0.f) {  // the pair's own block: exactly diagonal, real diagonal
-          if (i == ca) {
-            ya.y = 0.f;
-            yb = make_float2(0.f, 0.f);
-          } else {
-            yb.y = 0.f;
-            ya = make_float2(0.f, 0.f);
-          }
-        }
-        Cd[li * T + ca] = ya;
-        Cd[li * T + cb] = yb;
-        if (Jq.s != 0.f) {  // Vf rows: right rotation of the column pair q, in place
+      // the CTA's rows of V (or D): right rotation of the column pair q
+      if (Jq.s != 0.f) {
+        const float2 cuq = make_float2(uq.x, -uq.y);
+        const float2 q10 = make_float2(Jq.px * Jq.s, -Jq.py * Jq.s), q11 = make_float2(Jq.px * Jq.c, -Jq.py * Jq.c);
+#pragma unroll
+        for (int li = tid / NP; li < R; li += JC_NT / NP) {
           const float2 va = Vr[li * T + ca], vb = Vr[li * T + cb];
-          Vr[li * T + ca] = cadd(cscale(va, Jq.c), cmul(vb, cscale(qph, Jq.s)));
-          Vr[li * T + cb] = cadd(cscale(va, -Jq.s), cmul(vb, cscale(qph, Jq.c)));
+          if (REFINE) {  // D <- D J + (J - I)
+            float2 na = cadd(cscale(va, Jq.c), cmul(vb, cuq));
+            float2 nb = csub(cscale(vb, Jq.c), cmul(va, uq));
+            const int i = row0 + li;
+            if (i == ca || i == cb) {
+              const float cm1 = -Jq.s * Jq.s / (1.f + Jq.c);
+              if (i == ca) {
+                na.x += cm1;
+                nb = csub(nb, uq);
+              } else {
+                na = cadd(na, cuq);
+                nb.x += cm1;
+              }
+            }
+            Vr[li * T + ca] = na;
+            Vr[li * T + cb] = nb;
+          } else {
+            Vr[li * T + ca] = cadd(cscale(va, Jq.c), cmul(vb, q10));
+            Vr[li * T + cb] = cadd(cscale(va, -Jq.s), cmul(vb, q11));
+          }
         }
       }
       if (tid < 32)  // the table is the same in every CTA
@@ -586,6 +670,7 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
           nrot += rot[p].s != 0.f;
           offmax = fmaxf(offmax, gabs[p]);
         }
+      // (3) every CTA's new rows written (some into a neighbour), its reads of this round done
       cl.sync();
       cur ^= 1;
     }
@@ -602,20 +687,26 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
       }
     }
     __syncthreads();
-    const bool done = s_nrot == 0 || s_offmax <= 1e-6f * trace;
+    const bool done = s_nrot == 0 || (REFINE ? (a.stop_rel > 0.0 && double(s_offmax) <= a.stop_rel * trace)
+                                             : s_offmax <= 1e-6f * float(trace));
     __syncthreads();  // s_nrot / s_offmax read by every thread before the next sweep writes them
-    if (done) break;  // the float64 phase takes it from 1e-6 of the trace
+    if (done) break;  // float32 phase: the refinement takes it from 1e-6 of the trace
   }
-  for (int e = tid; e < R * T; e += JC_NT) a.Vf[size_t(row0) * T + e] = Vr[e];
-  if (rank == 0 && tid == 0) atomicAdd(&a.counters[1], unsigned(sweeps));  // float32 sweeps
+  if (REFINE) {
+    for (int e = tid; e < R * T; e += JC_NT) a.Cf[size_t(row0) * T + e] = Vr[e];  // D
+    if (rank == 0)  // the Rayleigh numerators (V^H C V)_ii, unscaled, for the selection
+      for (int i = tid; i < T; i += JC_NT) a.C[size_t(i) * T + i] = make_double2(d[i] / scale, 0.0);
+  } else {
+    for (int e = tid; e < R * T; e += JC_NT) a.Vf[size_t(row0) * T + e] = Vr[e];
+  }
+  if (rank == 0 && tid == 0) atomicAdd(&a.counters[REFINE ? 2 : 1], unsigned(sweeps));
 }
 
-template <int T>
+template <int T, bool REFINE>
 static cudaError_t launch_jacobi_cluster(const PcaArgs& a, cudaStream_t s, bool* ok) {
   *ok = false;
-  constexpr int R = T / JC;
-  const size_t smem = size_t(4) * R * T * sizeof(float2) + size_t(T / 2) * sizeof(RotF);
-  auto kern = k_jacobi_cluster<T>;
+  const size_t smem = JclSmem<T, REFINE>::bytes();
+  auto kern = k_jacobi_cluster<T, REFINE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) {
@@ -676,6 +767,26 @@ __global__ void __launch_bounds__(256) k_gemm_c64(int T, const double2* A, const
     __syncthreads();
   }
   out[size_t(r) * T + c] = acc;
+}
+
+// V = Vf + Vf D in float64 (D in a.Cf, the refinement's correction): the product
+// in float32 (its entries ~1e-6 of V's, so float32 leaves ~1e-13), added to Vf
+// exactly in float64. 16 x 16 output tiles, 16-wide k stages in shared memory.
+__global__ void __launch_bounds__(256) k_vcorr(PcaArgs a) {
+  __shared__ float2 As[16][17], Bs[16][17];
+  const int T = a.T, tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < T; k0 += 16) {
+    As[ty][tx] = a.Vf[size_t(r) * T + k0 + tx];
+    Bs[ty][tx] = a.Cf[size_t(k0 + ty) * T + c];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = cadd(acc, cmul(As[ty][k], Bs[k][tx]));
+    __syncthreads();
+  }
+  const float2 v = a.Vf[size_t(r) * T + c];
+  a.V[size_t(r) * T + c] = make_double2(double(v.x) + double(acc.x), double(v.y) + double(acc.y));
 }
 
 // Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
@@ -1199,8 +1310,8 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     // (1) float32 sweeps: on one 16-CTA cluster (T = 128, 256), else cooperative on a
     // quarter of the SMs
     bool on_cluster = false;
-    if (a.T == 256) e = launch_jacobi_cluster<256>(a, s, &on_cluster);
-    else if (a.T == 128) e = launch_jacobi_cluster<128>(a, s, &on_cluster);
+    if (a.T == 256) e = launch_jacobi_cluster<256, false>(a, s, &on_cluster);
+    else if (a.T == 128) e = launch_jacobi_cluster<128, false>(a, s, &on_cluster);
     if (e != cudaSuccess) return e;
     if (!on_cluster) {
       const int nf = nsm / 4 > 0 ? nsm / 4 : 1;
@@ -1211,20 +1322,32 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     const dim3 gg(a.T / 16, a.T / 16);
     k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), a.C, nullptr, 0, nullptr, a.Vf, a.C2);     // M = C Vf
     k_gemm_c64<<<gg, 256, 0, s>>>(int(a.T), nullptr, a.Vf, 1, a.C2, nullptr, a.C);     // C' = Vf^H M
-    k_vf_to_v<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+    *launches += 3;
     // (3) float64 sweeps on C' (off-diagonals ~1e-6 of the trace): at most two, fewer
     // when every entry met in a sweep is below 1e-12 of the trace. Two leave the
     // energy image within ~2e-5 of the float64 reference and the eigenvalues within
     // ~3e-8 of the largest (a third and fourth sweep halve the first figure only;
-    // the covariance itself carries float32 accumulation error)
+    // the covariance itself carries float32 accumulation error). On the cluster when
+    // the float32 phase ran there, else cooperative over all SMs (V = Vf first).
     PcaArgs b = a;
     b.max_sweeps = 2;
     b.stop_rel = 1e-12;
-    void* bargs[] = {&b};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_refine), dim3(nsm), dim3(256), bargs, 0, s);
+    bool ref_cluster = false;
+    if (on_cluster && a.T == 256) e = launch_jacobi_cluster<256, true>(b, s, &ref_cluster);
+    else if (on_cluster && a.T == 128) e = launch_jacobi_cluster<128, true>(b, s, &ref_cluster);
     if (e != cudaSuccess) return e;
+    if (ref_cluster) {
+      k_vcorr<<<gg, 256, 0, s>>>(a);  // V = Vf (I + D)
+      *launches += 1;
+    } else {
+      k_vf_to_v<<<(a.T * a.T + 255) / 256, 256, 0, s>>>(a);
+      void* bargs[] = {&b};
+      e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi_refine), dim3(nsm), dim3(256), bargs, 0, s);
+      if (e != cudaSuccess) return e;
+      *launches += 1;
+    }
     k_pca_select<<<1, 256, 0, s>>>(a);
-    *launches += 5;
+    *launches += 2;
   }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
