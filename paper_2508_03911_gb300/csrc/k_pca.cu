@@ -265,6 +265,28 @@ __device__ __forceinline__ bool refine_rot(double* d, int i, int j, float2 g, fl
   return true;
 }
 
+// The rotation of refine_rot for the cluster's refinement, whose rotations are
+// applied in float32 (the float64 refinement of c and ph would be rounded away):
+// the angle and the factors in float32 (approximate reciprocals, a few ulp), the
+// diagonal moved by t |g| in float64.
+__device__ __forceinline__ void refine_rot_f(double* d, int i, int j, float2 g, float ag, float tol,
+                                             float floor_abs, RotF& q) {
+  q = RotF{1.f, 0.f, 1.f, 0.f};
+  const double al = d[i], be = d[j];
+  if (!(ag > tol * sqrtf(fabsf(float(al))) * sqrtf(fabsf(float(be))) && ag > floor_abs && ag > 0.f)) return;
+  const float rg = __fdividef(1.f, ag);
+  const float zeta = float(be - al) * (0.5f * rg);
+  const float az = fabsf(zeta);
+  const float den = az > 1e18f ? 2.f * az : az + sqrtf(fmaf(az, az, 1.f));
+  const float t = __fdividef(zeta >= 0.f ? -1.f : 1.f, den);
+  if (t == 0.f) return;
+  const float c = rsqrtf(fmaf(t, t, 1.f));
+  const double tg = double(t * ag);
+  d[i] = al + tg;
+  d[j] = be - tg;
+  q = RotF{c, t * c, g.x * rg, g.y * rg};
+}
+
 // Refinement of the long-window eigensolver (T >= 128), cooperative over all SMs
 // with one grid barrier per round, on C' = Vf^H C Vf: the diagonal in float64 (a
 // copy in every CTA's shared memory, updated identically by every CTA), the
@@ -552,19 +574,39 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
   const float tol = REFINE ? float(a.tol) : 1e-6f;
   const float floor_abs = REFINE ? float(a.tol_abs * cmax) : 2e-7f * float(trace);
   const int max_sweeps = REFINE ? a.max_sweeps : 20;
-  // a thread's column pair q is the same in every round (the items are strided by JC_NT)
-  static_assert(JC_NT % NP == 0, "column pair per thread");
-  const int q = tid % NP;
+  // a thread's column pair q is the same in every round, and so is its pair row l
+  // (at most one: JC_NT >= PPC NP) with the slots of the pair rows' next positions
+  constexpr int NB = (PPC * NP + JC_NT - 1) / JC_NT;  // pair blocks per thread: pair rows l0 + k JC_NT / NP
+  static_assert(JC_NT % NP == 0 && NB <= 2, "pair blocks per thread");
+  const int q = tid % NP, l0 = tid / NP;
+  float2* nlo[NB];  // buffer 0 of the slot of the next position of each pair row
+  float2* nhi[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int l = l0 + k * (JC_NT / NP);
+    nlo[k] = nhi[k] = nullptr;
+    if (l >= PPC) continue;
+    const int p = rank * PPC + l, klo = p, khi = T - 1 - p;
+    int cta, slot;
+    jc_place(klo == 0 ? 0 : (klo == 1 ? T - 1 : klo - 1), T, PPC, cta, slot);
+    nlo[k] = (cta == rank ? C0 : cl.map_shared_rank(C0, cta)) + slot * T;
+    jc_place(khi - 1, T, PPC, cta, slot);
+    nhi[k] = (cta == rank ? C0 : cl.map_shared_rank(C0, cta)) + slot * T;
+  }
+  // indices of the thread's pair (rotation phase) and column pair in round 0; from one
+  // round to the next each moves to the following index of 1 .. T-1 (0 stays)
+  auto next_idx = [](int x) { return x == 0 ? 0 : (x == T - 1 ? 1 : x + 1); };
+  int ri = tid < NP ? rr_elem(tid, 0, T) : 0, rj = tid < NP ? rr_elem(T - 1 - tid, 0, T) : 0;
+  int ca = rr_elem(q, 0, T), cb = rr_elem(T - 1 - q, 0, T);
   int sweeps = 0, cur = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     unsigned nrot = 0;  // warp 0's running totals of the sweep
     float offmax = 0.f;
     for (int r = 0; r < T - 1; ++r) {
       const float2* Cs = C0 + cur * R * T;
-      float2* Cd = C0 + (cur ^ 1) * R * T;
       // (1) every pair's rotation, from its owner's rows
       if (tid < NP) {
-        const int p = tid, i = rr_elem(p, r, T), j = rr_elem(T - 1 - p, r, T);
+        const int p = tid, i = ri, j = rj;
         const float2* own = cl.map_shared_rank(Cs, p / PPC);
         const float2* lo = own + (p % PPC) * T;
         const float2 g = lo[j];
@@ -575,8 +617,7 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
         }
         const float ag = sqrtf(g.x * g.x + g.y * g.y);
         if (REFINE) {
-          RotV unused;
-          refine_rot(d, i, j, g, ag, tol, floor_abs, rot[p], unused);
+          refine_rot_f(d, i, j, g, ag, tol, floor_abs, rot[p]);
         } else {
           jacobi_rot_f(ci, cj, g, tol, floor_abs, rot[p]);
         }
@@ -586,11 +627,11 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
       // (2) the 2 x 2 blocks (pair rows x column pair q) of the CTA's pairs, written
       // to the slots of the rows' next positions
       const RotF Jq = rot[q];
-      const int ca = rr_elem(q, r, T), cb = rr_elem(T - 1 - q, r, T);
       const float2 uq = cscale(make_float2(Jq.px, Jq.py), Jq.s);  // u_q s (REFINE), ph_q s
 #pragma unroll
-      for (int l = tid / NP; l < PPC; l += JC_NT / NP) {
-        const int p = rank * PPC + l;
+      for (int k = 0; k < NB; ++k) {
+        const int l = l0 + k * (JC_NT / NP), p = rank * PPC + l;
+        if (l >= PPC) continue;
         const RotF Jp = rot[p];
         const float2* lo = Cs + l * T;
         const float2* hi = Cs + (R - 1 - l) * T;
@@ -623,19 +664,18 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
           c00.y = 0.f;
           c11.y = 0.f;
         }
-        // next positions of the pair's rows
-        const int klo = p, khi = T - 1 - p;
-        const int nlo = klo == 0 ? 0 : (klo == 1 ? T - 1 : klo - 1), nhi = khi - 1;
-        int cta, slot;
-        jc_place(nlo, T, PPC, cta, slot);
-        float2* dlo = (cta == rank ? Cd : cl.map_shared_rank(Cd, cta)) + slot * T;
-        jc_place(nhi, T, PPC, cta, slot);
-        float2* dhi = (cta == rank ? Cd : cl.map_shared_rank(Cd, cta)) + slot * T;
+        // into the slots of the rows' next positions, buffer cur ^ 1
+        float2* dlo = nlo[k] + (cur ^ 1) * R * T;
+        float2* dhi = nhi[k] + (cur ^ 1) * R * T;
         dlo[ca] = c00;
         dlo[cb] = c01;
         dhi[ca] = c10;
         dhi[cb] = c11;
       }
+      // (3) this CTA's new rows are written (some into a neighbour) and its reads of the
+      // round done: arrive on the cluster barrier, rotate the local rows of V while
+      // the others finish, then wait
+      asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
       // the CTA's rows of V (or D): right rotation of the column pair q
       if (Jq.s != 0.f) {
         const float2 cuq = make_float2(uq.x, -uq.y);
@@ -670,9 +710,12 @@ __global__ void __launch_bounds__(JC_NT) k_jacobi_cluster(PcaArgs a) {
           nrot += rot[p].s != 0.f;
           offmax = fmaxf(offmax, gabs[p]);
         }
-      // (3) every CTA's new rows written (some into a neighbour), its reads of this round done
-      cl.sync();
+      asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
       cur ^= 1;
+      ri = next_idx(ri);
+      rj = next_idx(rj);
+      ca = next_idx(ca);
+      cb = next_idx(cb);
     }
     sweeps = sweep + 1;
     if (tid < 32) {
