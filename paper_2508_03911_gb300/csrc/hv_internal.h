@@ -133,7 +133,8 @@ struct PcaArgs {
   float2* Cf2;
   float2* Vf;
   double2* V;           // T x T (large-T path)
-  double* rot;          // T/2 rotations (4 doubles each)
+  double* rot;          // T/2 rotations (4 doubles each); after the eigensolver, the
+                        // Rayleigh quotients and inverse norms of the columns of V
   unsigned* counters;   // 4 counters followed by one double (largest diagonal)
   double* cmax;         // = (double*)(counters + 4)
   double* lam;          // nwin x T eigenvalues, descending

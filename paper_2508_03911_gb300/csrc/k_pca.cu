@@ -832,19 +832,32 @@ __global__ void __launch_bounds__(256) k_vcorr(PcaArgs a) {
   a.V[size_t(r) * T + c] = make_double2(double(v.x) + double(acc.x), double(v.y) + double(acc.y));
 }
 
-// Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
-// sub-basis columns lo..hi of V as float32.
-// The eigenvalues are Rayleigh quotients diag(V^H C V)_i / |v_i|^2 (the columns of
-// V are unitary only to the float32 phase's accuracy), the vectors normalised.
-__global__ void k_pca_select(PcaArgs a) {
-  const int T = a.T;
-  __shared__ double lamv[512], inrm[512];
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double n2 = 0.0;
-    for (int t = 0; t < T; ++t) n2 += a.V[t * T + i].x * a.V[t * T + i].x + a.V[t * T + i].y * a.V[t * T + i].y;
-    lamv[i] = a.C[i * T + i].x / n2;
-    inrm[i] = 1.0 / sqrt(n2);
+// Rayleigh quotient and inverse norm of every column of V (the columns are unitary
+// only to the float32 phase's accuracy): lam_i = (V^H C V)_ii / |v_i|^2 with the
+// numerators on the diagonal of a.C, into scratch [lam_0 .. lam_T-1, 1/|v_0| ..].
+// 16 columns per CTA, 16 threads per column, float64 sums.
+__global__ void __launch_bounds__(256) k_pca_norms(PcaArgs a, double* scratch) {
+  const int T = a.T, i = blockIdx.x * 16 + threadIdx.x / 16, part = threadIdx.x % 16;
+  double n2 = 0.0;
+  for (int t = part; t < T; t += 16) {
+    const double2 v = a.V[size_t(t) * T + i];
+    n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
   }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  if (part == 0) {
+    scratch[i] = a.C[size_t(i) * T + i].x / n2;
+    scratch[T + i] = 1.0 / sqrt(n2);
+  }
+}
+
+// Ranks the eigenvalues (descending, ties by index), writes lam sorted and the
+// sub-basis columns lo..hi of V, normalised, as float32 (zero padding to Mpad).
+__global__ void __launch_bounds__(1024) k_pca_select(PcaArgs a, const double* scratch) {
+  const int T = a.T;
+  __shared__ double lamv[512];
+  __shared__ int col_of[512];  // column of V of each rank
+  for (int i = threadIdx.x; i < T; i += blockDim.x) lamv[i] = scratch[i];
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     const double li = lamv[i];
@@ -854,15 +867,21 @@ __global__ void k_pca_select(PcaArgs a) {
       rank += (lj > li) || (lj == li && j < i);
     }
     a.lam[rank] = li;
-    const int m = rank - int(a.lo - 1);
-    if (m >= 0 && m < int(a.M))
-      for (int t = 0; t < T; ++t) {
-        const double2 v = a.V[t * T + i];
-        a.Vs[size_t(t) * a.Mpad + m] = make_float2(float(v.x * inrm[i]), float(v.y * inrm[i]));
-      }
+    col_of[rank] = i;
   }
-  for (int e = threadIdx.x; e < T * int(a.Mpad); e += blockDim.x)
-    if (e % int(a.Mpad) >= int(a.M)) a.Vs[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int Mp = int(a.Mpad), lo = int(a.lo) - 1;
+  for (int e = threadIdx.x; e < T * Mp; e += blockDim.x) {
+    const int t = e / Mp, m = e % Mp;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < int(a.M)) {
+      const int i = col_of[lo + m];
+      const double2 x = a.V[size_t(t) * T + i];
+      const double r = scratch[T + i];
+      v = make_float2(float(x.x * r), float(x.y * r));
+    }
+    a.Vs[e] = v;
+  }
 }
 
 // One sweep's rounds of the CTA-local cyclic Jacobi on C (T x T) and V. The
@@ -1389,8 +1408,11 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
       if (e != cudaSuccess) return e;
       *launches += 1;
     }
-    k_pca_select<<<1, 256, 0, s>>>(a);
-    *launches += 2;
+    // the cooperative paths' rotation table is free by now: lam and 1/|v| of every column
+    double* scratch = a.rot;
+    k_pca_norms<<<a.T / 16, 256, 0, s>>>(a, scratch);
+    k_pca_select<<<1, 1024, 0, s>>>(a, scratch);
+    *launches += 3;
   }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
