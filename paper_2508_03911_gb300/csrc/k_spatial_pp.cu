@@ -89,6 +89,32 @@ struct RawSrc {
   }
 };
 
+// Two real raw columns as one complex line: line b of the strip is columns 2b
+// (real part) and 2b + 1 (imaginary part); 32 columns staged, rows 32 pixels apart.
+template <bool U8>
+struct PackedRawSrc {
+  static constexpr bool kAliasesBuf = true;  // staged inside the FFT buffer: read all before writing
+  const unsigned char* raw;
+  __device__ __forceinline__ float2 operator()(int t, int b) const {
+    if constexpr (U8) {
+      const uint16_t p = reinterpret_cast<const uint16_t*>(raw)[t * 16 + b];
+      return make_float2(float(p & 0xffu), float(p >> 8));
+    } else {
+      const uint32_t p = reinterpret_cast<const uint32_t*>(raw)[t * 16 + b];
+      return make_float2(float(p & 0xffffu), float(p >> 16));
+    }
+  }
+};
+
+// Bin k of line b to the buffer at buf[k * LD + b] (after every read of it).
+template <int LD>
+struct SmemOut {
+  static constexpr bool kSyncFirst = true;
+  static constexpr bool kJFast = false;
+  float2* buf;
+  __device__ __forceinline__ void operator()(int b, int k, float2 v) const { buf[k * LD + b] = v; }
+};
+
 // Bin k of line b straight to global memory at out[k * stride + b].
 struct GlobalOut {
   static constexpr bool kSyncFirst = false;
@@ -851,12 +877,17 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 // above each run as a launch of their own over a chunk of frames, so their
 // intermediates (S1, S2: 512 KB per frame) go through HBM once written and once
 // read. Here work items come in a fixed global order from an atomic ticket
-// counter: row r of the order holds the 16 strips of pass 1 of frame r, of pass
-// 2 of frame r - LAG and (ASP) of pass 3 of frame r - 2 LAG. S1 and S2 are rings
-// of RING frames that stay in L2. An item may start once the counters that make
-// its input complete and its output slot free have been published:
+// counter: row r of the order holds the column items of pass 1 of frame r, the 16
+// strips of pass 2 of frame r - LAG and (ASP) of pass 3 of frame r - 2 LAG. A
+// Fresnel column item transforms 16 columns (the chirped input is complex); an
+// ASP one 32 real columns, packed in pairs as the real and imaginary parts of 16
+// complex lines whose spectra Z are separated after the transform (for real a and
+// b, z = a + i b: A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / 2i),
+// so that a frame takes 8 column items instead of 16. S1 and S2 are rings of RING
+// frames that stay in L2. An item may start once the counters that make its input
+// complete and its output slot free have been published:
 //   pass 1 of f: the 16 row-pass items of f - RING have read S1 slot f mod RING
-//   pass 2 of f: the 16 column items of f wrote S1 slot; (ASP) the 16 column-IFFT
+//   pass 2 of f: the column items of f wrote S1 slot; (ASP) the 16 column-IFFT
 //                items of f - RING have read S2 slot
 //   pass 3 of f: the 16 row-pass items of f wrote S2 slot
 // A CTA is warp-specialised: one producer thread takes the tickets, waits (bounded
@@ -884,7 +915,7 @@ constexpr int FZ_LAG = 48;
 constexpr int FZ_BAR = 1;        // named barrier of the consumer warps
 constexpr size_t FZ_FRAME = size_t(RW_L) * RW_L;  // complex values per frame
 constexpr size_t FZ_BUF = size_t(256) * 16;       // complex values per buffer
-constexpr size_t FZ_RAW = 256 * 32;               // bytes of a raw strip (uint16), in the buffer's tail
+constexpr size_t FZ_RAW = 256 * 64;               // bytes of a raw strip (32 uint16 columns), in the buffer's tail
 // every wait is on a smaller ticket when the rings are longer than the lag; the
 // headroom above it keeps column items from waiting for a slot to be freed
 static_assert(kFusedRing > FZ_LAG, "the rings must outlast the lag between passes");
@@ -943,7 +974,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool asp = a.spatial == HV_SPATIAL_ASP;
   const bool u8 = a.in_kind == IN_U8;
-  const uint32_t npass = asp ? 3u : 2u, ipr = 16u * npass, R = a.ring;
+  // column items per frame (32 packed columns each for ASP, else 16), items per ticket row
+  const uint32_t n0 = asp ? 8u : 16u, npass = asp ? 3u : 2u, ipr = n0 + 16u * (npass - 1), R = a.ring;
   for (int e = tid; e < 256; e += FZ_THREADS) {
     tws[e] = __ldg(&a.tw_h[e]);
     cys[e] = asp ? make_float2(1.f, 0.f) : __ldg(&a.chirp_y[e]);
@@ -1002,8 +1034,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
         const uint32_t t = atomicAdd(a.fused_ctr, 1u);
         if (t >= nticket) return false;
         const uint32_t row = t / ipr, kk = t % ipr;
-        pass = kk / 16u;
-        strip = kk % 16u;
+        pass = kk < n0 ? 0u : 1u + (kk - n0) / 16u;
+        strip = kk < n0 ? kk : (kk - n0) % 16u;
         const long long fl = (long long)row - (long long)pass * FZ_LAG;
         if (fl >= 0 && fl < (long long)a.n) {
           f = uint32_t(fl);
@@ -1015,7 +1047,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
       while (true) {
         bool ready;
         if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 16u * gen;
-        else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 16u * (gen + 1) &&
+        else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= n0 * (gen + 1) &&
                                     (!asp || ld_acquire_u32(&done[2 * R + slot]) >= 16u * gen);
         else ready = ld_acquire_u32(&done[R + slot]) >= 16u * (gen + 1);
         drain(issued, false);
@@ -1046,11 +1078,11 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
       // (contiguous) by a 1-D bulk copy. The rings were written by other CTAs'
       // generic stores, fenced for the async proxy before their publication; this
       // thread acquired the counters that published them.
-      const uint32_t s0 = it.strip * 16u, slot = it.frame % R;
+      const uint32_t s0 = it.strip * (it.pass == 0 && asp ? 32u : 16u), slot = it.frame % R;
       desc[b] = it;
       const uint32_t fb = rw_smem(&full[b]);
       if (it.pass == 0) {
-        const uint32_t bytes = 256u * 16u * (u8 ? 1u : 2u);
+        const uint32_t bytes = 256u * (asp ? 32u : 16u) * (u8 ? 1u : 2u);
         const uint32_t rslot = uint32_t((a.raw.slot0 + it.frame) % a.raw.cap);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
         asm volatile(
@@ -1106,21 +1138,35 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
     }
     const FzItem it = desc[b];
     if (it.pass == FZ_STOP) break;
-    const uint32_t pass = it.pass, f = it.frame, s0 = it.strip * 16u, slot = f % R;
+    const uint32_t pass = it.pass, f = it.frame, s0 = it.strip * (pass == 0 && asp ? 32u : 16u), slot = f % R;
     float2* buf = bufs + b * FZ_BUF;
     float2* s1 = a.scratch1 + size_t(slot) * FZ_FRAME;
     float2* s2 = a.scratch2 + size_t(slot) * FZ_FRAME;
     const size_t tslot = (a.tq.slot0 + f) % a.tq.cap;
     if (pass == 0) {
-      // column FFT of 16 raw columns (conversion and chirp in the first stage) -> S1 [ky][x]
       const unsigned char* raw = raw_of(b);
       const GlobalOut out{s1 + s0, 256u};
       if (asp) {
-        if (u8) pp_stages<256, 1, -1, RawSrc<true, false, 16, true>, GlobalOut, 16, FZ_BAR>(
-                    RawSrc<true, false, 16, true>{raw, cys, make_float2(0.f, 0.f)}, buf, tws, out);
-        else pp_stages<256, 1, -1, RawSrc<false, false, 16, true>, GlobalOut, 16, FZ_BAR>(
-                 RawSrc<false, false, 16, true>{raw, cys, make_float2(0.f, 0.f)}, buf, tws, out);
+        // column FFT of 32 real raw columns, packed in pairs (conversion in the first
+        // stage), spectra Z of the 16 lines into the buffer [k][line]; then for bins
+        // k <= 128 the two columns' spectra A, B at k and (conjugate) at -k -> S1 [ky][x]
+        if (u8) pp_stages<256, 1, -1, PackedRawSrc<true>, SmemOut<16>, 16, FZ_BAR>(PackedRawSrc<true>{raw}, buf,
+                                                                                    tws, SmemOut<16>{buf});
+        else pp_stages<256, 1, -1, PackedRawSrc<false>, SmemOut<16>, 16, FZ_BAR>(PackedRawSrc<false>{raw}, buf,
+                                                                                  tws, SmemOut<16>{buf});
+        pp_sync<FZ_BAR, FZ_NT>();
+        const int line = tid % 16;
+        float4* o = reinterpret_cast<float4*>(s1 + s0 + 2 * line);  // columns 2 line, 2 line + 1
+#pragma unroll 3
+        for (int k = tid / 16; k <= 128; k += FZ_NT / 16) {
+          const float2 z = buf[k * 16 + line], w = buf[((256 - k) & 255) * 16 + line];  // Z(k), Z(-k)
+          const float ax = 0.5f * (z.x + w.x), ay = 0.5f * (z.y - w.y);  // A(k) = (Z + conj W) / 2
+          const float bx = 0.5f * (z.y + w.y), by = 0.5f * (w.x - z.x);  // B(k) = (Z - conj W) / 2i
+          o[size_t(k) * 128] = make_float4(ax, ay, bx, by);
+          if (k != 0 && k != 128) o[size_t(256 - k) * 128] = make_float4(ax, -ay, bx, -by);  // X(-k) = conj X(k)
+        }
       } else {
+        // column FFT of 16 raw columns (conversion and chirp in the first stage) -> S1 [ky][x]
         const float2 cx = __ldg(&a.chirp_x[s0 + (tid % 16)]);
         if (u8) pp_stages<256, 1, -1, RawSrc<true, true, 16, true>, GlobalOut, 16, FZ_BAR>(
                     RawSrc<true, true, 16, true>{raw, cys, cx}, buf, tws, out);
@@ -1236,18 +1282,20 @@ cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* laun
   if (a.n == 0) return cudaSuccess;
   if (!spatial_fused_supported(a)) return cudaErrorInvalidValue;
   const uint32_t npass = a.spatial == HV_SPATIAL_ASP ? 3u : 2u;
-  const uint64_t nt = (uint64_t(a.n) + uint64_t(npass - 1) * FZ_LAG) * 16u * npass;
+  const uint32_t ipr = (a.spatial == HV_SPATIAL_ASP ? 8u : 16u) + 16u * (npass - 1);  // items per ticket row
+  const uint64_t nt = (uint64_t(a.n) + uint64_t(npass - 1) * FZ_LAG) * ipr;
   if (nt >= (1ull << 31)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.fused_ctr, 0, (1 + 3 * size_t(a.ring)) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_spatial_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(FZ_SMEM));
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, nsm = 0;
-  // tensor maps: the raw ring (256 x cap 256 pixels, boxes of 16 x 256) and the S2 ring
-  // (256 x ring 256 complex, boxes of 16 x 256)
+  // tensor maps: the raw ring (256 x cap 256 pixels, boxes of 32 (ASP) or 16 x 256) and
+  // the S2 ring (256 x ring 256 complex, boxes of 16 x 256)
   CUtensorMap raw_map{}, s2_map{};
   const int bpp = a.in_kind == IN_U8 ? 1 : 2;
-  if (!encode_map_2d(&raw_map, a.raw.base, bpp, RW_L, uint64_t(a.raw.cap) * RW_L, uint64_t(RW_L) * bpp, 16, 256))
+  if (!encode_map_2d(&raw_map, a.raw.base, bpp, RW_L, uint64_t(a.raw.cap) * RW_L, uint64_t(RW_L) * bpp,
+                     a.spatial == HV_SPATIAL_ASP ? 32 : 16, 256))
     return cudaErrorNotSupported;
   if (a.spatial == HV_SPATIAL_ASP &&
       !encode_map_2d(&s2_map, a.scratch2, 8, RW_L, uint64_t(a.ring) * RW_L, uint64_t(RW_L) * 8, 16, 256))
