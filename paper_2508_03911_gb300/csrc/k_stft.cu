@@ -285,12 +285,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   }
 }
 
-// The moments of pixel `pix` for window w, from the lane group's reduced sums
-// (held by its lane jl = 0, the writer): M0, M1, M2 (bins -> kHz), then M1N and M2N
-// in float64, in that order among those the mask asks for, to out [w][image][pixel]
-// or, with post-processing fused, to the image ring slot of the window, adding
-// each image's sum over the warp's pixels into one of the slot's partial sums.
-// Called by every lane of the warp (the sums are reduced across it).
+// Post-processing fused into the moment epilogue: the moments of pixel `pix` for
+// window w, from the lane group's reduced sums (held by its lane jl = 0, the
+// writer) -- M0, M1, M2 (bins -> kHz), then M1N and M2N in float64, in that order
+// among those the mask asks for -- to the image ring slot of the window (or to
+// out [w][image][pixel] without a ring), adding each image's sum over the warp's
+// pixels into one of the slot's partial sums. Called by every lane of the warp
+// (the sums are reduced across it). The kernels take it in an instantiation of
+// their own (POST) and keep their plain epilogue otherwise: routing renders
+// without post-processing through this one measured 16 % slower for the walking
+// kernel, and even an untaken branch to it 4 %.
 __device__ __forceinline__ void emit_moments(const StftArgs& a, uint32_t w, size_t pix, const MomAcc& acc,
                                              bool writer, bool streaming) {
   const size_t HW = size_t(a.W) * a.H;
@@ -334,7 +338,7 @@ __device__ __forceinline__ void emit_moments(const StftArgs& a, uint32_t w, size
   }
 }
 
-template <int T>
+template <int T, bool POST>
 __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
     k_stft_warp(StftArgs a, const __grid_constant__ CUtensorMap qmap) {
   using Lw = WarpLayout<T>;
@@ -500,7 +504,22 @@ __global__ void __launch_bounds__(WarpLayout<T>::NT, (T <= 512 ? 3 : 1))
       acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
       acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
     }
-    emit_moments(a, w, p0 + px, acc, jl == 0, false);
+    if constexpr (POST) {
+      emit_moments(a, w, p0 + px, acc, jl == 0, false);
+    } else if (jl == 0) {
+      const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
+      float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
+      int q = 0;
+      if (a.mask & HV_MOM_M0) o[HW * q++] = acc.m0;
+      if (a.mask & HV_MOM_M1) o[HW * q++] = m1;
+      if (a.mask & HV_MOM_M2) o[HW * q++] = m2;
+      const double d0 = acc.m0;
+      if (a.mask & HV_MOM_M1N) o[HW * q++] = d0 > 0.0 ? float(double(m1) / d0) : 0.f;
+      if (a.mask & HV_MOM_M2N) {
+        const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
+        o[HW * q++] = float(sqrt(r > 0.0 ? r : 0.0));
+      }
+    }
   }
 }
 
@@ -529,7 +548,7 @@ struct WinCfg {
   static constexpr size_t bytes() { return (size_t(BT) * WR + (T - WarpPlan<T>::R1)) * sizeof(float2); }
 };
 
-template <int T, bool WIDE>
+template <int T, bool WIDE, bool POST>
 __global__ void __launch_bounds__(WinCfg<T, WIDE>::NT, WinCfg<T, WIDE>::OCC) k_stft_win(StftArgs a) {
   using Lw = WarpLayout<T>;
   using Wc = WinCfg<T, WIDE>;
@@ -596,7 +615,22 @@ __global__ void __launch_bounds__(WinCfg<T, WIDE>::NT, WinCfg<T, WIDE>::OCC) k_s
     acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
     acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
   }
-  emit_moments(a, w, p0 + px, acc, jl == 0, true);
+  if constexpr (POST) {
+    emit_moments(a, w, p0 + px, acc, jl == 0, true);
+  } else if (jl == 0) {
+    const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
+    float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
+    int q = 0;
+    if (a.mask & HV_MOM_M0) __stcs(&o[HW * q++], acc.m0);
+    if (a.mask & HV_MOM_M1) __stcs(&o[HW * q++], m1);
+    if (a.mask & HV_MOM_M2) __stcs(&o[HW * q++], m2);
+    const double d0 = acc.m0;
+    if (a.mask & HV_MOM_M1N) __stcs(&o[HW * q++], d0 > 0.0 ? float(double(m1) / d0) : 0.f);
+    if (a.mask & HV_MOM_M2N) {
+      const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
+      __stcs(&o[HW * q++], float(sqrt(r > 0.0 ? r : 0.0)));
+    }
+  }
 }
 
 // cuTensorMapEncodeTiled from the driver (resolved once through the runtime)
@@ -670,11 +704,12 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
       using Wc = WinCfg<T, W>;
       if (hw % Wc::BT) return cudaErrorNotSupported;
       const size_t smem = Wc::bytes();
-      cudaError_t e = cudaFuncSetAttribute(k_stft_win<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      auto kern = a.post_ring ? k_stft_win<T, W, true> : k_stft_win<T, W, false>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e != cudaSuccess) return e;
       const uint64_t grid = uint64_t(a.nwin) * (hw / Wc::BT);
       if (grid >= (1ull << 31)) return cudaErrorInvalidValue;
-      k_stft_win<T, W><<<unsigned(grid), Wc::NT, smem, s>>>(a);
+      kern<<<unsigned(grid), Wc::NT, smem, s>>>(a);
       return cudaGetLastError();
     };
     const cudaError_t e = a.kernel == STFT_WIDE ? launch_win(std::true_type{}) : launch_win(std::false_type{});
@@ -683,10 +718,10 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
   CUtensorMap map{};
   a.tma = queue_map(a, Lw::BT, &map) ? 1 : 0;
   const size_t smem = WarpSmem<T>::bytes(a.S, a.tma != 0);
-  cudaError_t e = cudaFuncSetAttribute(k_stft_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem));
+  auto kern = a.post_ring ? k_stft_warp<T, true> : k_stft_warp<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  k_stft_warp<T><<<unsigned(hw / Lw::BT), Lw::NT, smem, s>>>(a, map);
+  kern<<<unsigned(hw / Lw::BT), Lw::NT, smem, s>>>(a, map);
   return cudaGetLastError();
 }
 
