@@ -44,7 +44,7 @@ typedef enum {
  * memory (page-locked for full speed) whose copy is only queued: the call
  * returns before it has run, as the paper's pipeline runs asynchronously to its
  * input and output streams (Sec. III). */
-enum { HV_MEM_HOST = 0, HV_MEM_DEVICE = 1, HV_MEM_HOST_ASYNC = 2 };
+enum { HV_MEM_HOST = 0, HV_MEM_DEVICE = 1, HV_MEM_HOST_ASYNC = 2, HV_MEM_DEVICE_ASYNC = 3 };
 
 /* Spatial demodulation (Sec. III-B.1; benchmarks Sec. VI-B). */
 enum { HV_SPATIAL_NONE = 0, HV_SPATIAL_ASP = 1, HV_SPATIAL_FRESNEL = 2 };
@@ -159,7 +159,12 @@ hv_status hv_get_params(const hv_handle* h, hv_params* p);
  * only queued (HV_MEM_HOST_ASYNC: on the handle's copy stream, after the ring
  * slots it overwrites have been consumed; the buffer must stay unchanged until
  * hv_synchronize returns or until an hv_render with HV_MEM_HOST output that
- * renders windows using these frames returns). Frames are uint8 or uint16
+ * renders windows using these frames returns), or a device pointer whose copy is
+ * queued the same way (HV_MEM_DEVICE_ASYNC: the frames must be completely written
+ * when the call is made, since the copy stream is not ordered after the handle's
+ * stream or any other; the copy then overlaps the rendering of earlier frames
+ * instead of following it; the same lifetime rule as HV_MEM_HOST_ASYNC; only
+ * hv_push_frames takes it). Frames are uint8 or uint16
  * by pixel_bits, row-major, frames contiguous. All-or-nothing: if the ring
  * cannot take all n frames, nothing is copied and HV_ERR_QUEUE_FULL is returned
  * (backpressure; frames are never dropped). */

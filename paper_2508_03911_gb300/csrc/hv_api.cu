@@ -1073,7 +1073,8 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
   if (!h) return HV_ERR_ARG;
   if (n == 0) return HV_OK;
   if (!frames) return fail(h, HV_ERR_ARG, "frames is NULL");
-  if (mem_kind != HV_MEM_HOST && mem_kind != HV_MEM_DEVICE && mem_kind != HV_MEM_HOST_ASYNC)
+  if (mem_kind != HV_MEM_HOST && mem_kind != HV_MEM_DEVICE && mem_kind != HV_MEM_HOST_ASYNC &&
+      mem_kind != HV_MEM_DEVICE_ASYNC)
     return fail(h, HV_ERR_ARG, "bad mem_kind");
   if (!h->has_params && !h->pending) return fail(h, HV_ERR_STATE, "hv_set_params must come first");
   const hv_params& p = h->pending ? h->pend : h->cur;
@@ -1092,8 +1093,9 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
     // copy stream: wait until the slots being overwritten have been consumed
     hv_status sw = wait_slots_free(h, n);
     if (sw != HV_OK) return sw;
-    HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, cudaMemcpyHostToDevice, h->copy_stream));
-    if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, cudaMemcpyHostToDevice, h->copy_stream));
+    const cudaMemcpyKind dir = mem_kind == HV_MEM_DEVICE_ASYNC ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HV_CU(h, cudaMemcpyAsync(ring + slot * fb, src, n1 * fb, dir, h->copy_stream));
+    if (n1 < n) HV_CU(h, cudaMemcpyAsync(ring, src + n1 * fb, (n - n1) * fb, dir, h->copy_stream));
     HV_CU(h, cudaEventRecord(h->ev_pushed, h->copy_stream));
     if (mem_kind == HV_MEM_HOST) HV_CU(h, cudaEventSynchronize(h->ev_pushed));  // host buffer consumed on return
     HV_CU(h, cudaStreamWaitEvent(h->stream, h->ev_pushed, 0));

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libhv.so")
 
 HV_OK, HV_ERR_ARG, HV_ERR_STATE, HV_ERR_QUEUE_FULL = 0, -1, -2, -3
 HV_ERR_NOMEM, HV_ERR_CUDA, HV_ERR_TIMEOUT, HV_ERR_UNSUPPORTED = -4, -5, -6, -7
-HV_MEM_HOST, HV_MEM_DEVICE, HV_MEM_HOST_ASYNC = 0, 1, 2
+HV_MEM_HOST, HV_MEM_DEVICE, HV_MEM_HOST_ASYNC, HV_MEM_DEVICE_ASYNC = 0, 1, 2, 3
 HV_SPATIAL_NONE, HV_SPATIAL_ASP, HV_SPATIAL_FRESNEL = 0, 1, 2
 HV_TEMPORAL_STFT, HV_TEMPORAL_PCA, HV_TEMPORAL_NONE = 0, 1, 2
 HV_MOM_M0, HV_MOM_M1, HV_MOM_M2, HV_MOM_M1N, HV_MOM_M2N = 1, 2, 4, 8, 16
@@ -232,12 +232,14 @@ def _ptr_kind(x):
 
 
 def hv_push_frames(h, frames, n=None, async_=False) -> int:
-    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). async_: a host
-    source is only queued (HV_MEM_HOST_ASYNC; keep it unchanged until hv_synchronize).
+    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). async_: the copy
+    is only queued on the copy stream (HV_MEM_HOST_ASYNC for a host source,
+    HV_MEM_DEVICE_ASYNC for a device one, whose frames must be complete already);
+    keep the source unchanged until hv_synchronize.
     Returns the status (HV_OK or HV_ERR_QUEUE_FULL); other errors raise."""
     ptr, kind, _ = _ptr_kind(frames)
-    if async_ and kind == HV_MEM_HOST:
-        kind = HV_MEM_HOST_ASYNC
+    if async_:
+        kind = HV_MEM_HOST_ASYNC if kind == HV_MEM_HOST else HV_MEM_DEVICE_ASYNC
     n = frames.shape[0] if n is None else n
     s = lib().hv_push_frames(h, C.c_void_p(ptr), n, kind)
     if s not in (HV_OK, HV_ERR_QUEUE_FULL):

@@ -315,6 +315,40 @@ def test_async_host_push_and_render():
     check_images(img, O.render(fr, p))
 
 
+def test_async_device_push():
+    """Device frames pushed with HV_MEM_DEVICE_ASYNC: the copies run on the copy
+    stream after the ring slots they overwrite have been consumed, overlapping the
+    rendering of earlier frames, through a ring smaller than the stream (ragged
+    packets, ring wrap inside a packet); the images match the oracle."""
+    import torch
+    H = W = 64
+    T, S, n = 16, 8, 203
+    fr = synth.random_frames(n, H, W, 12, seed=9)
+    p = oracle_params(spatial="asp", T=T, stride=S, band_lo_bin=1, band_hi_bin=7, moments=("M0", "M1"),
+                      H=H, W=W)
+    src = to_device(fr)
+    r = hv.Renderer(W, H, 16, 50)
+    try:
+        hv.hv_set_params(r.h, to_hv(p))
+        wf = r.window_floats()
+        out = torch.zeros(n * wf, dtype=torch.float32, device="cuda")
+        got, a = 0, 0
+        for k in [21, 24, 24, 17, 24, 24, 24, 24, 21]:
+            assert r.push(src[a:a + k], async_=True) == hv.HV_OK
+            a += k
+            while True:
+                m = r.render(out[got * wf:])
+                got += m
+                if m == 0:
+                    break
+        assert a == n
+        r.synchronize()
+    finally:
+        r.close()
+    img = images_from(out.cpu().numpy(), got, p)
+    check_images(img, O.render(fr, p))
+
+
 def test_max_window_length():
     H, W, T = 16, 32, 1024
     fr = synth.random_frames(T + 256, H, W, 12, seed=11)
