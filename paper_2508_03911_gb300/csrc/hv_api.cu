@@ -66,7 +66,6 @@ struct hv_handle {
   uint64_t pushed = 0, next_win = 0, propagated = 0;
   hv_stats st{};
   std::string err;
-  std::vector<double> pca_lam;
   // PCA workspace
   void* pca_ws = nullptr;
   size_t pca_ws_bytes = 0;
@@ -74,13 +73,27 @@ struct hv_handle {
   bool pca_has_lam = false;
   bool pca_batched = false;   // T <= 64 with FP32 covariance: many windows per launch
   uint32_t pca_last_nwin = 1;
+  // long windows, several per render: the eigensolver of one window (16 SMs) runs on
+  // eig_stream while the handle's stream runs the next window's covariance and the
+  // previous window's projection; windows alternate between two sets of C, counters,
+  // eigenvalues and sub-basis (set 0 is the one in `pca`)
+  cudaStream_t eig_stream = nullptr;
+  cudaEvent_t ev_cov[2] = {}, ev_eig[2] = {};
+  double2* pca_C[2] = {};
+  unsigned* pca_cnt[2] = {};
+  double* pca_lam[2] = {};
+  float2* pca_Vs[2] = {};
+  const double* pca_lam_last = nullptr;  // eigenvalues of the last window rendered
   // stage timing
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // triples: before spatial, after spatial, after temporal
   size_t prof_used = 0;
   hv_profile prof_acc{};
-  std::vector<cudaEvent_t> pca_ev;   // groups of 4 per recorded PCA window
+  std::vector<cudaEvent_t> pca_ev;   // groups of 8 per recorded PCA window (start, end of spatial
+                                     // chunk -- pipelined windows only --, covariance, eigensolver,
+                                     // projection)
   size_t pca_ev_used = 0;
+  unsigned long long* pca_sweeps_dev = nullptr;  // float32 and refinement sweeps while profiling
   // focus sweep: transfer functions of the swept distances (DC bin zero), cached
   float2* sw_tables = nullptr;
   size_t sw_bytes = 0;
@@ -405,8 +418,10 @@ hv_status apply_pending(hv_handle* h) {
     const size_t b_stage = stage_part * sizeof(uint16_t) * (p.precision == HV_PREC_SPLIT_BF16 ? 2 : 1);
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
     const size_t b_matf = size_t(T) * T * sizeof(float2);
+    // the second window set of the pipelined long windows: C, counters, lam, Vs
+    const size_t b_set2 = batched ? 0 : al(b_mat) + al(b_cnt) + al(b_lam) + al(b_vs);
     const size_t total = al(b_part) + (NW + 2) * al(b_mat) + 3 * al(b_matf) + al(b_rot) + al(b_cnt) + al(b_lam) +
-                         al(b_vs) + al(b_tc) + al(b_stage);
+                         al(b_vs) + al(b_tc) + al(b_stage) + b_set2;
     s = ensure(h, &h->pca_ws, &h->pca_ws_bytes, total);
     if (s != HV_OK) return s;
     char* b = static_cast<char*>(h->pca_ws);
@@ -459,11 +474,27 @@ hv_status apply_pending(hv_handle* h) {
     a.tc_ntiles = ntiles;
     std::memcpy(a.tc_tile_i, ti, sizeof(ti));
     std::memcpy(a.tc_tile_j, tj, sizeof(tj));
+    b += al(b_stage);
+    h->pca_C[0] = a.C;
+    h->pca_cnt[0] = a.counters;
+    h->pca_lam[0] = a.lam;
+    h->pca_Vs[0] = a.Vs;
+    h->pca_C[1] = nullptr;
+    if (!batched) {
+      h->pca_C[1] = reinterpret_cast<double2*>(b);
+      b += al(b_mat);
+      h->pca_cnt[1] = reinterpret_cast<unsigned*>(b);
+      b += al(b_cnt);
+      h->pca_lam[1] = reinterpret_cast<double*>(b);
+      b += al(b_lam);
+      h->pca_Vs[1] = reinterpret_cast<float2*>(b);
+    }
     a.err = h->dev_err;
     a.nwin = 1;
     a.wstride = d.S;
     h->pca_batched = batched;
     h->pca_has_lam = false;
+    h->pca_lam_last = nullptr;
   }
   h->cur = p;
   h->has_params = true;
@@ -508,11 +539,15 @@ hv_status apply_pending(hv_handle* h) {
 hv_status prof_flush(hv_handle* h) {
   if (h->prof_used == 0 && h->pca_ev_used == 0) return HV_OK;
   HV_CU(h, cudaStreamSynchronize(h->stream));
-  for (size_t i = 0; i < h->pca_ev_used; i += 4) {
-    float a = 0.f, b = 0.f, c = 0.f;
-    HV_CU(h, cudaEventElapsedTime(&a, h->pca_ev[i], h->pca_ev[i + 1]));
-    HV_CU(h, cudaEventElapsedTime(&b, h->pca_ev[i + 1], h->pca_ev[i + 2]));
-    HV_CU(h, cudaEventElapsedTime(&c, h->pca_ev[i + 2], h->pca_ev[i + 3]));
+  for (size_t i = 0; i < h->pca_ev_used; i += 8) {
+    float sp = 0.f, a = 0.f, b = 0.f, c = 0.f;
+    HV_CU(h, cudaEventElapsedTime(&sp, h->pca_ev[i], h->pca_ev[i + 1]));
+    HV_CU(h, cudaEventElapsedTime(&a, h->pca_ev[i + 2], h->pca_ev[i + 3]));
+    HV_CU(h, cudaEventElapsedTime(&b, h->pca_ev[i + 4], h->pca_ev[i + 5]));
+    HV_CU(h, cudaEventElapsedTime(&c, h->pca_ev[i + 6], h->pca_ev[i + 7]));
+    // a pipelined window's spatial chunk runs inside the render's temporal span
+    h->prof_acc.spatial_ms += sp;
+    h->prof_acc.temporal_ms -= sp;
     h->prof_acc.pca_cov_ms += a;
     h->prof_acc.pca_eig_ms += b;
     h->prof_acc.pca_proj_ms += c;
@@ -849,11 +884,17 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   const uint32_t T = h->T, S = h->S;
   hv_status s = HV_OK;
   const uint64_t prop_before = h->st.frames_propagated;
+  // long PCA windows, several in this render: window by window, each window's
+  // spatial chunk and covariance on the handle's stream while the previous window's
+  // eigensolver runs on eig_stream (below)
+  const bool pca_pipe = h->cur.temporal == HV_TEMPORAL_PCA && !h->pca_batched && !capturing && nw >= 2 &&
+                        h->pca_C[1] != nullptr;
   s = prof_mark(h, 0);
   if (s != HV_OK) return s;
   // spatial transform of every frame of these windows not yet in the queue: one
   // contiguous range when windows overlap or touch (S <= T), else per window
-  if (S <= T) {
+  if (pca_pipe) {
+  } else if (S <= T) {
     const uint64_t lo = std::max(h->next_win, h->propagated);
     const uint64_t hi = h->next_win + uint64_t(nw - 1) * S + T;
     if (lo < hi) {
@@ -874,7 +915,7 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   }
   s = prof_mark(h, 1);
   if (s != HV_OK) return s;
-  if (!capturing) {
+  if (!capturing && !pca_pipe) {
     s = note_consumed(h);
     if (s != HV_OK) return s;
   }
@@ -899,6 +940,81 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   }
   if (none) {
     e = launch_copy_frames(tq, nw, h->W * h->H, dst, h->stream, &launches);
+  } else if (pca_pipe) {
+    // pipelined long windows: spatial chunk(w), covariance(w) and projection(w - 1)
+    // on the handle's stream around eigensolver(w - 1, then w) on eig_stream; every
+    // frame of the render's windows fits in the time queue at once
+    e = cudaSuccess;
+    auto window_args = [&](uint32_t w) {
+      PcaArgs a = h->pca;
+      const int k = int(w & 1);
+      a.nwin = 1;
+      a.wstride = S;
+      a.tq = RingRef{h->tq, h->Q, uint32_t((h->next_win + uint64_t(w) * S) % h->Q)};
+      a.C = h->pca_C[k];
+      a.counters = h->pca_cnt[k];
+      a.cmax = reinterpret_cast<double*>(a.counters + 4);
+      a.lam = h->pca_lam[k];
+      a.Vs = h->pca_Vs[k];
+      return a;
+    };
+    // stage profiling: each window's eight events (start and end of its spatial
+    // chunk, covariance, eigensolver and projection) on the stream that runs the
+    // stage; room for all windows of the render first (the flush synchronises,
+    // before anything is queued)
+    cudaEvent_t* evw[2] = {nullptr, nullptr};
+    if (h->prof && h->pca_ev_used + 8 * size_t(nw) > h->pca_ev.size()) {
+      s = prof_flush(h);
+      if (s != HV_OK) return s;
+      while (h->pca_ev.size() < 8 * size_t(nw)) {
+        cudaEvent_t x = nullptr;
+        HV_CU(h, cudaEventCreate(&x));
+        h->pca_ev.push_back(x);
+      }
+    }
+    for (uint32_t w = 0; w <= nw && e == cudaSuccess; ++w) {
+      if (w < nw) {
+        PcaArgs a = window_args(w);
+        cudaEvent_t* ev = nullptr;
+        if (h->prof) {
+          ev = evw[w & 1] = &h->pca_ev[h->pca_ev_used];
+          h->pca_ev_used += 8;
+        }
+        // the window's frames not yet in the time queue
+        const uint64_t a0 = h->next_win + uint64_t(w) * S, lo = std::max(a0, h->propagated);
+        if (ev) HV_CU(h, cudaEventRecord(ev[0], h->stream));
+        if (lo < a0 + T) {
+          s = propagate(h, lo, a0 + T);
+          if (s != HV_OK) return s;
+          h->propagated = a0 + T;
+          s = note_consumed(h);
+          if (s != HV_OK) return s;
+        }
+        if (ev) HV_CU(h, cudaEventRecord(ev[1], h->stream));
+        ev = ev ? ev + 2 : nullptr;
+        if (ev) e = cudaEventRecord(ev[0], h->stream);
+        if (e == cudaSuccess) e = launch_pca_cov(a, h->stream, &launches);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_cov[w & 1], h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->eig_stream, h->ev_cov[w & 1], 0);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], h->eig_stream);
+        if (e == cudaSuccess) e = launch_pca_eig(a, h->eig_stream, &launches);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], h->eig_stream);
+        if (e == cudaSuccess && h->prof) e = launch_pca_sweeps_add(a.counters, h->pca_sweeps_dev, h->eig_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_eig[w & 1], h->eig_stream);
+      }
+      if (w >= 1 && e == cudaSuccess) {
+        PcaArgs a = window_args(w - 1);
+        cudaEvent_t* ev = evw[(w - 1) & 1] ? evw[(w - 1) & 1] + 2 : nullptr;
+        e = cudaStreamWaitEvent(h->stream, h->ev_eig[(w - 1) & 1], 0);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], h->stream);
+        if (e == cudaSuccess) e = launch_pca_proj(a, dst + size_t(w - 1) * h->win_floats, h->stream, &launches);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[5], h->stream);
+      }
+    }
+    h->pca_last_nwin = 1;
+    h->pca_lam_last = h->pca_lam[(nw - 1) & 1];
+    h->pca_has_lam = true;
   } else if (h->cur.temporal == HV_TEMPORAL_PCA) {
     e = cudaSuccess;
     for (uint32_t w = 0; w < nw && e == cudaSuccess;) {
@@ -909,22 +1025,20 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
       h->pca_last_nwin = k;
       cudaEvent_t* ev = nullptr;
       if (h->prof) {
-        if (h->pca_ev_used + 4 > h->pca_ev.size()) {
+        if (h->pca_ev_used + 8 > h->pca_ev.size()) {
           s = prof_flush(h);
           if (s != HV_OK) return s;
         }
         ev = &h->pca_ev[h->pca_ev_used];
-        h->pca_ev_used += 4;
+        h->pca_ev_used += 8;
+        HV_CU(h, cudaEventRecord(ev[0], h->stream));  // no spatial chunk of its own
+        HV_CU(h, cudaEventRecord(ev[1], h->stream));
+        ev += 2;
       }
       e = launch_pca(h->pca, dst + size_t(w) * h->win_floats, h->stream, &launches, ev);
+      h->pca_lam_last = h->pca.lam + size_t(k - 1) * h->T;
       w += k;
-      if (h->prof && e == cudaSuccess) {
-        unsigned sw[2] = {0, 0};  // float32, float64 sweeps of the launch (synchronous read; profiling only)
-        HV_CU(h, cudaMemcpyAsync(sw, h->pca.counters + 1, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
-        HV_CU(h, cudaStreamSynchronize(h->stream));
-        h->prof_acc.pca_sweeps_f32 += sw[0];
-        h->prof_acc.pca_sweeps += sw[1];
-      }
+      if (h->prof && e == cudaSuccess) e = launch_pca_sweeps_add(h->pca.counters, h->pca_sweeps_dev, h->stream);
     }
     h->pca_has_lam = true;
   } else {
@@ -1020,6 +1134,11 @@ hv_status hv_open(const hv_open_desc* desc, hv_handle** out) {
     h->own_stream = true;
   }
   e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->eig_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_cov[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_eig[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pushed, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_consumed, cudaEventDisableTiming);
   for (int i = 0; i < hv_handle::NCONS && e == cudaSuccess; ++i)
@@ -1037,6 +1156,8 @@ hv_status hv_open(const hv_open_desc* desc, hv_handle** out) {
   if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("twiddles: ") + cudaGetErrorString(e));
   e = cudaMalloc(&h->dev_err, 16);
   if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&h->pca_sweeps_dev, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(h->pca_sweeps_dev, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) return bail(HV_ERR_NOMEM, std::string("error flags: ") + cudaGetErrorString(e));
   *out = h;
   return HV_OK;
@@ -1153,7 +1274,8 @@ hv_status hv_pca_eigenvalues(const hv_handle* h, double* out, uint32_t n) {
   if (!h->pca_has_lam || h->cur.temporal != HV_TEMPORAL_PCA) return HV_ERR_STATE;
   if (n > h->T) return HV_ERR_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return HV_ERR_CUDA;
-  const double* lam = h->pca.lam + size_t(h->pca_last_nwin - 1) * h->T;
+  const double* lam = h->pca_lam_last;
+  if (!lam) return HV_ERR_STATE;
   if (cudaMemcpyAsync(out, lam, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return HV_ERR_CUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HV_ERR_CUDA;
@@ -1179,7 +1301,7 @@ hv_status hv_profile_enable(hv_handle* h, int on) {
   if (on && h->prof_ev.empty()) {
     h->prof_ev.resize(3 * 256, nullptr);
     for (auto& e : h->prof_ev) HV_CU(h, cudaEventCreate(&e));
-    h->pca_ev.resize(4 * 64, nullptr);
+    h->pca_ev.resize(8 * 64, nullptr);
     for (auto& e : h->pca_ev) HV_CU(h, cudaEventCreate(&e));
   }
   if (on) {
@@ -1187,6 +1309,7 @@ hv_status hv_profile_enable(hv_handle* h, int on) {
     h->prof_used = 0;
     h->pca_ev_used = 0;
     h->prof_acc = hv_profile{};
+    HV_CU(h, cudaMemset(h->pca_sweeps_dev, 0, 2 * sizeof(unsigned long long)));
   }
   h->prof = on != 0;
   return HV_OK;
@@ -1197,6 +1320,10 @@ hv_status hv_profile_read(hv_handle* h, hv_profile* out) {
   HV_CU(h, cudaSetDevice(h->device));
   hv_status s = prof_flush(h);
   if (s != HV_OK) return s;
+  unsigned long long sw[2] = {0, 0};  // accumulated on the device by every profiled window
+  HV_CU(h, cudaMemcpy(sw, h->pca_sweeps_dev, sizeof(sw), cudaMemcpyDeviceToHost));
+  h->prof_acc.pca_sweeps_f32 = sw[0];
+  h->prof_acc.pca_sweeps = sw[1];
   *out = h->prof_acc;
   return HV_OK;
 }
@@ -1221,6 +1348,14 @@ hv_status hv_close(hv_handle* h) {
     cudaStreamSynchronize(h->copy_stream);
     cudaStreamDestroy(h->copy_stream);
   }
+  if (h->eig_stream) {
+    cudaStreamSynchronize(h->eig_stream);
+    cudaStreamDestroy(h->eig_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_cov[i]) cudaEventDestroy(h->ev_cov[i]);
+    if (h->ev_eig[i]) cudaEventDestroy(h->ev_eig[i]);
+  }
   if (h->ev_pushed) cudaEventDestroy(h->ev_pushed);
   if (h->ev_consumed) cudaEventDestroy(h->ev_consumed);
   for (auto& e : h->cons_ev)
@@ -1234,6 +1369,7 @@ hv_status hv_close(hv_handle* h) {
   dfree(h->s2);
   dfree(h->tw);
   dfree(h->dev_err);
+  dfree(h->pca_sweeps_dev);
   dfree(h->fused_ctr);
   dfree(h->asp_ht);
   dfree(h->staging);

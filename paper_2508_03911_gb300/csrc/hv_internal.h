@@ -155,8 +155,18 @@ size_t pca_partials_floats2(uint32_t T, uint32_t nchunks);
 size_t cov_tc_partials_floats(uint32_t ntiles, uint32_t nchunks);
 uint32_t cov_tc_tiles(uint32_t T, uint8_t* ti, uint8_t* tj);
 cudaError_t launch_cov_tc(PcaArgs& a, cudaStream_t s, int* launches);
-// ev (optional, 4 events): before covariance, after covariance, after eigensolver, after projection
+// ev (optional, 6 events): start and end of the covariance, of the eigensolver and of
+// the projection
 cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev);
+// Adds the float32 and refinement sweep counts of the last window (counters[1],
+// counters[2]) to total[0], total[1] (one thread; stage profiling).
+cudaError_t launch_pca_sweeps_add(const unsigned* counters, unsigned long long* total, cudaStream_t s);
+// The three stages of launch_pca, for callers that run them on different streams:
+// covariance into a.C (and the counters cleared), eigensolver (a.C, the shared
+// eigensolver scratch -> a.lam, a.Vs), projection (a.Vs, the window's frames -> out).
+cudaError_t launch_pca_cov(PcaArgs& a, cudaStream_t s, int* launches);
+cudaError_t launch_pca_eig(PcaArgs& a, cudaStream_t s, int* launches);
+cudaError_t launch_pca_proj(PcaArgs& a, float* out, cudaStream_t s, int* launches);
 
 // Autofocus: Tamura coefficients from per-(frame, distance) amplitude sums, and the
 // network input (2 x 2 binned log-magnitude spectrum, standardised, bfloat16)

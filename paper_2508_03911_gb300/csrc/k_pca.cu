@@ -1322,7 +1322,7 @@ size_t pca_partials_floats2(uint32_t T, uint32_t nchunks) {
   return size_t(nchunks) * (nT * (nT + 1) / 2) * TS * TS;
 }
 
-cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev) {
+cudaError_t launch_pca_cov(PcaArgs& a, cudaStream_t s, int* launches) {
   const size_t hw = size_t(a.W) * a.H;
   const int TS = a.T < uint32_t(COV_TS) ? int(a.T) : COV_TS;
   if (a.T % TS || TS % 16 || hw % 256 || a.T % PRJ_KS) return cudaErrorInvalidValue;
@@ -1332,7 +1332,6 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
   const dim3 g1(nT * (nT + 1) / 2, a.nchunks, a.nwin);
   cudaError_t e0 = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned) + sizeof(double), s);
   if (e0 != cudaSuccess) return e0;
-  if (ev) cudaEventRecord(ev[0], s);
   if (a.precision == HV_PREC_FP32 && (a.T == 32 || a.T == 64)) {
     const size_t smem = cov_small_smem(int(a.T));
     const dim3 gs(a.nchunks, a.nwin);
@@ -1353,9 +1352,11 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     cudaError_t et = launch_cov_tc(a, s, launches);
     if (et != cudaSuccess) return et;
   }
-  if (ev) cudaEventRecord(ev[1], s);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pca_eig(PcaArgs& a, cudaStream_t s, int* launches) {
+  cudaError_t e = cudaSuccess;
   if (a.T == 32) {
     e = launch_jacobi_small<32>(a, s);
   } else if (a.T == 64) {
@@ -1415,13 +1416,47 @@ cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cu
     *launches += 3;
   }
   if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[2], s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pca_proj(PcaArgs& a, float* out, cudaStream_t s, int* launches) {
+  cudaError_t e;
   if (a.Mpad % 64 == 0) e = launch_project<64>(a, out, s);
   else if (a.Mpad % 32 == 0) e = launch_project<32>(a, out, s);
   else e = launch_project<16>(a, out, s);
   if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[3], s);
   *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pca(PcaArgs& a, float* out, cudaStream_t s, int* launches, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], s);
+  cudaError_t e = launch_pca_cov(a, s, launches);
+  if (e != cudaSuccess) return e;
+  if (ev) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+  }
+  e = launch_pca_eig(a, s, launches);
+  if (e != cudaSuccess) return e;
+  if (ev) {
+    cudaEventRecord(ev[3], s);
+    cudaEventRecord(ev[4], s);
+  }
+  e = launch_pca_proj(a, out, s, launches);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[5], s);
+  return cudaSuccess;
+}
+
+// total[0] += float32 sweeps, total[1] += refinement sweeps of the last window
+__global__ void k_pca_sweeps_add(const unsigned* counters, unsigned long long* total) {
+  total[0] += counters[1];
+  total[1] += counters[2];
+}
+
+cudaError_t launch_pca_sweeps_add(const unsigned* counters, unsigned long long* total, cudaStream_t s) {
+  k_pca_sweeps_add<<<1, 1, 0, s>>>(counters, total);
   return cudaGetLastError();
 }
 

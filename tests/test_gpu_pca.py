@@ -73,6 +73,26 @@ def test_pca_parity(H, W, T, S, lohi, spatial):
     assert np.all(np.diff(lam) <= 0)
 
 
+def test_pca_long_windows_pipelined():
+    """Five overlapping long windows (T = 128, S = 64) in one render: the eigensolver
+    of each window runs on a second stream beside the next window's covariance and
+    the previous window's projection, the windows alternating between two buffer
+    sets; every window's image and the last window's eigenvalues against the
+    oracle."""
+    H = W = 64
+    T, S = 128, 64
+    fr = synth.random_frames(T + 4 * S + 9, H, W, 12, seed=77)
+    p = oracle_params(spatial="asp", z_m=0.4, temporal="pca", T=T, stride=S, pca_lo=2, pca_hi=64, H=H, W=W)
+    img, lam = gpu_pca(fr, p)
+    ref = oracle_windows(fr, p)
+    assert img.shape[0] == len(ref) == 5
+    for w, rw in enumerate(ref):
+        e = rel_l2(img[w], rw["E"])
+        assert e <= IMAGE_TOL, (w, e)
+    lam_ref = ref[-1]["lam"]
+    assert np.max(np.abs(lam - lam_ref)) <= LAM_TOL * lam_ref[0]
+
+
 @pytest.mark.parametrize("precision,tol", [("split_bf16", 1e-4), ("bf16", 5e-2)])
 @pytest.mark.parametrize("H,W,T", [(64, 64, 64), (128, 64, 256), (64, 128, 128)])
 def test_pca_tensor_core_covariance(precision, tol, H, W, T):
