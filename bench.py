@@ -5,8 +5,8 @@ Default workload (asp_stft_256_t512_s512, the shape of the paper's ASP + STFT
 512/512 benchmark row): 256x256 12-bit frames at fs = 71.4 kHz, angular-spectrum
 propagation at z = 0.30 m, STFT windows T = 512 with stride S = 512, moments
 M0/M1/M2 over 1-35 kHz (bins 8..250). One step streams 102,400 raw frames (25
-batches of 4,096 frames: hv_push_frames from a device-resident pool, queued on the
-copy stream, then hv_render of every complete window). Metric: raw frames
+batches of 4,096 frames: hv_push_frames from a device-resident pool, whose frames
+the spatial stage reads in place, then hv_render of every complete window). Metric: raw frames
 rendered per second. Other workloads by --workload (the paper-scale Fresnel
 stream with stride 64, PCA, batched uneven streams, learned autofocus).
 
@@ -321,9 +321,8 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
             if events is not None:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            # the pool is written once before the timed region: the copy into the
-            # input ring may run on the copy stream (HV_MEM_DEVICE_ASYNC), where it
-            # overlaps the rendering of the previous batch
+            # the pool is written once before the timed region and never changed:
+            # its frames may be read in place by the spatial stage (HV_MEM_DEVICE_ASYNC)
             st = r.push(pool_dev, async_=True)
             assert st == hv.HV_OK, st
             while r.render(out) > 0:  # every complete window, as a caller would

@@ -159,12 +159,14 @@ hv_status hv_get_params(const hv_handle* h, hv_params* p);
  * only queued (HV_MEM_HOST_ASYNC: on the handle's copy stream, after the ring
  * slots it overwrites have been consumed; the buffer must stay unchanged until
  * hv_synchronize returns or until an hv_render with HV_MEM_HOST output that
- * renders windows using these frames returns), or a device pointer whose copy is
- * queued the same way (HV_MEM_DEVICE_ASYNC: the frames must be completely written
- * when the call is made, since the copy stream is not ordered after the handle's
- * stream or any other; the copy then overlaps the rendering of earlier frames
- * instead of following it; the same lifetime rule as HV_MEM_HOST_ASYNC; only
- * hv_push_frames takes it). Frames are uint8 or uint16
+ * renders windows using these frames returns), or a device pointer whose frames
+ * the library reads in place (HV_MEM_DEVICE_ASYNC: they must be completely
+ * written when the call is made -- no stream is ordered before their use -- and
+ * stay valid and unchanged until every window that contains them has been
+ * rendered and hv_synchronize has returned; the spatial stage reads them straight
+ * from `frames`, nothing is copied; a pointer that is not 16-byte aligned is
+ * copied instead, on the copy stream after the ring slots it overwrites have been
+ * consumed; only hv_push_frames takes it). Frames are uint8 or uint16
  * by pixel_bits, row-major, frames contiguous. All-or-nothing: if the ring
  * cannot take all n frames, nothing is copied and HV_ERR_QUEUE_FULL is returned
  * (backpressure; frames are never dropped). */

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "../../include/hv.h"
@@ -33,6 +34,14 @@ struct hv_handle {
   cudaEvent_t cons_ev[NCONS] = {};
   uint64_t cons_hi[NCONS] = {};
   int cons_head = 0, cons_n = 0;
+  // frames pushed with HV_MEM_DEVICE_ASYNC are read in place: frames first .. first
+  // + n - 1 at ptr (oldest first); entries below the next window are dropped
+  struct Borrowed {
+    uint64_t first;
+    uint32_t n;
+    const void* ptr;
+  };
+  std::deque<Borrowed> borrowed;
   uint32_t max_w = 0, max_h = 0, bits = 8, cap = 0, tq_req = 0;
   void* raw = nullptr;
   // settings
@@ -582,13 +591,15 @@ bool cluster_ok(const hv_handle* h) {
          (h->cur.spatial == HV_SPATIAL_ASP || h->cur.spatial == HV_SPATIAL_FRESNEL);
 }
 
-hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
+// Spatial transform of frames r0 .. r1 - 1, whose raw frames are at `raw` (frame
+// r0 at slot raw.slot0); the time queue slots follow the frame numbers.
+hv_status propagate_run(hv_handle* h, uint64_t r0, uint64_t r1, RingRef raw) {
   // the cluster kernel needs no scratch, the fused transform keeps its intermediates
   // in rings: one persistent launch for all frames
   const bool whole = (h->sp_cluster && cluster_ok(h)) || h->sp_fused;
-  const uint64_t step = whole ? f1 - f0 : h->chunk;
-  for (uint64_t a = f0; a < f1; a += step) {
-    const uint32_t n = uint32_t(std::min<uint64_t>(step, f1 - a));
+  const uint64_t step = whole ? r1 - r0 : h->chunk;
+  for (uint64_t a = r0; a < r1; a += step) {
+    const uint32_t n = uint32_t(std::min<uint64_t>(step, r1 - a));
     SpatialArgs sa{};
     sa.err = h->dev_err;
     sa.spatial = h->cur.spatial;
@@ -596,7 +607,7 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     sa.W = h->W;
     sa.H = h->H;
     sa.n = n;
-    sa.raw = RingRef{h->raw, h->cap, uint32_t(a % h->cap)};
+    sa.raw = RingRef{raw.base, raw.cap, uint32_t((raw.slot0 + (a - r0)) % raw.cap)};
     sa.tq = RingRef{h->tq, h->Q, uint32_t(a % h->Q)};
     sa.scratch1 = h->s1;
     sa.scratch2 = h->s2;
@@ -617,6 +628,33 @@ hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1) {
     h->st.kernel_launches += launches;
     if (e != cudaSuccess) return cuda_fail(h, e, "spatial transform launch");
     h->st.frames_propagated += n;
+  }
+  return HV_OK;
+}
+
+// Spatial transform of frames f0 .. f1 - 1: runs of frames read in place from the
+// caller's memory (HV_MEM_DEVICE_ASYNC) and runs in the input ring, one after the
+// other. ring_only: the input ring whatever its contents (the autotuner's timing).
+hv_status propagate(hv_handle* h, uint64_t f0, uint64_t f1, bool ring_only = false) {
+  uint64_t a = f0;
+  while (a < f1) {
+    uint64_t end = f1;
+    RingRef raw{h->raw, h->cap, uint32_t(a % h->cap)};
+    if (!ring_only) {
+      for (const auto& b : h->borrowed) {
+        if (b.first + b.n <= a) continue;
+        if (b.first <= a) {  // a lies in this caller buffer
+          end = std::min<uint64_t>(f1, b.first + b.n);
+          raw = RingRef{const_cast<void*>(b.ptr), b.n, uint32_t(a - b.first)};
+        } else {  // the ring up to the next caller buffer
+          end = std::min<uint64_t>(f1, b.first);
+        }
+        break;
+      }
+    }
+    hv_status s = propagate_run(h, a, end, raw);
+    if (s != HV_OK) return s;
+    a = end;
   }
   return HV_OK;
 }
@@ -671,11 +709,11 @@ hv_status tune_spatial(hv_handle* h) {
     h->sp_fused = c.kind == 4;
     h->chunk = (c.kind == 2 || c.kind == 4) ? h->chunk : ch;
     const uint64_t before = h->st.frames_propagated;
-    hv_status st = propagate(h, 0, n);  // warm-up
+    hv_status st = propagate(h, 0, n, true);  // warm-up
     if (st != HV_OK) return st;
     HV_CU(h, cudaEventRecord(e0, h->stream));
     for (int rep = 0; rep < 2; ++rep) {
-      st = propagate(h, 0, n);
+      st = propagate(h, 0, n, true);
       if (st != HV_OK) return st;
     }
     HV_CU(h, cudaEventRecord(e1, h->stream));
@@ -1096,6 +1134,9 @@ hv_status enqueue_windows(hv_handle* h, float* dst, uint32_t nw, bool capturing)
   // graph: the group step records it after launching the graph instead
   if (!capturing) HV_CU(h, cudaEventRecord(h->ev_consumed, h->stream));
   h->next_win += uint64_t(nw) * S;
+  // caller buffers whose frames no window will read again
+  while (!h->borrowed.empty() && h->borrowed.front().first + h->borrowed.front().n <= h->next_win)
+    h->borrowed.pop_front();
   h->st.windows_rendered += nw;
   return HV_OK;
 }
@@ -1177,6 +1218,7 @@ hv_status hv_set_params(hv_handle* h, const hv_params* p) {
     h->st.frames_dropped += queued;
     h->next_win = h->pushed;
     h->propagated = h->pushed;
+    h->borrowed.clear();
   }
   h->pend = *p;
   h->pending = true;
@@ -1205,6 +1247,13 @@ hv_status hv_push_frames(hv_handle* h, const void* frames, uint32_t n, int mem_k
   }
   HV_CU(h, cudaSetDevice(h->device));
   if (mem_kind == HV_MEM_DEVICE) return enqueue_push_device(h, frames, n);
+  if (mem_kind == HV_MEM_DEVICE_ASYNC && (reinterpret_cast<uintptr_t>(frames) & 15) == 0) {
+    // read in place by the spatial stage (16-byte aligned, as its bulk copies need)
+    h->borrowed.push_back(hv_handle::Borrowed{h->pushed, n, frames});
+    h->pushed += n;
+    h->st.frames_pushed += n;
+    return HV_OK;
+  }
   const size_t fb = size_t(p.width) * p.height * (h->bits / 8);
   const uint32_t slot = uint32_t(h->pushed % h->cap);
   const uint32_t n1 = std::min(n, h->cap - slot);

@@ -232,10 +232,11 @@ def _ptr_kind(x):
 
 
 def hv_push_frames(h, frames, n=None, async_=False) -> int:
-    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). async_: the copy
-    is only queued on the copy stream (HV_MEM_HOST_ASYNC for a host source,
-    HV_MEM_DEVICE_ASYNC for a device one, whose frames must be complete already);
-    keep the source unchanged until hv_synchronize.
+    """Push frames (numpy / torch, shape (n, H, W), uint8 or uint16). async_: a host
+    source's copy is only queued on the copy stream (HV_MEM_HOST_ASYNC); a device
+    source, whose frames must be complete already, is read in place by the spatial
+    stage (HV_MEM_DEVICE_ASYNC); keep it unchanged until its windows are rendered
+    and hv_synchronize has returned.
     Returns the status (HV_OK or HV_ERR_QUEUE_FULL); other errors raise."""
     ptr, kind, _ = _ptr_kind(frames)
     if async_:

@@ -23,9 +23,10 @@ def _cuda():
     hv.lib()  # fails loudly when the extension is missing
 
 
-def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=None, tq=0):
+def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=None, tq=0, in_place=False):
     """Push `frames` (in packets) and render all complete windows through the C ABI
-    (rendering repeatedly after each packet until no window is left)."""
+    (rendering repeatedly after each packet until no window is left). in_place:
+    device packets pushed with HV_MEM_DEVICE_ASYNC, read in place."""
     import torch
     n, H, W = frames.shape
     bits = 8 if frames.dtype == np.uint8 else 16
@@ -42,7 +43,7 @@ def gpu_render(frames, p, packets=None, out_kind="device", extra=None, queue=Non
         packets = packets or [n]
         done, got = 0, 0
         for k in packets:
-            assert r.push(dev[done:done + k]) == hv.HV_OK
+            assert r.push(dev[done:done + k], async_=in_place) == hv.HV_OK
             done += k
             while True:
                 k_win = r.render(out[got * wf:])
@@ -315,26 +316,43 @@ def test_async_host_push_and_render():
     check_images(img, O.render(fr, p))
 
 
-def test_async_device_push():
-    """Device frames pushed with HV_MEM_DEVICE_ASYNC: the copies run on the copy
-    stream after the ring slots they overwrite have been consumed, overlapping the
-    rendering of earlier frames, through a ring smaller than the stream (ragged
-    packets, ring wrap inside a packet); the images match the oracle."""
+@pytest.mark.parametrize("spatial", ["asp", "fresnel"])
+def test_async_device_push(spatial):
+    """Device frames pushed with HV_MEM_DEVICE_ASYNC: read in place by the spatial
+    stage from aligned pointers, copied on the copy stream (after the ring slots
+    they overwrite have been consumed) from a pointer 2 bytes off alignment, mixed
+    with plain device and host pushes, ragged packets, through an input ring
+    smaller than the stream; a render's frames come from several sources in turn.
+    The images match the oracle."""
     import torch
     H = W = 64
     T, S, n = 16, 8, 203
     fr = synth.random_frames(n, H, W, 12, seed=9)
-    p = oracle_params(spatial="asp", T=T, stride=S, band_lo_bin=1, band_hi_bin=7, moments=("M0", "M1"),
+    p = oracle_params(spatial=spatial, T=T, stride=S, band_lo_bin=1, band_hi_bin=7, moments=("M0", "M1"),
                       H=H, W=W)
     src = to_device(fr)
+    flat = torch.empty(n * H * W + 1, dtype=torch.int16, device="cuda")
+    off = flat[1:].view(n, H, W)  # 2 bytes off 16-byte alignment
+    off.copy_(src)
+    torch.cuda.synchronize()
+    assert off.data_ptr() % 16 == 2
     r = hv.Renderer(W, H, 16, 50)
     try:
         hv.hv_set_params(r.h, to_hv(p))
         wf = r.window_floats()
         out = torch.zeros(n * wf, dtype=torch.float32, device="cuda")
         got, a = 0, 0
-        for k in [21, 24, 24, 17, 24, 24, 24, 24, 21]:
-            assert r.push(src[a:a + k], async_=True) == hv.HV_OK
+        kinds = ["in place", "in place", "offset", "in place", "device", "in place", "host", "offset", "in place"]
+        for k, kind in zip([21, 24, 24, 17, 24, 24, 24, 24, 21], kinds):
+            if kind == "in place":
+                st = r.push(src[a:a + k], async_=True)
+            elif kind == "offset":
+                st = r.push(off[a:a + k], async_=True)
+            elif kind == "device":
+                st = r.push(src[a:a + k])
+            else:
+                st = r.push(fr[a:a + k])
+            assert st == hv.HV_OK
             a += k
             while True:
                 m = r.render(out[got * wf:])
@@ -395,9 +413,12 @@ def test_queue_full_backpressure_and_empty_render():
         r.close()
 
 
-def test_set_params_is_delayed_to_the_next_window():
+@pytest.mark.parametrize("async_", [False, True])
+def test_set_params_is_delayed_to_the_next_window(async_):
     """A new z applies from the next window on; that window is computed wholly
-    with the new settings."""
+    with the new settings. async_: the device frames are read in place
+    (HV_MEM_DEVICE_ASYNC), so the frames the new settings transform again come
+    from the caller's buffer once more."""
     import torch
     H = W = 32
     fr = synth.random_frames(48, H, W, 12, seed=21)
@@ -408,10 +429,10 @@ def test_set_params_is_delayed_to_the_next_window():
         hv.hv_set_params(r.h, to_hv(p1))
         out = torch.zeros(8 * H * W, device="cuda")
         dev = to_device(fr)
-        r.push(dev[:24])
+        r.push(dev[:24], async_=async_)
         n1 = r.render(out)                      # windows at 0, 8
         hv.hv_set_params(r.h, to_hv(p2))
-        r.push(dev[24:])
+        r.push(dev[24:], async_=async_)
         n2 = r.render(out[n1 * H * W:])          # windows at 16, 24, 32 with z = 0.35
         torch.cuda.synchronize()
         img = out.cpu().numpy()[: (n1 + n2) * H * W].reshape(n1 + n2, 1, H, W)
@@ -481,6 +502,21 @@ def test_fused_spatial_field_parity(spatial, bits):
                          tq=150)
     ref = oracle_fields(fr, p)
     assert img.shape == ref.shape
+    for i in range(n):
+        assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
+    assert st["frames_propagated"] == n
+
+
+def test_fused_reads_frames_in_place():
+    """The fused transform reading device frames in place (HV_MEM_DEVICE_ASYNC):
+    one launch per pushed packet (1, 97 and 122 frames), each over the caller's
+    buffer; every field against the oracle."""
+    N, n = 256, 220
+    fr = synth.random_frames(n, N, N, 16, seed=431)
+    p = oracle_params(spatial="asp", z_m=0.27, temporal="none", T=1, stride=1, H=N, W=N)
+    img, st = gpu_render(fr, p, extra=dict(spatial_kernel="fused"), packets=[1, 97, 122], queue=160,
+                         tq=150, in_place=True)
+    ref = oracle_fields(fr, p)
     for i in range(n):
         assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
     assert st["frames_propagated"] == n
