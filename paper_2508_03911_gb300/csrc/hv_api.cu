@@ -199,7 +199,7 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
   }
   if (p.spatial_kernel > HV_SK_FUSED) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
   if (p.stft_kernel != 0 && p.stft_kernel != HV_STFT_WALK && p.stft_kernel != HV_STFT_WINDOW &&
-      p.stft_kernel != HV_STFT_WINDOW_WIDE) {
+      p.stft_kernel != HV_STFT_WINDOW_WIDE && p.stft_kernel != HV_STFT_WINDOW_PIPELINED) {
     why = "unknown stft_kernel";
     return HV_ERR_ARG;
   }
@@ -528,7 +528,9 @@ hv_status apply_pending(hv_handle* h) {
   // STFT kernel for windows that do not overlap: the caller's, the autotuner's (tuned),
   // else the walking kernel launched once per window (the plain form)
   h->stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? STFT_AUTO
-                   : (p.stft_kernel == HV_STFT_WINDOW_WIDE ? STFT_WIDE : STFT_WALK);
+                   : p.stft_kernel == HV_STFT_WINDOW_WIDE     ? STFT_WIDE
+                   : p.stft_kernel == HV_STFT_WINDOW_PIPELINED ? STFT_PIPE
+                                                               : STFT_WALK;
   h->tuning.stft_kernel = p.stft_kernel == 0 ? HV_STFT_WALK : p.stft_kernel;
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
     s = tune_spatial(h);
@@ -778,11 +780,11 @@ hv_status tune_temporal(hv_handle* h) {
   sa.nout = h->nout;
   sa.out = out;
   sa.err = h->dev_err;
-  const int kinds[3] = {STFT_WALK, STFT_AUTO, STFT_WIDE};
+  const int kinds[4] = {STFT_WALK, STFT_AUTO, STFT_WIDE, STFT_PIPE};
   float best = 1e30f;
   int best_kind = STFT_AUTO;
   hv_status st = HV_OK;
-  for (int ci = 0; ci < 3 && st == HV_OK; ++ci) {
+  for (int ci = 0; ci < 4 && st == HV_OK; ++ci) {
     sa.kernel = kinds[ci];
     int launches = 0;
     cudaError_t e = launch_stft(sa, h->stream, &launches);  // warm-up
@@ -808,8 +810,10 @@ hv_status tune_temporal(hv_handle* h) {
   cudaFree(out);
   if (st != HV_OK) return st;
   h->stft_kernel = best_kind;
-  h->tuning.stft_kernel = best_kind == STFT_WALK ? HV_STFT_WALK
-                          : (best_kind == STFT_WIDE ? HV_STFT_WINDOW_WIDE : HV_STFT_WINDOW);
+  h->tuning.stft_kernel = best_kind == STFT_WALK   ? HV_STFT_WALK
+                          : best_kind == STFT_WIDE ? HV_STFT_WINDOW_WIDE
+                          : best_kind == STFT_PIPE ? HV_STFT_WINDOW_PIPELINED
+                                                   : HV_STFT_WINDOW;
   h->tuning.tuned = 1;
   return HV_OK;
 }

@@ -87,7 +87,9 @@ struct StftArgs {
   int tma;              // set by the launcher: staged frames through a TMA tensor map
   int kernel;           // STFT_AUTO: windows that do not overlap (S >= T) one CTA per
                         // (window, pixel tile); STFT_WIDE: the same with twice the pixels
-                        // per CTA; STFT_WALK: CTAs walk all windows of their pixels
+                        // per CTA; STFT_PIPE: persistent CTAs over the (window, tile)
+                        // items, the next item's frames loaded while the current one is
+                        // transformed; STFT_WALK: CTAs walk all windows of their pixels
   // post-processing without convolution, fused into the epilogue: when post_ring is
   // set, the images of window w go to ring slot (post_count + w) mod post_R (layout
   // [R][nout][H*W]) instead of out, and when post_sums is set each image's sum is
@@ -100,7 +102,7 @@ struct StftArgs {
 // float64 sums of a post-processed image are kept as kPostSub partial sums, so that
 // the CTAs that produce it add into different words
 constexpr uint32_t kPostSub = 32;
-enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2 };
+enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2, STFT_PIPE = 3 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
 // Encodes a 2-D tiled TMA tensor map (map: a CUtensorMap, 64-byte aligned) over

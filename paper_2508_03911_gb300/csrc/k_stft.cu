@@ -56,6 +56,9 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// all but the newest N committed groups complete
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
 
@@ -633,6 +636,110 @@ __global__ void __launch_bounds__(WinCfg<T, WIDE>::NT, WinCfg<T, WIDE>::OCC) k_s
   }
 }
 
+// The window-per-CTA kernel made persistent and double-buffered: CTA c takes the
+// (window, pixel tile) items c, c + grid, ... and issues the cp.async copies of its
+// next item's frames into the other buffer before it transforms the current one,
+// so that its loads overlap its own FFT instead of only other CTAs'. Two padded
+// buffers per CTA: fewer CTAs per SM than the one-item kernel (3 at T = 512).
+template <int T, bool POST>
+__global__ void __launch_bounds__(WinCfg<T, false>::NT, 1) k_stft_winp(StftArgs a) {
+  using Lw = WarpLayout<T>;
+  using Wc = WinCfg<T, false>;
+  constexpr int NT = Wc::NT, LP = Lw::LP, PW = Lw::PW, BT = Wc::BT, WR = Wc::WR;
+  extern __shared__ __align__(16) unsigned char smem_winp[];
+  float2* rows0 = reinterpret_cast<float2*>(smem_winp);  // buffer b at rows0 + b BT WR
+  float2* tw = rows0 + 2 * BT * WR;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pl = lane / LP, jl = lane % LP;
+  const int px = warp * PW + pl;
+  const size_t HW = size_t(a.W) * a.H;
+  const uint32_t ntile = uint32_t(HW / BT);
+  const uint32_t nitem = a.nwin * ntile;
+  const float2* tq = static_cast<const float2*>(a.tq.base);
+  const uint32_t cap = a.tq.cap;
+  // item i: window i / ntile, pixels (i % ntile) BT ..; its frames into buffer b
+  auto fetch = [&](uint32_t i, int b) {
+    constexpr int FS = NT / BT;  // frames per pass of the CTA
+    const uint32_t w = i / ntile, p0 = (i % ntile) * BT;
+    float2* rows = rows0 + b * BT * WR;
+    const int c = tid % BT;
+    int f = tid / BT;
+    uint32_t g = a.tq.slot0 + w * a.S + uint32_t(f);
+    while (g >= cap) g -= cap;
+    for (; f < T; f += FS) {
+      cp_async8(&rows[c * WR + wpad(f)], &tq[size_t(g) * HW + p0 + c]);
+      g += FS;
+      if (g >= cap) g -= cap;
+    }
+    cp_async_commit();
+  };
+  uint32_t item = blockIdx.x;
+  if (item < nitem) fetch(item, 0);
+  {  // stage twiddles (the walking kernel's table layout)
+    constexpr int R1 = WarpPlan<T>::R1;
+    int NS = R1;
+    while (NS < T) {
+      const int rem = T / NS;
+      const int R = WarpPlan<T>::R2 != 0 ? WarpPlan<T>::R2 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
+      for (int idx = tid; idx < (R - 1) * NS; idx += NT) {
+        const int m = idx / NS + 1, jm = idx % NS;
+        tw[(NS - R1) + idx] = a.tw_t[jm * m * (T / (NS * R))];
+      }
+      NS *= R;
+    }
+  }
+  uint32_t band = 0;
+  {
+    constexpr int RL = Lw::RL, NBL = T / RL;
+#pragma unroll
+    for (int it = 0; it < Lw::ITL; ++it)
+#pragma unroll
+      for (int m = 0; m < RL; ++m) {
+        const uint32_t k = uint32_t(jl + LP * it + m * NBL);
+        if (k - a.klo <= a.khi - a.klo) band |= 1u << (it * RL + m);
+      }
+  }
+  const bool lower = a.khi < uint32_t(T / 2);
+  for (int b = 0; item < nitem; item += gridDim.x, b ^= 1) {
+    const uint32_t next = item + gridDim.x;
+    // the other buffer was released by the barrier that ended the previous item
+    if (next < nitem) {
+      fetch(next, b ^ 1);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();  // every thread's copies of this item landed
+    const uint32_t w = item / ntile, p0 = (item % ntile) * BT;
+    MomAcc acc{band, 0.f, 0.f, 0.f};
+    float2* row = rows0 + b * BT * WR + px * WR;
+    warp_fft<T, 1, LP, true>(row, row, tw, jl, acc, lower);
+#pragma unroll
+    for (int o = LP / 2; o > 0; o >>= 1) {
+      acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
+      acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
+      acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
+    }
+    if constexpr (POST) {
+      emit_moments(a, w, p0 + px, acc, jl == 0, true);
+    } else if (jl == 0) {
+      const float m1 = acc.m1 * a.fscale, m2 = acc.m2 * (a.fscale * a.fscale);  // bins -> kHz
+      float* o = a.out + size_t(w) * a.nout * HW + p0 + px;
+      int q = 0;
+      if (a.mask & HV_MOM_M0) __stcs(&o[HW * q++], acc.m0);
+      if (a.mask & HV_MOM_M1) __stcs(&o[HW * q++], m1);
+      if (a.mask & HV_MOM_M2) __stcs(&o[HW * q++], m2);
+      const double d0 = acc.m0;
+      if (a.mask & HV_MOM_M1N) __stcs(&o[HW * q++], d0 > 0.0 ? float(double(m1) / d0) : 0.f);
+      if (a.mask & HV_MOM_M2N) {
+        const double r = d0 > 0.0 ? double(m2) / d0 : 0.0;
+        __stcs(&o[HW * q++], float(sqrt(r > 0.0 ? r : 0.0)));
+      }
+    }
+    __syncthreads();  // every warp is done with this buffer before it is refilled
+  }
+}
+
 // cuTensorMapEncodeTiled from the driver (resolved once through the runtime)
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -712,6 +819,25 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
       kern<<<unsigned(grid), Wc::NT, smem, s>>>(a);
       return cudaGetLastError();
     };
+    if (a.kernel == STFT_PIPE) {
+      using Wc = WinCfg<T, false>;
+      if (hw % Wc::BT == 0) {
+        const size_t smem = 2 * size_t(Wc::BT) * Wc::WR * sizeof(float2) + (T - WarpPlan<T>::R1) * sizeof(float2);
+        auto kern = a.post_ring ? k_stft_winp<T, true> : k_stft_winp<T, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        int per_sm = 0, dev = 0, nsm = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Wc::NT, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm >= 1) {
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+          const uint64_t items = uint64_t(a.nwin) * (hw / Wc::BT);
+          const uint64_t grid = std::min<uint64_t>(items, uint64_t(per_sm) * nsm);
+          kern<<<unsigned(grid), Wc::NT, smem, s>>>(a);
+          return cudaGetLastError();
+        }
+      }
+    }
     const cudaError_t e = a.kernel == STFT_WIDE ? launch_win(std::true_type{}) : launch_win(std::false_type{});
     if (e != cudaErrorNotSupported) return e;
   }

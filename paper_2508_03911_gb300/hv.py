@@ -204,7 +204,7 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.spatial_chunk = spatial_chunk
     p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3, "fused": 4}[spatial_kernel]
     p.highpass_cpp = highpass
-    p.stft_kernel = {"auto": 0, "walk": 1, "window": 2, "window_wide": 3}[stft_kernel]
+    p.stft_kernel = {"auto": 0, "walk": 1, "window": 2, "window_wide": 3, "window_pipelined": 4}[stft_kernel]
     return p
 
 

@@ -578,7 +578,7 @@ def test_window_per_cta_stft(T, S, band):
     p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=band[0],
                       band_hi_bin=band[1], moments=ALL_MOMENTS, H=H, W=W)
     ref = O.render(fr, p)
-    for kern in ("window", "window_wide"):
+    for kern in ("window", "window_wide", "window_pipelined"):
         img, st = gpu_render(fr, p, extra=dict(stft_kernel=kern), packets=[T + S, n - T - S])
         check_images(img, ref)
         assert st["windows_rendered"] == ref.shape[0]
@@ -600,7 +600,7 @@ def test_stft_autotuner_times_both_kernels():
         n = r.render(out)  # the settings, and the autotuner, apply here
         torch.cuda.synchronize()
         t = hv.hv_get_tuning(r.h)
-        assert t["stft_kernel"] in (1, 2, 3) and min(t["stft_us_per_window"][:3]) > 0
+        assert t["stft_kernel"] in (1, 2, 3, 4) and min(t["stft_us_per_window"][:4]) > 0
         img = out.cpu().numpy()[: n * 3 * N * N].reshape(n, 3, N, N)
         check_images(img, O.render(fr, p))
     finally:
