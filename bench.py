@@ -537,7 +537,13 @@ def roofline(w, res, peaks):
         "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)"
     tun = res.get("tuning") or {}
     if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64:
-        traffic = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
+        # walking STFT: a launch over 1,024 new frames captured; a launch reads its
+        # new frames and the T - S frames of overlap once, so traffic scales with both
+        v = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
+        if v is not None:
+            ov = w["T"] - w["S"]
+            traffic = int(v * (frames_per_render + ov) / (1024 + ov))
+            traffic_per = "launch of the STFT kernel (1,024-frame ncu capture scaled to the launch's frames)"
     if (t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 512
             and tun.get("stft_kernel") in (2, 3)):
         # window-per-CTA STFT: a 1,024-frame launch captured, traffic in proportion to the frames
