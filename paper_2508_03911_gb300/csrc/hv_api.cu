@@ -376,7 +376,7 @@ hv_status apply_pending(hv_handle* h) {
   const size_t sbytes = size_t(fused ? std::max(chunk, kFusedRing) : chunk) * fbytes;
   if (fused) {
     s = ensure(h, reinterpret_cast<void**>(&h->fused_ctr), &h->fused_ctr_bytes,
-               (1 + 3 * size_t(kFusedRing)) * sizeof(unsigned));
+               (1 + kFusedPasses * size_t(kFusedRing)) * sizeof(unsigned));
     if (s != HV_OK) return s;
   }
   if (p.spatial != HV_SPATIAL_NONE) {
@@ -697,7 +697,7 @@ hv_status tune_spatial(hv_handle* h) {
     if (c.kind == 4 && !fused_ok) continue;
     const uint32_t ch = (c.kind == 2 || c.kind == 4) ? n : std::min(c.chunk, n);
     if (c.kind == 4 && ensure(h, reinterpret_cast<void**>(&h->fused_ctr), &h->fused_ctr_bytes,
-                              (1 + 3 * size_t(kFusedRing)) * sizeof(unsigned)) != HV_OK)
+                              (1 + kFusedPasses * size_t(kFusedRing)) * sizeof(unsigned)) != HV_OK)
       continue;
     if (c.kind != 2) {
       const size_t need = size_t(c.kind == 4 ? kFusedRing : ch) * fbytes;

@@ -42,7 +42,7 @@ struct SpatialArgs {
                         // bit 4: a fused-transform wait for another CTA's pass gave up); may be NULL
   // fused transform (one persistent launch for every pass of every frame, 256 x 256):
   // scratch1 / scratch2 are rings of `ring` frames each, fused_ctr holds
-  // 1 + 3 ring counters (ticket, then per-slot completed strips of each pass)
+  // 1 + kFusedPasses ring counters (ticket, then per-slot completed items of each pass)
   int use_fused;
   uint32_t ring;
   unsigned* fused_ctr;
@@ -55,6 +55,7 @@ cudaError_t launch_spatial_cluster(const SpatialArgs& a, cudaStream_t s, int* la
 // Fused transform: frames of 256 x 256, ASP or Fresnel; needs ring >= kFusedRing
 // frames in scratch1 (and scratch2 for ASP), fused_ctr and err.
 constexpr uint32_t kFusedRing = 96;
+constexpr uint32_t kFusedPasses = 4;  // counter sets: ASP takes four passes, Fresnel two
 bool spatial_fused_supported(const SpatialArgs& a);
 cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* launches);
 

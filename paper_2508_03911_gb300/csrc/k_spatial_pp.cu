@@ -877,19 +877,38 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 // above each run as a launch of their own over a chunk of frames, so their
 // intermediates (S1, S2: 512 KB per frame) go through HBM once written and once
 // read. Here work items come in a fixed global order from an atomic ticket
-// counter: row r of the order holds the column items of pass 1 of frame r, the 16
-// strips of pass 2 of frame r - LAG and (ASP) of pass 3 of frame r - 2 LAG. A
-// Fresnel column item transforms 16 columns (the chirped input is complex); an
-// ASP one 32 real columns, packed in pairs as the real and imaginary parts of 16
-// complex lines whose spectra Z are separated after the transform (for real a and
-// b, z = a + i b: A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / 2i),
-// so that a frame takes 8 column items instead of 16. S1 and S2 are rings of RING
-// frames that stay in L2. An item may start once the counters that make its input
-// complete and its output slot free have been published:
-//   pass 1 of f: the 16 row-pass items of f - RING have read S1 slot f mod RING
-//   pass 2 of f: the column items of f wrote S1 slot; (ASP) the 16 column-IFFT
-//                items of f - RING have read S2 slot
-//   pass 3 of f: the 16 row-pass items of f wrote S2 slot
+// counter: row r of the order holds the column items of frame r and the items of
+// each later pass of frame r - (the lags up to that pass). A Fresnel frame takes two passes of 16
+// items: 16 chirped (complex) columns per column item, 16 rows per row item,
+// the row FFT writing the time queue. ASP takes four passes, using that the
+// hologram is real:
+//   1. 8 column items of 32 real columns, packed in pairs as the real and
+//      imaginary parts of 16 complex lines whose spectra Z are separated after
+//      the transform (for real a and b, z = a + i b: A(k) = (Z(k) + conj Z(-k)) / 2,
+//      B(k) = (Z(k) - conj Z(-k)) / 2i). Only bins ky = 1 .. 127 are stored, row
+//      by row, with the real rows ky = 0 and 128 packed into row 0 as
+//      S1(0, x) + i S1(128, x): the other half is their conjugate.
+//   2. 8 row items over S1 rows 0 .. 127: the forward row FFT W(ky, .) is kept
+//      in the second half of the S1 slot (S3), then x H(ky) and the inverse row
+//      FFT give S2 rows 0 .. 127 (row 0 takes W(0) = (Wp(k) + conj Wp(-k)) / 2
+//      from the packed row's transform Wp).
+//   3. 8 mirror items: the spectrum of row ky in 128 .. 255 is
+//      conj W(256 - ky, -kx) (row 128: (Wp(k) - conj Wp(-k)) / 2i), read from S3;
+//      x H(ky) and the inverse row FFT give S2 rows 128 .. 255. A frame takes
+//      128 forward row FFTs instead of 256.
+//   4. 16 column-IFFT items of 16 columns of S2 write the time queue.
+// S1 (with S3) and S2 are rings of RING frames that stay in L2. An item may start
+// once the counters that make its input complete and its output slot free have
+// been published (P1 .. P4 the ASP passes above; each chain of release adds and
+// acquire loads orders what it covers, so a condition implied through an
+// earlier item's wait is not checked again):
+//   P1 of f: the P2 items of f - RING have read S1 slot f mod RING
+//   P2 of f: P1 of f wrote S1; the P4 items of f - RING have read S2 (and so the
+//            P3 items of f - RING have read S3)
+//   P3 of f: P2 of f wrote S3 (and so P4 of f - RING has read S2)
+//   P4 of f: P3 of f wrote S2 (and so P2 of f did)
+// and for Fresnel: column items of f after the row items of f - RING, row items
+// of f after the column items of f.
 // A CTA is warp-specialised: one producer thread takes the tickets, waits (bounded
 // spin on acquire loads) for each item's counters, stages its input strip into
 // one of two buffers with one copy (a TMA tensor copy, or a 1-D bulk copy)
@@ -898,7 +917,7 @@ static cudaError_t pass_by_len(const SpatialArgs& a, cudaStream_t s) {
 // staged strip while the next one streams in. The producer readies the following
 // item (ticket and counters) while the consumers still hold both buffers, so its
 // copy starts as soon as one frees. Every wait is on an item with a smaller
-// ticket (RING > LAG), a CTA takes its items in ticket order, and the producer
+// ticket (RING > 2 LAG), a CTA takes its items in ticket order, and the producer
 // publishes finished items from inside each of its waits, so the item with the
 // smallest unfinished ticket always completes: the launch ends. Raw frames are read with an evict-first L2
 // policy and the propagated frames stored with streaming stores, so that the two
@@ -912,13 +931,21 @@ constexpr int FZ_THREADS = FZ_NT + 32;
 // ticket held but not worked on delays the frames that wait for it (fetching one
 // ahead measured 1.5 % slower, lags of 40 and 56 rows 1-2 % slower)
 constexpr int FZ_LAG = 48;
+// ASP runs four passes of 8, 8, 8 and 16 items per frame (the row pass split into
+// the rows it transforms forward and the rows it takes as mirrors), so 40 items
+// per ticket row; FZ_LAG_ASP1 rows from the column pass to the row pass, then
+// FZ_LAG_ASP between the later passes. The rings must outlast the two later lags
+// (the row pass of frame f + R waits for the column IFFT of f)
+constexpr int FZ_LAG_ASP1 = 36;
+constexpr int FZ_LAG_ASP = 36;
 constexpr int FZ_BAR = 1;        // named barrier of the consumer warps
 constexpr size_t FZ_FRAME = size_t(RW_L) * RW_L;  // complex values per frame
 constexpr size_t FZ_BUF = size_t(256) * 16;       // complex values per buffer
 constexpr size_t FZ_RAW = 256 * 64;               // bytes of a raw strip (32 uint16 columns), in the buffer's tail
 // every wait is on a smaller ticket when the rings are longer than the lag; the
 // headroom above it keeps column items from waiting for a slot to be freed
-static_assert(kFusedRing > FZ_LAG, "the rings must outlast the lag between passes");
+static_assert(kFusedRing > FZ_LAG && kFusedRing > FZ_LAG_ASP1 && kFusedRing > 2 * FZ_LAG_ASP,
+              "the rings must outlast the lags between passes");
 // shared memory: pass twiddles (256), row-FFT stage-2 twiddles (240), Fresnel
 // chirp along y (256), two buffers of 16 lines x 256 (the column passes' lines
 // fastest with row stride 16, the row tile 16 x 256; a raw strip lands in the
@@ -955,6 +982,29 @@ struct FzItem {
   uint32_t pass, frame, strip;
 };
 
+// 256-point FFT of a row held by 16 lanes (lane jl: elements jl + 16 m in v[m]) as
+// 16 x 16: the 16-point DFTs over m, a transpose through the row's shared buffer
+// (XOR-swizzled), twiddles, the 16-point DFTs over the lanes' first digits. Bin
+// jl + 16 m ends in v[m]. DIR -1 forward, +1 inverse (unscaled).
+template <int DIR>
+__device__ __forceinline__ void row_fft16x16(float2 (&v)[16], float2* rowp, const float2* tw2, int jl) {
+  dft<16, DIR>(v);
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) rowp[16 * jl + (m ^ jl)] = v[m];
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    v[m] = rowp[16 * m + (jl ^ m)];
+    if (m > 0) {
+      float2 w = tw2[(m - 1) * 16 + jl];
+      if (DIR > 0) w.y = -w.y;
+      v[m] = cmul(v[m], w);
+    }
+  }
+  dft<16, DIR>(v);
+}
+
 __global__ void __launch_bounds__(FZ_THREADS, 3)
     k_spatial_fused(SpatialArgs a, uint32_t nticket, const __grid_constant__ CUtensorMap raw_map,
                     const __grid_constant__ CUtensorMap s2_map) {
@@ -974,8 +1024,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool asp = a.spatial == HV_SPATIAL_ASP;
   const bool u8 = a.in_kind == IN_U8;
-  // column items per frame (32 packed columns each for ASP, else 16), items per ticket row
-  const uint32_t n0 = asp ? 8u : 16u, npass = asp ? 3u : 2u, ipr = n0 + 16u * (npass - 1), R = a.ring;
+  // items per ticket row (ASP: 8 + 8 + 8 + 16, Fresnel: 16 + 16), rows between passes
+  const uint32_t ipr = asp ? 40u : 32u, R = a.ring;
   for (int e = tid; e < 256; e += FZ_THREADS) {
     tws[e] = __ldg(&a.tw_h[e]);
     cys[e] = asp ? make_float2(1.f, 0.f) : __ldg(&a.chirp_y[e]);
@@ -1034,9 +1084,10 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
         const uint32_t t = atomicAdd(a.fused_ctr, 1u);
         if (t >= nticket) return false;
         const uint32_t row = t / ipr, kk = t % ipr;
-        pass = kk < n0 ? 0u : 1u + (kk - n0) / 16u;
-        strip = kk < n0 ? kk : (kk - n0) % 16u;
-        const long long fl = (long long)row - (long long)pass * FZ_LAG;
+        pass = asp ? (kk < 24u ? kk >> 3 : 3u) : kk >> 4;
+        strip = asp ? (kk < 24u ? kk & 7u : kk - 24u) : kk & 15u;
+        const uint32_t off = !asp ? pass * FZ_LAG : pass == 0 ? 0u : FZ_LAG_ASP1 + (pass - 1) * FZ_LAG_ASP;
+        const long long fl = (long long)row - (long long)off;
         if (fl >= 0 && fl < (long long)a.n) {
           f = uint32_t(fl);
           break;
@@ -1046,10 +1097,12 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
       const long long t0 = clock64();
       while (true) {
         bool ready;
-        if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 16u * gen;
-        else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= n0 * (gen + 1) &&
-                                    (!asp || ld_acquire_u32(&done[2 * R + slot]) >= 16u * gen);
-        else ready = ld_acquire_u32(&done[R + slot]) >= 16u * (gen + 1);
+        if (!asp) ready = pass == 0 ? ld_acquire_u32(&done[R + slot]) >= 16u * gen
+                                    : ld_acquire_u32(&done[slot]) >= 16u * (gen + 1);
+        else if (pass == 0) ready = ld_acquire_u32(&done[R + slot]) >= 8u * gen;
+        else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 8u * (gen + 1) &&
+                                    ld_acquire_u32(&done[3 * R + slot]) >= 16u * gen;
+        else ready = ld_acquire_u32(&done[(pass - 1) * R + slot]) >= 8u * (gen + 1);
         drain(issued, false);
         if (ready) break;
         if ((*reinterpret_cast<const volatile unsigned*>(a.err) & 16u) || clock64() - t0 > limit) {
@@ -1079,6 +1132,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
       // generic stores, fenced for the async proxy before their publication; this
       // thread acquired the counters that published them.
       const uint32_t s0 = it.strip * (it.pass == 0 && asp ? 32u : 16u), slot = it.frame % R;
+      const float2* s1 = a.scratch1 + size_t(slot) * FZ_FRAME;
       desc[b] = it;
       const uint32_t fb = rw_smem(&full[b]);
       if (it.pass == 0) {
@@ -1091,15 +1145,25 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
             "l"(reinterpret_cast<uint64_t>(&raw_map)), "r"(int(s0)), "r"(int(rslot * 256u)), "r"(fb),
             "l"(pol_first)
             : "memory");
-      } else if (it.pass == 1) {
-        const float2* src = a.scratch1 + size_t(slot) * FZ_FRAME + size_t(s0) * 256;
+      } else if (it.pass == 1 || (asp && it.pass == 2)) {
+        // 16 rows of S1 (row pass), or (mirror pass) the S3 rows 256 - r of its
+        // output rows r = 143 + s0 - b, b = 0 .. 15: rows 113 - s0 .. 128 - s0; the
+        // first strip's last row (r = 128) is the packed row S3(0)
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
+        const float2* src = it.pass == 1 ? s1 + size_t(s0) * 256 : s1 + size_t(128 + 113 - s0) * 256;
+        const uint32_t bytes = it.pass == 2 && s0 == 0 ? 15u * 2048u : 32768u;
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                 rw_smem(bufs + b * FZ_BUF)),
-            "l"(src), "r"(32768u), "r"(fb)
+            "l"(src), "r"(bytes), "r"(fb)
             : "memory");
+        if (bytes != 32768u)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                  rw_smem(bufs + b * FZ_BUF + 15 * 256)),
+              "l"(s1 + size_t(128) * 256), "r"(2048u), "r"(fb)
+              : "memory");
       } else {
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(32768u) : "memory");
@@ -1148,8 +1212,9 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
       const GlobalOut out{s1 + s0, 256u};
       if (asp) {
         // column FFT of 32 real raw columns, packed in pairs (conversion in the first
-        // stage), spectra Z of the 16 lines into the buffer [k][line]; then for bins
-        // k <= 128 the two columns' spectra A, B at k and (conjugate) at -k -> S1 [ky][x]
+        // stage), spectra Z of the 16 lines into the buffer [k][line]; then the two
+        // columns' spectra A, B at bins 1 .. 127 -> S1 [ky][x], and at the real bins 0
+        // and 128 packed as A(0) + i A(128), B(0) + i B(128) -> S1 row 0
         if (u8) pp_stages<256, 1, -1, PackedRawSrc<true>, SmemOut<16>, 16, FZ_BAR>(PackedRawSrc<true>{raw}, buf,
                                                                                     tws, SmemOut<16>{buf});
         else pp_stages<256, 1, -1, PackedRawSrc<false>, SmemOut<16>, 16, FZ_BAR>(PackedRawSrc<false>{raw}, buf,
@@ -1157,13 +1222,18 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
         pp_sync<FZ_BAR, FZ_NT>();
         const int line = tid % 16;
         float4* o = reinterpret_cast<float4*>(s1 + s0 + 2 * line);  // columns 2 line, 2 line + 1
-#pragma unroll 3
-        for (int k = tid / 16; k <= 128; k += FZ_NT / 16) {
-          const float2 z = buf[k * 16 + line], w = buf[((256 - k) & 255) * 16 + line];  // Z(k), Z(-k)
-          const float ax = 0.5f * (z.x + w.x), ay = 0.5f * (z.y - w.y);  // A(k) = (Z + conj W) / 2
-          const float bx = 0.5f * (z.y + w.y), by = 0.5f * (w.x - z.x);  // B(k) = (Z - conj W) / 2i
-          o[size_t(k) * 128] = make_float4(ax, ay, bx, by);
-          if (k != 0 && k != 128) o[size_t(256 - k) * 128] = make_float4(ax, -ay, bx, -by);  // X(-k) = conj X(k)
+#pragma unroll
+        for (int k = tid / 16; k < 128; k += FZ_NT / 16) {
+          const float2 z = buf[k * 16 + line];  // Z(k)
+          if (k == 0) {
+            const float2 h = buf[128 * 16 + line];  // Z(128): A(128) = Re, B(128) = Im
+            o[0] = make_float4(z.x, h.x, z.y, h.y);
+          } else {
+            const float2 w = buf[(256 - k) * 16 + line];                    // Z(-k)
+            const float ax = 0.5f * (z.x + w.x), ay = 0.5f * (z.y - w.y);  // A(k) = (Z + conj W) / 2
+            const float bx = 0.5f * (z.y + w.y), by = 0.5f * (w.x - z.x);  // B(k) = (Z - conj W) / 2i
+            o[size_t(k) * 128] = make_float4(ax, ay, bx, by);
+          }
         }
       } else {
         // column FFT of 16 raw columns (conversion and chirp in the first stage) -> S1 [ky][x]
@@ -1173,61 +1243,87 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
         else pp_stages<256, 1, -1, RawSrc<false, true, 16, true>, GlobalOut, 16, FZ_BAR>(
                  RawSrc<false, true, 16, true>{raw, cys, cx}, buf, tws, out);
       }
-    } else if (pass == 1) {
-      // 16 rows ky = s0 .. s0 + 15 of S1 -> row FFT [x H, row IFFT]; the staged strip of
-      // S1 is dead: drop its L2 lines unwritten
-      asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s1 + size_t(s0) * 256 + size_t(tid) * 16) : "memory");
-      float2* rowp = buf + rb * 256;
-      const int ky = int(s0) + rb;
-      float2 v[16];
-#pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = rowp[jl + 16 * m];
-      dft<16, -1>(v);
-      __syncwarp();
-#pragma unroll
-      for (int m = 0; m < 16; ++m) rowp[16 * jl + (m ^ jl)] = v[m];
-      __syncwarp();
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        v[m] = rowp[16 * m + (jl ^ m)];
-        if (m > 0) v[m] = cmul(v[m], tw2[(m - 1) * 16 + jl]);
-      }
-      dft<16, -1>(v);
+    } else if (pass == 3 || (pass == 1 && !asp)) {
       if (asp) {
-        const float2* hrow = a.asp_h + size_t(ky) * 256;
-#pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], __ldg(&hrow[jl + 16 * m]));
-        dft<16, +1>(v);
-        __syncwarp();
-#pragma unroll
-        for (int m = 0; m < 16; ++m) rowp[16 * jl + (m ^ jl)] = v[m];
-        __syncwarp();
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          v[m] = rowp[16 * m + (jl ^ m)];
-          if (m > 0) {
-            float2 w = tw2[(m - 1) * 16 + jl];
-            w.y = -w.y;
-            v[m] = cmul(v[m], w);
-          }
-        }
-        dft<16, +1>(v);
-        float2* out = s2 + size_t(ky) * 256;  // S2 [ky][x]
-#pragma unroll
-        for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
+        // column IFFT of 16 columns x = s0 .. s0 + 15 of S2 -> time queue [y][x]
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s2 + s0 + size_t(tid) * 256) : "memory");
+        pp_stages<256, 1, +1, SmemSrc<16>, GlobalOutCs, 16, FZ_BAR>(SmemSrc<16>{buf}, buf, tws,
+                                                                    GlobalOutCs{tq + tslot * FZ_FRAME + s0, 256u});
       } else {
-        float2* out = tq + (tslot * 256 + size_t(ky)) * 256;  // time queue [ky][kx]
+        // 16 rows ky = s0 .. s0 + 15 of S1 -> row FFT -> time queue [ky][kx]
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s1 + size_t(s0) * 256 + size_t(tid) * 16) : "memory");
+        float2* rowp = buf + rb * 256;
+        float2 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = rowp[jl + 16 * m];
+        row_fft16x16<-1>(v, rowp, tw2, jl);
+        float2* out = tq + (tslot * 256 + size_t(s0 + rb)) * 256;
 #pragma unroll
         for (int m = 0; m < 16; ++m) __stcs(&out[jl + 16 * m], v[m]);
       }
     } else {
-      // column IFFT of 16 columns x = s0 .. s0 + 15 of S2 -> time queue [y][x]
-      asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s2 + s0 + size_t(tid) * 256) : "memory");
-      pp_stages<256, 1, +1, SmemSrc<16>, GlobalOutCs, 16, FZ_BAR>(SmemSrc<16>{buf}, buf, tws,
-                                                                  GlobalOutCs{tq + tslot * FZ_FRAME + s0, 256u});
+      float2* rowp = buf + rb * 256;
+      float2 v[16];
+      int ky;
+      if (pass == 1) {
+        // rows ky = s0 .. s0 + 15 of S1 (row 0 packed with row 128): forward row FFT,
+        // kept in S3 for the mirror pass; the staged strip of S1 is dead: drop its
+        // L2 lines unwritten
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(s1 + size_t(s0) * 256 + size_t(tid) * 16) : "memory");
+        ky = int(s0) + rb;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = rowp[jl + 16 * m];
+        row_fft16x16<-1>(v, rowp, tw2, jl);
+        float2* w3 = s1 + size_t(128 + ky) * 256;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) w3[jl + 16 * m] = v[m];
+        if (s0 == 0 && warp == 0) {
+          // row 0: W(0, k) = (Wp(k) + conj Wp(-k)) / 2 through the row's buffer
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < 16; ++m) rowp[jl + 16 * m] = v[m];
+          __syncwarp();
+          if (rb == 0) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+              const float2 w = rowp[(256 - jl - 16 * m) & 255];
+              v[m] = make_float2(0.5f * (v[m].x + w.x), 0.5f * (v[m].y - w.y));
+            }
+          }
+        }
+      } else {
+        // mirror rows ky = 143 + s0 - b of buffer row b, spectrum conj W(256 - ky, -kx);
+        // row 128 from the packed row: W(128, k) = (Wp(k) - conj Wp(-k)) / 2i. The
+        // staged rows of S3 are dead (16 threads a row; the first strip's last 16
+        // threads reach S3 row 0 from 15 rows before it)
+        const float2* w3 = s1 + size_t(s0 == 0 && tid >= 240 ? 128 - 15 : 128 + 113 - s0) * 256;
+        asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(w3 + size_t(tid) * 16) : "memory");
+        ky = 143 + int(s0) - rb;
+        if (ky == 128) {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float2 z = rowp[jl + 16 * m], w = rowp[(256 - jl - 16 * m) & 255];
+            v[m] = make_float2(0.5f * (z.y + w.y), 0.5f * (w.x - z.x));
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float2 w = rowp[(256 - jl - 16 * m) & 255];
+            v[m] = make_float2(w.x, -w.y);
+          }
+        }
+      }
+      // x H(ky), inverse row FFT -> S2 [ky][x]
+      const float2* hrow = a.asp_h + size_t(ky) * 256;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = cmul(v[m], __ldg(&hrow[jl + 16 * m]));
+      row_fft16x16<+1>(v, rowp, tw2, jl);
+      float2* out = s2 + size_t(ky) * 256;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) out[jl + 16 * m] = v[m];
     }
     // the ring stores are read back by bulk copies (the async proxy) of other CTAs
-    if (pass == 0 || (pass == 1 && asp)) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    if (pass == 0 || (asp && pass < 3)) asm volatile("fence.proxy.async.global;\n" ::: "memory");
     // every consumer is done with the buffer and has issued the item's stores
     pp_sync<FZ_BAR, FZ_NT>();
     if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&freed[b])) : "memory");
@@ -1281,11 +1377,11 @@ bool spatial_fused_supported(const SpatialArgs& a) {
 cudaError_t launch_spatial_fused(const SpatialArgs& a, cudaStream_t s, int* launches) {
   if (a.n == 0) return cudaSuccess;
   if (!spatial_fused_supported(a)) return cudaErrorInvalidValue;
-  const uint32_t npass = a.spatial == HV_SPATIAL_ASP ? 3u : 2u;
-  const uint32_t ipr = (a.spatial == HV_SPATIAL_ASP ? 8u : 16u) + 16u * (npass - 1);  // items per ticket row
-  const uint64_t nt = (uint64_t(a.n) + uint64_t(npass - 1) * FZ_LAG) * ipr;
+  const bool asp = a.spatial == HV_SPATIAL_ASP;
+  // ticket rows: one per frame plus the lags of the last pass; items per row
+  const uint64_t nt = (uint64_t(a.n) + (asp ? FZ_LAG_ASP1 + 2u * FZ_LAG_ASP : FZ_LAG)) * (asp ? 40u : 32u);
   if (nt >= (1ull << 31)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(a.fused_ctr, 0, (1 + 3 * size_t(a.ring)) * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(a.fused_ctr, 0, (1 + kFusedPasses * size_t(a.ring)) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_spatial_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(FZ_SMEM));
   if (e != cudaSuccess) return e;
