@@ -1038,7 +1038,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
     for (int b = 0; b < 2; ++b) {
       // full: the producer's arrival with the item's byte count, completed by its copy
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&full[b])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(rw_smem(&freed[b])) : "memory");
+      // freed: one arrival per consumer warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(rw_smem(&freed[b])), "n"(FZ_NT / 32) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -1324,9 +1325,11 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
     }
     // the ring stores are read back by bulk copies (the async proxy) of other CTAs
     if (pass == 0 || (asp && pass < 3)) asm volatile("fence.proxy.async.global;\n" ::: "memory");
-    // every consumer is done with the buffer and has issued the item's stores
-    pp_sync<FZ_BAR, FZ_NT>();
-    if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&freed[b])) : "memory");
+    // this warp is done with the buffer and has issued its stores: each warp releases
+    // the buffer on its own and goes on to the next staged item (a column pass's
+    // named barriers keep the warps in step within an item)
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(rw_smem(&freed[b])) : "memory");
   }
 }
 
