@@ -425,11 +425,29 @@ def run_hv(args, w, rank, world, dist, tuned=1, quick=False):
     e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e_value = job_value(world, e2e_steps, frames_per_step, e2e_s)
     r2.close()
+    # the host link's own rate for comparison: plain pinned host-to-device copies of
+    # the same pool (best of three, CUDA events), outside the timed region
+    link = torch.empty(host_pool.shape, dtype=host_pool.dtype, device=dev)
+    link_gbs = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            link.copy_(host_pool, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            link_gbs = max(link_gbs, host_pool.numel() * host_pool.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del link
 
     out = dict(value=value, elapsed_ms=elapsed_ms, lat_ms=lat_ms, prof=prof, launches=launches,
                 clocks=clk, e2e=dict(value=e2e_value, unit="frames/s",
                                      h2d_bytes_per_step=h2d // e2e_steps,
-                                     d2h_bytes_per_step=d2h // e2e_steps),
+                                     d2h_bytes_per_step=d2h // e2e_steps,
+                                     h2d_gbs=round(h2d / e2e_s / 1e9, 1),
+                                     host_link_h2d_gbs=round(link_gbs, 1),
+                                     what=("pinned frames pushed (HV_MEM_HOST_ASYNC), images read back; "
+                                           "h2d_gbs is the frames' rate over the host link, "
+                                           "host_link_h2d_gbs that of plain pinned copies of the same pool")),
                 frames_per_step=frames_per_step, tuning=tuning)
     if library:
         out["library"] = library
