@@ -251,6 +251,20 @@ hv_status hv_profile_read(hv_handle* h, hv_profile* out);
  * and the images of that launch are not valid. */
 hv_status hv_synchronize(hv_handle* h);
 
+/* Fault injection for tests of that failure path (no part of the method; the
+ * paper's own guard is backpressure, Sec. III). what = HV_INJECT_FUSED_STALL:
+ * the next launch of the fused 256 x 256 spatial transform of this handle makes
+ * its row items wait on a condition that nothing sets, as if another CTA's pass
+ * never finished. The producers' bounded waits give up (about 2^31 SM clocks, a
+ * second), every CTA returns, the launch ends, and the next hv_synchronize
+ * returns HV_ERR_CUDA; the device flags stay set, so the handle is to be closed.
+ * Nothing faults, traps or hangs. The injection waits for the next fused launch
+ * (the autotuner's timing launches included); HV_INJECT_NONE cancels it.
+ * HV_ERR_ARG for another value of `what`. */
+#define HV_INJECT_NONE 0
+#define HV_INJECT_FUSED_STALL 1
+hv_status hv_debug_inject(hv_handle* h, int what);
+
 /* Free every resource of the handle. NULL is accepted (no-op). */
 hv_status hv_close(hv_handle* h);
 

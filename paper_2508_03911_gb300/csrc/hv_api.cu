@@ -60,6 +60,7 @@ struct hv_handle {
   int sp_cluster = 0;         // 1: whole-frame cluster kernel
   int sp_pp = 0;              // 1: persistent multi-pass kernels
   int sp_fused = 0;           // 1: fused transform (s1 / s2 are rings of kFusedRing frames)
+  int inject = HV_INJECT_NONE;  // pending fault injection (hv_debug_inject)
   int stft_kernel = STFT_AUTO;  // STFT kernel for windows that do not overlap (autotuner's choice)
   unsigned* fused_ctr = nullptr;  // its ticket and per-slot counters
   size_t fused_ctr_bytes = 0;
@@ -625,6 +626,10 @@ hv_status propagate_run(hv_handle* h, uint64_t r0, uint64_t r1, RingRef raw) {
     sa.use_fused = h->sp_fused;
     sa.ring = kFusedRing;
     sa.fused_ctr = h->fused_ctr;
+    if (h->inject == HV_INJECT_FUSED_STALL && sa.use_fused && spatial_fused_supported(sa)) {
+      sa.stall = 1;
+      h->inject = HV_INJECT_NONE;
+    }
     int launches = 0;
     cudaError_t e = launch_spatial(sa, h->stream, &launches);
     h->st.kernel_launches += launches;
@@ -1390,6 +1395,13 @@ hv_status hv_synchronize(hv_handle* h) {
   HV_CU(h, cudaMemcpy(&flags, h->dev_err, sizeof(flags), cudaMemcpyDeviceToHost));
   if (flags != 0)
     return fail(h, HV_ERR_CUDA, "a kernel's bounded wait gave up (device flags " + std::to_string(flags) + ")");
+  return HV_OK;
+}
+
+hv_status hv_debug_inject(hv_handle* h, int what) {
+  if (!h) return HV_ERR_ARG;
+  if (what != HV_INJECT_NONE && what != HV_INJECT_FUSED_STALL) return fail(h, HV_ERR_ARG, "bad injection");
+  h->inject = what;
   return HV_OK;
 }
 

@@ -46,6 +46,7 @@ struct SpatialArgs {
   int use_fused;
   uint32_t ring;
   unsigned* fused_ctr;
+  int stall;            // fault injection (tests): the fused row items wait on a condition nothing sets
 };
 cudaError_t launch_spatial(const SpatialArgs& a, cudaStream_t s, int* launches);
 bool spatial_cluster_supported(const SpatialArgs& a);

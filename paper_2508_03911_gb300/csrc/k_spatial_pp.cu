@@ -1104,6 +1104,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 3)
         else if (pass == 1) ready = ld_acquire_u32(&done[slot]) >= 8u * (gen + 1) &&
                                     ld_acquire_u32(&done[3 * R + slot]) >= 16u * gen;
         else ready = ld_acquire_u32(&done[(pass - 1) * R + slot]) >= 8u * (gen + 1);
+        if (a.stall && pass == 1) ready = false;  // fault injection: a condition nothing sets
         drain(issued, false);
         if (ready) break;
         if ((*reinterpret_cast<const volatile unsigned*>(a.err) & 16u) || clock64() - t0 > limit) {

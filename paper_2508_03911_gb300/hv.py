@@ -24,6 +24,7 @@ HV_SPATIAL_NONE, HV_SPATIAL_ASP, HV_SPATIAL_FRESNEL = 0, 1, 2
 HV_TEMPORAL_STFT, HV_TEMPORAL_PCA, HV_TEMPORAL_NONE = 0, 1, 2
 HV_MOM_M0, HV_MOM_M1, HV_MOM_M2, HV_MOM_M1N, HV_MOM_M2N = 1, 2, 4, 8, 16
 HV_PREC_FP32, HV_PREC_BF16, HV_PREC_SPLIT_BF16 = 0, 1, 2
+HV_INJECT_NONE, HV_INJECT_FUSED_STALL = 0, 1
 
 STATUS_NAMES = {0: "HV_OK", -1: "HV_ERR_ARG", -2: "HV_ERR_STATE", -3: "HV_ERR_QUEUE_FULL",
                 -4: "HV_ERR_NOMEM", -5: "HV_ERR_CUDA", -6: "HV_ERR_TIMEOUT",
@@ -127,6 +128,7 @@ def lib() -> C.CDLL:
         "hv_get_stats": ([C.c_void_p, P(hv_stats)], C.c_int),
         "hv_get_tuning": ([C.c_void_p, P(hv_tuning)], C.c_int),
         "hv_synchronize": ([C.c_void_p], C.c_int),
+        "hv_debug_inject": ([C.c_void_p, C.c_int], C.c_int),
         "hv_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
         "hv_profile_read": ([C.c_void_p, P(hv_profile)], C.c_int),
         "hv_close": ([C.c_void_p], C.c_int),
@@ -297,6 +299,10 @@ def hv_get_tuning(h) -> dict:
 
 def hv_synchronize(h):
     _check(h, lib().hv_synchronize(h))
+
+
+def hv_debug_inject(h, what: int):
+    _check(h, lib().hv_debug_inject(h, what))
 
 
 def hv_close(h):

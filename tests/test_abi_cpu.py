@@ -37,6 +37,7 @@ def test_version_and_null_handling():
     n = ctypes.c_uint32(7)
     assert L.hv_render(None, None, 0, 0, ctypes.byref(n)) == hv.HV_ERR_ARG
     assert L.hv_get_stats(None, None) == hv.HV_ERR_ARG
+    assert L.hv_debug_inject(None, hv.HV_INJECT_FUSED_STALL) == hv.HV_ERR_ARG
 
 
 def test_open_rejects_bad_descriptor_without_touching_a_device():

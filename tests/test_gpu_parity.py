@@ -549,6 +549,51 @@ def test_fused_rejects_other_sizes():
         r.close()
 
 
+def test_fused_stall_is_reported_and_the_context_stays_usable():
+    """Failure path of the fused transform's device waits, by fault injection (no
+    GPU fault): the row items of one launch wait on a condition that nothing sets.
+    The producers' bounded waits give up after about a second, every CTA returns,
+    and hv_synchronize reports HV_ERR_CUDA. The launch before it on the same handle
+    was exact, and a new handle on the same context renders exact fields after it."""
+    import time
+    import torch
+    N, n = 256, 40
+    fr = synth.random_frames(2 * n, N, N, 16, seed=437)
+    p = oracle_params(spatial="asp", z_m=0.27, temporal="none", T=1, stride=1, H=N, W=N)
+    dev = to_device(fr)
+    ref = oracle_fields(fr, p)
+    r = hv.Renderer(N, N, 16, 2 * n)
+    try:
+        hv.hv_set_params(r.h, to_hv(p, spatial_kernel="fused"))
+        with pytest.raises(hv.HvError) as ei:
+            hv.hv_debug_inject(r.h, 7)
+        assert ei.value.status == hv.HV_ERR_ARG
+        wf = r.window_floats()
+        out = torch.zeros(2 * n * wf, dtype=torch.float32, device="cuda")
+        assert r.push(dev[:n]) == hv.HV_OK
+        got = 0
+        while (k := r.render(out[got * wf:])) > 0:
+            got += k
+        r.synchronize()
+        img = images_from(out.cpu().numpy(), got, p)
+        for i in range(n):
+            assert rel_l2(img[i], ref[i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[i]))
+        hv.hv_debug_inject(r.h, hv.HV_INJECT_FUSED_STALL)
+        assert r.push(dev[n:]) == hv.HV_OK
+        t0 = time.perf_counter()
+        while (k := r.render(out[got * wf:])) > 0:
+            got += k
+        with pytest.raises(hv.HvError) as ei:
+            r.synchronize()
+        assert ei.value.status == hv.HV_ERR_CUDA and "bounded wait" in str(ei.value)
+        assert time.perf_counter() - t0 < 30
+    finally:
+        r.close()
+    img, _ = gpu_render(fr[n:], p, extra=dict(spatial_kernel="fused"))
+    for i in range(n):
+        assert rel_l2(img[i], ref[n + i]) <= FIELD_TOL, (i, rel_l2(img[i], ref[n + i]))
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("spatial", ["fresnel", "asp"])
 def test_fused_paper_scale_stream_prefix(spatial):
