@@ -653,6 +653,102 @@ def test_stft_autotuner_times_both_kernels():
 
 
 @pytest.mark.slow
+def test_default_bench_configuration_every_pixel():
+    """The default bench workload in the launch configuration bench.py times: its
+    1,024-frame pool of 256x256 12-bit frames tiled to 4,096 on the device, ASP
+    z = 0.30 m, STFT T = S = 512, M0/M1/M2 over 1-35 kHz; two batches pushed in
+    place (HV_MEM_DEVICE_ASYNC) on an explicit stream, the autotuned kernels, every
+    complete window rendered after each push. Each of the 16 windows is one of the
+    pool's two windows: every pixel of every moment against the oracle."""
+    import torch
+
+    import bench
+    w = bench.WORKLOADS[bench.DEFAULT]
+    assert (w["N"], w["bits"], w["spatial"], w["T"], w["S"]) == (256, 12, "asp", 512, 512)
+    pool = bench.make_pool(w, w["pool"])
+    klo, khi = bench.band_bins(w)
+    B = w["batch"]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    pool_dev = torch.from_numpy(pool.view(np.int16)).to(dev).repeat(B // w["pool"], 1, 1).contiguous()
+    torch.cuda.synchronize()
+    r = hv.Renderer(256, 256, 16, 2 * B, stream=stream.cuda_stream)
+    try:
+        r.set_params(256, 256, spatial=w["spatial"], z=w["z"], T=w["T"], stride=w["S"], fs=w["fs"],
+                     band=(klo, khi), moments=w["moments"], tuned=1)
+        wf = r.window_floats()
+        out = torch.zeros((2 * B // w["S"] + 2) * wf, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        got = 0
+        for _ in range(2):
+            assert r.push(pool_dev, async_=True) == hv.HV_OK
+            while (k := r.render(out[got * wf:])) > 0:
+                got += k
+        r.synchronize()
+        tuning = hv.hv_get_tuning(r.h)
+        host = out.cpu().numpy()
+    finally:
+        r.close()
+    assert got == 2 * B // w["S"]
+    assert tuning["tuned"] == 1
+    p = oracle_params(spatial=w["spatial"], z_m=w["z"], T=w["T"], stride=w["S"], fs_hz=w["fs"],
+                      band_lo_bin=klo, band_hi_bin=khi, moments=w["moments"], H=256, W=256)
+    img = images_from(host, got, p)
+    ref = O.render(pool, p)
+    assert ref.shape[0] == 2
+    for i in range(got):
+        check_images(img[i:i + 1], ref[i % 2:i % 2 + 1])
+
+
+@pytest.mark.slow
+def test_paper_scale_stream_bench_configuration_every_pixel():
+    """The paper-scale stream workload in the launch configuration bench.py times:
+    its 1,024-frame pool of 256x256 12-bit frames tiled to 4,096 on the device,
+    Fresnel z = 0.25 m, STFT T = 512, S = 64, M0/M1/M2 over 1-35 kHz; two batches
+    pushed in place on an explicit stream, the autotuned kernels. The stream has
+    period 1,024 frames, so window i equals window i mod 16 of the pool repeated:
+    every pixel of every moment of all 121 windows against the oracle."""
+    import torch
+
+    import bench
+    w = bench.WORKLOADS["stream_fresnel_256_t512_s64"]
+    assert (w["N"], w["bits"], w["spatial"], w["T"], w["S"]) == (256, 12, "fresnel", 512, 64)
+    pool = bench.make_pool(w, w["pool"])
+    klo, khi = bench.band_bins(w)
+    B, T, S = w["batch"], w["T"], w["S"]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    pool_dev = torch.from_numpy(pool.view(np.int16)).to(dev).repeat(B // w["pool"], 1, 1).contiguous()
+    torch.cuda.synchronize()
+    r = hv.Renderer(256, 256, 16, 2 * B, stream=stream.cuda_stream)
+    try:
+        r.set_params(256, 256, spatial=w["spatial"], z=w["z"], T=T, stride=S, fs=w["fs"],
+                     band=(klo, khi), moments=w["moments"], tuned=1)
+        wf = r.window_floats()
+        nwin = (2 * B - T) // S + 1
+        out = torch.zeros((nwin + 2) * wf, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        got = 0
+        for _ in range(2):
+            assert r.push(pool_dev, async_=True) == hv.HV_OK
+            while (k := r.render(out[got * wf:])) > 0:
+                got += k
+        r.synchronize()
+        host = out.cpu().numpy()
+    finally:
+        r.close()
+    assert got == nwin
+    p = oracle_params(spatial=w["spatial"], z_m=w["z"], T=T, stride=S, fs_hz=w["fs"],
+                      band_lo_bin=klo, band_hi_bin=khi, moments=w["moments"], H=256, W=256)
+    img = images_from(host, got, p)
+    period = w["pool"] // S
+    ref = O.render(np.concatenate([pool, pool[:T - S]]), p)
+    assert ref.shape[0] == period
+    for i in range(got):
+        check_images(img[i:i + 1], ref[i % period:i % period + 1])
+
+
+@pytest.mark.slow
 def test_window_per_cta_stft_paper_asp_shape():
     """The paper's ASP + STFT 512/512 shape at 256 x 256 (12-bit, ASP z = 0.30 m,
     M0/M1/M2 over 1-35 kHz at 71.4 kHz) through the fused transform and the
