@@ -1410,7 +1410,8 @@ def main():
     ap.add_argument("--batches", type=int, default=0, help="batches per step (0: the workload's)")
     ap.add_argument("--tq-frames", type=int, default=0,
                     help="time-queue capacity in frames (0: automatic; small for profiling runs)")
-    ap.add_argument("--stft-kernel", choices=["auto", "walk", "window", "window_wide", "window_pipelined"], default="auto",
+    ap.add_argument("--stft-kernel", choices=["auto", "walk", "window", "window_wide", "window_pipelined",
+                                               "window_tma", "window_tma_pipelined"], default="auto",
                     help="fix the STFT kernel for windows that do not overlap instead of autotuning it")
     ap.add_argument("--af-train", type=int, default=50000,
                     help="autofocus workload: training holograms (0: untrained weights, no accuracy block)")
@@ -1511,11 +1512,13 @@ def main():
                            ["mp16", "mp32", "mp64", "mp128", "mp256", "pp64", "pp128", "pp256",
                             "pp512", "cluster", "fused"],
                            [round(v, 4) for v in res["tuning"]["candidate_us_per_frame"][:11]])),
-                       "stft_kernel": {1: "walk", 2: "window", 3: "window_wide", 4: "window_pipelined"}.get(
+                       "stft_kernel": {1: "walk", 2: "window", 3: "window_wide", 4: "window_pipelined",
+                                       5: "window_tma", 6: "window_tma_pipelined"}.get(
                            res["tuning"].get("stft_kernel"), "walk"),
                        "stft_candidates_us_per_window": dict(zip(
-                           ["walk", "window", "window_wide", "window_pipelined"],
-                           [round(v, 3) for v in res["tuning"]["stft_us_per_window"][:4]]))},
+                           ["walk", "window", "window_wide", "window_pipelined", "window_tma",
+                            "window_tma_pipelined"],
+                           [round(v, 3) for v in res["tuning"]["stft_us_per_window"][:6]]))},
         }
         if plain is not None:
             line["forms"] = {"plain": round(plain["value"], 1), "tuned": round(res["value"], 1),

@@ -113,9 +113,15 @@ typedef struct {
   int32_t stft_kernel;        /* STFT kernel for windows that do not overlap (S >= T):
                                  0 = automatic (the autotuner's choice when tuned = 1,
                                  else the walking kernel launched once per window),
-                                 HV_STFT_WALK, HV_STFT_WINDOW, HV_STFT_WINDOW_WIDE or
+                                 HV_STFT_WALK, HV_STFT_WINDOW, HV_STFT_WINDOW_WIDE,
                                  HV_STFT_WINDOW_PIPELINED (persistent CTAs that load
-                                 their next window tile while transforming one)   */
+                                 their next window tile while transforming one),
+                                 HV_STFT_WINDOW_TMA or HV_STFT_WINDOW_TMA_PIPELINED
+                                 (T = 512: a window tile brought in by TMA tensor
+                                 loads and transformed in place; the second
+                                 persistent and double-buffered; at other T, and
+                                 where a window's queue slots wrap, the
+                                 HV_STFT_WINDOW kernel runs instead)              */
   uint32_t reserved;
 } hv_params;
 
@@ -198,24 +204,28 @@ typedef struct {
   int32_t tuned;                    /* 1 once the autotuner has run                   */
   int32_t spatial_kernel;           /* HV_SK_MULTIPASS, _CLUSTER, _PERSISTENT or _FUSED */
   uint32_t spatial_chunk;           /* frames per multi-pass launch                   */
-  int32_t stft_kernel;              /* HV_STFT_WALK, _WINDOW, _WINDOW_WIDE or
-                                       _WINDOW_PIPELINED                              */
+  int32_t stft_kernel;              /* HV_STFT_WALK, _WINDOW, _WINDOW_WIDE,
+                                       _WINDOW_PIPELINED, _WINDOW_TMA or
+                                       _WINDOW_TMA_PIPELINED                          */
   float candidate_us_per_frame[12]; /* measured us per frame: multi-pass with 16, 32, 64,
                                        128, 256 frames per launch; persistent
                                        multi-pass with 64, 128, 256, 512; the cluster
                                        kernel; the fused transform (0 where not
                                        applicable)                                    */
-  float stft_us_per_window[4];      /* measured us per window of the STFT kernels:
+  float stft_us_per_window[6];      /* measured us per window of the STFT kernels:
                                        walking (CTAs walk every window of their
                                        pixels), one CTA per (window, pixel tile), the
                                        same with twice the pixels per CTA, persistent
                                        double-buffered CTAs over the (window, tile)
-                                       items; 0 where not applicable (the last three
-                                       need S >= T)                                   */
+                                       items, the TMA-fed kernel, the same persistent
+                                       and double-buffered; 0 where not applicable
+                                       (all but the first need S >= T, the last two
+                                       T = 512)                                       */
 } hv_tuning;
 
 /* STFT kernels the autotuner chooses between (windows that do not overlap). */
-enum { HV_STFT_WALK = 1, HV_STFT_WINDOW = 2, HV_STFT_WINDOW_WIDE = 3, HV_STFT_WINDOW_PIPELINED = 4 };
+enum { HV_STFT_WALK = 1, HV_STFT_WINDOW = 2, HV_STFT_WINDOW_WIDE = 3, HV_STFT_WINDOW_PIPELINED = 4,
+       HV_STFT_WINDOW_TMA = 5, HV_STFT_WINDOW_TMA_PIPELINED = 6 };
 
 /* The autotuner's choices for the applied settings. Errors: HV_ERR_STATE. */
 hv_status hv_get_tuning(const hv_handle* h, hv_tuning* t);

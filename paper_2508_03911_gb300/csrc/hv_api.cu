@@ -200,7 +200,8 @@ hv_status validate(const hv_handle* h, const hv_params& p, Derived& d, std::stri
   }
   if (p.spatial_kernel > HV_SK_FUSED) { why = "unknown spatial_kernel"; return HV_ERR_ARG; }
   if (p.stft_kernel != 0 && p.stft_kernel != HV_STFT_WALK && p.stft_kernel != HV_STFT_WINDOW &&
-      p.stft_kernel != HV_STFT_WINDOW_WIDE && p.stft_kernel != HV_STFT_WINDOW_PIPELINED) {
+      p.stft_kernel != HV_STFT_WINDOW_WIDE && p.stft_kernel != HV_STFT_WINDOW_PIPELINED &&
+      p.stft_kernel != HV_STFT_WINDOW_TMA && p.stft_kernel != HV_STFT_WINDOW_TMA_PIPELINED) {
     why = "unknown stft_kernel";
     return HV_ERR_ARG;
   }
@@ -531,6 +532,8 @@ hv_status apply_pending(hv_handle* h) {
   h->stft_kernel = p.stft_kernel == HV_STFT_WINDOW ? STFT_AUTO
                    : p.stft_kernel == HV_STFT_WINDOW_WIDE     ? STFT_WIDE
                    : p.stft_kernel == HV_STFT_WINDOW_PIPELINED ? STFT_PIPE
+                   : p.stft_kernel == HV_STFT_WINDOW_TMA       ? STFT_TMA
+                   : p.stft_kernel == HV_STFT_WINDOW_TMA_PIPELINED ? STFT_TMA_PIPE
                                                                : STFT_WALK;
   h->tuning.stft_kernel = p.stft_kernel == 0 ? HV_STFT_WALK : p.stft_kernel;
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
@@ -758,9 +761,11 @@ hv_status tune_spatial(hv_handle* h) {
 }
 
 // Autotuner of the STFT for windows that do not overlap (S >= T): times the
-// walking kernel (CTAs walk every window of their pixels) and the kernel with one
-// CTA per (window, pixel tile) on the handle's time queue (its contents are being
-// flushed, so any values do) and keeps the faster.
+// walking kernel (CTAs walk every window of their pixels), the kernels with one
+// CTA per (window, pixel tile) (plain, wide, persistent double-buffered) and, at
+// T = 512, the TMA-fed ones (one CTA per item, persistent double-buffered) on the
+// handle's time queue (its contents are being flushed, so any values do) and
+// keeps the fastest.
 hv_status tune_temporal(hv_handle* h) {
   const uint32_t T = h->T, S = h->S;
   const uint32_t nwin = std::min<uint32_t>(16, (h->Q - T) / S + 1);
@@ -785,11 +790,14 @@ hv_status tune_temporal(hv_handle* h) {
   sa.nout = h->nout;
   sa.out = out;
   sa.err = h->dev_err;
-  const int kinds[4] = {STFT_WALK, STFT_AUTO, STFT_WIDE, STFT_PIPE};
+  const int kinds[6] = {STFT_WALK, STFT_AUTO, STFT_WIDE, STFT_PIPE, STFT_TMA, STFT_TMA_PIPE};
   float best = 1e30f;
   int best_kind = STFT_AUTO;
   hv_status st = HV_OK;
-  for (int ci = 0; ci < 4 && st == HV_OK; ++ci) {
+  for (int ci = 0; ci < 6 && st == HV_OK; ++ci) {
+    // the TMA-fed kernels exist for T = 512 only (elsewhere they would time the
+    // window-per-CTA kernel again)
+    if ((kinds[ci] == STFT_TMA || kinds[ci] == STFT_TMA_PIPE) && T != 512) continue;
     sa.kernel = kinds[ci];
     int launches = 0;
     cudaError_t e = launch_stft(sa, h->stream, &launches);  // warm-up
@@ -815,10 +823,12 @@ hv_status tune_temporal(hv_handle* h) {
   cudaFree(out);
   if (st != HV_OK) return st;
   h->stft_kernel = best_kind;
-  h->tuning.stft_kernel = best_kind == STFT_WALK   ? HV_STFT_WALK
-                          : best_kind == STFT_WIDE ? HV_STFT_WINDOW_WIDE
-                          : best_kind == STFT_PIPE ? HV_STFT_WINDOW_PIPELINED
-                                                   : HV_STFT_WINDOW;
+  h->tuning.stft_kernel = best_kind == STFT_WALK       ? HV_STFT_WALK
+                          : best_kind == STFT_WIDE     ? HV_STFT_WINDOW_WIDE
+                          : best_kind == STFT_PIPE     ? HV_STFT_WINDOW_PIPELINED
+                          : best_kind == STFT_TMA      ? HV_STFT_WINDOW_TMA
+                          : best_kind == STFT_TMA_PIPE ? HV_STFT_WINDOW_TMA_PIPELINED
+                                                       : HV_STFT_WINDOW;
   h->tuning.tuned = 1;
   return HV_OK;
 }

@@ -104,7 +104,7 @@ struct StftArgs {
 // float64 sums of a post-processed image are kept as kPostSub partial sums, so that
 // the CTAs that produce it add into different words
 constexpr uint32_t kPostSub = 32;
-enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2, STFT_PIPE = 3 };
+enum { STFT_AUTO = 0, STFT_WALK = 1, STFT_WIDE = 2, STFT_PIPE = 3, STFT_TMA = 4, STFT_TMA_PIPE = 5 };
 cudaError_t launch_stft(const StftArgs& a, cudaStream_t s, int* launches);
 
 // Encodes a 2-D tiled TMA tensor map (map: a CUtensorMap, 64-byte aligned) over

@@ -77,7 +77,7 @@ class hv_peaks(C.Structure):
 class hv_tuning(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("spatial_kernel", C.c_int32), ("spatial_chunk", C.c_uint32),
                 ("stft_kernel", C.c_int32), ("candidate_us_per_frame", C.c_float * 12),
-                ("stft_us_per_window", C.c_float * 4)]
+                ("stft_us_per_window", C.c_float * 6)]
 
 
 class hv_post(C.Structure):
@@ -206,7 +206,8 @@ def make_params(width, height, spatial="asp", z=0.3, lam=852e-9, pitch=20e-6, pi
     p.spatial_chunk = spatial_chunk
     p.spatial_kernel = {"auto": 0, "multipass": 1, "cluster": 2, "persistent": 3, "fused": 4}[spatial_kernel]
     p.highpass_cpp = highpass
-    p.stft_kernel = {"auto": 0, "walk": 1, "window": 2, "window_wide": 3, "window_pipelined": 4}[stft_kernel]
+    p.stft_kernel = {"auto": 0, "walk": 1, "window": 2, "window_wide": 3, "window_pipelined": 4,
+                     "window_tma": 5, "window_tma_pipelined": 6}[stft_kernel]
     return p
 
 

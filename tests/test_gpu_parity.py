@@ -623,7 +623,8 @@ def test_window_per_cta_stft(T, S, band):
     p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=band[0],
                       band_hi_bin=band[1], moments=ALL_MOMENTS, H=H, W=W)
     ref = O.render(fr, p)
-    for kern in ("window", "window_wide", "window_pipelined"):
+    # window_tma*: kernels of their own at T = 512, the window-per-CTA kernel elsewhere
+    for kern in ("window", "window_wide", "window_pipelined", "window_tma", "window_tma_pipelined"):
         img, st = gpu_render(fr, p, extra=dict(stft_kernel=kern), packets=[T + S, n - T - S])
         check_images(img, ref)
         assert st["windows_rendered"] == ref.shape[0]

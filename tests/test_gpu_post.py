@@ -67,6 +67,8 @@ def test_gaussian_renorm_accumulate_stft():
 
 @pytest.mark.parametrize("T,S,form", [(16, 16, dict(tuned=1)), (16, 16, dict(stft_kernel="window_wide")),
                                       (16, 16, dict(stft_kernel="window_pipelined")),
+                                      (512, 512, dict(stft_kernel="window_tma")),
+                                      (512, 512, dict(stft_kernel="window_tma_pipelined")),
                                       (16, 4, dict(tuned=1)), (16, 4, dict(tuned=0))])
 def test_renorm_accumulate_fused_into_the_stft(T, S, form):
     """Without a convolution the STFT epilogue writes the image ring and adds each
