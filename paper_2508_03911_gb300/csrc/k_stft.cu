@@ -763,6 +763,12 @@ constexpr int WT_TW2 = 31 * 8;   // w32^(r k2) at (k2 - 1) 8 + r
 constexpr size_t WT_TILE = size_t(WT_T) * WT_BT;  // float2 per tile
 constexpr size_t wt_smem(int tiles) { return 1024 + (tiles * WT_TILE + WT_TW1 + WT_TW2) * sizeof(float2); }
 
+// Lanes of the TMA-fed window kernels: each half-warp holds 8 lanes of each of the
+// warp's two pixels (lanes 0-7 and 16-23 the first, 8-15 and 24-31 the second), so
+// that the 16 lanes of one 64-bit shared-memory access phase cover both halves of
+// the 16-byte chunks and, under the swizzle, 16 different bank pairs.
+__device__ __forceinline__ int wt_jl(int lane) { return (lane & 7) | ((lane & 16) >> 1); }
+
 // Twiddle tables and band bits of the TMA-fed window kernels.
 __device__ __forceinline__ uint32_t wt_setup(const StftArgs& a, float2* tw1, float2* tw2, int tid, int jl) {
   for (int e = tid; e < WT_TW1; e += WT_NT) tw1[e] = a.tw_t[(e % 32) * (e / 32 + 1)];
@@ -792,7 +798,7 @@ __device__ __forceinline__ void wt_load(const StftArgs& a, const CUtensorMap* qm
 template <bool POST>
 __device__ __forceinline__ void wt_window(const StftArgs& a, float2* tile, const float2* tw1, const float2* tw2,
                                           uint32_t band, int px, int jl, uint32_t w, uint32_t p0) {
-  constexpr int T = WT_T, LP = 16;
+  constexpr int T = WT_T;
   const size_t HW = size_t(a.W) * a.H;
   // sample t of pixel px: 16-byte chunk px / 2 of row t sits at chunk
   // (px / 2) ^ ((t >> 1) & 3), px % 2 selects its half
@@ -827,12 +833,16 @@ __device__ __forceinline__ void wt_window(const StftArgs& a, float2* tile, const
     for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw2[(k2 - 1) * 8 + r]);
     add_moments<32, 16, 32>(v, 0, float(jl), acc);
   }
-#pragma unroll
-  for (int o = LP / 2; o > 0; o >>= 1) {
+  // the pixel's 16 lanes: lane ^ 16, then within the group of 8
+  auto fold = [&](int o) {
     acc.m0 += __shfl_xor_sync(0xffffffffu, acc.m0, o);
     acc.m1 += __shfl_xor_sync(0xffffffffu, acc.m1, o);
     acc.m2 += __shfl_xor_sync(0xffffffffu, acc.m2, o);
-  }
+  };
+  fold(16);
+  fold(4);
+  fold(2);
+  fold(1);
   if constexpr (POST) {
     emit_moments(a, w, p0 + px, acc, jl == 0, true);
   } else if (jl == 0) {
@@ -861,7 +871,7 @@ __global__ void __launch_bounds__(WT_NT, 5) k_stft_wt(StftArgs a, const __grid_c
   float2* tile = reinterpret_cast<float2*>(smem_wt + ((1024u - (smem_addr(smem_wt) & 1023u)) & 1023u));
   float2* tw1 = tile + WT_TILE;
   float2* tw2 = tw1 + WT_TW1;
-  const int tid = threadIdx.x, lane = tid & 31, jl = lane % 16, px = (tid >> 5) * 2 + lane / 16;
+  const int tid = threadIdx.x, lane = tid & 31, jl = wt_jl(lane), px = (tid >> 5) * 2 + ((lane >> 3) & 1);
   const uint32_t ntile = uint32_t(size_t(a.W) * a.H / WT_BT);
   const uint32_t w = blockIdx.x / ntile, p0 = (blockIdx.x % ntile) * WT_BT;
   const uint32_t mbar = smem_addr(&s_full);
@@ -891,7 +901,7 @@ __global__ void __launch_bounds__(WT_NT, 3) k_stft_wtp(StftArgs a, const __grid_
   float2* tiles = reinterpret_cast<float2*>(smem_wt + ((1024u - (smem_addr(smem_wt) & 1023u)) & 1023u));
   float2* tw1 = tiles + 2 * WT_TILE;
   float2* tw2 = tw1 + WT_TW1;
-  const int tid = threadIdx.x, lane = tid & 31, jl = lane % 16, px = (tid >> 5) * 2 + lane / 16;
+  const int tid = threadIdx.x, lane = tid & 31, jl = wt_jl(lane), px = (tid >> 5) * 2 + ((lane >> 3) & 1);
   const uint32_t ntile = uint32_t(size_t(a.W) * a.H / WT_BT);
   const uint32_t items = a.nwin * ntile;
   if (tid == 0) {
