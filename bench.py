@@ -563,9 +563,11 @@ def roofline(w, res, peaks):
             traffic = int(v * (frames_per_render + ov) / (1024 + ov))
             traffic_per = "launch of the STFT kernel (1,024-frame ncu capture scaled to the launch's frames)"
     if (t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 512
-            and tun.get("stft_kernel") in (2, 3)):
-        # window-per-CTA STFT: a 1,024-frame launch captured, traffic in proportion to the frames
-        v = profiled_traffic("stft_win_512_asp_256.md", ["k_stft.cu", "fft_dev.cuh"])
+            and tun.get("stft_kernel") in (2, 5)):
+        # window STFT (window-per-CTA, or TMA-fed): a 1,024-frame launch captured,
+        # traffic in proportion to the frames
+        prof = "stft_wt_512_asp_256.md" if tun.get("stft_kernel") == 5 else "stft_win_512_asp_256.md"
+        v = profiled_traffic(prof, ["k_stft.cu", "fft_dev.cuh"])
         if v is not None:
             traffic = int(v * frames_per_render / 1024)
             traffic_per = "render (the STFT launch; 1,024-frame ncu capture scaled to the render's frames)"
