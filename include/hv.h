@@ -110,8 +110,7 @@ typedef struct {
                                  radius sqrt((m/W)^2 + (n/H)^2) in cycles per pixel is
                                  below this cutoff are zeroed; 0 = off. Folded into
                                  the transfer function. */
-  int32_t stft_kernel;        /* STFT kernel (the window kernels for S >= T, the
-                                 TMA-fed ones for T = 512 and any S):
+  int32_t stft_kernel;        /* STFT kernel for windows that do not overlap (S >= T):
                                  0 = automatic (the autotuner's choice when tuned = 1,
                                  else the walking kernel launched once per window),
                                  HV_STFT_WALK, HV_STFT_WINDOW, HV_STFT_WINDOW_WIDE,
@@ -120,9 +119,9 @@ typedef struct {
                                  HV_STFT_WINDOW_TMA or HV_STFT_WINDOW_TMA_PIPELINED
                                  (T = 512: a window tile brought in by TMA tensor
                                  loads and transformed in place; the second
-                                 persistent and double-buffered; the queue's
-                                 capacity, first slot and S multiples of 64; else
-                                 the HV_STFT_WINDOW or the walking kernel runs)   */
+                                 persistent and double-buffered; at other T, and
+                                 where a window's queue slots wrap, the
+                                 HV_STFT_WINDOW kernel runs instead)              */
   uint32_t reserved;
 } hv_params;
 
@@ -220,8 +219,8 @@ typedef struct {
                                        double-buffered CTAs over the (window, tile)
                                        items, the TMA-fed kernel, the same persistent
                                        and double-buffered; 0 where not applicable
-                                       (the window kernels need S >= T, the TMA-fed
-                                       ones T = 512; they run for any stride)         */
+                                       (all but the first need S >= T, the last two
+                                       T = 512)                                       */
 } hv_tuning;
 
 /* STFT kernels the autotuner chooses between (windows that do not overlap). */

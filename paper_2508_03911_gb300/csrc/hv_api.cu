@@ -540,7 +540,7 @@ hv_status apply_pending(hv_handle* h) {
     s = tune_spatial(h);
     if (s != HV_OK) return s;
   }
-  if (p.tuned && p.stft_kernel == 0 && p.temporal == HV_TEMPORAL_STFT && (d.S >= d.T || d.T == 512)) {
+  if (p.tuned && p.stft_kernel == 0 && p.temporal == HV_TEMPORAL_STFT && d.S >= d.T) {
     s = tune_temporal(h);
     if (s != HV_OK) return s;
   }
@@ -760,11 +760,10 @@ hv_status tune_spatial(hv_handle* h) {
   return HV_OK;
 }
 
-// Autotuner of the STFT: times the walking kernel (CTAs walk every window of their
-// pixels), for windows that do not overlap (S >= T) the kernels with one CTA per
-// (window, pixel tile) (plain, wide, persistent double-buffered) and, at T = 512,
-// the TMA-fed ones (one CTA per item, persistent double-buffered; overlapping
-// windows too, the windows of a pixel tile sharing their frames in L2) on the
+// Autotuner of the STFT for windows that do not overlap (S >= T): times the
+// walking kernel (CTAs walk every window of their pixels), the kernels with one
+// CTA per (window, pixel tile) (plain, wide, persistent double-buffered) and, at
+// T = 512, the TMA-fed ones (one CTA per item, persistent double-buffered) on the
 // handle's time queue (its contents are being flushed, so any values do) and
 // keeps the fastest.
 hv_status tune_temporal(hv_handle* h) {
@@ -796,10 +795,9 @@ hv_status tune_temporal(hv_handle* h) {
   int best_kind = STFT_AUTO;
   hv_status st = HV_OK;
   for (int ci = 0; ci < 6 && st == HV_OK; ++ci) {
-    // the TMA-fed kernels exist for T = 512 only, the window-per-CTA ones for windows
-    // that do not overlap (elsewhere they would time another candidate again)
-    const bool tma = kinds[ci] == STFT_TMA || kinds[ci] == STFT_TMA_PIPE;
-    if ((tma && T != 512) || (!tma && kinds[ci] != STFT_WALK && S < T)) continue;
+    // the TMA-fed kernels exist for T = 512 only (elsewhere they would time the
+    // window-per-CTA kernel again)
+    if ((kinds[ci] == STFT_TMA || kinds[ci] == STFT_TMA_PIPE) && T != 512) continue;
     sa.kernel = kinds[ci];
     int launches = 0;
     cudaError_t e = launch_stft(sa, h->stream, &launches);  // warm-up

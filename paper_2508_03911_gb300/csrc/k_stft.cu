@@ -782,20 +782,15 @@ __device__ __forceinline__ uint32_t wt_setup(const StftArgs& a, float2* tw1, flo
   return band;
 }
 
-// One thread: the window's T frames of pixels p0 .. p0 + 7 into `tile` by eight
-// TMA tensor loads of 64 queue slots each, completing on `mbar`. The host keeps
-// the queue capacity, the first slot and the stride multiples of 64, so a chunk
-// never straddles the end of the queue; the chunks wrap around it one by one.
+// One thread: the window's T frames of pixels p0 .. p0 + 7 into `tile` by two
+// TMA tensor loads completing on `mbar`.
 __device__ __forceinline__ void wt_load(const StftArgs& a, const CUtensorMap* qmap, float2* tile, uint32_t mbar,
                                         uint32_t w, uint32_t p0) {
-  uint32_t slot = uint32_t((uint64_t(a.tq.slot0) + uint64_t(w) * a.S) % a.tq.cap);
+  uint32_t slot = a.tq.slot0 + w * a.S;  // the host keeps slot + T within the queue
+  while (slot >= a.tq.cap) slot -= a.tq.cap;
   mbar_arrive_tx(mbar, uint32_t(WT_T * WT_BT * 8));
-#pragma unroll
-  for (int c = 0; c < WT_T / 64; ++c) {
-    tma_load_2d(smem_addr(tile + c * 64 * WT_BT), qmap, int(p0), int(slot), mbar);
-    slot += 64;
-    if (slot >= a.tq.cap) slot -= a.tq.cap;
-  }
+  tma_load_2d(smem_addr(tile), qmap, int(p0), int(slot), mbar);
+  tma_load_2d(smem_addr(tile + 256 * WT_BT), qmap, int(p0), int(slot + 256), mbar);
 }
 
 // The two FFT stages of the warp's two pixels in the landed tile, the moments,
@@ -877,9 +872,8 @@ __global__ void __launch_bounds__(WT_NT, 5) k_stft_wt(StftArgs a, const __grid_c
   float2* tw1 = tile + WT_TILE;
   float2* tw2 = tw1 + WT_TW1;
   const int tid = threadIdx.x, lane = tid & 31, jl = wt_jl(lane), px = (tid >> 5) * 2 + ((lane >> 3) & 1);
-  // items tile-major: the windows of one pixel tile run together, so overlapping
-  // windows find their shared frames in L2
-  const uint32_t w = blockIdx.x % a.nwin, p0 = (blockIdx.x / a.nwin) * WT_BT;
+  const uint32_t ntile = uint32_t(size_t(a.W) * a.H / WT_BT);
+  const uint32_t w = blockIdx.x / ntile, p0 = (blockIdx.x % ntile) * WT_BT;
   const uint32_t mbar = smem_addr(&s_full);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
@@ -908,13 +902,14 @@ __global__ void __launch_bounds__(WT_NT, 3) k_stft_wtp(StftArgs a, const __grid_
   float2* tw1 = tiles + 2 * WT_TILE;
   float2* tw2 = tw1 + WT_TW1;
   const int tid = threadIdx.x, lane = tid & 31, jl = wt_jl(lane), px = (tid >> 5) * 2 + ((lane >> 3) & 1);
-  const uint32_t items = a.nwin * uint32_t(size_t(a.W) * a.H / WT_BT);
+  const uint32_t ntile = uint32_t(size_t(a.W) * a.H / WT_BT);
+  const uint32_t items = a.nwin * ntile;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&s_full[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     const uint32_t i0 = blockIdx.x;
-    if (i0 < items) wt_load(a, &qmap, tiles, smem_addr(&s_full[0]), i0 % a.nwin, (i0 / a.nwin) * WT_BT);
+    if (i0 < items) wt_load(a, &qmap, tiles, smem_addr(&s_full[0]), i0 / ntile, (i0 % ntile) * WT_BT);
   }
   const uint32_t band = wt_setup(a, tw1, tw2, tid, jl);
   uint32_t k = 0;
@@ -926,7 +921,7 @@ __global__ void __launch_bounds__(WT_NT, 3) k_stft_wtp(StftArgs a, const __grid_
     if (tid == 0 && nxt < items) {
       // the tile's generic reads and writes (item k - 1) before the async-proxy load
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      wt_load(a, &qmap, tiles + (b ^ 1) * WT_TILE, smem_addr(&s_full[b ^ 1]), nxt % a.nwin, (nxt / a.nwin) * WT_BT);
+      wt_load(a, &qmap, tiles + (b ^ 1) * WT_TILE, smem_addr(&s_full[b ^ 1]), nxt / ntile, (nxt % ntile) * WT_BT);
     }
     const bool landed = mbar_wait(smem_addr(&s_full[b]), (k >> 1) & 1);
     if (!__syncthreads_and(landed)) {
@@ -938,7 +933,7 @@ __global__ void __launch_bounds__(WT_NT, 3) k_stft_wtp(StftArgs a, const __grid_
       }
       return;
     }
-    wt_window<POST>(a, tiles + b * WT_TILE, tw1, tw2, band, px, jl, i % a.nwin, (i / a.nwin) * WT_BT);
+    wt_window<POST>(a, tiles + b * WT_TILE, tw1, tw2, band, px, jl, i / ntile, (i % ntile) * WT_BT);
   }
 }
 
@@ -997,16 +992,17 @@ bool encode_map_2d_u64(void* map, const void* base, uint64_t inner, uint64_t out
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The TMA-fed window kernels (T = 512, any stride): cudaErrorNotSupported unless
-// the queue capacity, its first slot and the stride are multiples of 64 (whole
-// 64-slot chunks), or when the tensor map cannot be made.
+// The TMA-fed window kernel (T = 512, S >= T): cudaErrorNotSupported when a
+// window's queue slots wrap around the queue or the tensor map cannot be made.
 static cudaError_t launch_wt(const StftArgs& a, cudaStream_t s) {
   const size_t hw = size_t(a.W) * a.H;
-  if (hw % WT_BT || a.T != uint32_t(WT_T) || a.S == 0 || a.S % 64 || a.tq.cap % 64 || a.tq.slot0 % 64 ||
-      a.tq.cap < uint32_t(WT_T))
-    return cudaErrorNotSupported;
+  if (hw % WT_BT || a.T != uint32_t(WT_T) || a.S < a.T) return cudaErrorNotSupported;
+  for (uint32_t w = 0; w < a.nwin; ++w) {
+    const uint64_t slot = (uint64_t(a.tq.slot0) + uint64_t(w) * a.S) % a.tq.cap;
+    if (slot + WT_T > a.tq.cap) return cudaErrorNotSupported;
+  }
   CUtensorMap map{};
-  if (!encode_map_2d_u64(&map, a.tq.base, hw, a.tq.cap, hw * 8, WT_BT, 64, true)) return cudaErrorNotSupported;
+  if (!encode_map_2d_u64(&map, a.tq.base, hw, a.tq.cap, hw * 8, WT_BT, 256, true)) return cudaErrorNotSupported;
   const uint64_t items = uint64_t(a.nwin) * (hw / WT_BT);
   if (items >= (1ull << 31)) return cudaErrorInvalidValue;
   if (a.kernel == STFT_TMA_PIPE) {
@@ -1039,10 +1035,9 @@ static cudaError_t launch_warp(const StftArgs& a0, cudaStream_t s) {
     return cudaErrorInvalidValue;
   StftArgs a = a0;
   if constexpr (T == WT_T) {
-    if (a.kernel == STFT_TMA || a.kernel == STFT_TMA_PIPE) {
+    if (a.S >= uint32_t(T) && (a.kernel == STFT_TMA || a.kernel == STFT_TMA_PIPE)) {
       const cudaError_t e = launch_wt(a, s);
-      // else (queue not in 64-slot chunks) the window-per-CTA or the walking kernel
-      if (e != cudaErrorNotSupported) return e;
+      if (e != cudaErrorNotSupported) return e;  // else a window wraps: the window-per-CTA kernel
     }
   }
   if (a.S >= uint32_t(T) && a.kernel != STFT_WALK) {

@@ -247,26 +247,6 @@ def test_long_window_kernel_paths(T, S, band):
     check_images(img, O.render(fr, p))
 
 
-@pytest.mark.parametrize("S,tq", [(64, 0), (128, 1536), (192, 0), (512, 0), (640, 1280), (64, 1000)])
-def test_tma_window_kernels_any_stride(S, tq):
-    """The TMA-fed window kernels at T = 512 for overlapping and separate windows:
-    64-slot chunks loaded one by one around the end of a small queue (1,536 and
-    1,280 slots), and a queue of 1,000 slots (not whole chunks) falling back to the
-    walking or window-per-CTA kernel; both forms, every moment against the oracle."""
-    T = 512
-    H, W = 16, 32
-    n = T + 6 * S + 3
-    fr = synth.random_frames(n, H, W, 12, seed=S + tq + 7)
-    p = oracle_params(spatial="fresnel", T=T, stride=S, fs_hz=71400.0, band_lo_bin=2,
-                      band_hi_bin=T // 2 + 20, moments=ALL_MOMENTS, H=H, W=W)
-    ref = O.render(fr, p)
-    for kern in ("window_tma", "window_tma_pipelined"):
-        img, st = gpu_render(fr, p, tq=tq, packets=[T + S, 2 * S + 1, n - T - 3 * S - 1],
-                             extra=dict(stft_kernel=kern))
-        check_images(img, ref)
-        assert st["windows_rendered"] == ref.shape[0]
-
-
 @pytest.mark.parametrize("T,S,tq", [(512, 256, 0), (1024, 256, 0), (64, 16, 0), (128, 32, 256),
                                     (512, 64, 1000), (256, 48, 0)])
 def test_staged_frame_paths(T, S, tq):
