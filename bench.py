@@ -540,7 +540,10 @@ def roofline(w, res, peaks):
     if t_tm >= t_sp:
         flops = alg["stft_flops"] * frames_per_render
         byts = alg["stft_bytes"] * frames_per_render
-        kern, t = "k_stft (time FFT + band moments)", t_tm
+        names = {1: "k_stft_warp", 2: "k_stft_win", 3: "k_stft_win (wide)", 4: "k_stft_winp", 5: "k_stft_wt",
+                 6: "k_stft_wtp"}
+        sk = (res.get("tuning") or {}).get("stft_kernel")
+        kern, t = f"{names.get(sk, 'k_stft_warp')} (time FFT + band moments)", t_tm
     else:
         flops = alg["spatial_flops"] * frames_per_render
         byts = (w["N"] ** 2) * ((1 if w["bits"] <= 8 else 2) + 8) * frames_per_render
@@ -554,7 +557,7 @@ def roofline(w, res, peaks):
     traffic_per = "launch of the STFT kernel" if t_tm >= t_sp else \
         "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)"
     tun = res.get("tuning") or {}
-    if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64:
+    if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64 and tun.get("stft_kernel") in (1, None):
         # walking STFT: a launch over 1,024 new frames captured; a launch reads its
         # new frames and the T - S frames of overlap once, so traffic scales with both
         v = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
