@@ -557,7 +557,7 @@ def roofline(w, res, peaks):
     traffic_per = "launch of the STFT kernel" if t_tm >= t_sp else \
         "render (all spatial pass launches; cold-cache ncu capture, L2 flushed)"
     tun = res.get("tuning") or {}
-    if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64 and tun.get("stft_kernel") in (1, None):
+    if t_tm >= t_sp and w["T"] == 512 and w["N"] == 256 and w["S"] == 64 and tun.get("stft_kernel") in (0, 1, None):
         # walking STFT: a launch over 1,024 new frames captured; a launch reads its
         # new frames and the T - S frames of overlap once, so traffic scales with both
         v = profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])

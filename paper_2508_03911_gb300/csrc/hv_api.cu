@@ -535,11 +535,11 @@ hv_status apply_pending(hv_handle* h) {
                    : p.stft_kernel == HV_STFT_WINDOW_TMA       ? STFT_TMA
                    : p.stft_kernel == HV_STFT_WINDOW_TMA_PIPELINED ? STFT_TMA_PIPE
                                                                : STFT_WALK;
-  h->tuning.stft_kernel = p.stft_kernel == 0 ? HV_STFT_WALK : p.stft_kernel;
   if (p.tuned && p.spatial_kernel == HV_SK_AUTO) {
-    s = tune_spatial(h);
+    s = tune_spatial(h);  // rewrites the tuning record
     if (s != HV_OK) return s;
   }
+  h->tuning.stft_kernel = p.stft_kernel == 0 ? HV_STFT_WALK : p.stft_kernel;
   if (p.tuned && p.stft_kernel == 0 && p.temporal == HV_TEMPORAL_STFT && d.S >= d.T) {
     s = tune_temporal(h);
     if (s != HV_OK) return s;
