@@ -62,3 +62,34 @@ def test_reference_arm_uses_the_one_core_procedure():
     assert seen == [(1, b.ONE_CORE_SPATIAL_FRAMES, b.ONE_CORE_ROW_FRAC)] * 5
     assert value == np.median([103.0, 104.0, 105.0])  # warm-up samples dropped
     assert b.run_reference(args, w, 1) is None        # other ranks do no work
+
+
+def test_roofline_names_the_dominant_kernel_and_takes_only_its_own_profile():
+    """The roofline entry: the dominant stage from the live stage times, the STFT
+    kernel named from the tuning record, and a committed profile's DRAM traffic only
+    for the kernel that profile captured (scaled to the render's frames)."""
+    b = _bench()
+    b._ALU.update(fp32_tflops=76.5, fp64_tflops=1.25, source="test figures")
+    peaks = {"hbm_gbs": 6784.8}
+    walk = b.profiled_traffic("stft_warp_512_stream_fresnel_256.md", ["k_stft.cu", "fft_dev.cuh"])
+    fused = b.profiled_traffic("spatial_fused_asp_256.md", ["k_spatial_pp.cu", "fft_dev.cuh"])
+    assert walk and fused  # the committed summaries match the committed sources
+
+    w = b.WORKLOADS["stream_fresnel_256_t512_s64"]
+    prof = {"renders": 1, "frames": 4096, "spatial_ms": 1.0, "temporal_ms": 2.7}
+    for sk in (1, 0):  # the walking kernel, or no STFT choice recorded (it then runs)
+        r = b.roofline(w, {"prof": prof, "frames_per_step": 4096,
+                           "tuning": {"stft_kernel": sk, "spatial_kernel": 4}}, peaks)
+        assert r["kernel"].startswith("k_stft_warp")
+        assert r["traffic"] == int(walk * (4096 + 448) / (1024 + 448))
+    r = b.roofline(w, {"prof": prof, "frames_per_step": 4096,
+                       "tuning": {"stft_kernel": 5, "spatial_kernel": 4}}, peaks)
+    assert r["kernel"].startswith("k_stft_wt") and r["traffic"] is None
+
+    w = b.WORKLOADS[b.DEFAULT]
+    prof = {"renders": 1, "frames": 4096, "spatial_ms": 1.54, "temporal_ms": 0.39}
+    r = b.roofline(w, {"prof": prof, "frames_per_step": 4096,
+                       "tuning": {"stft_kernel": 5, "spatial_kernel": 4}}, peaks)
+    assert r["kernel"].startswith("k_spatial_fused") and r["bound"] == "alu"
+    assert r["traffic"] == int(fused * 4096 / 1024)
+    assert r["frac"] > 0 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
